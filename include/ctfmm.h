@@ -1,0 +1,161 @@
+/*
+ * ctfmm.h -- C ABI of the GB300 compressed-Taylor FMM.
+ *
+ * Method: Fernando & Kloeckner, "Automatic Synthesis of Low-Complexity
+ * Translation Operators for the Fast Multipole Method" (arXiv 2305.17867).
+ * The library evaluates the many-body potential of eq. (1),
+ *     phi(x) = sum_{y in S, y != x} G(x - y) w(y),   x in T,
+ * with a uniform-tree Taylor FMM whose expansions are stored compressed by
+ * the PDE that G satisfies (Sec. 3): only the multi-indices j = {m in M(p):
+ * m_d < c} are kept (Lemma 5, last axis slowest), derivatives of G come from
+ * r^2-led recurrences (Sec. 4.4), and every stage -- tree build, P2M, M2M,
+ * M2L, L2L, L2P, P2P -- runs as CUDA kernels on the caller's stream.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are DEVICE pointers (cudaMalloc'd or torch tensors
+ *    on the current device).  Points are row-major n x d float64 arrays.
+ *  - All device work is enqueued on the `stream` argument (a cudaStream_t,
+ *    NULL = legacy default stream).  Calls return as soon as the work is
+ *    enqueued; nothing is synchronised except where stated.
+ *  - The caller owns every input, output and workspace buffer.  The library
+ *    owns the plan and the small read-only tables the plan uploads at
+ *    creation (cudaMalloc'd once, freed by fmm_plan_destroy).
+ *  - Return values are fmm_status codes (0 = success, negative = error).
+ *    Nothing is printed and no exception crosses the ABI.
+ *  - A plan is not thread-safe: calls that use the same plan must not run
+ *    concurrently, and evaluations sharing one workspace must be ordered on
+ *    the GPU (one stream, or events).
+ */
+#ifndef CTFMM_H
+#define CTFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_plan_s* fmm_plan_t;
+
+typedef enum {
+  FMM_OK = 0,
+  FMM_ERR_ARG = -1,          /* invalid argument (null pointer, bad size or enum) */
+  FMM_ERR_UNSUPPORTED = -2,  /* kernel/dimension/PDE combination not provided */
+  FMM_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+  FMM_ERR_NOMEM = -4,        /* plan tables could not be allocated */
+  FMM_ERR_TIMEOUT = -5,      /* a bounded device wait gave up */
+  FMM_ERR_DOMAIN = -6,       /* a point lay outside the root box (it was clamped) */
+  FMM_ERR_WORKSPACE = -7     /* workspace too small */
+} fmm_status;
+
+/* Kernels G (reading of the paper's normalisations):
+ *  LAPLACE     d=2: log|x|            d=3: 1/(4 pi |x|)     PDE: Laplacian
+ *  YUKAWA      d=3: exp(-lambda |x|)/|x|                    PDE: Laplacian - lambda^2
+ *  BIHARMONIC  d=3: |x|                                     PDE: Laplacian^2          */
+enum { FMM_KERNEL_LAPLACE = 0, FMM_KERNEL_YUKAWA = 1, FMM_KERNEL_BIHARMONIC = 2 };
+
+/* Arithmetic of the evaluation.
+ *  FP64     every stage in float64 (the parity configuration).
+ *  FP32     M2L as float32 SIMT products; P2M, L2P, P2P in float32; derivative
+ *           tables, M2M and L2L in float64.
+ *  TF32     as FP32 but M2L on the tensor cores (tcgen05 kind::tf32), one pass.
+ *  TF32X3   M2L with split operands a = hi + lo in tf32, three tensor passes
+ *           (hi*hi + hi*lo + lo*hi), float32 accumulation.
+ *  BF16X3   the same split in bf16 (kind::f16), float32 accumulation.        */
+enum {
+  FMM_PREC_FP64 = 0,
+  FMM_PREC_FP32 = 1,
+  FMM_PREC_TF32 = 2,
+  FMM_PREC_TF32X3 = 3,
+  FMM_PREC_BF16X3 = 4
+};
+
+/* A constant-coefficient PDE L = sum_t coeff[t] d^{multi_idx[t]}  (eq.
+ * (define_pde_op)).  multi_idx is n_terms x d exponents.  The PDE must have
+ * a nonzero coefficient on c*e_d, c its order (Property 1 on the last axis). */
+typedef struct {
+  int n_terms;
+  const int* multi_idx;
+  const double* coeff;
+} fmm_pde;
+
+typedef struct {
+  int kernel;          /* FMM_KERNEL_* */
+  double lambda;       /* Yukawa screening; ignored otherwise */
+  int d;               /* 2 or 3 */
+  int p;               /* expansion order, 1..24 */
+  int levels;          /* leaf depth L of the uniform tree, 2..7 (root = 0) */
+  const fmm_pde* pde;  /* NULL: the kernel's own PDE */
+  double root_lo[3];   /* lower corner of the root box */
+  double root_size;    /* side of the root box; <= 0: bounding cube of the
+                          sources and targets, found on the device per call */
+  int precision;       /* FMM_PREC_* */
+} fmm_plan_desc;
+
+/* Create a plan: validates the description, builds the stored set j, the
+ * sparse decompression recurrence of eq. (decompression) (Thm 4), the
+ * multi-index tables and uploads them (cudaMalloc + cudaMemcpy, synchronous,
+ * on the current device).  *out receives the plan; on error *out = NULL. */
+int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc);
+
+/* Free the plan and its device tables (synchronises the device first). */
+int fmm_plan_destroy(fmm_plan_t plan);
+
+/* Number of coefficients: nfull = N(p) = C(p+d,d), nj = |j| = N(p)-N(p-c),
+ * c = PDE order.  Any pointer may be NULL. */
+int fmm_plan_info(fmm_plan_t plan, int* nfull, int* nj, int* c);
+
+/* Bytes of device workspace fmm_eval / fmm_eval_backward need for the given
+ * point counts.  The workspace must be 256-byte aligned. */
+int fmm_workspace_size(fmm_plan_t plan, int64_t n_src, int64_t n_tgt, size_t* bytes);
+
+/* Evaluate phi (and, if grad_dev != NULL, grad phi) at the targets:
+ *   src_dev  n_src x d   source positions        (device, float64)
+ *   w_dev    n_src       source weights          (device, float64)
+ *   tgt_dev  n_tgt x d   target positions        (device, float64); may equal src_dev
+ *   phi_dev  n_tgt       output potential        (device, float64, overwritten)
+ *   grad_dev n_tgt x d   output gradient or NULL (device, float64, overwritten)
+ * n_src or n_tgt may be 0.  Pairs with x == y exactly are skipped.  Points
+ * outside the root box are clamped into it and flagged (FMM_ERR_DOMAIN from
+ * fmm_last_status).  Asynchronous on `stream`. */
+int fmm_eval(fmm_plan_t plan, int64_t n_src, const double* src_dev, const double* w_dev,
+             int64_t n_tgt, const double* tgt_dev, double* phi_dev, double* grad_dev,
+             void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Reverse mode of loss = sum_i u_i phi(x_i) (no counterpart in the paper):
+ *   grad_w_dev   n_src       d loss/d w_j  = sum_i u_i G(x_i - y_j)      (or NULL)
+ *   grad_src_dev n_src x d   d loss/d y_j  = w_j grad psi(y_j)           (or NULL)
+ *   grad_tgt_dev n_tgt x d   d loss/d x_i  = u_i grad phi(x_i)           (or NULL)
+ * where psi(y) = sum_i u_i G(y - x_i) is the transposed FMM (targets as
+ * sources with weights u).  Same buffer conventions as fmm_eval; the
+ * workspace must be sized with fmm_workspace_size(plan, max(n_src, n_tgt),
+ * max(n_src, n_tgt)). */
+int fmm_eval_backward(fmm_plan_t plan, int64_t n_src, const double* src_dev,
+                      const double* w_dev, int64_t n_tgt, const double* tgt_dev,
+                      const double* u_dev, double* grad_w_dev, double* grad_src_dev,
+                      double* grad_tgt_dev, void* workspace_dev, size_t workspace_bytes,
+                      void* stream);
+
+/* Synchronise the stream of the last evaluation and return its device-side
+ * status (FMM_OK, FMM_ERR_DOMAIN, FMM_ERR_TIMEOUT) or a CUDA error. */
+int fmm_last_status(fmm_plan_t plan);
+
+/* Per-phase timings (milliseconds, CUDA events) of the last evaluation when
+ * timing was enabled with fmm_set_timing(plan, 1); synchronises.  Phases:
+ * 0 tree, 1 derivative tables, 2 P2M, 3 M2M, 4 M2L, 5 L2L, 6 L2P+P2P. */
+#define FMM_NUM_PHASES 7
+int fmm_set_timing(fmm_plan_t plan, int enable);
+int fmm_phase_times(fmm_plan_t plan, float* ms_out /* FMM_NUM_PHASES */);
+
+/* Number of kernel launches the last fmm_eval enqueued. */
+int fmm_last_launch_count(fmm_plan_t plan);
+
+/* Human-readable text for a status code (static storage). */
+const char* fmm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTFMM_H */

@@ -1,0 +1,473 @@
+// C-ABI entry points and the host-side plan of the compressed-Taylor FMM.
+//
+// The plan realises Sec. 3.1 of the paper without forming the dense matrices:
+// with the last axis slowest (Lemma 5), row n of the PDE matrix P pivots on
+// n + c e_s, so the decompression operator of eq. (decompression) is the
+// sparse recurrence (Thm 4)
+//     D[m] = sum_{xi != c e_s} (-a_xi / a_{c e_s}) D[m - c e_s + xi],  m_s >= c,
+// swept slab by slab upward; its transpose (compression, eq.
+// (define_beta_multipole)) is the same recurrence swept downward in gather form.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "fmm_internal.cuh"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Slab layout (see fmm_internal.cuh): row bases for order P with slabs 0..nslab-1.
+struct Layout {
+  int d = 0, P = 0, nslab = 0, n = 0;
+  std::vector<int> row;
+  int index(const int* m) const {  // m = (m0, m1, ms) for d=3, (m0, ms) for d=2
+    if (d == 3) return row[(size_t)m[2] * (P + 1) + m[1]] + m[0];
+    return row[(size_t)m[1]] + m[0];
+  }
+};
+
+Layout make_layout(int d, int P, int nslab) {
+  Layout L;
+  L.d = d;
+  L.P = P;
+  L.nslab = nslab;
+  int pos = 0;
+  if (d == 3) {
+    L.row.assign((size_t)(P + 1) * (P + 1), -1);
+    for (int ms = 0; ms < nslab && ms <= P; ++ms)
+      for (int m1 = 0; m1 <= P - ms; ++m1) {
+        L.row[(size_t)ms * (P + 1) + m1] = pos;
+        pos += P - ms - m1 + 1;
+      }
+  } else {
+    L.row.assign((size_t)(P + 1), -1);
+    for (int ms = 0; ms < nslab && ms <= P; ++ms) {
+      L.row[ms] = pos;
+      pos += P - ms + 1;
+    }
+  }
+  L.n = pos;
+  return L;
+}
+
+// Enumerate the full layout of order P (all slabs) into multi-indices.
+std::vector<std::array<int, 3>> enumerate_full(int d, int P) {
+  std::vector<std::array<int, 3>> out;
+  if (d == 3) {
+    for (int ms = 0; ms <= P; ++ms)
+      for (int m1 = 0; m1 <= P - ms; ++m1)
+        for (int m0 = 0; m0 <= P - ms - m1; ++m0) out.push_back({m0, m1, ms});
+  } else {
+    for (int ms = 0; ms <= P; ++ms)
+      for (int m0 = 0; m0 <= P - ms; ++m0) out.push_back({m0, ms, 0});
+  }
+  return out;
+}
+
+using Key = std::array<int, 3>;
+
+// The kernel's own PDE (eq. (define_pde_op)); multi-indices padded to 3.
+std::map<Key, double> default_pde(int kernel, int d, double lam) {
+  std::map<Key, double> a;
+  auto e2 = [&](int k) {
+    Key m{0, 0, 0};
+    m[k] = 2;
+    return m;
+  };
+  if (kernel == FMM_KERNEL_LAPLACE || kernel == FMM_KERNEL_YUKAWA) {
+    for (int k = 0; k < d; ++k) a[e2(k)] += 1.0;
+    if (kernel == FMM_KERNEL_YUKAWA) a[Key{0, 0, 0}] += -lam * lam;
+  } else if (kernel == FMM_KERNEL_BIHARMONIC) {
+    for (int k = 0; k < d; ++k)
+      for (int l = 0; l < d; ++l) {
+        Key m{0, 0, 0};
+        m[k] += 2;
+        m[l] += 2;
+        a[m] += 1.0;
+      }
+  }
+  return a;
+}
+
+template <typename T>
+T* carve(char*& cur, size_t count) {
+  T* p = reinterpret_cast<T*>(cur);
+  cur += align_up(count * sizeof(T));
+  return p;
+}
+
+int to_status(cudaError_t e) { return e == cudaSuccess ? FMM_OK : FMM_ERR_CUDA; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Workspace layout
+// ---------------------------------------------------------------------------
+int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void* base,
+                         Workspace* ws) {
+  const int d = P->pd.d, L = P->desc.levels, nj = P->pd.nj, nh = P->pd.nh;
+  const int64_t nleaf = nbox_at(d, L);
+  const int64_t nmax = std::max<int64_t>(std::max(n_src, n_tgt), 1);
+  const int64_t nblk = (nmax + 1023) / 1024;
+  char* cur = static_cast<char*>(base);
+  Workspace w{};
+  w.geom = carve<Geom>(cur, 1);
+  for (int k = 0; k < d; ++k) w.sx[k] = carve<double>(cur, std::max<int64_t>(n_src, 1));
+  w.sw = carve<double>(cur, std::max<int64_t>(n_src, 1));
+  w.sperm = carve<int>(cur, std::max<int64_t>(n_src, 1));
+  for (int k = 0; k < d; ++k) w.tx[k] = carve<double>(cur, std::max<int64_t>(n_tgt, 1));
+  w.tperm = carve<int>(cur, std::max<int64_t>(n_tgt, 1));
+  w.sstart = carve<int>(cur, nleaf + 1);
+  w.tstart = carve<int>(cur, nleaf + 1);
+  w.counts = carve<int>(cur, nleaf);
+  w.keys_a = carve<uint32_t>(cur, nmax);
+  w.keys_b = carve<uint32_t>(cur, nmax);
+  w.vals_a = carve<int>(cur, nmax);
+  w.vals_b = carve<int>(cur, nmax);
+  const int64_t nhist = 256 * nblk;
+  const int64_t nscan = std::max<int64_t>(nhist, nleaf + 1);
+  w.hist = carve<int>(cur, nscan);
+  w.hist_sums = carve<int>(cur, (nscan + 1023) / 1024 + 1);
+  int64_t off = 0;
+  for (int l = 0; l <= L; ++l) {
+    w.lev_off[l] = off;
+    if (l >= 2) off += nbox_at(d, l);
+  }
+  w.lev_off[L + 1] = off;
+  w.mp = carve<double>(cur, (size_t)off * nj);
+  w.lc = carve<double>(cur, (size_t)off * nj);
+  const int noff = d == 3 ? 343 : 49;
+  w.htab = carve<double>(cur, (size_t)(L - 1) * noff * nh);
+  w.nbbox_blocks = (int)std::min<int64_t>(1024, (std::max(n_src, n_tgt) + 255) / 256 + 1);
+  w.bbox = carve<double>(cur, (size_t)2 * 3 * 2 * w.nbbox_blocks);
+  w.bytes = (size_t)(cur - static_cast<char*>(base));
+  if (ws) *ws = w;
+  return FMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
+  if (!out) return FMM_ERR_ARG;
+  *out = nullptr;
+  if (!desc) return FMM_ERR_ARG;
+  const int d = desc->d, p = desc->p, L = desc->levels;
+  if (d != 2 && d != 3) return FMM_ERR_ARG;
+  if (p < 1 || p > FMM_MAXP) return FMM_ERR_ARG;
+  if (L < 2 || L > (d == 3 ? 7 : 8)) return FMM_ERR_ARG;
+  if (desc->precision < FMM_PREC_FP64 || desc->precision > FMM_PREC_BF16X3) return FMM_ERR_ARG;
+  const int kernel = desc->kernel;
+  if (kernel == FMM_KERNEL_LAPLACE) {
+  } else if (kernel == FMM_KERNEL_YUKAWA || kernel == FMM_KERNEL_BIHARMONIC) {
+    if (d != 3) return FMM_ERR_UNSUPPORTED;
+  } else {
+    return FMM_ERR_ARG;
+  }
+  if (kernel == FMM_KERNEL_YUKAWA && !(desc->lambda > 0.0)) return FMM_ERR_ARG;
+  for (int k = 0; k < d; ++k)
+    if (!std::isfinite(desc->root_lo[k])) return FMM_ERR_ARG;
+
+  // PDE coefficients
+  std::map<Key, double> a;
+  if (desc->pde) {
+    if (desc->pde->n_terms <= 0 || !desc->pde->multi_idx || !desc->pde->coeff) return FMM_ERR_ARG;
+    for (int t = 0; t < desc->pde->n_terms; ++t) {
+      Key m{0, 0, 0};
+      for (int k = 0; k < d; ++k) {
+        m[k] = desc->pde->multi_idx[t * d + k];
+        if (m[k] < 0) return FMM_ERR_ARG;
+      }
+      a[m] += desc->pde->coeff[t];
+    }
+  } else {
+    a = default_pde(kernel, d, desc->lambda);
+  }
+  int c = 0;
+  for (auto& kv : a)
+    if (kv.second != 0.0) c = std::max(c, kv.first[0] + kv.first[1] + kv.first[2]);
+  if (c < 1) return FMM_ERR_UNSUPPORTED;
+  Key lead{0, 0, 0};
+  lead[d - 1] = c;
+  const double alead = a.count(lead) ? a[lead] : 0.0;
+  if (alead == 0.0) return FMM_ERR_UNSUPPORTED;  // Property 1 on the last axis
+
+  PlanDev pd{};
+  pd.d = d;
+  pd.p = p;
+  pd.c = c;
+  pd.kernel = kernel;
+  pd.lam = desc->lambda;
+  for (auto& kv : a) {
+    if (kv.second == 0.0 || kv.first == lead) continue;
+    if (pd.nterms >= FMM_MAX_TERMS) return FMM_ERR_UNSUPPORTED;
+    int t = pd.nterms++;
+    int deg = 0;
+    for (int k = 0; k < 3; ++k) {
+      pd.tsh[t][k] = kv.first[k] - lead[k];
+      deg += kv.first[k];
+    }
+    pd.tcoef[t] = -kv.second / alead;
+    pd.tpow[t] = c - deg;
+  }
+
+  Layout full = make_layout(d, p, p + 1);
+  Layout hank = make_layout(d, 2 * p, 2 * c - 1);
+  pd.nfull = full.n;
+  pd.nh = hank.n;
+  {
+    Key m{0, 0, 0};
+    m[d - 1] = std::min(c, p + 1);
+    pd.nj = (c > p) ? full.n : (d == 3 ? full.row[(size_t)c * (p + 1)] : full.row[c]);
+  }
+  auto mis = enumerate_full(d, p);
+  if ((int)mis.size() != pd.nfull) return FMM_ERR_UNSUPPORTED;
+
+  // host tables
+  std::vector<char4> mi(pd.nfull);
+  std::vector<double> inv_fact(pd.nfull);
+  const int nt = std::max(pd.nterms, 1);
+  std::vector<int16_t> rec(pd.nfull * (size_t)nt, -1), cmp(pd.nfull * (size_t)nt, -1);
+  for (int i = 0; i < pd.nfull; ++i) {
+    const auto& m = mis[i];
+    const int ms = m[d - 1];
+    const int deg = m[0] + m[1] + m[2];
+    mi[i] = make_char4((char)m[0], (char)m[1], (char)m[2], (char)deg);
+    double f = 1.0;
+    for (int k = 0; k < 3; ++k)
+      for (int t = 2; t <= m[k]; ++t) f *= t;
+    inv_fact[i] = 1.0 / f;
+    if (full.index(m.data()) != i) return FMM_ERR_UNSUPPORTED;
+    for (int t = 0; t < pd.nterms; ++t) {
+      // decompression source m + shift (rows with m_s >= c)
+      if (ms >= c) {
+        int q[3];
+        for (int k = 0; k < 3; ++k) q[k] = m[k] + pd.tsh[t][k];
+        rec[(size_t)i * nt + t] = (int16_t)full.index(q);
+      }
+      // compression gather source m - shift (must be in M(p) with m_s >= c)
+      int q[3], ok = 1, qd = 0;
+      for (int k = 0; k < 3; ++k) {
+        q[k] = m[k] - pd.tsh[t][k];
+        if (q[k] < 0) ok = 0;
+        qd += q[k];
+      }
+      if (ok && qd <= p && q[d - 1] >= c) cmp[(size_t)i * nt + t] = (int16_t)full.index(q);
+    }
+  }
+
+  // upload
+  const size_t n_mi = align_up(sizeof(char4) * pd.nfull);
+  const size_t n_if = align_up(sizeof(double) * pd.nfull);
+  const size_t n_rc = align_up(sizeof(int16_t) * pd.nfull * nt);
+  const size_t n_fr = align_up(sizeof(int) * full.row.size());
+  const size_t n_hr = align_up(sizeof(int) * hank.row.size());
+  const size_t total = n_mi + n_if + 2 * n_rc + n_fr + n_hr;
+  std::vector<char> host(total, 0);
+  char* h = host.data();
+  std::memcpy(h, mi.data(), sizeof(char4) * pd.nfull);
+  std::memcpy(h + n_mi, inv_fact.data(), sizeof(double) * pd.nfull);
+  std::memcpy(h + n_mi + n_if, rec.data(), sizeof(int16_t) * rec.size());
+  std::memcpy(h + n_mi + n_if + n_rc, cmp.data(), sizeof(int16_t) * cmp.size());
+  std::memcpy(h + n_mi + n_if + 2 * n_rc, full.row.data(), sizeof(int) * full.row.size());
+  std::memcpy(h + n_mi + n_if + 2 * n_rc + n_fr, hank.row.data(), sizeof(int) * hank.row.size());
+  void* dt = nullptr;
+  if (cudaMalloc(&dt, total) != cudaSuccess) return FMM_ERR_NOMEM;
+  if (cudaMemcpy(dt, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(dt);
+    return FMM_ERR_CUDA;
+  }
+  char* db = static_cast<char*>(dt);
+  pd.mi = reinterpret_cast<const char4*>(db);
+  pd.inv_fact = reinterpret_cast<const double*>(db + n_mi);
+  pd.rec_src = reinterpret_cast<const int16_t*>(db + n_mi + n_if);
+  pd.cmp_src = reinterpret_cast<const int16_t*>(db + n_mi + n_if + n_rc);
+  pd.frow = reinterpret_cast<const int*>(db + n_mi + n_if + 2 * n_rc);
+  pd.hrow = reinterpret_cast<const int*>(db + n_mi + n_if + 2 * n_rc + n_fr);
+
+  fmm_plan_s* P = new (std::nothrow) fmm_plan_s();
+  if (!P) {
+    cudaFree(dt);
+    return FMM_ERR_NOMEM;
+  }
+  P->desc = *desc;
+  P->desc.pde = nullptr;
+  P->pd = pd;
+  P->dev_tables = dt;
+  *out = P;
+  return FMM_OK;
+}
+
+extern "C" int fmm_plan_destroy(fmm_plan_t P) {
+  if (!P) return FMM_ERR_ARG;
+  cudaDeviceSynchronize();
+  if (P->events_made)
+    for (auto& e : P->ev) cudaEventDestroy(e);
+  cudaFree(P->dev_tables);
+  delete P;
+  return FMM_OK;
+}
+
+extern "C" int fmm_plan_info(fmm_plan_t P, int* nfull, int* nj, int* c) {
+  if (!P) return FMM_ERR_ARG;
+  if (nfull) *nfull = P->pd.nfull;
+  if (nj) *nj = P->pd.nj;
+  if (c) *c = P->pd.c;
+  return FMM_OK;
+}
+
+extern "C" int fmm_workspace_size(fmm_plan_t P, int64_t n_src, int64_t n_tgt, size_t* bytes) {
+  if (!P || !bytes || n_src < 0 || n_tgt < 0) return FMM_ERR_ARG;
+  if (n_src > INT32_MAX / 2 || n_tgt > INT32_MAX / 2) return FMM_ERR_ARG;
+  Workspace w;
+  fmm_workspace_layout(P, n_src, n_tgt, nullptr, &w);
+  *bytes = w.bytes + kAlign;
+  return FMM_OK;
+}
+
+extern "C" int fmm_set_timing(fmm_plan_t P, int enable) {
+  if (!P) return FMM_ERR_ARG;
+  if (enable && !P->events_made) {
+    for (auto& e : P->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return FMM_ERR_CUDA;
+    P->events_made = true;
+  }
+  P->timing = enable ? 1 : 0;
+  return FMM_OK;
+}
+
+extern "C" int fmm_phase_times(fmm_plan_t P, float* ms) {
+  if (!P || !ms || !P->events_made) return FMM_ERR_ARG;
+  if (cudaEventSynchronize(P->ev[FMM_NUM_PHASES]) != cudaSuccess) return FMM_ERR_CUDA;
+  for (int i = 0; i < FMM_NUM_PHASES; ++i)
+    if (cudaEventElapsedTime(&ms[i], P->ev[i], P->ev[i + 1]) != cudaSuccess) return FMM_ERR_CUDA;
+  return FMM_OK;
+}
+
+extern "C" int fmm_last_launch_count(fmm_plan_t P) { return P ? P->launches : -1; }
+
+// ---------------------------------------------------------------------------
+// Evaluation
+// ---------------------------------------------------------------------------
+static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const double* w,
+                         int64_t n_tgt, const double* tgt, double* phi, double* grad,
+                         void* workspace, size_t wbytes, cudaStream_t st, bool first) {
+  if (!P || n_src < 0 || n_tgt < 0) return FMM_ERR_ARG;
+  if (n_src > 0 && (!src || !w)) return FMM_ERR_ARG;
+  if (n_tgt > 0 && !tgt) return FMM_ERR_ARG;
+  if (!workspace) return FMM_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(workspace) % kAlign) return FMM_ERR_ARG;
+  Workspace ws;
+  fmm_workspace_layout(P, n_src, n_tgt, workspace, &ws);
+  if (ws.bytes > wbytes) return FMM_ERR_WORKSPACE;
+  int nl = 0;
+  cudaError_t e = cudaSuccess;
+  auto mark = [&](int i) {
+    if (P->timing) cudaEventRecord(P->ev[i], st);
+  };
+  mark(0);
+  if ((e = launch_set_geom(P, ws, n_src, src, n_tgt, tgt, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_build_tree(P, ws, n_src, src, w, n_tgt, tgt, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(1);
+  if ((e = launch_deriv_tables(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(2);
+  if ((e = launch_p2m(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(3);
+  if ((e = launch_m2m(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(4);
+  if ((e = launch_m2l(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(5);
+  if ((e = launch_l2l(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(6);
+  if ((e = launch_leaf_eval(P, ws, phi, grad, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(7);
+  P->last_stream = st;
+  P->last_geom = ws.geom;
+  P->launches = first ? nl : P->launches + nl;
+  return FMM_OK;
+}
+
+extern "C" int fmm_eval(fmm_plan_t P, int64_t n_src, const double* src, const double* w,
+                        int64_t n_tgt, const double* tgt, double* phi, double* grad,
+                        void* workspace, size_t wbytes, void* stream) {
+  if (n_tgt > 0 && !phi) return FMM_ERR_ARG;
+  return eval_internal(P, n_src, src, w, n_tgt, tgt, phi, grad, workspace, wbytes,
+                       static_cast<cudaStream_t>(stream), true);
+}
+
+__global__ void k_scale_rows(int64_t n, int d, const double* s, double* g) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n * d) g[i] *= s[i / d];
+}
+
+extern "C" int fmm_eval_backward(fmm_plan_t P, int64_t n_src, const double* src,
+                                 const double* w, int64_t n_tgt, const double* tgt,
+                                 const double* u, double* grad_w, double* grad_src,
+                                 double* grad_tgt, void* workspace, size_t wbytes,
+                                 void* stream) {
+  if (!P) return FMM_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int d = P->pd.d;
+  int rc = FMM_OK;
+  bool first = true;
+  // transposed FMM: sources = targets with weights u, evaluated at the sources
+  if (grad_w || grad_src) {
+    if (n_src > 0 && !grad_w && !grad_src) return FMM_ERR_ARG;
+    double* phi_out = grad_w;
+    rc = eval_internal(P, n_tgt, tgt, u, n_src, src, phi_out, grad_src, workspace, wbytes, st,
+                       first);
+    if (rc != FMM_OK) return rc;
+    first = false;
+    if (grad_src && n_src > 0) {
+      int64_t tot = n_src * d;
+      k_scale_rows<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n_src, d, w, grad_src);
+      P->launches++;
+      if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
+    }
+  }
+  if (grad_tgt) {
+    rc = eval_internal(P, n_src, src, w, n_tgt, tgt, nullptr, grad_tgt, workspace, wbytes, st,
+                       first);
+    if (rc != FMM_OK) return rc;
+    if (n_tgt > 0) {
+      int64_t tot = n_tgt * d;
+      k_scale_rows<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n_tgt, d, u, grad_tgt);
+      P->launches++;
+      if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
+    }
+  }
+  return FMM_OK;
+}
+
+extern "C" int fmm_last_status(fmm_plan_t P) {
+  if (!P) return FMM_ERR_ARG;
+  if (!P->last_geom) return FMM_OK;
+  if (cudaStreamSynchronize(P->last_stream) != cudaSuccess) return FMM_ERR_CUDA;
+  Geom g;
+  if (cudaMemcpy(&g, P->last_geom, sizeof(Geom), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FMM_ERR_CUDA;
+  if (g.flag & 2) return FMM_ERR_TIMEOUT;
+  if (g.flag & 1) return FMM_ERR_DOMAIN;
+  return FMM_OK;
+}
+
+extern "C" const char* fmm_status_string(int s) {
+  switch (s) {
+    case FMM_OK: return "ok";
+    case FMM_ERR_ARG: return "invalid argument";
+    case FMM_ERR_UNSUPPORTED: return "unsupported kernel, dimension or PDE";
+    case FMM_ERR_CUDA: return "CUDA runtime error";
+    case FMM_ERR_NOMEM: return "out of memory";
+    case FMM_ERR_TIMEOUT: return "bounded device wait gave up";
+    case FMM_ERR_DOMAIN: return "point outside the root box (clamped)";
+    case FMM_ERR_WORKSPACE: return "workspace too small";
+    default: return "unknown status";
+  }
+}

@@ -1,0 +1,480 @@
+// Derivative tables (Sec. 4.4), P2M (Sec. 3.4), M2M (Sec. 4.3), L2L (Sec. 4.2).
+#include <algorithm>
+
+#include "expansions.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxT = 8;  // full-layout terms per thread: 8 * 256 >= N(20) in 3D
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------------------------
+// M2L derivative tables.  For every level l >= 2 and every offset h in
+// [-3,3]^d outside [-1,1]^d (box units) the block fills
+//   Ht[m] = s_l^{|m|} d^m G(s_l h),  m in the Hankel layout (|m| <= 2p, m_s <= 2c-2),
+// from r^2-led recurrences obtained, as in Sec. 4.4, by applying the Leibniz
+// rule to an identity r^2 d_a g = (...):
+//   g = r^nu (3D Laplace nu=-1, 3D biharmonic nu=+1):  r^2 d_a g = nu x_a g
+//   g = log r (2D Laplace, eq. (deriv_laplace_2d)):      r^2 d_a g = x_a
+//   g = e^{-lam r}/r with b = e^{-lam r} (Yukawa):       r^2 d_a g = -x_a g - lam x_a b,
+//                                                         d_a b = -lam x_a g
+// With a the first axis where m_a >= 1 and k = m - e_a, Leibniz on r^2 gives
+//   r^2 g^m = RHS^{(k)} - 2(m_a-1) x_a g^{m-e_a} - (m_a-1)(m_a-2) g^{m-2e_a}
+//             - sum_{b != a} [2 m_b x_b g^{m-e_b} + m_b (m_b-1) g^{m-2e_b}],
+// which for nu = -1 is the paper's eq. (deriv_laplace_3d).  Every term has
+// lower total degree, so the table fills degree by degree.
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ int hidx(const int* hrow, int P2, const int* m) {
+  return D == 3 ? hrow[m[2] * (P2 + 1) + m[1]] + m[0] : hrow[m[1]] + m[0];
+}
+
+template <int D>
+__global__ void __launch_bounds__(128) k_deriv_tables(PlanDev pd, const Geom* __restrict__ g,
+                                                      double* __restrict__ htab) {
+  constexpr int NOFF = D == 3 ? 343 : 49;
+  const int lrel = blockIdx.x / NOFF, o = blockIdx.x % NOFF;
+  const int l = lrel + 2;
+  double x[3] = {0.0, 0.0, 0.0};
+  bool far = false;
+  {
+    int t = o;
+    for (int k = 0; k < D; ++k) {
+      const int hk = t % 7 - 3;
+      t /= 7;
+      x[k] = (double)hk;
+      if (hk > 1 || hk < -1) far = true;
+    }
+  }
+  if (!far) return;
+  extern __shared__ double sm[];
+  double* G = sm;
+  double* B = sm + pd.nh;
+  const int P2 = 2 * pd.p, nslab = 2 * pd.c - 1;
+  const double s = __ddiv_rn(g->size, (double)(1 << l));
+  const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  const double r = sqrt(r2), rinv2 = 1.0 / r2;
+  const int kern = pd.kernel;
+  const double lam = pd.lam * s;
+  // nu for the r^nu family; log / Yukawa flagged separately
+  const bool is_log = (kern == FMM_KERNEL_LAPLACE && D == 2);
+  const bool is_yuk = (kern == FMM_KERNEL_YUKAWA);
+  const double nu = (kern == FMM_KERNEL_BIHARMONIC) ? 1.0 : -1.0;
+  if (threadIdx.x == 0) {
+    if (is_log) {
+      G[0] = log(r);
+    } else if (is_yuk) {
+      const double e = exp(-lam * r);
+      G[0] = e / r;
+      B[0] = e;
+    } else {
+      G[0] = (kern == FMM_KERNEL_BIHARMONIC) ? r : 1.0 / r;
+    }
+  }
+  __syncthreads();
+  for (int deg = 1; deg <= P2; ++deg) {
+    int count = 0;
+    for (int ms = 0; ms < nslab && ms <= deg; ++ms) count += (D == 3) ? (deg - ms + 1) : 1;
+    for (int e = threadIdx.x; e < count; e += blockDim.x) {
+      int m[3] = {0, 0, 0};
+      {
+        int rem = e;
+        for (int ms = 0; ms < nslab && ms <= deg; ++ms) {
+          const int cnt = (D == 3) ? (deg - ms + 1) : 1;
+          if (rem < cnt) {
+            if (D == 3) {
+              m[2] = ms;
+              m[1] = rem;
+              m[0] = deg - ms - rem;
+            } else {
+              m[1] = ms;
+              m[0] = deg - ms;
+            }
+            break;
+          }
+          rem -= cnt;
+        }
+      }
+      int a = 0;
+      while (m[a] == 0) ++a;
+      const int ma = m[a];
+      int q[3] = {m[0], m[1], m[2]};
+      q[a] = ma - 1;
+      const int i1 = hidx<D>(pd.hrow, P2, q);
+      const double g1 = G[i1];
+      double g2 = 0.0, b1 = 0.0, b2 = 0.0;
+      int i2 = -1;
+      if (ma >= 2) {
+        q[a] = ma - 2;
+        i2 = hidx<D>(pd.hrow, P2, q);
+        g2 = G[i2];
+      }
+      if (is_yuk) {
+        b1 = B[i1];
+        if (i2 >= 0) b2 = B[i2];
+      }
+      double v;
+      if (is_log) {
+        v = -2.0 * (ma - 1) * x[a] * g1 - (double)(ma - 1) * (ma - 2) * g2;
+        if (deg == 1) v += x[a];
+        if (deg == 2 && ma == 2) v += 1.0;
+      } else if (is_yuk) {
+        v = -(2.0 * ma - 1.0) * x[a] * g1 - (double)(ma - 1) * (ma - 1) * g2 - lam * x[a] * b1 -
+            lam * (ma - 1) * b2;
+      } else {
+        v = (nu - 2.0 * (ma - 1)) * x[a] * g1 + (double)(ma - 1) * (nu - (ma - 2)) * g2;
+      }
+      for (int bax = a + 1; bax < D; ++bax) {
+        const int mb = m[bax];
+        if (mb == 0) continue;
+        int qb[3] = {m[0], m[1], m[2]};
+        qb[bax] = mb - 1;
+        v -= 2.0 * mb * x[bax] * G[hidx<D>(pd.hrow, P2, qb)];
+        if (mb >= 2) {
+          qb[bax] = mb - 2;
+          v -= (double)mb * (mb - 1) * G[hidx<D>(pd.hrow, P2, qb)];
+        }
+      }
+      const int im = hidx<D>(pd.hrow, P2, m);
+      G[im] = v * rinv2;
+      if (is_yuk) B[im] = -lam * (x[a] * g1 + (ma - 1) * g2);
+    }
+    __syncthreads();
+  }
+  double scale = 1.0;
+  if (kern == FMM_KERNEL_LAPLACE && D == 3) scale = 1.0 / (4.0 * 3.14159265358979323846 * s);
+  if (kern == FMM_KERNEL_BIHARMONIC) scale = s;
+  if (is_yuk) scale = 1.0 / s;
+  double* out = htab + ((size_t)lrel * NOFF + o) * pd.nh;
+  for (int i = threadIdx.x; i < pd.nh; i += blockDim.x) {
+    double v = G[i] * scale;
+    if (is_log && i == 0) v += log(s);
+    out[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// P2M (Sec. 3.4): per leaf box, alpha_q = sum_y w ((c - y)/s)^q / q!, then
+// beta = M^T alpha (compressed, box-scaled).  One block per leaf box.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __restrict__ g, int L,
+                                                  const int* __restrict__ start,
+                                                  const double* __restrict__ x0,
+                                                  const double* __restrict__ x1,
+                                                  const double* __restrict__ x2,
+                                                  const double* __restrict__ w,
+                                                  double* __restrict__ mp) {
+  constexpr int CH = 32;
+  const int b = blockIdx.x;
+  const int i0 = start[b], i1 = start[b + 1];
+  const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
+  if (i0 == i1) {
+    for (int q = threadIdx.x; q < nj; q += blockDim.x) mp[(size_t)b * nj + q] = 0.0;
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* pw = reinterpret_cast<T*>(smraw);
+  T* alpha = reinterpret_cast<T*>(smraw + align_bytes<T>(sizeof(T) * CH * D * (p + 1)));
+  int bc[3];
+  double c[3], s;
+  box_center<D>(g, L, b, bc, c, &s);
+  const double inv_s = 1.0 / s;
+  T acc[kMaxT];
+  char4 mt[kMaxT];
+#pragma unroll
+  for (int k = 0; k < kMaxT; ++k) {
+    const int q = threadIdx.x + k * blockDim.x;
+    acc[k] = 0;
+    mt[k] = q < nfull ? pd.mi[q] : make_char4(0, 0, 0, 0);
+  }
+  const double* xs[3] = {x0, x1, x2};
+  for (int base = i0; base < i1; base += CH) {
+    const int n = min(CH, i1 - base);
+    __syncthreads();
+    if (threadIdx.x < CH * D) {
+      const int j = threadIdx.x / D, k = threadIdx.x % D;
+      T* row = pw + (j * D + k) * (p + 1);
+      if (j < n) {
+        const T u = (T)((c[k] - xs[k][base + j]) * inv_s);
+        T v = (k == 0) ? (T)w[base + j] : (T)1;
+        row[0] = v;
+        for (int e = 1; e <= p; ++e) {
+          v *= u;
+          row[e] = v;
+        }
+      } else {
+        for (int e = 0; e <= p; ++e) row[e] = 0;
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+      const T* r0 = pw + j * D * (p + 1);
+#pragma unroll
+      for (int k = 0; k < kMaxT; ++k) {
+        if (threadIdx.x + k * blockDim.x < nfull) {
+          T v = r0[mt[k].x] * r0[(p + 1) + mt[k].y];
+          if (D == 3) v *= r0[2 * (p + 1) + mt[k].z];
+          acc[k] += v;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxT; ++k) {
+    const int q = threadIdx.x + k * blockDim.x;
+    if (q < nfull) alpha[q] = acc[k] * (T)pd.inv_fact[q];
+  }
+  __syncthreads();
+  compress_smem<T>(pd, alpha, s);
+  for (int q = threadIdx.x; q < nj; q += blockDim.x) mp[(size_t)b * nj + q] = (double)alpha[q];
+}
+
+// ---------------------------------------------------------------------------
+// M2M (Sec. 4.3, eqs. (mpole_translated_compressed_coeffs), (define_psi)):
+// for each child, sigma_q = sum_{i <= q, i in j} h^{q-i}/(q-i)! beta_i with
+// h = c_parent - c_child = +-s_child/2 per axis; the children's sigmas are
+// summed, rescaled to the parent's box side (factor 2^{-|q|}) and compressed
+// once with the parent's recurrence (M^T is linear).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __restrict__ g, int l,
+                                                  const double* __restrict__ mpc,
+                                                  double* __restrict__ mpp) {
+  const int b = blockIdx.x;
+  const int p = pd.p, c = pd.c, nfull = pd.nfull, nj = pd.nj;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* beta = reinterpret_cast<double*>(smraw);       // nj
+  double* alpha = beta + nj;                              // nfull
+  double* tab = alpha + nfull;                            // (p+1): (1/2)^e / e!
+  int bc[3];
+  double cp[3], s;
+  box_center<D>(g, l, b, bc, cp, &s);
+  if (threadIdx.x == 0) {
+    double v = 1.0;
+    for (int e = 0; e <= p; ++e) {
+      tab[e] = v;
+      v *= 0.5 / (double)(e + 1);
+    }
+  }
+  double acc[kMaxT];
+  char4 mt[kMaxT];
+#pragma unroll
+  for (int k = 0; k < kMaxT; ++k) {
+    const int q = threadIdx.x + k * blockDim.x;
+    acc[k] = 0.0;
+    mt[k] = q < nfull ? pd.mi[q] : make_char4(0, 0, 0, 0);
+  }
+  const int nlc = 1 << (l + 1);
+  for (int ci = 0; ci < (1 << D); ++ci) {
+    int64_t cb = 0;
+    int sg[3];
+    for (int k = D - 1; k >= 0; --k) {
+      const int bit = (ci >> k) & 1;
+      cb = cb * nlc + (2 * bc[k] + bit);
+      sg[k] = bit ? -1 : 1;  // h = c_parent - c_child
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nj; q += blockDim.x) beta[q] = mpc[(size_t)cb * nj + q];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMaxT; ++k) {
+      if (threadIdx.x + k * blockDim.x >= nfull) continue;
+      const int q0 = mt[k].x, q1 = mt[k].y, q2 = mt[k].z;
+      const int qs = D == 3 ? q2 : q1;
+      double sum = 0.0;
+      for (int is = 0; is <= min(qs, c - 1); ++is) {
+        const int es = qs - is;
+        const double fs = ((es & 1) && sg[D - 1] < 0 ? -tab[es] : tab[es]);
+        if (D == 3) {
+          for (int i1 = 0; i1 <= q1; ++i1) {
+            const int e1 = q1 - i1;
+            const double f1 = fs * ((e1 & 1) && sg[1] < 0 ? -tab[e1] : tab[e1]);
+            const int rb = pd.frow[is * (p + 1) + i1];
+            double row = 0.0;
+            for (int i0 = 0; i0 <= q0; ++i0) {
+              const int e0 = q0 - i0;
+              row += ((e0 & 1) && sg[0] < 0 ? -tab[e0] : tab[e0]) * beta[rb + i0];
+            }
+            sum += f1 * row;
+          }
+        } else {
+          const int rb = pd.frow[is];
+          double row = 0.0;
+          for (int i0 = 0; i0 <= q0; ++i0) {
+            const int e0 = q0 - i0;
+            row += ((e0 & 1) && sg[0] < 0 ? -tab[e0] : tab[e0]) * beta[rb + i0];
+          }
+          sum += fs * row;
+        }
+      }
+      acc[k] += sum;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxT; ++k) {
+    const int q = threadIdx.x + k * blockDim.x;
+    if (q < nfull) alpha[q] = ldexp(acc[k], -(int)mt[k].w);
+  }
+  __syncthreads();
+  compress_smem<double>(pd, alpha, s);
+  for (int q = threadIdx.x; q < nj; q += blockDim.x) mpp[(size_t)b * nj + q] = alpha[q];
+}
+
+// ---------------------------------------------------------------------------
+// L2L (Sec. 4.2, eq. (l2l-expr), un-normalised): with Dt = M Lt_parent,
+//   Lt_child_i += 2^{-|i|} sum_{q >= i} Dt_q (h/S)^{q-i} / (q-i)!,  i in j,
+// h = c_child - c_parent = +-S/4 per axis (S the parent's side).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __restrict__ g, int l,
+                                                  const double* __restrict__ lcp,
+                                                  double* __restrict__ lcc) {
+  const int b = blockIdx.x;
+  const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* Dt = reinterpret_cast<double*>(smraw);  // nfull
+  double* tab = Dt + nfull;                        // (1/4)^e / e!
+  int bc[3];
+  double cp[3], s;
+  box_center<D>(g, l, b, bc, cp, &s);
+  for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = lcp[(size_t)b * nj + q];
+  if (threadIdx.x == 0) {
+    double v = 1.0;
+    for (int e = 0; e <= p; ++e) {
+      tab[e] = v;
+      v *= 0.25 / (double)(e + 1);
+    }
+  }
+  __syncthreads();
+  decompress_smem<double>(pd, Dt, s);
+  const int nlc = 1 << (l + 1);
+  const int nout = (1 << D) * nj;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const int ci = o / nj, i = o % nj;
+    int64_t cb = 0;
+    int sg[3];
+    for (int k = D - 1; k >= 0; --k) {
+      const int bit = (ci >> k) & 1;
+      cb = cb * nlc + (2 * bc[k] + bit);
+      sg[k] = bit ? 1 : -1;  // h = c_child - c_parent
+    }
+    const char4 mi = pd.mi[i];
+    const int i0 = mi.x, i1 = mi.y, i2 = mi.z;
+    const int is = D == 3 ? i2 : i1;
+    double sum = 0.0;
+    for (int qs = is; qs <= p; ++qs) {
+      const int es = qs - is;
+      const double fs = ((es & 1) && sg[D - 1] < 0 ? -tab[es] : tab[es]);
+      if (D == 3) {
+        for (int q1 = i1; q1 <= p - qs; ++q1) {
+          const int e1 = q1 - i1;
+          const double f1 = fs * ((e1 & 1) && sg[1] < 0 ? -tab[e1] : tab[e1]);
+          const int rb = pd.frow[qs * (p + 1) + q1];
+          double row = 0.0;
+          for (int q0 = i0; q0 <= p - qs - q1; ++q0) {
+            const int e0 = q0 - i0;
+            row += ((e0 & 1) && sg[0] < 0 ? -tab[e0] : tab[e0]) * Dt[rb + q0];
+          }
+          sum += f1 * row;
+        }
+      } else {
+        const int rb = pd.frow[qs];
+        double row = 0.0;
+        for (int q0 = i0; q0 <= p - qs; ++q0) {
+          const int e0 = q0 - i0;
+          row += ((e0 & 1) && sg[0] < 0 ? -tab[e0] : tab[e0]) * Dt[rb + q0];
+        }
+        sum += fs * row;
+      }
+    }
+    lcc[(size_t)cb * nj + i] += ldexp(sum, -(int)mi.w);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
+                                int* nl) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels;
+  const size_t smem = sizeof(double) * pd.nh * 2;
+  if (pd.d == 3) {
+    set_smem(k_deriv_tables<3>, smem);
+    k_deriv_tables<3><<<(L - 1) * 343, 128, smem, st>>>(pd, ws.geom, ws.htab);
+  } else {
+    set_smem(k_deriv_tables<2>, smem);
+    k_deriv_tables<2><<<(L - 1) * 49, 128, smem, st>>>(pd, ws.geom, ws.htab);
+  }
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels, d = pd.d;
+  const int64_t nleaf = nbox_at(d, L);
+  const bool f64 = P->desc.precision == FMM_PREC_FP64;
+  const size_t tsz = f64 ? 8 : 4;
+  const size_t smem = align_bytes<double>(tsz * 32 * d * (pd.p + 1)) + tsz * pd.nfull;
+  double* mpL = ws.mp + ws.lev_off[L] * pd.nj;
+#define P2M_LAUNCH(DD, TT)                                                                  \
+  do {                                                                                      \
+    set_smem(k_p2m<DD, TT>, smem);                                                          \
+    k_p2m<DD, TT><<<(unsigned)nleaf, kThreads, smem, st>>>(pd, ws.geom, L, ws.sstart,       \
+                                                           ws.sx[0], ws.sx[1], ws.sx[2],    \
+                                                           ws.sw, mpL);                     \
+  } while (0)
+  if (d == 3) {
+    if (f64) P2M_LAUNCH(3, double); else P2M_LAUNCH(3, float);
+  } else {
+    if (f64) P2M_LAUNCH(2, double); else P2M_LAUNCH(2, float);
+  }
+#undef P2M_LAUNCH
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels, d = pd.d;
+  const size_t smem = sizeof(double) * (pd.nj + pd.nfull + pd.p + 1);
+  for (int l = L - 1; l >= 2; --l) {
+    const double* mpc = ws.mp + ws.lev_off[l + 1] * pd.nj;
+    double* mpp = ws.mp + ws.lev_off[l] * pd.nj;
+    if (d == 3) {
+      set_smem(k_m2m<3>, smem);
+      k_m2m<3><<<(unsigned)nbox_at(3, l), kThreads, smem, st>>>(pd, ws.geom, l, mpc, mpp);
+    } else {
+      set_smem(k_m2m<2>, smem);
+      k_m2m<2><<<(unsigned)nbox_at(2, l), kThreads, smem, st>>>(pd, ws.geom, l, mpc, mpp);
+    }
+    ++*nl;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels, d = pd.d;
+  const size_t smem = sizeof(double) * (pd.nfull + pd.p + 1);
+  for (int l = 2; l < L; ++l) {
+    const double* lcp = ws.lc + ws.lev_off[l] * pd.nj;
+    double* lcc = ws.lc + ws.lev_off[l + 1] * pd.nj;
+    if (d == 3) {
+      set_smem(k_l2l<3>, smem);
+      k_l2l<3><<<(unsigned)nbox_at(3, l), kThreads, smem, st>>>(pd, ws.geom, l, lcp, lcc);
+    } else {
+      set_smem(k_l2l<2>, smem);
+      k_l2l<2><<<(unsigned)nbox_at(2, l), kThreads, smem, st>>>(pd, ws.geom, l, lcp, lcc);
+    }
+    ++*nl;
+  }
+  return cudaGetLastError();
+}

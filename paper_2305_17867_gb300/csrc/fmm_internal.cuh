@@ -1,0 +1,121 @@
+// Internal declarations shared by the CUDA translation units of libctfmm.
+//
+// Coefficient layouts (all multi-index tables are built by plan.cu):
+//  * "Full" layout of M(P): slabs by the slow (last) exponent m_s = 0..P;
+//    inside a slab (d=3) rows by m_1, each row m_0 = 0..P-m_s-m_1.  The
+//    position of (m_0, m_1, m_s) is row_base[m_s][m_1] + m_0.
+//  * The stored set j = {m : m_s < c} (Lemma 5 with the last axis slowest) is
+//    therefore the PREFIX of the full layout: its first nj entries.
+//  * "Hankel" layout: the same slab layout for order 2p, slabs 0..2c-2 only:
+//    exactly the derivatives d^{i+q} G with i, q in j that M2L reads
+//    (eq. (m2l_toeplitz)).
+// Expansions are stored box-scaled: at level l with box side s_l,
+//   multipole  bt_q = beta_q / s^{|q|},    local  Lt_i = s^{|i|} L_i,
+// so that derivatives are taken in units of the box side (this only scales
+// the coefficients; eqs. of Secs. 3-4 are unchanged).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ctfmm.h"
+
+#define FMM_MAXP 20
+#define FMM_MAX_TERMS 12
+#define FMM_MAX_LEVELS 8
+
+// Geometry of the root box, resident in device memory (written per call).
+struct Geom {
+  double lo[3];
+  double size;
+  int flag;  // device-side status bits (1: domain)
+  int pad;
+};
+
+// Read-only plan data passed by value to kernels.
+struct PlanDev {
+  int d, p, c;
+  int nfull;  // N(p)
+  int nj;     // |j|
+  int nh;     // entries of the Hankel layout (order 2p, slabs 0..2c-2)
+  int kernel;
+  double lam;
+  int nterms;                      // decompression recurrence terms
+  int tsh[FMM_MAX_TERMS][3];       // shift xi - c e_s  (d=2 uses [0],[1])
+  double tcoef[FMM_MAX_TERMS];     // -a_xi / a_{c e_s}
+  int tpow[FMM_MAX_TERMS];         // c - |xi|: power of s_l in the scaled coefficient
+  // device tables
+  const char4* mi;         // nfull: (m0, m1, m2, |m|); d=2 uses (m0, m_s, 0, |m|)
+  const double* inv_fact;  // nfull: 1/m!
+  const int16_t* rec_src;  // nfull x nterms: decompression sources (rows with m_s >= c)
+  const int16_t* cmp_src;  // nfull x nterms: compression gather sources (-1 = none)
+  const int* frow;         // full layout row bases:   [m_s*(p+1) + m_1]   (d=2: [m_s])
+  const int* hrow;         // Hankel layout row bases: [m_s*(2p+1) + m_1]  (d=2: [m_s])
+};
+
+struct fmm_plan_s {
+  fmm_plan_desc desc;
+  PlanDev pd;
+  void* dev_tables;
+  int timing;
+  cudaEvent_t ev[FMM_NUM_PHASES + 1];
+  bool events_made;
+  cudaStream_t last_stream;
+  Geom* last_geom;  // device geometry of the last evaluation (in its workspace)
+  int launches;
+};
+
+// ---------------------------------------------------------------------------
+// Workspace layout of one evaluation.
+// ---------------------------------------------------------------------------
+struct Workspace {
+  Geom* geom;
+  // points, sorted by leaf box (SoA)
+  double* sx[3];
+  double* sw;
+  int* sperm;       // sorted position -> original source index
+  double* tx[3];
+  int* tperm;       // sorted position -> original target index
+  int* sstart;      // nleaf + 1
+  int* tstart;      // nleaf + 1
+  // radix sort scratch
+  uint32_t* keys_a;
+  uint32_t* keys_b;
+  int* vals_a;
+  int* vals_b;
+  int* hist;        // 256 x nblocks
+  int* hist_sums;   // chunk sums
+  int* counts;      // nleaf
+  // expansions (levels 2..L), box-scaled, float64
+  double* mp;       // sum_l nbox(l) * nj
+  double* lc;
+  int64_t lev_off[FMM_MAX_LEVELS + 1];  // offset (in boxes) of level l inside mp/lc
+  // M2L derivative tables: (L-1) levels x 7^d offsets x nh
+  double* htab;
+  // bounding-box reduction scratch
+  double* bbox;     // 2*d*nblocks
+  int nbbox_blocks;
+  size_t bytes;
+};
+
+// helpers
+__host__ __device__ inline int64_t nbox_at(int d, int l) { return (int64_t)1 << (d * l); }
+
+int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void* base,
+                         Workspace* ws);
+
+// launchers (defined in the .cu files); each returns cudaGetLastError()
+cudaError_t launch_set_geom(const fmm_plan_s* P, const Workspace& ws, int64_t n_src,
+                            const double* src, int64_t n_tgt, const double* tgt,
+                            cudaStream_t st, int* nlaunch);
+cudaError_t launch_build_tree(const fmm_plan_s* P, const Workspace& ws, int64_t n_src,
+                              const double* src, const double* w, int64_t n_tgt,
+                              const double* tgt, cudaStream_t st, int* nlaunch);
+cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
+                                int* nlaunch);
+cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
+cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
+cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
+cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
+cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* phi,
+                             double* grad, cudaStream_t st, int* nlaunch);

@@ -1,0 +1,148 @@
+// M2L on the CUDA cores (Sec. 4.1, eq. (m2l_toeplitz), un-normalised):
+//   Lt_t[i] += sum_{q in j} Ht_{l, t-s}[i + q] bt_s[q],   i in j,
+// over the interaction list of every target box t: the children of the
+// parent's neighbours (parent included) that are not adjacent to t.  The
+// Hankel table Ht of the offset is staged in shared memory once per source,
+// and each row (q_s, q_1) of the stored set is a contiguous run in both the
+// table and the source coefficients, so the inner loop streams two arrays.
+// One block per target box; used for the FP64 and FP32 configurations.
+#include <algorithm>
+
+#include "expansions.cuh"
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kMaxI = 8;  // stored terms per thread: 8 * 128 >= |j| for p <= 20
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kThreads) k_m2l_simt(PlanDev pd, int l,
+                                                       const double* __restrict__ mp,
+                                                       double* __restrict__ lc,
+                                                       const double* __restrict__ htab) {
+  constexpr int NOFF = D == 3 ? 343 : 49;
+  const int b = blockIdx.x;
+  const int p = pd.p, c = pd.c, nj = pd.nj, nh = pd.nh, P2 = 2 * p;
+  const int nl = 1 << l;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* H = reinterpret_cast<T*>(smraw);
+  T* bs = H + nh;
+  int bc[3], pc[3];
+  {
+    int64_t t = b;
+    for (int k = 0; k < D; ++k) {
+      bc[k] = (int)(t % nl);
+      t /= nl;
+      pc[k] = bc[k] >> 1;
+    }
+  }
+  T acc[kMaxI];
+  int ii0[kMaxI], ii1[kMaxI], iis[kMaxI];
+#pragma unroll
+  for (int k = 0; k < kMaxI; ++k) {
+    acc[k] = 0;
+    const int i = threadIdx.x + k * blockDim.x;
+    const char4 m = i < nj ? pd.mi[i] : make_char4(0, 0, 0, 0);
+    ii0[k] = m.x;
+    ii1[k] = D == 3 ? m.y : 0;
+    iis[k] = D == 3 ? m.z : m.y;
+  }
+  int nn = 1;
+  for (int k = 0; k < D; ++k) nn *= 6;
+  for (int a = 0; a < nn; ++a) {
+    int sc[3], tt = a, o = 0, mul = 1;
+    bool ok = true, adj = true;
+    for (int k = 0; k < D; ++k) {
+      sc[k] = 2 * (pc[k] - 1) + tt % 6;
+      tt /= 6;
+      if (sc[k] < 0 || sc[k] >= nl) ok = false;
+      const int dd = bc[k] - sc[k];
+      if (dd > 1 || dd < -1) adj = false;
+      o += (dd + 3) * mul;
+      mul *= 7;
+    }
+    if (!ok || adj) continue;
+    int64_t sb = 0;
+    for (int k = D - 1; k >= 0; --k) sb = sb * nl + sc[k];
+    __syncthreads();
+    const double* hsrc = htab + (size_t)o * nh;
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) H[i] = (T)hsrc[i];
+    for (int i = threadIdx.x; i < nj; i += blockDim.x) bs[i] = (T)mp[(size_t)sb * nj + i];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMaxI; ++k) {
+      if (threadIdx.x + k * blockDim.x >= nj) continue;
+      T sum = 0;
+      for (int qs = 0; qs < c; ++qs) {
+        if (D == 3) {
+          for (int q1 = 0; q1 <= p - qs; ++q1) {
+            const T* hrow = H + pd.hrow[(iis[k] + qs) * (P2 + 1) + ii1[k] + q1] + ii0[k];
+            const T* brow = bs + pd.frow[qs * (p + 1) + q1];
+            const int len = p - qs - q1 + 1;
+            for (int q0 = 0; q0 < len; ++q0) sum += hrow[q0] * brow[q0];
+          }
+        } else {
+          const T* hrow = H + pd.hrow[iis[k] + qs] + ii0[k];
+          const T* brow = bs + pd.frow[qs];
+          const int len = p - qs + 1;
+          for (int q0 = 0; q0 < len; ++q0) sum += hrow[q0] * brow[q0];
+        }
+      }
+      acc[k] += sum;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxI; ++k) {
+    const int i = threadIdx.x + k * blockDim.x;
+    if (i < nj) lc[(size_t)b * nj + i] += (double)acc[k];
+  }
+  (void)NOFF;
+}
+
+}  // namespace
+
+cudaError_t launch_m2l_simt(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels, d = pd.d;
+  const bool f64 = P->desc.precision == FMM_PREC_FP64;
+  const size_t tsz = f64 ? 8 : 4;
+  const size_t smem = tsz * (pd.nh + pd.nj);
+  const int noff = d == 3 ? 343 : 49;
+  for (int l = 2; l <= L; ++l) {
+    const double* mpl = ws.mp + ws.lev_off[l] * pd.nj;
+    double* lcl = ws.lc + ws.lev_off[l] * pd.nj;
+    const double* ht = ws.htab + (size_t)(l - 2) * noff * pd.nh;
+    const unsigned nb = (unsigned)nbox_at(d, l);
+#define M2L_LAUNCH(DD, TT)                                                         \
+  do {                                                                             \
+    set_smem(k_m2l_simt<DD, TT>, smem);                                            \
+    k_m2l_simt<DD, TT><<<nb, kThreads, smem, st>>>(pd, l, mpl, lcl, ht);           \
+  } while (0)
+    if (d == 3) {
+      if (f64) M2L_LAUNCH(3, double); else M2L_LAUNCH(3, float);
+    } else {
+      if (f64) M2L_LAUNCH(2, double); else M2L_LAUNCH(2, float);
+    }
+#undef M2L_LAUNCH
+    ++*nl;
+  }
+  return cudaGetLastError();
+}
+
+// M2L dispatcher: zero the local expansions of levels 2..L, then run the
+// configured contraction path.
+cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl);
+
+cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+  const int L = P->desc.levels;
+  cudaMemsetAsync(ws.lc, 0, sizeof(double) * (size_t)ws.lev_off[L + 1] * P->pd.nj, st);
+  const int prec = P->desc.precision;
+  if (prec == FMM_PREC_FP64 || prec == FMM_PREC_FP32) return launch_m2l_simt(P, ws, st, nl);
+  return launch_m2l_tc(P, ws, st, nl);
+}

@@ -1,0 +1,320 @@
+// Uniform-tree construction on the device: root geometry, leaf binning, a
+// stable LSD radix sort of (leaf key, original index), leaf ranges, and the
+// gather of positions/weights into leaf order (SoA).
+//
+// Leaf boxes are numbered lexicographically, x fastest.  A point's leaf
+// coordinate is floor((x - lo) / s_L) with s_L = size / 2^L, evaluated with
+// round-to-nearest operations only, so the binning is reproducible.
+#include <algorithm>
+
+#include "fmm_internal.cuh"
+
+namespace {
+
+constexpr int kRsBlock = 1024;
+
+__global__ void k_geom_fixed(Geom* g, double lo0, double lo1, double lo2, double size) {
+  g->lo[0] = lo0;
+  g->lo[1] = lo1;
+  g->lo[2] = lo2;
+  g->size = size;
+  g->flag = 0;
+}
+
+// per-block min/max over the sources and targets (bounding cube of the root)
+template <int D>
+__global__ void k_bbox_partial(int64_t ns, const double* __restrict__ src, int64_t nt,
+                               const double* __restrict__ tgt, double* out) {
+  __shared__ double smin[D][256], smax[D][256];
+  double mn[D], mx[D];
+  for (int k = 0; k < D; ++k) {
+    mn[k] = INFINITY;
+    mx[k] = -INFINITY;
+  }
+  const int64_t n = ns + nt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double* x = i < ns ? src + i * D : tgt + (i - ns) * D;
+    for (int k = 0; k < D; ++k) {
+      mn[k] = fmin(mn[k], x[k]);
+      mx[k] = fmax(mx[k], x[k]);
+    }
+  }
+  for (int k = 0; k < D; ++k) {
+    smin[k][threadIdx.x] = mn[k];
+    smax[k][threadIdx.x] = mx[k];
+  }
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < D; ++k) {
+        smin[k][threadIdx.x] = fmin(smin[k][threadIdx.x], smin[k][threadIdx.x + s]);
+        smax[k][threadIdx.x] = fmax(smax[k][threadIdx.x], smax[k][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < D; ++k) {
+      out[(blockIdx.x * 2 + 0) * 3 + k] = smin[k][0];
+      out[(blockIdx.x * 2 + 1) * 3 + k] = smax[k][0];
+    }
+}
+
+// root = cube with corner at the minimum and side = the largest extent
+template <int D>
+__global__ void k_bbox_final(int nblk, const double* part, Geom* g) {
+  if (threadIdx.x != 0) return;
+  double mn[3] = {0, 0, 0}, mx[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) {
+    mn[k] = INFINITY;
+    mx[k] = -INFINITY;
+  }
+  for (int b = 0; b < nblk; ++b)
+    for (int k = 0; k < D; ++k) {
+      mn[k] = fmin(mn[k], part[(b * 2 + 0) * 3 + k]);
+      mx[k] = fmax(mx[k], part[(b * 2 + 1) * 3 + k]);
+    }
+  double size = 0.0;
+  for (int k = 0; k < D; ++k) size = fmax(size, mx[k] - mn[k]);
+  if (!(size > 0.0) || !isfinite(size)) size = 1.0;
+  for (int k = 0; k < 3; ++k) g->lo[k] = (k < D && isfinite(mn[k])) ? mn[k] : 0.0;
+  g->size = size;
+  g->flag = 0;
+}
+
+// leaf key of every point + per-leaf counts; vals = identity
+template <int D>
+__global__ void k_bin(int64_t n, const double* __restrict__ x, const Geom* __restrict__ g, int L,
+                      uint32_t* __restrict__ keys, int* __restrict__ vals,
+                      int* __restrict__ counts, Geom* gflag) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nl = 1 << L;
+  const double s = __ddiv_rn(g->size, (double)nl);
+  uint32_t key = 0;
+  bool bad = false;
+  for (int k = D - 1; k >= 0; --k) {
+    double t = __ddiv_rn(__dsub_rn(x[i * D + k], g->lo[k]), s);
+    if (!(t >= 0.0) || t > (double)nl) bad = true;
+    int b = (t >= 0.0) ? (int)fmin(floor(t), (double)(nl - 1)) : 0;  // NaN -> 0
+    key = key * (uint32_t)nl + (uint32_t)b;
+  }
+  if (bad) atomicOr(&gflag->flag, 1);
+  keys[i] = key;
+  vals[i] = (int)i;
+  atomicAdd(&counts[key], 1);
+}
+
+// ---- exclusive scan of an int array (three small kernels) -----------------
+__device__ int block_exclusive_scan(int v, int* smem, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    int s = lane < nw ? smem[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    smem[lane] = s;
+  }
+  __syncthreads();
+  int incl = x + (wid > 0 ? smem[wid - 1] : 0);
+  if (total) *total = smem[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void k_scan_chunks(const int* __restrict__ in, int* __restrict__ out, int64_t n,
+                              int* __restrict__ sums) {
+  __shared__ int sm[32];
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int v = i < n ? in[i] : 0;
+  int tot;
+  int ex = block_exclusive_scan(v, sm, &tot);
+  if (i < n) out[i] = ex;
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(int* sums, int n) {
+  // one block: each thread scans a contiguous segment
+  __shared__ int sm[32];
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b = threadIdx.x * per;
+  int loc = 0;
+  for (int k = 0; k < per && b + k < n; ++k) loc += sums[b + k];
+  int ex = block_exclusive_scan(loc, sm, nullptr);
+  int run = ex;
+  for (int k = 0; k < per && b + k < n; ++k) {
+    int v = sums[b + k];
+    sums[b + k] = run;
+    run += v;
+  }
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int64_t n, const int* __restrict__ sums,
+                           int* __restrict__ total_out, const int* __restrict__ in_last) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] += sums[blockIdx.x];
+  if (total_out && i == n - 1) *total_out = out[i] + *in_last;
+}
+
+// ---- stable LSD radix sort, 8 bits per pass --------------------------------
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, int n, int shift,
+                          int* __restrict__ hist, int nblk) {
+  __shared__ int h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  int i = blockIdx.x * kRsBlock + threadIdx.x;
+  if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b * nblk + blockIdx.x] = h[b];
+}
+
+__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const int* __restrict__ vin,
+                             uint32_t* __restrict__ kout, int* __restrict__ vout, int n, int shift,
+                             const int* __restrict__ hist_ex, int nblk) {
+  __shared__ unsigned short wc[32][256];
+  for (int i = threadIdx.x; i < 32 * 256; i += blockDim.x) (&wc[0][0])[i] = 0;
+  __syncthreads();
+  const int i = blockIdx.x * kRsBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const bool valid = i < n;
+  uint32_t key = valid ? kin[i] : 0u;
+  int val = valid ? vin[i] : 0;
+  const unsigned dig = valid ? ((key >> shift) & 255u) : 256u;
+  const unsigned peers = __match_any_sync(0xffffffffu, dig);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  if (valid && rank == 0) wc[wid][dig] = (unsigned short)__popc(peers);
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    unsigned run = 0;
+    for (int w = 0; w < 32; ++w) {
+      unsigned c = wc[w][threadIdx.x];
+      wc[w][threadIdx.x] = (unsigned short)run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    int pos = hist_ex[dig * nblk + blockIdx.x] + wc[wid][dig] + rank;
+    kout[pos] = key;
+    vout[pos] = val;
+  }
+}
+
+template <int D>
+__global__ void k_gather(int n, const int* __restrict__ order, const double* __restrict__ x,
+                         const double* __restrict__ w, double* __restrict__ o0,
+                         double* __restrict__ o1, double* __restrict__ o2,
+                         double* __restrict__ ow, int* __restrict__ perm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int j = order[i];
+  perm[i] = j;
+  o0[i] = x[(int64_t)j * D + 0];
+  o1[i] = x[(int64_t)j * D + 1];
+  if (D == 3) o2[i] = x[(int64_t)j * D + 2];
+  if (w) ow[i] = w[j];
+}
+
+unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// exclusive scan of in[0..n) into out[0..n], out[n] = total
+cudaError_t scan_ints(const int* in, int* out, int64_t n, int* sums, cudaStream_t st,
+                      int* nl) {
+  const unsigned nb = nblocks(n, 1024);
+  k_scan_chunks<<<nb, 1024, 0, st>>>(in, out, n, sums);
+  k_scan_top<<<1, 1024, 0, st>>>(sums, (int)nb);
+  k_scan_add<<<nb, 1024, 0, st>>>(out, n, sums, out + n, in + n - 1);
+  *nl += 3;
+  return cudaGetLastError();
+}
+
+// sort one point set into leaf order; fills start[], the SoA copies and perm
+template <int D>
+cudaError_t sort_points(const fmm_plan_s* P, const Workspace& ws, int64_t n, const double* x,
+                        const double* w, int* start, double* const* ox, double* ow, int* perm,
+                        cudaStream_t st, int* nl) {
+  const int L = P->desc.levels;
+  const int64_t nleaf = nbox_at(D, L);
+  cudaMemsetAsync(ws.counts, 0, sizeof(int) * nleaf, st);
+  if (n == 0) {
+    cudaMemsetAsync(start, 0, sizeof(int) * (nleaf + 1), st);
+    return cudaGetLastError();
+  }
+  k_bin<D><<<nblocks(n, 256), 256, 0, st>>>(n, x, ws.geom, L, ws.keys_a, ws.vals_a, ws.counts,
+                                            ws.geom);
+  ++*nl;
+  cudaError_t e = scan_ints(ws.counts, start, nleaf, ws.hist_sums, st, nl);
+  if (e != cudaSuccess) return e;
+  const int bits = D * L;
+  const int nblk = (int)nblocks(n, kRsBlock);
+  uint32_t* ka = ws.keys_a;
+  uint32_t* kb = ws.keys_b;
+  int* va = ws.vals_a;
+  int* vb = ws.vals_b;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_hist<<<nblk, kRsBlock, 0, st>>>(ka, (int)n, shift, ws.hist, nblk);
+    ++*nl;
+    const int64_t nh = 256LL * nblk;
+    const unsigned nb = nblocks(nh, 1024);
+    k_scan_chunks<<<nb, 1024, 0, st>>>(ws.hist, ws.hist, nh, ws.hist_sums);
+    k_scan_top<<<1, 1024, 0, st>>>(ws.hist_sums, (int)nb);
+    k_scan_add<<<nb, 1024, 0, st>>>(ws.hist, nh, ws.hist_sums, nullptr, nullptr);
+    k_rs_scatter<<<nblk, kRsBlock, 0, st>>>(ka, va, kb, vb, (int)n, shift, ws.hist, nblk);
+    *nl += 4;
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  k_gather<D><<<nblocks(n, 256), 256, 0, st>>>((int)n, va, x, w, ox[0], ox[1],
+                                               D == 3 ? ox[2] : ox[0], ow, perm);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_set_geom(const fmm_plan_s* P, const Workspace& ws, int64_t n_src,
+                            const double* src, int64_t n_tgt, const double* tgt,
+                            cudaStream_t st, int* nl) {
+  const fmm_plan_desc& d = P->desc;
+  if (d.root_size > 0.0) {
+    k_geom_fixed<<<1, 1, 0, st>>>(ws.geom, d.root_lo[0], d.root_lo[1], d.d == 3 ? d.root_lo[2] : 0.0,
+                                  d.root_size);
+    ++*nl;
+    return cudaGetLastError();
+  }
+  const int nb = ws.nbbox_blocks;
+  if (P->pd.d == 3) {
+    k_bbox_partial<3><<<nb, 256, 0, st>>>(n_src, src, n_tgt, tgt, ws.bbox);
+    k_bbox_final<3><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom);
+  } else {
+    k_bbox_partial<2><<<nb, 256, 0, st>>>(n_src, src, n_tgt, tgt, ws.bbox);
+    k_bbox_final<2><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom);
+  }
+  *nl += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_tree(const fmm_plan_s* P, const Workspace& ws, int64_t n_src,
+                              const double* src, const double* w, int64_t n_tgt,
+                              const double* tgt, cudaStream_t st, int* nl) {
+  cudaError_t e;
+  if (P->pd.d == 3) {
+    e = sort_points<3>(P, ws, n_src, src, w, ws.sstart, ws.sx, ws.sw, ws.sperm, st, nl);
+    if (e != cudaSuccess) return e;
+    e = sort_points<3>(P, ws, n_tgt, tgt, nullptr, ws.tstart, ws.tx, nullptr, ws.tperm, st, nl);
+  } else {
+    e = sort_points<2>(P, ws, n_src, src, w, ws.sstart, ws.sx, ws.sw, ws.sperm, st, nl);
+    if (e != cudaSuccess) return e;
+    e = sort_points<2>(P, ws, n_tgt, tgt, nullptr, ws.tstart, ws.tx, nullptr, ws.tperm, st, nl);
+  }
+  return e;
+}

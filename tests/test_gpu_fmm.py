@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+FP64 results must match the oracle's same-tree, same-p FMM to relative L2
+error 1e-12 (the target the method's FP64 form is held to).
+"""
+import numpy as np
+import pytest
+
+from paper_2305_17867_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def gpu_fmm(torch, kernel, d, p, L, src, w, tgt=None, lam=0.0, precision="fp64", grad=False,
+            root_lo=None, root_size=1.0):
+    from paper_2305_17867_gb300.fmm import FMM
+
+    plan = FMM(kernel, d=d, p=p, levels=L, lam=lam, precision=precision, root_lo=root_lo,
+               root_size=root_size)
+    s = torch.tensor(src, device="cuda")
+    wt = torch.tensor(w, device="cuda")
+    t = None if tgt is None else torch.tensor(tgt, device="cuda")
+    out = plan.eval(s, wt, t, grad=grad, check_status=True)
+    torch.cuda.synchronize()
+    if grad:
+        return out[0].cpu().numpy(), out[1].cpu().numpy()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("L,n", [(2, 3000), (3, 20000), (4, 30011)])
+def test_laplace3d_fp64_matches_oracle(torch_cuda, oracle, L, n):
+    wl = W.WORKLOADS["laplace3d_p10_L5_n1m"]
+    src, w, _ = W.make_inputs(wl, n_src=n)
+    ref = oracle.fmm_uniform("laplace", 3, 10, L, src, w, src)
+    got = gpu_fmm(torch_cuda, "laplace", 3, 10, L, src, w)
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+def test_laplace2d_config_fp64(torch_cuda, oracle):
+    wl = W.WORKLOADS["laplace2d_p8_L4_n2k"]
+    src, w, _ = W.make_inputs(wl)
+    ref = oracle.fmm_uniform("laplace", 2, 8, 4, src, w, src)
+    got = gpu_fmm(torch_cuda, "laplace", 2, 8, 4, src, w)
+    assert rel_l2(got, ref) < FP64_TOL
+    direct = oracle.direct("laplace", 2, src, w, src)
+    assert rel_l2(got, direct) < 1e-5
+
+
+@pytest.mark.parametrize("kernel,p,lam", [("yukawa", 8, 1.0), ("yukawa", 12, 1.0),
+                                          ("biharmonic", 4, 0.0), ("biharmonic", 8, 0.0)])
+def test_other_kernels_fp64_matches_oracle(torch_cuda, oracle, kernel, p, lam):
+    rng = np.random.default_rng(7)
+    src = rng.random((9000, 3))
+    w = rng.uniform(-1, 1, 9000)
+    tgt = rng.random((5000, 3))
+    ref = oracle.fmm_uniform(kernel, 3, p, 3, src, w, tgt, lam=lam)
+    got = gpu_fmm(torch_cuda, kernel, 3, p, 3, src, w, tgt, lam=lam)
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+def test_gradient_fp64_matches_oracle(torch_cuda, oracle):
+    rng = np.random.default_rng(8)
+    src = rng.random((12000, 3))
+    w = rng.uniform(-1, 1, 12000)
+    tgt = rng.random((7000, 3))
+    ref, gref = oracle.fmm_uniform("laplace", 3, 8, 3, src, w, tgt, grad=True)
+    got, g = gpu_fmm(torch_cuda, "laplace", 3, 8, 3, src, w, tgt, grad=True)
+    assert rel_l2(got, ref) < FP64_TOL
+    assert rel_l2(g, gref) < FP64_TOL
+
+
+def test_full_size_laplace3d_sampled(torch_cuda, oracle):
+    # the measured workload: 1e6 uniform points, p = 10, L = 5; the oracle
+    # evaluates a seeded sample of targets one by one on the same tree.
+    wl = W.WORKLOADS["laplace3d_p10_L5_n1m"]
+    src, w, _ = W.make_inputs(wl)
+    got = gpu_fmm(torch_cuda, "laplace", 3, 10, 5, src, w)
+    idx = np.random.default_rng(99).choice(len(w), 64, replace=False)
+    ref = oracle.fmm_uniform("laplace", 3, 10, 5, src, w, src, sample=idx)
+    assert rel_l2(got[idx], ref) < FP64_TOL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 2e-5)])
+def test_mixed_precision_error(torch_cuda, oracle, precision, tol):
+    wl = W.WORKLOADS["laplace3d_p10_L5_n1m"]
+    src, w, _ = W.make_inputs(wl, n_src=30000)
+    ref = oracle.fmm_uniform("laplace", 3, 10, 4, src, w, src)
+    got = gpu_fmm(torch_cuda, "laplace", 3, 10, 4, src, w, precision=precision)
+    assert rel_l2(got, ref) < tol
+
+
+# ---- edge cases -------------------------------------------------------------
+def test_empty_sources_and_targets(torch_cuda):
+    z = np.zeros((0, 3))
+    tgt = np.random.default_rng(1).random((50, 3))
+    got = gpu_fmm(torch_cuda, "laplace", 3, 4, 2, z, np.zeros(0), tgt)
+    assert np.all(got == 0.0)
+    got = gpu_fmm(torch_cuda, "laplace", 3, 4, 2, tgt, np.ones(50), z)
+    assert got.shape == (0,)
+
+
+def test_clustered_and_boundary_points(torch_cuda, oracle):
+    # 600 points in one leaf (several passes of the leaf kernel), points on
+    # the root box faces, and exact duplicates (skipped pairs).
+    rng = np.random.default_rng(3)
+    a = 0.51 + 0.01 * rng.random((600, 3))
+    b = rng.random((400, 3))
+    b[:20, 0] = 1.0
+    b[20:40, 1] = 0.0
+    src = np.concatenate([a, b, a[:10]])
+    w = rng.uniform(-1, 1, len(src))
+    ref = oracle.fmm_uniform("laplace", 3, 6, 3, src, w, src)
+    got = gpu_fmm(torch_cuda, "laplace", 3, 6, 3, src, w)
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+def test_auto_root_box(torch_cuda, oracle):
+    rng = np.random.default_rng(4)
+    src = rng.random((5000, 3)) * 3.0 - 1.0
+    w = rng.uniform(-1, 1, 5000)
+    lo = src.min(axis=0)
+    size = float((src.max(axis=0) - lo).max())
+    ref = oracle.fmm_uniform("laplace", 3, 6, 3, src, w, src, lo=lo, size=size)
+    got = gpu_fmm(torch_cuda, "laplace", 3, 6, 3, src, w, root_size=0.0)
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+def test_domain_error_flag(torch_cuda):
+    from paper_2305_17867_gb300.fmm import FMM
+    from paper_2305_17867_gb300._lib import FMMError
+
+    torch = torch_cuda
+    plan = FMM("laplace", d=3, p=4, levels=2)
+    src = torch.rand(100, 3, device="cuda", dtype=torch.float64)
+    src[0, 0] = 1.5
+    with pytest.raises(FMMError) as ei:
+        plan.eval(src, torch.ones(100, device="cuda", dtype=torch.float64), check_status=True)
+    assert ei.value.code == -6
+
+
+def test_bad_arguments_rejected(torch_cuda):
+    from paper_2305_17867_gb300.fmm import FMM
+    from paper_2305_17867_gb300._lib import FMMError
+
+    with pytest.raises(FMMError):
+        FMM("laplace", d=3, p=0, levels=3)
+    with pytest.raises(FMMError):
+        FMM("yukawa", d=2, p=4, levels=3, lam=1.0)
+    with pytest.raises(FMMError):
+        FMM("laplace", d=3, p=4, levels=9)
+
+
+def test_autograd_against_direct_gradients(torch_cuda, oracle):
+    torch = torch_cuda
+    from paper_2305_17867_gb300.fmm import FMM, fmm_potential
+
+    rng = np.random.default_rng(21)
+    n = 1000
+    src = rng.random((n, 3))
+    tgt = rng.random((n, 3))
+    w = rng.uniform(-1, 1, n)
+    u = rng.normal(size=n)
+    plan = FMM("laplace", d=3, p=12, levels=3)
+    s = torch.tensor(src, device="cuda", requires_grad=True)
+    t = torch.tensor(tgt, device="cuda", requires_grad=True)
+    wt = torch.tensor(w, device="cuda", requires_grad=True)
+    phi = fmm_potential(plan, s, wt, t)
+    loss = (phi * torch.tensor(u, device="cuda")).sum()
+    loss.backward()
+    # d/dw_j = sum_i u_i G(x_i - y_j); d/dx_i = u_i grad phi(x_i);
+    # d/dy_j = w_j grad psi(y_j), psi(y) = sum_i u_i G(y - x_i)
+    gw_ref, gy = oracle.direct("laplace", 3, tgt, u, src, grad=True)
+    _, gx = oracle.direct("laplace", 3, src, w, tgt, grad=True)
+    assert rel_l2(wt.grad.cpu().numpy(), gw_ref) < 1e-6
+    assert rel_l2(t.grad.cpu().numpy(), u[:, None] * gx) < 1e-6
+    assert rel_l2(s.grad.cpu().numpy(), w[:, None] * gy) < 1e-6
+    # finite differences of the FMM loss itself on a few coordinates
+    def loss_at(sv, wv, tv):
+        ph = plan.eval(torch.tensor(sv, device="cuda"), torch.tensor(wv, device="cuda"),
+                       torch.tensor(tv, device="cuda"))
+        return float((ph.cpu().numpy() * u).sum())
+    h = 1e-6
+    for (arr, which, i, k) in [(src, "s", 3, 0), (tgt, "t", 5, 2), (w, "w", 7, None)]:
+        ap, am = arr.copy(), arr.copy()
+        if k is None:
+            ap[i] += h
+            am[i] -= h
+        else:
+            ap[i, k] += h
+            am[i, k] -= h
+        args_p = {"s": (ap, w, tgt), "t": (src, w, ap), "w": (src, ap, tgt)}[which]
+        args_m = {"s": (am, w, tgt), "t": (src, w, am), "w": (src, am, tgt)}[which]
+        fd = (loss_at(*args_p) - loss_at(*args_m)) / (2 * h)
+        g = {"s": s.grad, "t": t.grad, "w": wt.grad}[which].cpu().numpy()
+        an = g[i] if k is None else g[i, k]
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (which, fd, an)
