@@ -147,6 +147,16 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
   w.htab = carve<double>(cur, (size_t)(L - 1) * noff * nh);
   w.nbbox_blocks = (int)std::min<int64_t>(1024, (std::max(n_src, n_tgt) + 255) / 256 + 1);
   w.bbox = carve<double>(cur, (size_t)2 * 3 * 2 * w.nbbox_blocks);
+  const int prec = P->desc.precision;
+  if (d == 3 && (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3)) {
+    w.tc_jp = (nj + 31) / 32 * 32;
+    w.tc_mp = (nj + 127) / 128 * 128;
+    const int halves = prec == FMM_PREC_TF32X3 ? 2 : 1;
+    for (int h = 0; h < halves; ++h) {
+      w.tc_bpar[h] = carve<float>(cur, (size_t)nbox_at(3, L) * w.tc_jp);
+      w.tc_tmat[h] = carve<float>(cur, (size_t)343 * w.tc_mp * w.tc_jp);
+    }
+  }
   w.bytes = (size_t)(cur - static_cast<char*>(base));
   if (ws) *ws = w;
   return FMM_OK;
@@ -164,6 +174,7 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   if (p < 1 || p > FMM_MAXP) return FMM_ERR_ARG;
   if (L < 2 || L > (d == 3 ? 7 : 8)) return FMM_ERR_ARG;
   if (desc->precision < FMM_PREC_FP64 || desc->precision > FMM_PREC_BF16X3) return FMM_ERR_ARG;
+  if (desc->precision == FMM_PREC_BF16X3) return FMM_ERR_UNSUPPORTED;
   const int kernel = desc->kernel;
   if (kernel == FMM_KERNEL_LAPLACE) {
   } else if (kernel == FMM_KERNEL_YUKAWA || kernel == FMM_KERNEL_BIHARMONIC) {

@@ -95,6 +95,12 @@ struct Workspace {
   // bounding-box reduction scratch
   double* bbox;     // 2*d*nblocks
   int nbbox_blocks;
+  // tensor-core M2L operands (tf32 hi / lo): parity-split multipoles of the
+  // finest level and the dense offset matrices of one level
+  int tc_jp;        // |j| padded to a multiple of 32 (K)
+  int tc_mp;        // |j| padded to a multiple of 128 (M)
+  float* tc_bpar[2];
+  float* tc_tmat[2];
   size_t bytes;
 };
 

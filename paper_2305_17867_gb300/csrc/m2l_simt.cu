@@ -107,14 +107,15 @@ __global__ void __launch_bounds__(kThreads) k_m2l_simt(PlanDev pd, int l,
 
 }  // namespace
 
-cudaError_t launch_m2l_simt(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+cudaError_t launch_m2l_simt_levels(const fmm_plan_s* P, const Workspace& ws, int l0, int l1,
+                                   cudaStream_t st, int* nl) {
   const PlanDev& pd = P->pd;
-  const int L = P->desc.levels, d = pd.d;
+  const int d = pd.d;
   const bool f64 = P->desc.precision == FMM_PREC_FP64;
   const size_t tsz = f64 ? 8 : 4;
   const size_t smem = tsz * (pd.nh + pd.nj);
   const int noff = d == 3 ? 343 : 49;
-  for (int l = 2; l <= L; ++l) {
+  for (int l = l0; l <= l1; ++l) {
     const double* mpl = ws.mp + ws.lev_off[l] * pd.nj;
     double* lcl = ws.lc + ws.lev_off[l] * pd.nj;
     const double* ht = ws.htab + (size_t)(l - 2) * noff * pd.nh;
@@ -143,6 +144,6 @@ cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   const int L = P->desc.levels;
   cudaMemsetAsync(ws.lc, 0, sizeof(double) * (size_t)ws.lev_off[L + 1] * P->pd.nj, st);
   const int prec = P->desc.precision;
-  if (prec == FMM_PREC_FP64 || prec == FMM_PREC_FP32) return launch_m2l_simt(P, ws, st, nl);
+  if (prec == FMM_PREC_FP64 || prec == FMM_PREC_FP32) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
   return launch_m2l_tc(P, ws, st, nl);
 }

@@ -1,6 +1,349 @@
-// Tensor-core M2L (tcgen05): placeholder until the kernel lands.
-#include "fmm_internal.cuh"
+// Tensor-core M2L (tcgen05, kind::tf32) -- eq. (m2l_toeplitz) grouped by
+// translation offset into dense contractions on the fifth-generation tensor
+// cores, with the accumulator in TMEM.
+//
+// For a level with half-grid size H = 2^(l-1), write every box as 2T + pi
+// (T its parent's coordinate, pi in {0,1}^3 its position in the parent).
+// A target of class pi receives, from source child sigma of the parent
+// T + delta (delta in {-1,0,1}^3), the translation with offset
+// h = pi - sigma - 2 delta, whenever h is not adjacent (max |h_k| >= 2).
+// For a fixed (pi, sigma, delta) the sources of a tile of targets T are the
+// same tile of parents shifted by delta, so with the multipoles stored
+// parity-split, Bpar[sigma][Tz][Ty][Tx][q], one 5-D TMA box (zero-filled
+// outside the domain) is the B operand, and the dense offset matrix
+//   A_h[i][q] = Ht_h[i + q]   (i, q in j)
+// is the A operand.  One CTA owns one (tile of 4x4x8 targets, pi, 128-row
+// block of i), accumulates D[i][T] = sum_{sigma,delta,q} A_h[i][q] Bpar[...][q]
+// over the 189 offsets in TMEM, and adds D into the FP64 local expansions.
+//
+// Precision: TF32 (one pass) or TF32x3 (a = a_hi + a_lo split, three passes
+// a_hi b_hi + a_hi b_lo + a_lo b_hi), FP32 accumulation.
+#include <algorithm>
+#include <cstring>
 
-cudaError_t launch_m2l_tc(const fmm_plan_s*, const Workspace&, cudaStream_t, int*) {
-  return cudaErrorNotSupported;
+#include "expansions.cuh"
+#include "tc_ptx.cuh"
+
+cudaError_t launch_m2l_simt_levels(const fmm_plan_s* P, const Workspace& ws, int l0, int l1,
+                                   cudaStream_t st, int* nl);
+
+namespace {
+
+constexpr int kBM = 128;        // rows of A / TMEM lanes
+constexpr int kRowBytes = 128;  // one K chunk: 32 fp32
+constexpr int kTileBytesA = kBM * kRowBytes;
+constexpr int kMaxN = 128;
+constexpr int kTileBytesB = kMaxN * kRowBytes;
+constexpr int kThreads = 128;
+
+template <int NPASS>
+struct Cfg {
+  static constexpr int kStages = NPASS == 1 ? 6 : 3;
+  static constexpr int kStage = NPASS == 1 ? kTileBytesA + kTileBytesB
+                                           : 2 * (kTileBytesA + kTileBytesB);
+  static constexpr int kSmem = 1024 + kStages * kStage + 256;
+};
+
+// ---- operand packing ------------------------------------------------------
+// multipoles of level l (lexicographic boxes, FP64, nj per box) ->
+// Bpar[sigma][Tz][Ty][Tx][JP] fp32 (tf32-rounded hi, and lo for the split)
+__global__ void k_pack_beta(const double* __restrict__ mp, int l, int nj, int JP,
+                            float* __restrict__ bhi, float* __restrict__ blo) {
+  const int nl = 1 << l, H = nl >> 1;
+  const int64_t nbox = (int64_t)nl * nl * nl;
+  const int64_t tot = nbox * JP;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % JP);
+    const int64_t b = e / JP;
+    const int x = (int)(b % nl), y = (int)((b / nl) % nl), z = (int)(b / ((int64_t)nl * nl));
+    const int sg = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+    const int64_t dst = ((((int64_t)sg * H + (z >> 1)) * H + (y >> 1)) * H + (x >> 1)) * JP + q;
+    const double v = q < nj ? mp[b * nj + q] : 0.0;
+    const float hi = tc::tf32_rna((float)v);
+    bhi[dst] = hi;
+    if (blo) blo[dst] = tc::tf32_rna((float)(v - (double)hi));
+  }
+}
+
+// dense offset matrices A_h[i][q] = Ht_h[i + q] for the 343 offsets of a level
+template <int D>
+__global__ void k_build_tmat(PlanDev pd, const double* __restrict__ htab, int MP, int JP,
+                             float* __restrict__ thi, float* __restrict__ tlo) {
+  const int o = blockIdx.x;
+  {
+    int t = o;
+    bool far = false;
+    for (int k = 0; k < D; ++k) {
+      const int hk = t % 7 - 3;
+      t /= 7;
+      if (hk > 1 || hk < -1) far = true;
+    }
+    if (!far) return;
+  }
+  const double* H = htab + (size_t)o * pd.nh;
+  const int P2 = 2 * pd.p;
+  const int rows = 8;
+  const int i0 = blockIdx.y * rows;
+  for (int e = threadIdx.x; e < rows * JP; e += blockDim.x) {
+    const int i = i0 + e / JP, q = e % JP;
+    double v = 0.0;
+    if (i < pd.nj && q < pd.nj) {
+      const char4 a = pd.mi[i], b = pd.mi[q];
+      const int m0 = a.x + b.x, m1 = a.y + b.y, m2 = a.z + b.z;
+      const int idx = D == 3 ? pd.hrow[m2 * (P2 + 1) + m1] + m0 : pd.hrow[m1] + m0;
+      v = H[idx];
+    }
+    const size_t dst = ((size_t)o * MP + i) * JP + q;
+    const float hi = tc::tf32_rna((float)v);
+    thi[dst] = hi;
+    if (tlo) tlo[dst] = tc::tf32_rna((float)(v - (double)hi));
+  }
+}
+
+// ---- the contraction --------------------------------------------------------
+template <int NPASS>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_m2l_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
+             const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBlo,
+             int l, int nj, int jchunks, int MP, int BX, int BY, int BZ, int ntx, int nty,
+             double* __restrict__ lc, int* __restrict__ err) {
+  using C = Cfg<NPASS>;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::kStages * C::kStage);
+  uint64_t* empty = full + C::kStages;
+  uint64_t* accb = empty + C::kStages;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pi = blockIdx.y, mt = blockIdx.z;
+  const int tile = blockIdx.x;
+  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+  const int X0 = tx * BX, Y0 = ty * BY, Z0 = tz * BZ;
+  const int N = BX * BY * BZ;
+  const int nl = 1 << l, H = nl >> 1;
+  const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
+  const uint32_t bytesA = kTileBytesA, bytesB = (uint32_t)N * kRowBytes;
+  const uint32_t stage_tx = (NPASS == 1 ? 1u : 2u) * (bytesA + bytesB);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(accb, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tslot, 128);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int kk = 0;
+    int last_round[C::kStages];
+    for (int s = 0; s < C::kStages; ++s) last_round[s] = -1;
+    bool ok = true;
+    for (int c = 0; c < 216 && ok; ++c) {
+      const int sg = c & 7, di = c >> 3;
+      const int dx = di % 3 - 1, dy = (di / 3) % 3 - 1, dz = di / 9 - 1;
+      const int hx = px - (sg & 1) - 2 * dx, hy = py - ((sg >> 1) & 1) - 2 * dy,
+                hz = pz - ((sg >> 2) & 1) - 2 * dz;
+      if (hx >= -1 && hx <= 1 && hy >= -1 && hy <= 1 && hz >= -1 && hz <= 1) continue;
+      const int hidx = (hx + 3) + 7 * (hy + 3) + 49 * (hz + 3);
+      for (int ch = 0; ch < jchunks; ++ch, ++kk) {
+        const int s = kk % C::kStages, r = kk / C::kStages;
+        if (r > 0 && !tc::mbar_wait(&empty[s], (r - 1) & 1, err)) {
+          ok = false;
+          break;
+        }
+        unsigned char* st = sm + s * C::kStage;
+        tc::mbar_expect_tx(&full[s], stage_tx);
+        last_round[s] = r;
+        tc::tma_load_2d(st, &tmA, &full[s], ch * 32, hidx * MP + mt * kBM);
+        tc::tma_load_5d(st + kTileBytesA, &tmB, &full[s], ch * 32, X0 + dx, Y0 + dy, Z0 + dz, sg);
+        if (NPASS == 3) {
+          tc::tma_load_2d(st + kTileBytesA + kTileBytesB, &tmAlo, &full[s], ch * 32,
+                          hidx * MP + mt * kBM);
+          tc::tma_load_5d(st + 2 * kTileBytesA + kTileBytesB, &tmBlo, &full[s], ch * 32, X0 + dx,
+                          Y0 + dy, Z0 + dz, sg);
+        }
+      }
+    }
+    if (!ok) {  // drain copies still in flight before the CTA leaves
+      for (int s = 0; s < C::kStages; ++s)
+        if (last_round[s] >= 0) {
+          const long long t0 = clock64();
+          while (!tc::mbar_try_wait(&full[s], last_round[s] & 1) &&
+                 clock64() - t0 < tc::kWaitCycles) {
+          }
+        }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t id = tc::idesc(2, kBM, N);
+    int kk = 0;
+    bool ok = true;
+    for (int c = 0; c < 216 && ok; ++c) {
+      const int sg = c & 7, di = c >> 3;
+      const int dx = di % 3 - 1, dy = (di / 3) % 3 - 1, dz = di / 9 - 1;
+      const int hx = px - (sg & 1) - 2 * dx, hy = py - ((sg >> 1) & 1) - 2 * dy,
+                hz = pz - ((sg >> 2) & 1) - 2 * dz;
+      if (hx >= -1 && hx <= 1 && hy >= -1 && hy <= 1 && hz >= -1 && hz <= 1) continue;
+      for (int ch = 0; ch < jchunks; ++ch, ++kk) {
+        const int s = kk % C::kStages, r = kk / C::kStages;
+        if (!tc::mbar_wait(&full[s], r & 1, err)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t st = tc::smem_u32(sm + s * C::kStage);
+        const uint64_t a = tc::desc_sw128(st), b = tc::desc_sw128(st + kTileBytesA);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          // advance 8 tf32 (32 bytes) along K inside the swizzle atom
+          const uint64_t adv = (uint64_t)(k * 32) >> 4;
+          tc::mma_tf32(tmem, a + adv, b + adv, id, (kk | k) != 0);
+          if (NPASS == 3) {
+            const uint64_t alo = tc::desc_sw128(st + kTileBytesA + kTileBytesB);
+            const uint64_t blo = tc::desc_sw128(st + 2 * kTileBytesA + kTileBytesB);
+            tc::mma_tf32(tmem, a + adv, blo + adv, id, 1);
+            tc::mma_tf32(tmem, alo + adv, b + adv, id, 1);
+          }
+        }
+        tc::mma_commit(&empty[s]);
+      }
+    }
+    // always arrive: the barrier then completes only once every MMA issued so
+    // far has finished, so TMEM is never released under a running MMA
+    tc::mma_commit(accb);
+  }
+  __syncwarp();
+  // ---------------- epilogue: TMEM -> FP64 local expansions ----------------
+  bool okacc = tc::mbar_wait(accb, 0, err);
+  if (!okacc) {  // aborted: still let in-flight MMAs drain (time-bounded)
+    const long long t0 = clock64();
+    while (!tc::mbar_try_wait(accb, 0) && clock64() - t0 < tc::kWaitCycles) {
+    }
+  }
+  okacc = okacc && !(*(volatile int*)err & 2);
+  tc::fence_after();
+  if (okacc) {
+    const int i = mt * kBM + warp * 32 + lane;
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      uint32_t r[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = c0 + j;
+        const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
+        if (x < H && y < H && z < H && i < nj) {
+          const int64_t t = ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
+          lc[t * nj + i] += (double)__uint_as_float(r[j]);
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// ---- host side: tensor maps ---------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims,
+              const cuuint64_t* strides, const cuuint32_t* box) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, base, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+template <int NPASS>
+cudaError_t run_level(const fmm_plan_s* P, const Workspace& ws, int l, cudaStream_t st) {
+  using C = Cfg<NPASS>;
+  const PlanDev& pd = P->pd;
+  const int nj = pd.nj, JP = ws.tc_jp, MP = ws.tc_mp;
+  const int nl = 1 << l, H = nl >> 1;
+  const int64_t nbox = (int64_t)nl * nl * nl;
+  const int noff = 343;
+  const double* mpl = ws.mp + ws.lev_off[l] * nj;
+  double* lcl = ws.lc + ws.lev_off[l] * nj;
+  const double* ht = ws.htab + (size_t)(l - 2) * noff * pd.nh;
+  float* blo = NPASS == 3 ? ws.tc_bpar[1] : nullptr;
+  float* tlo = NPASS == 3 ? ws.tc_tmat[1] : nullptr;
+  {
+    const int64_t tot = nbox * JP;
+    const unsigned nb = (unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 64);
+    k_pack_beta<<<nb, 256, 0, st>>>(mpl, l, nj, JP, ws.tc_bpar[0], blo);
+  }
+  k_build_tmat<3><<<dim3(noff, MP / 8), 256, 0, st>>>(pd, ht, MP, JP, ws.tc_tmat[0], tlo);
+  const int BX = std::min(8, H), BY = 4, BZ = 4;
+  CUtensorMap mA, mAlo, mB, mBlo;
+  cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
+  cuuint64_t sA[1] = {(cuuint64_t)JP * 4};
+  cuuint32_t bA[2] = {32, (cuuint32_t)kBM};
+  cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)H, 8};
+  cuuint64_t sB[4] = {(cuuint64_t)JP * 4, (cuuint64_t)JP * 4 * H, (cuuint64_t)JP * 4 * H * H,
+                      (cuuint64_t)JP * 4 * H * H * H};
+  cuuint32_t bB[5] = {32, (cuuint32_t)BX, (cuuint32_t)BY, (cuuint32_t)BZ, 1};
+  if (!make_map(&mA, ws.tc_tmat[0], 2, dA, sA, bA)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, ws.tc_bpar[0], 5, dB, sB, bB)) return cudaErrorInvalidValue;
+  mAlo = mA;
+  mBlo = mB;
+  if (NPASS == 3) {
+    if (!make_map(&mAlo, ws.tc_tmat[1], 2, dA, sA, bA)) return cudaErrorInvalidValue;
+    if (!make_map(&mBlo, ws.tc_bpar[1], 5, dB, sB, bB)) return cudaErrorInvalidValue;
+  }
+  const int ntx = (H + BX - 1) / BX, nty = (H + BY - 1) / BY, ntz = (H + BZ - 1) / BZ;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_m2l_tc<NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    attr = true;
+  }
+  dim3 grid(ntx * nty * ntz, 8, MP / kBM);
+  k_m2l_tc<NPASS><<<grid, kThreads, C::kSmem, st>>>(mA, mAlo, mB, mBlo, l, nj, JP / 32, MP, BX,
+                                                    BY, BZ, ntx, nty, lcl, &ws.geom->flag);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+  const int L = P->desc.levels;
+  if (P->pd.d != 3) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
+  // level 2 (8 target parents) is too small for the tiled kernel
+  cudaError_t e = launch_m2l_simt_levels(P, ws, 2, std::min(2, L), st, nl);
+  if (e != cudaSuccess) return e;
+  const bool split = P->desc.precision == FMM_PREC_TF32X3;
+  for (int l = 3; l <= L; ++l) {
+    e = split ? run_level<3>(P, ws, l, st) : run_level<1>(P, ws, l, st);
+    if (e != cudaSuccess) return e;
+    *nl += 3;
+  }
+  return cudaSuccess;
 }
