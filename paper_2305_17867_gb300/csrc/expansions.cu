@@ -239,98 +239,94 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
 // ---------------------------------------------------------------------------
 // M2M (Sec. 4.3, eqs. (mpole_translated_compressed_coeffs), (define_psi)):
 // for each child, sigma_q = sum_{i <= q, i in j} h^{q-i}/(q-i)! beta_i with
-// h = c_parent - c_child = +-s_child/2 per axis; the children's sigmas are
-// summed, rescaled to the parent's box side (factor 2^{-|q|}) and compressed
-// once with the parent's recurrence (M^T is linear).
+// h = c_parent - c_child = +-s_child/2 per axis.  The multi-binomial shift is
+// a product of 1D Taylor shifts, applied one axis at a time (x, then y on the
+// embedded slabs m_s < c, then the slow axis into every slab); the children's
+// sigmas are summed, rescaled to the parent's side (2^{-|q|}) and compressed
+// once with the parent's recurrence (M^T is linear).  One block per parent;
+// the 2^d children are shifted concurrently.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __restrict__ g, int l,
                                                   const double* __restrict__ mpc,
                                                   double* __restrict__ mpp) {
+  constexpr int NC = 1 << D;
   const int b = blockIdx.x;
   const int p = pd.p, c = pd.c, nfull = pd.nfull, nj = pd.nj;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* beta = reinterpret_cast<double*>(smraw);       // nj
-  double* alpha = beta + nj;                              // nfull
-  double* tab = alpha + nfull;                            // (p+1): (1/2)^e / e!
+  double* bet = reinterpret_cast<double*>(smraw);  // NC * nj
+  double* X = bet + NC * nj;                        // NC * nj
+  double* Y = X + NC * nj;                          // NC * nj  (D == 3)
+  double* sig = Y + NC * nj;                        // nfull
+  double* tab = sig + nfull;                        // 2 (sign) x (p+1): (+-1/2)^e / e!
   int bc[3];
   double cp[3], s;
   box_center<D>(g, l, b, bc, cp, &s);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x <= p) {
     double v = 1.0;
-    for (int e = 0; e <= p; ++e) {
-      tab[e] = v;
-      v *= 0.5 / (double)(e + 1);
-    }
-  }
-  double acc[kMaxT];
-  char4 mt[kMaxT];
-#pragma unroll
-  for (int k = 0; k < kMaxT; ++k) {
-    const int q = threadIdx.x + k * blockDim.x;
-    acc[k] = 0.0;
-    mt[k] = q < nfull ? pd.mi[q] : make_char4(0, 0, 0, 0);
+    for (int e = 1; e <= (int)threadIdx.x; ++e) v *= 0.5 / (double)e;
+    tab[threadIdx.x] = v;                                  // h = +1/2 (child bit 0)
+    tab[(p + 1) + threadIdx.x] = (threadIdx.x & 1) ? -v : v;  // h = -1/2 (child bit 1)
   }
   const int nlc = 1 << (l + 1);
-  for (int ci = 0; ci < (1 << D); ++ci) {
+  for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
+    const int ci = e / nj, q = e % nj;
     int64_t cb = 0;
-    int sg[3];
-    for (int k = D - 1; k >= 0; --k) {
-      const int bit = (ci >> k) & 1;
-      cb = cb * nlc + (2 * bc[k] + bit);
-      sg[k] = bit ? -1 : 1;  // h = c_parent - c_child
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < nj; q += blockDim.x) beta[q] = mpc[(size_t)cb * nj + q];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kMaxT; ++k) {
-      if (threadIdx.x + k * blockDim.x >= nfull) continue;
-      const int q0 = mt[k].x, q1 = mt[k].y, q2 = mt[k].z;
-      const int qs = D == 3 ? q2 : q1;
-      double sum = 0.0;
-      for (int is = 0; is <= min(qs, c - 1); ++is) {
-        const int es = qs - is;
-        const double fs = ((es & 1) && sg[D - 1] < 0 ? -tab[es] : tab[es]);
-        if (D == 3) {
-          for (int i1 = 0; i1 <= q1; ++i1) {
-            const int e1 = q1 - i1;
-            const double f1 = fs * ((e1 & 1) && sg[1] < 0 ? -tab[e1] : tab[e1]);
-            const int rb = pd.frow[is * (p + 1) + i1];
-            double row = 0.0;
-            for (int i0 = 0; i0 <= q0; ++i0) {
-              const int e0 = q0 - i0;
-              row += ((e0 & 1) && sg[0] < 0 ? -tab[e0] : tab[e0]) * beta[rb + i0];
-            }
-            sum += f1 * row;
-          }
-        } else {
-          const int rb = pd.frow[is];
-          double row = 0.0;
-          for (int i0 = 0; i0 <= q0; ++i0) {
-            const int e0 = q0 - i0;
-            row += ((e0 & 1) && sg[0] < 0 ? -tab[e0] : tab[e0]) * beta[rb + i0];
-          }
-          sum += fs * row;
-        }
-      }
-      acc[k] += sum;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < kMaxT; ++k) {
-    const int q = threadIdx.x + k * blockDim.x;
-    if (q < nfull) alpha[q] = ldexp(acc[k], -(int)mt[k].w);
+    for (int k = D - 1; k >= 0; --k) cb = cb * nlc + (2 * bc[k] + ((ci >> k) & 1));
+    bet[e] = mpc[(size_t)cb * nj + q];
   }
   __syncthreads();
-  compress_smem<double>(pd, alpha, s);
-  for (int q = threadIdx.x; q < nj; q += blockDim.x) mpp[(size_t)b * nj + q] = alpha[q];
+  // x shift on the stored slabs: X[q] = sum_{t <= q0} f[t] bet[q - t]
+  for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
+    const int ci = e / nj, q = e % nj;
+    const double* f = tab + (ci & 1) * (p + 1);
+    const int q0 = pd.mi[q].x;
+    double acc = 0.0;
+    for (int t = 0; t <= q0; ++t) acc += f[t] * bet[e - t];
+    X[e] = acc;
+  }
+  __syncthreads();
+  const double* Zin = X;
+  if (D == 3) {
+    // y shift: Y[q0, q1, is] = sum_{t <= q1} f[t] X[q0, q1 - t, is]
+    for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
+      const int ci = e / nj, q = e % nj;
+      const double* f = tab + ((ci >> 1) & 1) * (p + 1);
+      const char4 m = pd.mi[q];
+      const double* Xc = X + ci * nj;
+      double acc = 0.0;
+      for (int t = 0; t <= m.y; ++t) acc += f[t] * Xc[pd.frow[m.z * (p + 1) + m.y - t] + m.x];
+      Y[e] = acc;
+    }
+    __syncthreads();
+    Zin = Y;
+  }
+  // slow-axis shift into every slab, summed over the children, rescaled
+  for (int q = threadIdx.x; q < nfull; q += blockDim.x) {
+    const char4 m = pd.mi[q];
+    const int q0 = m.x, q1 = D == 3 ? m.y : 0, qs = D == 3 ? m.z : m.y;
+    double acc = 0.0;
+    for (int ci = 0; ci < NC; ++ci) {
+      const double* f = tab + ((ci >> (D - 1)) & 1) * (p + 1);
+      const double* Zc = Zin + ci * nj;
+      for (int is = 0; is <= min(qs, c - 1); ++is) {
+        const int src = D == 3 ? pd.frow[is * (p + 1) + q1] + q0 : pd.frow[is] + q0;
+        acc += f[qs - is] * Zc[src];
+      }
+    }
+    sig[q] = ldexp(acc, -(int)m.w);
+  }
+  __syncthreads();
+  compress_smem<double>(pd, sig, s);
+  for (int q = threadIdx.x; q < nj; q += blockDim.x) mpp[(size_t)b * nj + q] = sig[q];
 }
 
 // ---------------------------------------------------------------------------
 // L2L (Sec. 4.2, eq. (l2l-expr), un-normalised): with Dt = M Lt_parent,
 //   Lt_child_i += 2^{-|i|} sum_{q >= i} Dt_q (h/S)^{q-i} / (q-i)!,  i in j,
-// h = c_child - c_parent = +-S/4 per axis (S the parent's side).
+// h = c_child - c_parent = +-S/4 per axis.  Applied as 1D shifts along x
+// (two sign variants), y (four variants) and the slow axis (eight children,
+// stored slabs only); the x and y partial shifts are shared by the children.
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __restrict__ g, int l,
@@ -340,61 +336,64 @@ __global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __rest
   const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
   extern __shared__ __align__(16) unsigned char smraw[];
   double* Dt = reinterpret_cast<double*>(smraw);  // nfull
-  double* tab = Dt + nfull;                        // (1/4)^e / e!
+  double* X = Dt + nfull;                          // 2 * nfull
+  double* Y = X + 2 * nfull;                       // 4 * nfull (D == 3)
+  double* tab = Y + (D == 3 ? 4 * nfull : 0);      // 2 x (p+1): (-+1/4)^e / e!
   int bc[3];
   double cp[3], s;
   box_center<D>(g, l, b, bc, cp, &s);
   for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = lcp[(size_t)b * nj + q];
-  if (threadIdx.x == 0) {
+  if (threadIdx.x <= p) {
     double v = 1.0;
-    for (int e = 0; e <= p; ++e) {
-      tab[e] = v;
-      v *= 0.25 / (double)(e + 1);
-    }
+    for (int e = 1; e <= (int)threadIdx.x; ++e) v *= 0.25 / (double)e;
+    tab[threadIdx.x] = (threadIdx.x & 1) ? -v : v;  // child bit 0: h/S = -1/4
+    tab[(p + 1) + threadIdx.x] = v;                  // child bit 1: h/S = +1/4
   }
   __syncthreads();
   decompress_smem<double>(pd, Dt, s);
+  // x shift: X[v][q] = sum_{t >= 0} g_v[t] Dt[q + t] along the row of q
+  for (int e = threadIdx.x; e < 2 * nfull; e += blockDim.x) {
+    const int v = e / nfull, q = e % nfull;
+    const char4 m = pd.mi[q];
+    const int qs = D == 3 ? m.z : m.y, q1 = D == 3 ? m.y : 0;
+    const int len = p - qs - q1 - m.x + 1;
+    const double* gv = tab + v * (p + 1);
+    double acc = 0.0;
+    for (int t = 0; t < len; ++t) acc += gv[t] * Dt[q + t];
+    X[e] = acc;
+  }
+  __syncthreads();
+  const double* Zin = X;
+  if (D == 3) {
+    for (int e = threadIdx.x; e < 4 * nfull; e += blockDim.x) {
+      const int v = e / nfull, q = e % nfull;  // v = sx + 2 sy
+      const char4 m = pd.mi[q];
+      const double* gv = tab + (v >> 1) * (p + 1);
+      const double* Xv = X + (v & 1) * nfull;
+      double acc = 0.0;
+      for (int t = 0; t <= p - m.z - m.x - m.y; ++t)
+        acc += gv[t] * Xv[pd.frow[m.z * (p + 1) + m.y + t] + m.x];
+      Y[e] = acc;
+    }
+    __syncthreads();
+    Zin = Y;
+  }
+  constexpr int NC = 1 << D;
   const int nlc = 1 << (l + 1);
-  const int nout = (1 << D) * nj;
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    const int ci = o / nj, i = o % nj;
+  for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
+    const int ci = e / nj, i = e % nj;
+    const char4 m = pd.mi[i];
+    const int i0 = m.x, i1 = D == 3 ? m.y : 0, is = D == 3 ? m.z : m.y;
+    const double* gv = tab + ((ci >> (D - 1)) & 1) * (p + 1);
+    const double* Zv = Zin + (ci & (NC / 2 - 1)) * nfull;
+    double acc = 0.0;
+    for (int qs = is; qs <= p - i0 - i1; ++qs) {
+      const int src = D == 3 ? pd.frow[qs * (p + 1) + i1] + i0 : pd.frow[qs] + i0;
+      acc += gv[qs - is] * Zv[src];
+    }
     int64_t cb = 0;
-    int sg[3];
-    for (int k = D - 1; k >= 0; --k) {
-      const int bit = (ci >> k) & 1;
-      cb = cb * nlc + (2 * bc[k] + bit);
-      sg[k] = bit ? 1 : -1;  // h = c_child - c_parent
-    }
-    const char4 mi = pd.mi[i];
-    const int i0 = mi.x, i1 = mi.y, i2 = mi.z;
-    const int is = D == 3 ? i2 : i1;
-    double sum = 0.0;
-    for (int qs = is; qs <= p; ++qs) {
-      const int es = qs - is;
-      const double fs = ((es & 1) && sg[D - 1] < 0 ? -tab[es] : tab[es]);
-      if (D == 3) {
-        for (int q1 = i1; q1 <= p - qs; ++q1) {
-          const int e1 = q1 - i1;
-          const double f1 = fs * ((e1 & 1) && sg[1] < 0 ? -tab[e1] : tab[e1]);
-          const int rb = pd.frow[qs * (p + 1) + q1];
-          double row = 0.0;
-          for (int q0 = i0; q0 <= p - qs - q1; ++q0) {
-            const int e0 = q0 - i0;
-            row += ((e0 & 1) && sg[0] < 0 ? -tab[e0] : tab[e0]) * Dt[rb + q0];
-          }
-          sum += f1 * row;
-        }
-      } else {
-        const int rb = pd.frow[qs];
-        double row = 0.0;
-        for (int q0 = i0; q0 <= p - qs; ++q0) {
-          const int e0 = q0 - i0;
-          row += ((e0 & 1) && sg[0] < 0 ? -tab[e0] : tab[e0]) * Dt[rb + q0];
-        }
-        sum += fs * row;
-      }
-    }
-    lcc[(size_t)cb * nj + i] += ldexp(sum, -(int)mi.w);
+    for (int k = D - 1; k >= 0; --k) cb = cb * nlc + (2 * bc[k] + ((ci >> k) & 1));
+    lcc[(size_t)cb * nj + i] += ldexp(acc, -(int)m.w);
   }
 }
 
@@ -444,7 +443,7 @@ cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
 cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels, d = pd.d;
-  const size_t smem = sizeof(double) * (pd.nj + pd.nfull + pd.p + 1);
+  const size_t smem = sizeof(double) * (3 * (1 << d) * pd.nj + pd.nfull + 2 * (pd.p + 1));
   for (int l = L - 1; l >= 2; --l) {
     const double* mpc = ws.mp + ws.lev_off[l + 1] * pd.nj;
     double* mpp = ws.mp + ws.lev_off[l] * pd.nj;
@@ -463,7 +462,7 @@ cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
 cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels, d = pd.d;
-  const size_t smem = sizeof(double) * (pd.nfull + pd.p + 1);
+  const size_t smem = sizeof(double) * (7 * pd.nfull + 2 * (pd.p + 1));
   for (int l = 2; l < L; ++l) {
     const double* lcp = ws.lc + ws.lev_off[l] * pd.nj;
     double* lcc = ws.lc + ws.lev_off[l + 1] * pd.nj;

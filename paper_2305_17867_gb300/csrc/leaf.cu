@@ -53,7 +53,7 @@ __device__ __forceinline__ void pair_kernel(T r2, T lam, T& v, T& f1) {
   }
 }
 
-template <int K, int D, typename T>
+template <int K, int D, typename T, bool GRAD>
 __global__ void __launch_bounds__(kThreads) k_leaf(
     PlanDev pd, const Geom* __restrict__ g, int L, const double* __restrict__ lc,
     const int* __restrict__ tstart, const double* __restrict__ tx0,
@@ -118,9 +118,11 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
                 v = v * u[0] + coef[base + k];
               }
               far += v * py * pz;
-              gf[0] += dv * py * pz;
-              gf[1] += v * pym * pz;
-              gf[2] += v * py * pzm;
+              if (GRAD) {
+                gf[0] += dv * py * pz;
+                gf[1] += v * pym * pz;
+                gf[2] += v * py * pzm;
+              }
             }
             pym = pym * u[1] + py;
             py *= u[1];
@@ -135,8 +137,10 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
               v = v * u[0] + coef[base + k];
             }
             far += v * pz;
-            gf[0] += dv * pz;
-            gf[1] += v * pzm;
+            if (GRAD) {
+              gf[0] += dv * pz;
+              gf[1] += v * pzm;
+            }
           }
           ++row;
         }
@@ -176,8 +180,10 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
               const T wj = swt[jj];
               nv += wj * v;
               wsum += wj;
-              const T fw = wj * f1;
-              for (int k = 0; k < D; ++k) ng[k] += fw * dxv[k];
+              if (GRAD) {
+                const T fw = wj * f1;
+                for (int k = 0; k < D; ++k) ng[k] += fw * dxv[k];
+              }
             }
           }
         }
@@ -188,10 +194,11 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
       far += __shfl_down_sync(0xffffffffu, far, off, tpt);
       nv += __shfl_down_sync(0xffffffffu, nv, off, tpt);
       wsum += __shfl_down_sync(0xffffffffu, wsum, off, tpt);
-      for (int k = 0; k < D; ++k) {
-        gf[k] += __shfl_down_sync(0xffffffffu, gf[k], off, tpt);
-        ng[k] += __shfl_down_sync(0xffffffffu, ng[k], off, tpt);
-      }
+      if (GRAD)
+        for (int k = 0; k < D; ++k) {
+          gf[k] += __shfl_down_sync(0xffffffffu, gf[k], off, tpt);
+          ng[k] += __shfl_down_sync(0xffffffffu, ng[k], off, tpt);
+        }
     }
     if (valid && lane == 0) {
       double phi_scale, grad_scale;  // near-field units -> physical
@@ -212,25 +219,32 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
       double ph = (double)far + phi_scale * (double)nv;
       if (K == FMM_KERNEL_LAPLACE && D == 2) ph += log(s) * (double)wsum;
       if (phi) phi[orig] = ph;
-      if (grad)
+      if (GRAD && grad)
         for (int k = 0; k < D; ++k)
           grad[(size_t)orig * D + k] = (double)gf[k] * inv_s + grad_scale * (double)ng[k];
     }
   }
 }
 
-template <int K, int D, typename T>
-void leaf_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
-                 cudaStream_t st) {
+template <int K, int D, typename T, bool GRAD>
+void leaf_launch_g(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
+                   cudaStream_t st) {
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels;
   const size_t smem = sizeof(double) * pd.nfull + sizeof(T) * (pd.nfull + 1) +
                       sizeof(T) * (D + 1) * kThreads + 16;
-  set_smem(k_leaf<K, D, T>, smem);
-  k_leaf<K, D, T><<<(unsigned)nbox_at(D, L), kThreads, smem, st>>>(
+  set_smem(k_leaf<K, D, T, GRAD>, smem);
+  k_leaf<K, D, T, GRAD><<<(unsigned)nbox_at(D, L), kThreads, smem, st>>>(
       pd, ws.geom, L, ws.lc + ws.lev_off[L] * pd.nj, ws.tstart, ws.tx[0], ws.tx[1],
       D == 3 ? ws.tx[2] : ws.tx[0], ws.tperm, ws.sstart, ws.sx[0], ws.sx[1],
       D == 3 ? ws.sx[2] : ws.sx[0], ws.sw, phi, grad);
+}
+
+template <int K, int D, typename T>
+void leaf_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
+                 cudaStream_t st) {
+  if (grad) leaf_launch_g<K, D, T, true>(P, ws, phi, grad, st);
+  else leaf_launch_g<K, D, T, false>(P, ws, phi, grad, st);
 }
 
 }  // namespace

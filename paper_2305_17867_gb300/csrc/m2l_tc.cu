@@ -34,7 +34,6 @@ constexpr int kRowBytes = 128;  // one K chunk: 32 fp32
 constexpr int kTileBytesA = kBM * kRowBytes;
 constexpr int kMaxN = 128;
 constexpr int kTileBytesB = kMaxN * kRowBytes;
-constexpr int kThreads = 128;
 
 template <int NPASS>
 struct Cfg {
@@ -102,8 +101,36 @@ __global__ void k_build_tmat(PlanDev pd, const double* __restrict__ htab, int MP
 }
 
 // ---- the contraction --------------------------------------------------------
+// Warp roles: warps 0-3 drain TMEM (TMEM lanes 32w..32w+31 = rows i), warp 4
+// lane 0 issues TMA, warp 5 lane 0 issues MMA.  The tensor cores truncate when
+// they accumulate, so a long K loop in one accumulator drifts; each offset's
+// partial product (|j|/32 K-chunks) therefore goes to one of two TMEM buffers,
+// and the draining warps add it into float registers (round-to-nearest)
+// while the MMA warp fills the other buffer.
+constexpr int kEpiWarps = 4;
+constexpr int kTcThreads = (kEpiWarps + 2) * 32;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// (sigma, delta) decode of combination c = sigma + 8 * delta_index; false if
+// the offset is adjacent (not in the interaction list)
+__device__ __forceinline__ bool combo(int c, int px, int py, int pz, int& sg, int& dx, int& dy,
+                                      int& dz, int& hidx) {
+  sg = c & 7;
+  const int di = c >> 3;
+  dx = di % 3 - 1;
+  dy = (di / 3) % 3 - 1;
+  dz = di / 9 - 1;
+  const int hx = px - (sg & 1) - 2 * dx, hy = py - ((sg >> 1) & 1) - 2 * dy,
+            hz = pz - ((sg >> 2) & 1) - 2 * dz;
+  hidx = (hx + 3) + 7 * (hy + 3) + 49 * (hz + 3);
+  return !(hx >= -1 && hx <= 1 && hy >= -1 && hy <= 1 && hz >= -1 && hz <= 1);
+}
+
 template <int NPASS>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
              const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBlo,
              int l, int nj, int jchunks, int MP, int BX, int BY, int BZ, int ntx, int nty,
@@ -114,15 +141,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::kStages * C::kStage);
   uint64_t* empty = full + C::kStages;
-  uint64_t* accb = empty + C::kStages;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(accb + 1);
+  uint64_t* accf = empty + C::kStages;  // [2] accumulator filled (MMA commit)
+  uint64_t* acce = accf + 2;            // [2] accumulator drained (4 warp arrivals)
+  uint64_t* drainb = acce + 2;          // all MMAs of this CTA finished
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drainb + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pi = blockIdx.y, mt = blockIdx.z;
   const int tile = blockIdx.x;
   const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
   const int X0 = tx * BX, Y0 = ty * BY, Z0 = tz * BZ;
-  const int N = BX * BY * BZ;
+  const int N = BX * BY * BZ;                         // rows the TMA box fills
+  const int Nmma = N < 16 ? 16 : (N + 15) / 16 * 16;  // MMA width; extra columns discarded
   const int nl = 1 << l, H = nl >> 1;
   const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
   const uint32_t bytesA = kTileBytesA, bytesB = (uint32_t)N * kRowBytes;
@@ -133,28 +163,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(accb, 1);
+    for (int bf = 0; bf < 2; ++bf) {
+      tc::mbar_init(&accf[bf], 1);
+      tc::mbar_init(&acce[bf], kEpiWarps);
+    }
+    tc::mbar_init(drainb, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tslot, 128);
+  if (warp == 0) tc::tmem_alloc(tslot, 256);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
 
-  if (warp == 0 && lane == 0) {
+  if (warp == kEpiWarps && lane == 0) {
     // ---------------- TMA producer ----------------
     int kk = 0;
     int last_round[C::kStages];
     for (int s = 0; s < C::kStages; ++s) last_round[s] = -1;
     bool ok = true;
     for (int c = 0; c < 216 && ok; ++c) {
-      const int sg = c & 7, di = c >> 3;
-      const int dx = di % 3 - 1, dy = (di / 3) % 3 - 1, dz = di / 9 - 1;
-      const int hx = px - (sg & 1) - 2 * dx, hy = py - ((sg >> 1) & 1) - 2 * dy,
-                hz = pz - ((sg >> 2) & 1) - 2 * dz;
-      if (hx >= -1 && hx <= 1 && hy >= -1 && hy <= 1 && hz >= -1 && hz <= 1) continue;
-      const int hidx = (hx + 3) + 7 * (hy + 3) + 49 * (hz + 3);
+      int sg, dx, dy, dz, hidx;
+      if (!combo(c, px, py, pz, sg, dx, dy, dz, hidx)) continue;
       for (int ch = 0; ch < jchunks; ++ch, ++kk) {
         const int s = kk % C::kStages, r = kk / C::kStages;
         if (r > 0 && !tc::mbar_wait(&empty[s], (r - 1) & 1, err)) {
@@ -183,17 +213,21 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
     }
-  } else if (warp == 1 && lane == 0) {
+  } else if (warp == kEpiWarps + 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    const uint32_t id = tc::idesc(2, kBM, N);
-    int kk = 0;
+    const uint32_t id = tc::idesc(2, kBM, Nmma);
+    int kk = 0, g = 0;
     bool ok = true;
     for (int c = 0; c < 216 && ok; ++c) {
-      const int sg = c & 7, di = c >> 3;
-      const int dx = di % 3 - 1, dy = (di / 3) % 3 - 1, dz = di / 9 - 1;
-      const int hx = px - (sg & 1) - 2 * dx, hy = py - ((sg >> 1) & 1) - 2 * dy,
-                hz = pz - ((sg >> 2) & 1) - 2 * dz;
-      if (hx >= -1 && hx <= 1 && hy >= -1 && hy <= 1 && hz >= -1 && hz <= 1) continue;
+      int sg, dx, dy, dz, hidx;
+      if (!combo(c, px, py, pz, sg, dx, dy, dz, hidx)) continue;
+      const int bf = g & 1;
+      if (g >= 2 && !tc::mbar_wait(&acce[bf], ((g >> 1) - 1) & 1, err)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(bf * 128);
       for (int ch = 0; ch < jchunks; ++ch, ++kk) {
         const int s = kk % C::kStages, r = kk / C::kStages;
         if (!tc::mbar_wait(&full[s], r & 1, err)) {
@@ -203,54 +237,81 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_after();
         const uint32_t st = tc::smem_u32(sm + s * C::kStage);
         const uint64_t a = tc::desc_sw128(st), b = tc::desc_sw128(st + kTileBytesA);
+        const uint64_t alo = tc::desc_sw128(st + kTileBytesA + kTileBytesB);
+        const uint64_t blo = tc::desc_sw128(st + 2 * kTileBytesA + kTileBytesB);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          // advance 8 tf32 (32 bytes) along K inside the swizzle atom
-          const uint64_t adv = (uint64_t)(k * 32) >> 4;
-          tc::mma_tf32(tmem, a + adv, b + adv, id, (kk | k) != 0);
+          const uint64_t adv = (uint64_t)(k * 32) >> 4;  // 8 tf32 = 32 bytes along K
+          tc::mma_tf32(dacc, a + adv, b + adv, id, (ch | k) != 0);
           if (NPASS == 3) {
-            const uint64_t alo = tc::desc_sw128(st + kTileBytesA + kTileBytesB);
-            const uint64_t blo = tc::desc_sw128(st + 2 * kTileBytesA + kTileBytesB);
-            tc::mma_tf32(tmem, a + adv, blo + adv, id, 1);
-            tc::mma_tf32(tmem, alo + adv, b + adv, id, 1);
+            tc::mma_tf32(dacc, a + adv, blo + adv, id, 1);
+            tc::mma_tf32(dacc, alo + adv, b + adv, id, 1);
           }
         }
         tc::mma_commit(&empty[s]);
       }
+      if (!ok) break;
+      tc::mma_commit(&accf[bf]);
+      ++g;
     }
-    // always arrive: the barrier then completes only once every MMA issued so
-    // far has finished, so TMEM is never released under a running MMA
-    tc::mma_commit(accb);
-  }
-  __syncwarp();
-  // ---------------- epilogue: TMEM -> FP64 local expansions ----------------
-  bool okacc = tc::mbar_wait(accb, 0, err);
-  if (!okacc) {  // aborted: still let in-flight MMAs drain (time-bounded)
-    const long long t0 = clock64();
-    while (!tc::mbar_try_wait(accb, 0) && clock64() - t0 < tc::kWaitCycles) {
+    // the commit arrives once every MMA issued so far has finished; waiting
+    // for it (time-bounded, also on the error path) means TMEM is never freed
+    // under a running MMA
+    tc::mma_commit(drainb);
+    {
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(drainb, 0) && clock64() - t0 < tc::kWaitCycles) {
+      }
     }
-  }
-  okacc = okacc && !(*(volatile int*)err & 2);
-  tc::fence_after();
-  if (okacc) {
-    const int i = mt * kBM + warp * 32 + lane;
-    for (int c0 = 0; c0 < N; c0 += 32) {
-      uint32_t r[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+  } else if (warp < kEpiWarps) {
+    // ---------------- drain TMEM into float registers ----------------
+    float sum[128];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = c0 + j;
-        const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
-        if (x < H && y < H && z < H && i < nj) {
-          const int64_t t = ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
-          lc[t * nj + i] += (double)__uint_as_float(r[j]);
+    for (int j = 0; j < 128; ++j) sum[j] = 0.f;
+    bool ok = true;
+    int g = 0;
+    for (int c = 0; c < 216; ++c) {
+      int sg, dx, dy, dz, hidx;
+      if (!combo(c, px, py, pz, sg, dx, dy, dz, hidx)) continue;
+      const int bf = g & 1;
+      if (!tc::mbar_wait(&accf[bf], (g >> 1) & 1, err)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
+      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bf * 128);
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        if (cc * 32 < N) {
+          uint32_t r[32];
+          tc::tmem_ld32(base + (uint32_t)(cc * 32), r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sum[cc * 32 + j] += __uint_as_float(r[j]);
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[bf]);
+      ++g;
+    }
+    ok = ok && !(*(volatile int*)err & 2);
+    if (ok) {
+      const int i = mt * kBM + warp * 32 + lane;
+#pragma unroll
+      for (int n = 0; n < 128; ++n) {
+        if (n < N) {
+          const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
+          if (x < H && y < H && z < H && i < nj) {
+            const int64_t t = ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
+            lc[t * nj + i] += (double)sum[n];
+          }
         }
       }
     }
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 // ---- host side: tensor maps ---------------------------------------------------
@@ -302,7 +363,7 @@ cudaError_t run_level(const fmm_plan_s* P, const Workspace& ws, int l, cudaStrea
     k_pack_beta<<<nb, 256, 0, st>>>(mpl, l, nj, JP, ws.tc_bpar[0], blo);
   }
   k_build_tmat<3><<<dim3(noff, MP / 8), 256, 0, st>>>(pd, ht, MP, JP, ws.tc_tmat[0], tlo);
-  const int BX = std::min(8, H), BY = 4, BZ = 4;
+  const int BX = std::min(8, H), BY = std::min(4, H), BZ = std::min(4, H);
   CUtensorMap mA, mAlo, mB, mBlo;
   cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
   cuuint64_t sA[1] = {(cuuint64_t)JP * 4};
@@ -326,7 +387,7 @@ cudaError_t run_level(const fmm_plan_s* P, const Workspace& ws, int l, cudaStrea
     attr = true;
   }
   dim3 grid(ntx * nty * ntz, 8, MP / kBM);
-  k_m2l_tc<NPASS><<<grid, kThreads, C::kSmem, st>>>(mA, mAlo, mB, mBlo, l, nj, JP / 32, MP, BX,
+  k_m2l_tc<NPASS><<<grid, kTcThreads, C::kSmem, st>>>(mA, mAlo, mB, mBlo, l, nj, JP / 32, MP, BX,
                                                     BY, BZ, ntx, nty, lcl, &ws.geom->flag);
   return cudaGetLastError();
 }
@@ -336,11 +397,9 @@ cudaError_t run_level(const fmm_plan_s* P, const Workspace& ws, int l, cudaStrea
 cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
   const int L = P->desc.levels;
   if (P->pd.d != 3) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
-  // level 2 (8 target parents) is too small for the tiled kernel
-  cudaError_t e = launch_m2l_simt_levels(P, ws, 2, std::min(2, L), st, nl);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   const bool split = P->desc.precision == FMM_PREC_TF32X3;
-  for (int l = 3; l <= L; ++l) {
+  for (int l = 2; l <= L; ++l) {
     e = split ? run_level<3>(P, ws, l, st) : run_level<1>(P, ws, l, st);
     if (e != cudaSuccess) return e;
     *nl += 3;
