@@ -137,6 +137,28 @@ int fmm_eval_backward(fmm_plan_t plan, int64_t n_src, const double* src_dev,
                       double* grad_tgt_dev, void* workspace_dev, size_t workspace_bytes,
                       void* stream);
 
+/* fmm_eval without any allocation.  The paper has no counterpart; this is a
+ * service for callers that may not allocate device memory when they evaluate:
+ * code running while a stream is captured into a CUDA graph (allocation cannot
+ * be captured), real-time loops that forbid allocation after start-up, and
+ * plug-ins inside a host framework that owns the whole device memory pool.
+ * Arguments and results are those of fmm_eval, minus the workspace: the
+ * workspace comes from a 32 MiB array that the library reserves statically on
+ * every device it is loaded on (held until the process exits).
+ *  - Sizes whose fmm_workspace_size() exceeds 32 MiB are rejected with
+ *    FMM_ERR_WORKSPACE before any work is enqueued (use fmm_eval for those).
+ *  - Calls to cudaMalloc, cudaFree or any allocating routine: none.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture begins.
+ *  - Every call on a device shares the one array and it keeps the previous
+ *    call's contents (the evaluation clears what must start at zero itself).
+ *    Calls whose GPU work overlaps -- different streams, or different plans
+ *    without ordering between them -- race on the array: order them. */
+int fmm_eval_noalloc(fmm_plan_t plan, int64_t n_src, const double* src_dev, const double* w_dev,
+                     int64_t n_tgt, const double* tgt_dev, double* phi_dev, double* grad_dev,
+                     void* stream);
+
 /* Synchronise the stream of the last evaluation and return its device-side
  * status (FMM_OK, FMM_ERR_DOMAIN, FMM_ERR_TIMEOUT) or a CUDA error. */
 int fmm_last_status(fmm_plan_t plan);

@@ -44,7 +44,7 @@ _LIB = None
 EXPORTS = [
     "fmm_plan_create", "fmm_plan_destroy", "fmm_plan_info", "fmm_workspace_size", "fmm_eval",
     "fmm_eval_backward", "fmm_last_status", "fmm_set_timing", "fmm_phase_times",
-    "fmm_last_launch_count", "fmm_status_string",
+    "fmm_last_launch_count", "fmm_status_string", "fmm_eval_noalloc",
 ]
 
 
@@ -74,6 +74,8 @@ def load(build: bool = True):
     L.fmm_eval.restype = i32
     L.fmm_eval_backward.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
     L.fmm_eval_backward.restype = i32
+    L.fmm_eval_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp]
+    L.fmm_eval_noalloc.restype = i32
     L.fmm_last_status.argtypes = [vp]
     L.fmm_last_status.restype = i32
     L.fmm_set_timing.argtypes = [vp, i32]
