@@ -152,9 +152,12 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
     w.tc_jp = (nj + 31) / 32 * 32;
     w.tc_mp = (nj + 127) / 128 * 128;
     const int halves = prec == FMM_PREC_TF32X3 ? 2 : 1;
+    // homogeneous kernels (3D Laplace, biharmonic) share one set of offset
+    // matrices across levels (exact power-of-two scale per level)
+    const int tlev = (P->pd.kernel == FMM_KERNEL_YUKAWA) ? (L - 1) : 1;
     for (int h = 0; h < halves; ++h) {
-      w.tc_bpar[h] = carve<float>(cur, (size_t)nbox_at(3, L) * w.tc_jp);
-      w.tc_tmat[h] = carve<float>(cur, (size_t)343 * w.tc_mp * w.tc_jp);
+      w.tc_bpar[h] = carve<float>(cur, (size_t)off * w.tc_jp);
+      w.tc_tmat[h] = carve<float>(cur, (size_t)tlev * 343 * w.tc_mp * w.tc_jp);
     }
   }
   w.bytes = (size_t)(cur - static_cast<char*>(base));

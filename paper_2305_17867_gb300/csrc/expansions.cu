@@ -236,6 +236,93 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
   for (int q = threadIdx.x; q < nj; q += blockDim.x) mp[(size_t)b * nj + q] = (double)alpha[q];
 }
 
+// P2M, one warp per leaf box (used when N(p) <= 32 * kWarpTerms).  Lane j of
+// a 32-source chunk builds the power table of its source (weight folded into
+// the first axis); lane t then accumulates terms q = t, t+32, ...; the
+// compression sweep runs warp-synchronously.
+constexpr int kWarpTerms = 32;
+constexpr int kP2mWarps = 4;
+
+template <int D, typename T>
+__global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
+    PlanDev pd, const Geom* __restrict__ g, int L, int64_t nleaf, const int* __restrict__ start,
+    const double* __restrict__ x0, const double* __restrict__ x1, const double* __restrict__ x2,
+    const double* __restrict__ w, double* __restrict__ mp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kP2mWarps + warp;
+  if (b >= nleaf) return;
+  const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
+  const int P1 = p + 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const size_t per_warp = align_bytes<T>(sizeof(T) * (32 * D * P1 + nfull));
+  T* pw = reinterpret_cast<T*>(smraw + warp * per_warp);  // [32][D][p+1]
+  T* alpha = pw + 32 * D * P1;                            // [nfull]
+  const int i0 = start[b], i1 = start[b + 1];
+  if (i0 == i1) {
+    for (int q = lane; q < nj; q += 32) mp[(size_t)b * nj + q] = 0.0;
+    return;
+  }
+  int bc[3];
+  double c[3], s;
+  box_center<D>(g, L, b, bc, c, &s);
+  const double inv_s = 1.0 / s;
+  const int nt = (nfull + 31) / 32;
+  T acc[kWarpTerms];
+  int qoff[kWarpTerms];
+#pragma unroll
+  for (int t = 0; t < kWarpTerms; ++t) {
+    acc[t] = 0;
+    const int q = lane + 32 * t;
+    qoff[t] = 0;
+    if (t < nt && q < nfull) {
+      const char4 m = pd.mi[q];
+      qoff[t] = m.x | (m.y << 8) | (m.z << 16);
+    }
+  }
+  const double* xs[3] = {x0, x1, x2};
+  for (int base = i0; base < i1; base += 32) {
+    const int n = min(32, i1 - base);
+    __syncwarp();
+    {
+      T* row = pw + lane * D * P1;
+      if (lane < n) {
+        for (int k = 0; k < D; ++k) {
+          const T u = (T)((c[k] - xs[k][base + lane]) * inv_s);
+          T v = (k == 0) ? (T)w[base + lane] : (T)1;
+          row[k * P1] = v;
+          for (int e = 1; e <= p; ++e) {
+            v *= u;
+            row[k * P1 + e] = v;
+          }
+        }
+      } else {
+        for (int e = 0; e < D * P1; ++e) row[e] = 0;
+      }
+    }
+    __syncwarp();
+    for (int j = 0; j < n; ++j) {
+      const T* r0 = pw + j * D * P1;
+#pragma unroll
+      for (int t = 0; t < kWarpTerms; ++t) {
+        if (t < nt) {
+          const int o = qoff[t];
+          T v = r0[o & 0xff] * r0[P1 + ((o >> 8) & 0xff)];
+          if (D == 3) v *= r0[2 * P1 + (o >> 16)];
+          acc[t] += v;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kWarpTerms; ++t) {
+    const int q = lane + 32 * t;
+    if (t < nt && q < nfull) alpha[q] = acc[t] * (T)pd.inv_fact[q];
+  }
+  __syncwarp();
+  compress_warp<T>(pd, alpha, s, lane);
+  for (int q = lane; q < nj; q += 32) mp[(size_t)b * nj + q] = (double)alpha[q];
+}
+
 // ---------------------------------------------------------------------------
 // M2M (Sec. 4.3, eqs. (mpole_translated_compressed_coeffs), (define_psi)):
 // for each child, sigma_q = sum_{i <= q, i in j} h^{q-i}/(q-i)! beta_i with
@@ -423,6 +510,27 @@ cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   const size_t tsz = f64 ? 8 : 4;
   const size_t smem = align_bytes<double>(tsz * 32 * d * (pd.p + 1)) + tsz * pd.nfull;
   double* mpL = ws.mp + ws.lev_off[L] * pd.nj;
+  if (pd.nfull <= 32 * kWarpTerms) {
+    const size_t tsz2 = f64 ? 8 : 4;
+    const size_t pwb = align_bytes<double>(tsz2 * (32 * d * (pd.p + 1) + pd.nfull));
+    const size_t sm2 = pwb * kP2mWarps;
+    const unsigned nb = (unsigned)((nleaf + kP2mWarps - 1) / kP2mWarps);
+#define P2MW(DD, TT)                                                                         \
+  do {                                                                                       \
+    set_smem(k_p2m_warp<DD, TT>, sm2);                                                       \
+    k_p2m_warp<DD, TT><<<nb, 32 * kP2mWarps, sm2, st>>>(pd, ws.geom, L, nleaf, ws.sstart,    \
+                                                        ws.sx[0], ws.sx[1], ws.sx[2], ws.sw, \
+                                                        mpL);                                \
+  } while (0)
+    if (d == 3) {
+      if (f64) P2MW(3, double); else P2MW(3, float);
+    } else {
+      if (f64) P2MW(2, double); else P2MW(2, float);
+    }
+#undef P2MW
+    ++*nl;
+    return cudaGetLastError();
+  }
 #define P2M_LAUNCH(DD, TT)                                                                  \
   do {                                                                                      \
     set_smem(k_p2m<DD, TT>, smem);                                                          \

@@ -75,3 +75,23 @@ template <typename T>
 __host__ __device__ __forceinline__ size_t align_bytes(size_t n) {
   return (n + 15) / 16 * 16;
 }
+
+// Warp-synchronous version of compress_smem: one warp owns `a`.
+template <typename T>
+__device__ void compress_warp(const PlanDev& pd, T* a, double s, int lane) {
+  const int nt = pd.nterms > 0 ? pd.nterms : 1;
+  T coef[FMM_MAX_TERMS];
+  for (int t = 0; t < pd.nterms; ++t) coef[t] = (T)scaled_coef(pd, t, s);
+  for (int ms = pd.p - 1; ms >= 0; --ms) {
+    const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
+    for (int i = b0 + lane; i < b1; i += 32) {
+      T v = a[i];
+      for (int t = 0; t < pd.nterms; ++t) {
+        const int src = pd.cmp_src[i * nt + t];
+        if (src >= 0) v += coef[t] * a[src];
+      }
+      a[i] = v;
+    }
+    __syncwarp();
+  }
+}

@@ -44,13 +44,22 @@ struct Cfg {
 };
 
 // ---- operand packing ------------------------------------------------------
-// multipoles of level l (lexicographic boxes, FP64, nj per box) ->
-// Bpar[sigma][Tz][Ty][Tx][JP] fp32 (tf32-rounded hi, and lo for the split)
-__global__ void k_pack_beta(const double* __restrict__ mp, int l, int nj, int JP,
+// multipoles of every level l >= 2 (lexicographic boxes, FP64, nj per box) ->
+// Bpar_l[sigma][Tz][Ty][Tx][JP] fp32 (tf32-rounded hi, and lo for the split);
+// blockIdx.y = l - 2, levels stored back to back like the expansions.
+struct LevOff {
+  int64_t o[FMM_MAX_LEVELS + 1];
+};
+
+__global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off, int nj, int JP,
                             float* __restrict__ bhi, float* __restrict__ blo) {
+  const int l = blockIdx.y + 2;
   const int nl = 1 << l, H = nl >> 1;
   const int64_t nbox = (int64_t)nl * nl * nl;
   const int64_t tot = nbox * JP;
+  const double* mpl = mp + lev_off.o[l] * nj;
+  float* bh = bhi + lev_off.o[l] * JP;
+  float* bl = blo ? blo + lev_off.o[l] * JP : nullptr;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(e % JP);
@@ -58,10 +67,10 @@ __global__ void k_pack_beta(const double* __restrict__ mp, int l, int nj, int JP
     const int x = (int)(b % nl), y = (int)((b / nl) % nl), z = (int)(b / ((int64_t)nl * nl));
     const int sg = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
     const int64_t dst = ((((int64_t)sg * H + (z >> 1)) * H + (y >> 1)) * H + (x >> 1)) * JP + q;
-    const double v = q < nj ? mp[b * nj + q] : 0.0;
+    const double v = q < nj ? mpl[b * nj + q] : 0.0;
     const float hi = tc::tf32_rna((float)v);
-    bhi[dst] = hi;
-    if (blo) blo[dst] = tc::tf32_rna((float)(v - (double)hi));
+    bh[dst] = hi;
+    if (bl) bl[dst] = tc::tf32_rna((float)(v - (double)hi));
   }
 }
 
@@ -70,6 +79,9 @@ template <int D>
 __global__ void k_build_tmat(PlanDev pd, const double* __restrict__ htab, int MP, int JP,
                              float* __restrict__ thi, float* __restrict__ tlo) {
   const int o = blockIdx.x;
+  htab += (size_t)blockIdx.z * 343 * pd.nh;
+  thi += (size_t)blockIdx.z * 343 * MP * JP;
+  if (tlo) tlo += (size_t)blockIdx.z * 343 * MP * JP;
   {
     int t = o;
     bool far = false;
@@ -129,12 +141,34 @@ __device__ __forceinline__ bool combo(int c, int px, int py, int pz, int& sg, in
   return !(hx >= -1 && hx <= 1 && hy >= -1 && hy <= 1 && hz >= -1 && hz <= 1);
 }
 
+// One launch covers every level: blocks [first_block, first_block + 8 ntiles)
+// of grid.x belong to level l (block = tile * 8 + pi), grid.y = 128-row block.
+struct TcLevel {
+  CUtensorMap A, Alo, B, Blo;  // offset matrices and parity-split multipoles
+  double* lc;                  // local expansions of the level
+  float scale;                 // exact power of two (shared offset matrices)
+  int l, BX, BY, BZ, ntx, nty, first_block;
+};
+struct TcParams {
+  TcLevel lev[FMM_MAX_LEVELS];
+  int nlev, nj, jchunks, MP;
+  int* err;
+};
+
 template <int NPASS>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_m2l_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmAlo,
-             const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmBlo,
-             int l, int nj, int jchunks, int MP, int BX, int BY, int BZ, int ntx, int nty,
-             double* __restrict__ lc, int* __restrict__ err) {
+    k_m2l_tc(const __grid_constant__ TcParams prm) {
+  int li = 0;
+  while (li + 1 < prm.nlev && (int)blockIdx.x >= prm.lev[li + 1].first_block) ++li;
+  const TcLevel& LV = prm.lev[li];
+  const CUtensorMap* tmA = &LV.A;
+  const CUtensorMap* tmAlo = &LV.Alo;
+  const CUtensorMap* tmB = &LV.B;
+  const CUtensorMap* tmBlo = &LV.Blo;
+  const int l = LV.l, nj = prm.nj, jchunks = prm.jchunks, MP = prm.MP;
+  const int BX = LV.BX, BY = LV.BY, BZ = LV.BZ, ntx = LV.ntx, nty = LV.nty;
+  double* __restrict__ lc = LV.lc;
+  int* __restrict__ err = prm.err;
   using C = Cfg<NPASS>;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
@@ -147,8 +181,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drainb + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int pi = blockIdx.y, mt = blockIdx.z;
-  const int tile = blockIdx.x;
+  const int lb = (int)blockIdx.x - LV.first_block;
+  const int pi = lb & 7, mt = blockIdx.y;
+  const int tile = lb >> 3;
   const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
   const int X0 = tx * BX, Y0 = ty * BY, Z0 = tz * BZ;
   const int N = BX * BY * BZ;                         // rows the TMA box fills
@@ -194,12 +229,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         unsigned char* st = sm + s * C::kStage;
         tc::mbar_expect_tx(&full[s], stage_tx);
         last_round[s] = r;
-        tc::tma_load_2d(st, &tmA, &full[s], ch * 32, hidx * MP + mt * kBM);
-        tc::tma_load_5d(st + kTileBytesA, &tmB, &full[s], ch * 32, X0 + dx, Y0 + dy, Z0 + dz, sg);
+        tc::tma_load_2d(st, tmA, &full[s], ch * 32, hidx * MP + mt * kBM);
+        tc::tma_load_5d(st + kTileBytesA, tmB, &full[s], ch * 32, X0 + dx, Y0 + dy, Z0 + dz, sg);
         if (NPASS == 3) {
-          tc::tma_load_2d(st + kTileBytesA + kTileBytesB, &tmAlo, &full[s], ch * 32,
+          tc::tma_load_2d(st + kTileBytesA + kTileBytesB, tmAlo, &full[s], ch * 32,
                           hidx * MP + mt * kBM);
-          tc::tma_load_5d(st + 2 * kTileBytesA + kTileBytesB, &tmBlo, &full[s], ch * 32, X0 + dx,
+          tc::tma_load_5d(st + 2 * kTileBytesA + kTileBytesB, tmBlo, &full[s], ch * 32, X0 + dx,
                           Y0 + dy, Z0 + dz, sg);
         }
       }
@@ -303,7 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
           if (x < H && y < H && z < H && i < nj) {
             const int64_t t = ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
-            lc[t * nj + i] += (double)sum[n];
+            lc[t * nj + i] += (double)(sum[n] * LV.scale);
           }
         }
       }
@@ -345,50 +380,73 @@ bool make_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims,
 }
 
 template <int NPASS>
-cudaError_t run_level(const fmm_plan_s* P, const Workspace& ws, int l, cudaStream_t st) {
+cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st) {
   using C = Cfg<NPASS>;
   const PlanDev& pd = P->pd;
+  const int L = P->desc.levels;
   const int nj = pd.nj, JP = ws.tc_jp, MP = ws.tc_mp;
-  const int nl = 1 << l, H = nl >> 1;
-  const int64_t nbox = (int64_t)nl * nl * nl;
   const int noff = 343;
-  const double* mpl = ws.mp + ws.lev_off[l] * nj;
-  double* lcl = ws.lc + ws.lev_off[l] * nj;
-  const double* ht = ws.htab + (size_t)(l - 2) * noff * pd.nh;
+  const bool shared_t = pd.kernel != FMM_KERNEL_YUKAWA;  // homogeneous G
+  const int tlev = shared_t ? 1 : (L - 1);
   float* blo = NPASS == 3 ? ws.tc_bpar[1] : nullptr;
   float* tlo = NPASS == 3 ? ws.tc_tmat[1] : nullptr;
-  {
-    const int64_t tot = nbox * JP;
-    const unsigned nb = (unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 64);
-    k_pack_beta<<<nb, 256, 0, st>>>(mpl, l, nj, JP, ws.tc_bpar[0], blo);
+  LevOff lo;
+  for (int l = 0; l <= FMM_MAX_LEVELS; ++l) lo.o[l] = l <= L + 1 ? ws.lev_off[l] : 0;
+  k_pack_beta<<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, ws.tc_bpar[0], blo);
+  k_build_tmat<3><<<dim3(noff, MP / 8, tlev), 256, 0, st>>>(pd, ws.htab, MP, JP, ws.tc_tmat[0],
+                                                            tlo);
+  TcParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.nj = nj;
+  prm.jchunks = JP / 32;
+  prm.MP = MP;
+  prm.err = &ws.geom->flag;
+  int nb = 0;
+  // largest level first: its tiles start earliest
+  for (int l = L; l >= 2; --l) {
+    TcLevel& v = prm.lev[prm.nlev++];
+    const int nl = 1 << l, H = nl >> 1;
+    v.l = l;
+    v.BX = std::min(8, H);
+    v.BY = std::min(4, H);
+    v.BZ = std::min(4, H);
+    v.ntx = (H + v.BX - 1) / v.BX;
+    v.nty = (H + v.BY - 1) / v.BY;
+    const int ntz = (H + v.BZ - 1) / v.BZ;
+    v.first_block = nb;
+    nb += v.ntx * v.nty * ntz * 8;
+    v.lc = ws.lc + ws.lev_off[l] * nj;
+    const int ti = shared_t ? 0 : l - 2;
+    float* th = ws.tc_tmat[0] + (size_t)ti * noff * MP * JP;
+    float* bh = ws.tc_bpar[0] + ws.lev_off[l] * JP;
+    v.scale = 1.0f;
+    if (shared_t) {  // Ht_l = Ht_2 * (s_2/s_l)^{-deg}: deg -1 (Laplace), +1 (biharmonic)
+      const int k = l - 2;
+      v.scale = pd.kernel == FMM_KERNEL_LAPLACE ? std::ldexp(1.0f, k) : std::ldexp(1.0f, -k);
+    }
+    cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
+    cuuint64_t sA[1] = {(cuuint64_t)JP * 4};
+    cuuint32_t bA[2] = {32, (cuuint32_t)kBM};
+    cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)H, 8};
+    cuuint64_t sB[4] = {(cuuint64_t)JP * 4, (cuuint64_t)JP * 4 * H, (cuuint64_t)JP * 4 * H * H,
+                        (cuuint64_t)JP * 4 * H * H * H};
+    cuuint32_t bB[5] = {32, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ, 1};
+    if (!make_map(&v.A, th, 2, dA, sA, bA)) return cudaErrorInvalidValue;
+    if (!make_map(&v.B, bh, 5, dB, sB, bB)) return cudaErrorInvalidValue;
+    v.Alo = v.A;
+    v.Blo = v.B;
+    if (NPASS == 3) {
+      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA))
+        return cudaErrorInvalidValue;
+      if (!make_map(&v.Blo, blo + ws.lev_off[l] * JP, 5, dB, sB, bB)) return cudaErrorInvalidValue;
+    }
   }
-  k_build_tmat<3><<<dim3(noff, MP / 8), 256, 0, st>>>(pd, ht, MP, JP, ws.tc_tmat[0], tlo);
-  const int BX = std::min(8, H), BY = std::min(4, H), BZ = std::min(4, H);
-  CUtensorMap mA, mAlo, mB, mBlo;
-  cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
-  cuuint64_t sA[1] = {(cuuint64_t)JP * 4};
-  cuuint32_t bA[2] = {32, (cuuint32_t)kBM};
-  cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)H, 8};
-  cuuint64_t sB[4] = {(cuuint64_t)JP * 4, (cuuint64_t)JP * 4 * H, (cuuint64_t)JP * 4 * H * H,
-                      (cuuint64_t)JP * 4 * H * H * H};
-  cuuint32_t bB[5] = {32, (cuuint32_t)BX, (cuuint32_t)BY, (cuuint32_t)BZ, 1};
-  if (!make_map(&mA, ws.tc_tmat[0], 2, dA, sA, bA)) return cudaErrorInvalidValue;
-  if (!make_map(&mB, ws.tc_bpar[0], 5, dB, sB, bB)) return cudaErrorInvalidValue;
-  mAlo = mA;
-  mBlo = mB;
-  if (NPASS == 3) {
-    if (!make_map(&mAlo, ws.tc_tmat[1], 2, dA, sA, bA)) return cudaErrorInvalidValue;
-    if (!make_map(&mBlo, ws.tc_bpar[1], 5, dB, sB, bB)) return cudaErrorInvalidValue;
-  }
-  const int ntx = (H + BX - 1) / BX, nty = (H + BY - 1) / BY, ntz = (H + BZ - 1) / BZ;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_m2l_tc<NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     attr = true;
   }
-  dim3 grid(ntx * nty * ntz, 8, MP / kBM);
-  k_m2l_tc<NPASS><<<grid, kTcThreads, C::kSmem, st>>>(mA, mAlo, mB, mBlo, l, nj, JP / 32, MP, BX,
-                                                    BY, BZ, ntx, nty, lcl, &ws.geom->flag);
+  k_m2l_tc<NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
   return cudaGetLastError();
 }
 
@@ -397,12 +455,8 @@ cudaError_t run_level(const fmm_plan_s* P, const Workspace& ws, int l, cudaStrea
 cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
   const int L = P->desc.levels;
   if (P->pd.d != 3) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
-  cudaError_t e = cudaSuccess;
   const bool split = P->desc.precision == FMM_PREC_TF32X3;
-  for (int l = 2; l <= L; ++l) {
-    e = split ? run_level<3>(P, ws, l, st) : run_level<1>(P, ws, l, st);
-    if (e != cudaSuccess) return e;
-    *nl += 3;
-  }
-  return cudaSuccess;
+  const cudaError_t e = split ? run_all_levels<3>(P, ws, st) : run_all_levels<1>(P, ws, st);
+  *nl += 3;
+  return e;
 }
