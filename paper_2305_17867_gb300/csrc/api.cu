@@ -148,6 +148,11 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
   w.nbbox_blocks = (int)std::min<int64_t>(1024, (std::max(n_src, n_tgt) + 255) / 256 + 1);
   w.bbox = carve<double>(cur, (size_t)2 * 3 * 2 * w.nbbox_blocks);
   const int prec = P->desc.precision;
+  if (d == 3 && prec != FMM_PREC_FP64) {
+    w.sxr = carve<float4>(cur, std::max<int64_t>(n_src, 1));
+    w.txr = carve<float4>(cur, std::max<int64_t>(n_tgt, 1));
+    w.lcoef = carve<float>(cur, (size_t)nleaf * P->pd.nfull);
+  }
   if (d == 3 && (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3)) {
     w.tc_jp = (nj + 31) / 32 * 32;
     w.tc_mp = (nj + 127) / 128 * 128;

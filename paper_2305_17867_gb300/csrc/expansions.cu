@@ -170,6 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
                                                   const double* __restrict__ x1,
                                                   const double* __restrict__ x2,
                                                   const double* __restrict__ w,
+                                                  const float4* __restrict__ rel,
                                                   double* __restrict__ mp) {
   constexpr int CH = 32;
   const int b = blockIdx.x;
@@ -202,8 +203,15 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
       const int j = threadIdx.x / D, k = threadIdx.x % D;
       T* row = pw + (j * D + k) * (p + 1);
       if (j < n) {
-        const T u = (T)((c[k] - xs[k][base + j]) * inv_s);
-        T v = (k == 0) ? (T)w[base + j] : (T)1;
+        T u, v;
+        if (rel) {  // (c - y)/s = -(y - c)/s from the box-relative copy
+          const float4 r = rel[base + j];
+          u = (T)(-(k == 0 ? r.x : (k == 1 ? r.y : r.z)));
+          v = (k == 0) ? (T)r.w : (T)1;
+        } else {
+          u = (T)((c[k] - xs[k][base + j]) * inv_s);
+          v = (k == 0) ? (T)w[base + j] : (T)1;
+        }
         row[0] = v;
         for (int e = 1; e <= p; ++e) {
           v *= u;
@@ -243,11 +251,11 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
 constexpr int kWarpTerms = 32;
 constexpr int kP2mWarps = 4;
 
-template <int D, typename T>
+template <int D, typename T, int NT>
 __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
     PlanDev pd, const Geom* __restrict__ g, int L, int64_t nleaf, const int* __restrict__ start,
     const double* __restrict__ x0, const double* __restrict__ x1, const double* __restrict__ x2,
-    const double* __restrict__ w, double* __restrict__ mp) {
+    const double* __restrict__ w, const float4* __restrict__ rel, double* __restrict__ mp) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t b = (int64_t)blockIdx.x * kP2mWarps + warp;
   if (b >= nleaf) return;
@@ -267,10 +275,10 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
   box_center<D>(g, L, b, bc, c, &s);
   const double inv_s = 1.0 / s;
   const int nt = (nfull + 31) / 32;
-  T acc[kWarpTerms];
-  int qoff[kWarpTerms];
+  T acc[NT];
+  int qoff[NT];
 #pragma unroll
-  for (int t = 0; t < kWarpTerms; ++t) {
+  for (int t = 0; t < NT; ++t) {
     acc[t] = 0;
     const int q = lane + 32 * t;
     qoff[t] = 0;
@@ -286,9 +294,17 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
     {
       T* row = pw + lane * D * P1;
       if (lane < n) {
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (rel) r = rel[base + lane];
         for (int k = 0; k < D; ++k) {
-          const T u = (T)((c[k] - xs[k][base + lane]) * inv_s);
-          T v = (k == 0) ? (T)w[base + lane] : (T)1;
+          T u, v;
+          if (rel) {  // (c - y)/s = -(y - c)/s from the box-relative copy
+            u = (T)(-(k == 0 ? r.x : (k == 1 ? r.y : r.z)));
+            v = (k == 0) ? (T)r.w : (T)1;
+          } else {
+            u = (T)((c[k] - xs[k][base + lane]) * inv_s);
+            v = (k == 0) ? (T)w[base + lane] : (T)1;
+          }
           row[k * P1] = v;
           for (int e = 1; e <= p; ++e) {
             v *= u;
@@ -303,7 +319,7 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
     for (int j = 0; j < n; ++j) {
       const T* r0 = pw + j * D * P1;
 #pragma unroll
-      for (int t = 0; t < kWarpTerms; ++t) {
+      for (int t = 0; t < NT; ++t) {
         if (t < nt) {
           const int o = qoff[t];
           T v = r0[o & 0xff] * r0[P1 + ((o >> 8) & 0xff)];
@@ -314,7 +330,7 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
     }
   }
 #pragma unroll
-  for (int t = 0; t < kWarpTerms; ++t) {
+  for (int t = 0; t < NT; ++t) {
     const int q = lane + 32 * t;
     if (t < nt && q < nfull) alpha[q] = acc[t] * (T)pd.inv_fact[q];
   }
@@ -515,12 +531,19 @@ cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
     const size_t pwb = align_bytes<double>(tsz2 * (32 * d * (pd.p + 1) + pd.nfull));
     const size_t sm2 = pwb * kP2mWarps;
     const unsigned nb = (unsigned)((nleaf + kP2mWarps - 1) / kP2mWarps);
-#define P2MW(DD, TT)                                                                         \
-  do {                                                                                       \
-    set_smem(k_p2m_warp<DD, TT>, sm2);                                                       \
-    k_p2m_warp<DD, TT><<<nb, 32 * kP2mWarps, sm2, st>>>(pd, ws.geom, L, nleaf, ws.sstart,    \
-                                                        ws.sx[0], ws.sx[1], ws.sx[2], ws.sw, \
-                                                        mpL);                                \
+    const int ntl = (pd.nfull + 31) / 32;
+#define P2MW_NT(DD, TT, NTT)                                                                \
+  do {                                                                                      \
+    set_smem(k_p2m_warp<DD, TT, NTT>, sm2);                                                 \
+    k_p2m_warp<DD, TT, NTT><<<nb, 32 * kP2mWarps, sm2, st>>>(                               \
+        pd, ws.geom, L, nleaf, ws.sstart, ws.sx[0], ws.sx[1], ws.sx[2], ws.sw, ws.sxr, mpL); \
+  } while (0)
+#define P2MW(DD, TT)                                                                        \
+  do {                                                                                      \
+    if (ntl <= 4) P2MW_NT(DD, TT, 4);                                                       \
+    else if (ntl <= 10) P2MW_NT(DD, TT, 10);                                                \
+    else if (ntl <= 16) P2MW_NT(DD, TT, 16);                                                \
+    else P2MW_NT(DD, TT, 32);                                                               \
   } while (0)
     if (d == 3) {
       if (f64) P2MW(3, double); else P2MW(3, float);
@@ -528,6 +551,7 @@ cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
       if (f64) P2MW(2, double); else P2MW(2, float);
     }
 #undef P2MW
+#undef P2MW_NT
     ++*nl;
     return cudaGetLastError();
   }
@@ -536,7 +560,7 @@ cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
     set_smem(k_p2m<DD, TT>, smem);                                                          \
     k_p2m<DD, TT><<<(unsigned)nleaf, kThreads, smem, st>>>(pd, ws.geom, L, ws.sstart,       \
                                                            ws.sx[0], ws.sx[1], ws.sx[2],    \
-                                                           ws.sw, mpL);                     \
+                                                           ws.sw, ws.sxr, mpL);             \
   } while (0)
   if (d == 3) {
     if (f64) P2M_LAUNCH(3, double); else P2M_LAUNCH(3, float);

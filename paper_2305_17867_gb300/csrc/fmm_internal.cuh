@@ -101,6 +101,11 @@ struct Workspace {
   int tc_mp;        // |j| padded to a multiple of 128 (M)
   float* tc_bpar[2];
   float* tc_tmat[2];
+  // FP32 leaf path: box-relative coordinates (x - c_own)/s and weight, and the
+  // decompressed far-field coefficients M Lt / m! of every leaf
+  float4* sxr;
+  float4* txr;
+  float* lcoef;
   size_t bytes;
 };
 

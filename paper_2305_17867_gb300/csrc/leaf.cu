@@ -240,6 +240,265 @@ void leaf_launch_g(const fmm_plan_s* P, const Workspace& ws, double* phi, double
       D == 3 ? ws.sx[2] : ws.sx[0], ws.sw, phi, grad);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 leaf path (d = 3).
+//
+// The gather of the tree build gives every sorted point float (x - c_own)/s
+// and its weight, c_own the centre of its own leaf.
+// k_leaf_coef: one warp per leaf decompresses Lt (FP64) and stores Dt/m! as
+// float, so the evaluation kernel reads ready coefficients.
+// k_leaf_fast: one block of four warps per target leaf; lane = target, warp w
+// takes every fourth source and every fourth polynomial row, so a source is a
+// single broadcast float4 read per warp; partial sums meet in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kCoefWarps = 4;
+
+__global__ void __launch_bounds__(32 * kCoefWarps) k_leaf_coef(PlanDev pd, const Geom* __restrict__ g,
+                                                               int L, int64_t nleaf,
+                                                               const double* __restrict__ lc,
+                                                               float* __restrict__ coef) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kCoefWarps + warp;
+  if (b >= nleaf) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* Dt = reinterpret_cast<double*>(smraw) + (size_t)warp * pd.nfull;
+  const double s = __ddiv_rn(g->size, (double)(1 << L));
+  const int nt = pd.nterms > 0 ? pd.nterms : 1;
+  double cf[FMM_MAX_TERMS];
+  for (int t = 0; t < pd.nterms; ++t) cf[t] = scaled_coef(pd, t, s);
+  for (int q = lane; q < pd.nj; q += 32) Dt[q] = lc[(size_t)b * pd.nj + q];
+  __syncwarp();
+  for (int ms = pd.c; ms <= pd.p; ++ms) {
+    const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
+    for (int i = b0 + lane; i < b1; i += 32) {
+      double v = 0.0;
+      for (int t = 0; t < pd.nterms; ++t) v += cf[t] * Dt[pd.rec_src[i * nt + t]];
+      Dt[i] = v;
+    }
+    __syncwarp();
+  }
+  for (int q = lane; q < pd.nfull; q += 32)
+    coef[(size_t)b * pd.nfull + q] = (float)(Dt[q] * pd.inv_fact[q]);
+}
+
+constexpr int kFastWarps = 4;   // target leaves per block (one warp each)
+constexpr int kStageSrc = 256;  // staged sources per warp and chunk
+
+// Near-field pair in box units without a branch: the x == y pair (r2 == 0)
+// contributes nothing.  Returns G's scaled value and d G / (r dr) factor.
+__device__ __forceinline__ float rsqrt_fast(float x) {  // hardware approximation, ~2^-23
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float exp_fast(float x) {  // 2^(x log2 e) on the SFU
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x * 1.4426950408889634f));
+  return y;
+}
+
+template <int K>
+__device__ __forceinline__ void pair_masked(float r2, float lam, float& v, float& f1) {
+  const bool ok = r2 > 0.f;
+  const float ri = ok ? rsqrt_fast(r2) : 0.f;
+  if (K == FMM_KERNEL_LAPLACE) {
+    v = ri;
+    f1 = -ri * ri * ri;
+  } else if (K == FMM_KERNEL_YUKAWA) {
+    const float r = r2 * ri;
+    const float e = ok ? exp_fast(-lam * r) : 0.f;
+    v = e * ri;
+    f1 = e * (-lam * ri * ri - ri * ri * ri);
+  } else {
+    v = r2 * ri;
+    f1 = ri;
+  }
+}
+
+template <int K, bool GRAD>
+__global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
+    PlanDev pd, const Geom* __restrict__ g, int L, int64_t nleaf, const float* __restrict__ coef,
+    const int* __restrict__ tstart, const float4* __restrict__ txr, const int* __restrict__ tperm,
+    const int* __restrict__ sstart, const float4* __restrict__ sxr, double* __restrict__ phi,
+    double* __restrict__ grad) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kFastWarps + warp;
+  __shared__ float4 stage[kFastWarps][kStageSrc];
+  if (b >= nleaf) return;
+  const int t0 = tstart[b], t1 = tstart[b + 1];
+  if (t0 == t1) return;
+  float4* src = stage[warp];
+  const int p = pd.p, nl = 1 << L;
+  int bc[3];
+  {
+    int64_t t = b;
+    for (int k = 0; k < 3; ++k) {
+      bc[k] = (int)(t % nl);
+      t /= nl;
+    }
+  }
+  const double s = __ddiv_rn(g->size, (double)nl);
+  const float lam = (float)(pd.lam * s);
+  const float* cb = coef + (size_t)b * pd.nfull;
+  double phi_scale, grad_scale;
+  if (K == FMM_KERNEL_LAPLACE) {
+    phi_scale = 1.0 / (4.0 * 3.14159265358979323846 * s);
+    grad_scale = phi_scale / s;
+  } else if (K == FMM_KERNEL_YUKAWA) {
+    phi_scale = 1.0 / s;
+    grad_scale = 1.0 / (s * s);
+  } else {
+    phi_scale = s;
+    grad_scale = 1.0;
+  }
+  // lanes own targets tb + lane and tb + 32 + lane (up to 64 per sweep)
+  for (int tb = t0; tb < t1; tb += 64) {
+    const int ta = tb + lane, tb2 = tb + 32 + lane;
+    const bool va = ta < t1, vb = tb2 < t1;
+    const bool two = (t1 - tb) > 32;  // warp-uniform
+    float ua[3] = {0.f, 0.f, 0.f}, ub[3] = {0.f, 0.f, 0.f};
+    if (va) {
+      const float4 q = txr[ta];
+      ua[0] = q.x;
+      ua[1] = q.y;
+      ua[2] = q.z;
+    }
+    if (vb) {
+      const float4 q = txr[tb2];
+      ub[0] = q.x;
+      ub[1] = q.y;
+      ub[2] = q.z;
+    }
+    float na = 0.f, nb = 0.f, ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
+    for (int rr = 0; rr < 9; ++rr) {
+      const int dy = rr % 3 - 1, dz = rr / 3 - 1;
+      const int by = bc[1] + dy, bz = bc[2] + dz;
+      if (by < 0 || by >= nl || bz < 0 || bz >= nl) continue;
+      const int bx0 = max(bc[0] - 1, 0), bx1 = min(bc[0] + 1, nl - 1);
+      const int64_t rowb = ((int64_t)bz * nl + by) * nl;
+      const int j0 = sstart[rowb + bx0], j1 = sstart[rowb + bx1 + 1];
+      const int e1 = sstart[rowb + bx0 + 1], e2 = sstart[rowb + min(bx0 + 2, bx1 + 1)];
+      for (int jb = j0; jb < j1; jb += kStageSrc) {
+        const int n = min(kStageSrc, j1 - jb);
+        __syncwarp();
+        for (int q = lane; q < n; q += 32) {
+          const int j = jb + q;
+          float4 v = sxr[j];
+          const int bx = bx0 + (j >= e1) + (j >= e2);
+          v.x += (float)(bx - bc[0]);
+          v.y += (float)dy;
+          v.z += (float)dz;
+          src[q] = v;
+        }
+        __syncwarp();
+        if (!two) {
+#pragma unroll 4
+          for (int q = 0; q < n; ++q) {
+            const float4 v = src[q];
+            const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
+            float pv, f1;
+            pair_masked<K>(dx * dx + dyv * dyv + dzv * dzv, lam, pv, f1);
+            na += v.w * pv;
+            if (GRAD) {
+              const float fw = v.w * f1;
+              ga[0] += fw * dx;
+              ga[1] += fw * dyv;
+              ga[2] += fw * dzv;
+            }
+          }
+        } else {
+#pragma unroll 2
+          for (int q = 0; q < n; ++q) {
+            const float4 v = src[q];
+            const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
+            const float ex = ub[0] - v.x, eyv = ub[1] - v.y, ezv = ub[2] - v.z;
+            float pv, f1, pw, f2;
+            pair_masked<K>(dx * dx + dyv * dyv + dzv * dzv, lam, pv, f1);
+            pair_masked<K>(ex * ex + eyv * eyv + ezv * ezv, lam, pw, f2);
+            na += v.w * pv;
+            nb += v.w * pw;
+            if (GRAD) {
+              const float fa = v.w * f1, fb = v.w * f2;
+              ga[0] += fa * dx;
+              ga[1] += fa * dyv;
+              ga[2] += fa * dzv;
+              gb[0] += fb * ex;
+              gb[1] += fb * eyv;
+              gb[2] += fb * ezv;
+            }
+          }
+        }
+      }
+    }
+    // far field for both target slots, each lane on its own targets
+    for (int slot = 0; slot < (two ? 2 : 1); ++slot) {
+      const bool valid = slot == 0 ? va : vb;
+      const float u0 = slot == 0 ? ua[0] : ub[0];
+      const float u1 = slot == 0 ? ua[1] : ub[1];
+      const float u2 = slot == 0 ? ua[2] : ub[2];
+      float far = 0.f, gf[3] = {0.f, 0.f, 0.f};
+      float pz = 1.f, pzm = 0.f;
+      for (int ms = 0; ms <= p; ++ms) {
+        float py = 1.f, pym = 0.f;
+        for (int m1 = 0; m1 <= p - ms; ++m1) {
+          const int base = pd.frow[ms * (p + 1) + m1];
+          const int len = p - ms - m1 + 1;
+          float v = cb[base + len - 1], dv = 0.f;
+          for (int k = len - 2; k >= 0; --k) {
+            if (GRAD) dv = dv * u0 + v;
+            v = v * u0 + cb[base + k];
+          }
+          far += v * py * pz;
+          if (GRAD) {
+            gf[0] += dv * py * pz;
+            gf[1] += v * pym * pz;
+            gf[2] += v * py * pzm;
+          }
+          pym = pym * u1 + py;
+          py *= u1;
+        }
+        pzm = pzm * u2 + pz;
+        pz *= u2;
+      }
+      if (valid) {
+        const int t = slot == 0 ? ta : tb2;
+        const int orig = tperm[t];
+        const float nv = slot == 0 ? na : nb;
+        if (phi) phi[orig] = (double)far + phi_scale * (double)nv;
+        if (GRAD && grad) {
+          const float gn0 = slot == 0 ? ga[0] : gb[0], gn1 = slot == 0 ? ga[1] : gb[1],
+                      gn2 = slot == 0 ? ga[2] : gb[2];
+          grad[(size_t)orig * 3 + 0] = (double)gf[0] / s + grad_scale * (double)gn0;
+          grad[(size_t)orig * 3 + 1] = (double)gf[1] / s + grad_scale * (double)gn1;
+          grad[(size_t)orig * 3 + 2] = (double)gf[2] / s + grad_scale * (double)gn2;
+        }
+      }
+    }
+  }
+}
+
+template <int K>
+void leaf_fast_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
+                      cudaStream_t st) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels;
+  const int64_t nleaf = nbox_at(3, L);
+  const size_t sm = sizeof(double) * pd.nfull * kCoefWarps;
+  set_smem(k_leaf_coef, sm);
+  k_leaf_coef<<<(unsigned)((nleaf + kCoefWarps - 1) / kCoefWarps), 32 * kCoefWarps, sm, st>>>(
+      pd, ws.geom, L, nleaf, ws.lc + ws.lev_off[L] * pd.nj, ws.lcoef);
+  const unsigned nbk = (unsigned)((nleaf + kFastWarps - 1) / kFastWarps);
+  if (grad)
+    k_leaf_fast<K, true><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, L, nleaf, ws.lcoef,
+                                                         ws.tstart, ws.txr, ws.tperm, ws.sstart,
+                                                         ws.sxr, phi, grad);
+  else
+    k_leaf_fast<K, false><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, L, nleaf, ws.lcoef,
+                                                          ws.tstart, ws.txr, ws.tperm, ws.sstart,
+                                                          ws.sxr, phi, grad);
+}
+
 template <int K, int D, typename T>
 void leaf_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
                  cudaStream_t st) {
@@ -253,6 +512,13 @@ cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* p
                              cudaStream_t st, int* nl) {
   const bool f64 = P->desc.precision == FMM_PREC_FP64;
   const int k = P->pd.kernel, d = P->pd.d;
+  if (!f64 && d == 3) {
+    if (k == FMM_KERNEL_LAPLACE) leaf_fast_launch<FMM_KERNEL_LAPLACE>(P, ws, phi, grad, st);
+    else if (k == FMM_KERNEL_YUKAWA) leaf_fast_launch<FMM_KERNEL_YUKAWA>(P, ws, phi, grad, st);
+    else leaf_fast_launch<FMM_KERNEL_BIHARMONIC>(P, ws, phi, grad, st);
+    *nl += 2;
+    return cudaGetLastError();
+  }
   if (d == 2) {
     if (f64) leaf_launch<FMM_KERNEL_LAPLACE, 2, double>(P, ws, phi, grad, st);
     else leaf_launch<FMM_KERNEL_LAPLACE, 2, float>(P, ws, phi, grad, st);
@@ -269,3 +535,4 @@ cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* p
   ++*nl;
   return cudaGetLastError();
 }
+

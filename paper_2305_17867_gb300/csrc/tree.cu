@@ -82,6 +82,21 @@ __global__ void k_bbox_final(int nblk, const double* part, Geom* g) {
   g->flag = 0;
 }
 
+}  // namespace
+
+// (x - lo) / s rounded as an IEEE division.  The product with 1/s differs
+// from the quotient by at most an ulp, which matters only when the quotient is
+// within an ulp of an integer (a box face); those rare points take the exact
+// division, so every point lands in the same leaf as with the division.
+__device__ __forceinline__ double leaf_coord(double x, double lo, double s, double inv_s) {
+  const double d = __dsub_rn(x, lo);
+  const double t = d * inv_s;
+  if (fabs(t - rint(t)) < 1e-6) return __ddiv_rn(d, s);
+  return t;
+}
+
+namespace {
+
 // leaf key of every point + per-leaf counts; vals = identity
 template <int D>
 __global__ void k_bin(int64_t n, const double* __restrict__ x, const Geom* __restrict__ g, int L,
@@ -90,11 +105,11 @@ __global__ void k_bin(int64_t n, const double* __restrict__ x, const Geom* __res
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int nl = 1 << L;
-  const double s = __ddiv_rn(g->size, (double)nl);
+  const double s = __ddiv_rn(g->size, (double)nl), inv_s = 1.0 / s;
   uint32_t key = 0;
   bool bad = false;
   for (int k = D - 1; k >= 0; --k) {
-    double t = __ddiv_rn(__dsub_rn(x[i * D + k], g->lo[k]), s);
+    const double t = leaf_coord(x[i * D + k], g->lo[k], s, inv_s);
     if (!(t >= 0.0) || t > (double)nl) bad = true;
     int b = (t >= 0.0) ? (int)fmin(floor(t), (double)(nl - 1)) : 0;  // NaN -> 0
     key = key * (uint32_t)nl + (uint32_t)b;
@@ -224,6 +239,28 @@ __global__ void k_gather(int n, const int* __restrict__ order, const double* __r
   if (w) ow[i] = w[j];
 }
 
+// FP32 path (d = 3): sorted points as float4 (x - c_own)/s and weight, c_own
+// the centre of the point's own leaf.
+__global__ void k_gather_rel(int n, const int* __restrict__ order, const double* __restrict__ x,
+                             const double* __restrict__ w, const Geom* __restrict__ g, int L,
+                             float4* __restrict__ out, int* __restrict__ perm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int j = order[i];
+  perm[i] = j;
+  const int nl = 1 << L;
+  const double s = __ddiv_rn(g->size, (double)nl), inv_s = 1.0 / s;
+  float u[3];
+  for (int k = 0; k < 3; ++k) {
+    const double xv = x[(int64_t)j * 3 + k];
+    const double t = leaf_coord(xv, g->lo[k], s, inv_s);
+    const int b = (t >= 0.0) ? (int)fmin(floor(t), (double)(nl - 1)) : 0;
+    const double c = __dadd_rn(g->lo[k], __dmul_rn((double)b + 0.5, s));
+    u[k] = (float)((xv - c) * inv_s);
+  }
+  out[i] = make_float4(u[0], u[1], u[2], w ? (float)w[j] : 0.f);
+}
+
 unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // exclusive scan of in[0..n) into out[0..n], out[n] = total
@@ -241,7 +278,7 @@ cudaError_t scan_ints(const int* in, int* out, int64_t n, int* sums, cudaStream_
 template <int D>
 cudaError_t sort_points(const fmm_plan_s* P, const Workspace& ws, int64_t n, const double* x,
                         const double* w, int* start, double* const* ox, double* ow, int* perm,
-                        cudaStream_t st, int* nl) {
+                        float4* rel, cudaStream_t st, int* nl) {
   const int L = P->desc.levels;
   const int64_t nleaf = nbox_at(D, L);
   cudaMemsetAsync(ws.counts, 0, sizeof(int) * nleaf, st);
@@ -273,8 +310,12 @@ cudaError_t sort_points(const fmm_plan_s* P, const Workspace& ws, int64_t n, con
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  k_gather<D><<<nblocks(n, 256), 256, 0, st>>>((int)n, va, x, w, ox[0], ox[1],
-                                               D == 3 ? ox[2] : ox[0], ow, perm);
+  if (rel)
+    k_gather_rel<<<nblocks(n, 256), 256, 0, st>>>((int)n, va, x, w, ws.geom, P->desc.levels, rel,
+                                                  perm);
+  else
+    k_gather<D><<<nblocks(n, 256), 256, 0, st>>>((int)n, va, x, w, ox[0], ox[1],
+                                                 D == 3 ? ox[2] : ox[0], ow, perm);
   ++*nl;
   return cudaGetLastError();
 }
@@ -308,13 +349,16 @@ cudaError_t launch_build_tree(const fmm_plan_s* P, const Workspace& ws, int64_t 
                               const double* tgt, cudaStream_t st, int* nl) {
   cudaError_t e;
   if (P->pd.d == 3) {
-    e = sort_points<3>(P, ws, n_src, src, w, ws.sstart, ws.sx, ws.sw, ws.sperm, st, nl);
+    // the FP32 path keeps only the box-relative float4 copies
+    e = sort_points<3>(P, ws, n_src, src, w, ws.sstart, ws.sx, ws.sw, ws.sperm, ws.sxr, st, nl);
     if (e != cudaSuccess) return e;
-    e = sort_points<3>(P, ws, n_tgt, tgt, nullptr, ws.tstart, ws.tx, nullptr, ws.tperm, st, nl);
+    e = sort_points<3>(P, ws, n_tgt, tgt, nullptr, ws.tstart, ws.tx, nullptr, ws.tperm, ws.txr,
+                       st, nl);
   } else {
-    e = sort_points<2>(P, ws, n_src, src, w, ws.sstart, ws.sx, ws.sw, ws.sperm, st, nl);
+    e = sort_points<2>(P, ws, n_src, src, w, ws.sstart, ws.sx, ws.sw, ws.sperm, nullptr, st, nl);
     if (e != cudaSuccess) return e;
-    e = sort_points<2>(P, ws, n_tgt, tgt, nullptr, ws.tstart, ws.tx, nullptr, ws.tperm, st, nl);
+    e = sort_points<2>(P, ws, n_tgt, tgt, nullptr, ws.tstart, ws.tx, nullptr, ws.tperm, nullptr,
+                       st, nl);
   }
   return e;
 }
