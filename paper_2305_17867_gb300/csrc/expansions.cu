@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
 // once with the parent's recurrence (M^T is linear).  One block per parent;
 // the 2^d children are shifted concurrently.
 // ---------------------------------------------------------------------------
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __restrict__ g, int l,
                                                   const double* __restrict__ mpc,
                                                   double* __restrict__ mpp) {
@@ -357,47 +357,47 @@ __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __rest
   const int b = blockIdx.x;
   const int p = pd.p, c = pd.c, nfull = pd.nfull, nj = pd.nj;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* bet = reinterpret_cast<double*>(smraw);  // NC * nj
-  double* X = bet + NC * nj;                        // NC * nj
-  double* Y = X + NC * nj;                          // NC * nj  (D == 3)
-  double* sig = Y + NC * nj;                        // nfull
-  double* tab = sig + nfull;                        // 2 (sign) x (p+1): (+-1/2)^e / e!
+  T* bet = reinterpret_cast<T*>(smraw);  // NC * nj
+  T* X = bet + NC * nj;                   // NC * nj
+  T* Y = X + NC * nj;                     // NC * nj  (D == 3)
+  T* sig = Y + NC * nj;                   // nfull
+  T* tab = sig + nfull;                   // 2 (sign) x (p+1): (+-1/2)^e / e!
   int bc[3];
   double cp[3], s;
   box_center<D>(g, l, b, bc, cp, &s);
   if (threadIdx.x <= p) {
     double v = 1.0;
     for (int e = 1; e <= (int)threadIdx.x; ++e) v *= 0.5 / (double)e;
-    tab[threadIdx.x] = v;                                  // h = +1/2 (child bit 0)
-    tab[(p + 1) + threadIdx.x] = (threadIdx.x & 1) ? -v : v;  // h = -1/2 (child bit 1)
+    tab[threadIdx.x] = (T)v;                                      // h = +1/2 (child bit 0)
+    tab[(p + 1) + threadIdx.x] = (T)((threadIdx.x & 1) ? -v : v);  // h = -1/2 (child bit 1)
   }
   const int nlc = 1 << (l + 1);
   for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
     const int ci = e / nj, q = e % nj;
     int64_t cb = 0;
     for (int k = D - 1; k >= 0; --k) cb = cb * nlc + (2 * bc[k] + ((ci >> k) & 1));
-    bet[e] = mpc[(size_t)cb * nj + q];
+    bet[e] = (T)mpc[(size_t)cb * nj + q];
   }
   __syncthreads();
   // x shift on the stored slabs: X[q] = sum_{t <= q0} f[t] bet[q - t]
   for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
     const int ci = e / nj, q = e % nj;
-    const double* f = tab + (ci & 1) * (p + 1);
+    const T* f = tab + (ci & 1) * (p + 1);
     const int q0 = pd.mi[q].x;
-    double acc = 0.0;
+    T acc = 0;
     for (int t = 0; t <= q0; ++t) acc += f[t] * bet[e - t];
     X[e] = acc;
   }
   __syncthreads();
-  const double* Zin = X;
+  const T* Zin = X;
   if (D == 3) {
     // y shift: Y[q0, q1, is] = sum_{t <= q1} f[t] X[q0, q1 - t, is]
     for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
       const int ci = e / nj, q = e % nj;
-      const double* f = tab + ((ci >> 1) & 1) * (p + 1);
+      const T* f = tab + ((ci >> 1) & 1) * (p + 1);
       const char4 m = pd.mi[q];
-      const double* Xc = X + ci * nj;
-      double acc = 0.0;
+      const T* Xc = X + ci * nj;
+      T acc = 0;
       for (int t = 0; t <= m.y; ++t) acc += f[t] * Xc[pd.frow[m.z * (p + 1) + m.y - t] + m.x];
       Y[e] = acc;
     }
@@ -408,20 +408,20 @@ __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __rest
   for (int q = threadIdx.x; q < nfull; q += blockDim.x) {
     const char4 m = pd.mi[q];
     const int q0 = m.x, q1 = D == 3 ? m.y : 0, qs = D == 3 ? m.z : m.y;
-    double acc = 0.0;
+    T acc = 0;
     for (int ci = 0; ci < NC; ++ci) {
-      const double* f = tab + ((ci >> (D - 1)) & 1) * (p + 1);
-      const double* Zc = Zin + ci * nj;
+      const T* f = tab + ((ci >> (D - 1)) & 1) * (p + 1);
+      const T* Zc = Zin + ci * nj;
       for (int is = 0; is <= min(qs, c - 1); ++is) {
         const int src = D == 3 ? pd.frow[is * (p + 1) + q1] + q0 : pd.frow[is] + q0;
         acc += f[qs - is] * Zc[src];
       }
     }
-    sig[q] = ldexp(acc, -(int)m.w);
+    sig[q] = acc * (T)ldexp(1.0, -(int)m.w);
   }
   __syncthreads();
-  compress_smem<double>(pd, sig, s);
-  for (int q = threadIdx.x; q < nj; q += blockDim.x) mpp[(size_t)b * nj + q] = sig[q];
+  compress_smem<T>(pd, sig, s);
+  for (int q = threadIdx.x; q < nj; q += blockDim.x) mpp[(size_t)b * nj + q] = (double)sig[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -431,49 +431,49 @@ __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __rest
 // (two sign variants), y (four variants) and the slow axis (eight children,
 // stored slabs only); the x and y partial shifts are shared by the children.
 // ---------------------------------------------------------------------------
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __restrict__ g, int l,
                                                   const double* __restrict__ lcp,
                                                   double* __restrict__ lcc) {
   const int b = blockIdx.x;
   const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* Dt = reinterpret_cast<double*>(smraw);  // nfull
-  double* X = Dt + nfull;                          // 2 * nfull
-  double* Y = X + 2 * nfull;                       // 4 * nfull (D == 3)
-  double* tab = Y + (D == 3 ? 4 * nfull : 0);      // 2 x (p+1): (-+1/4)^e / e!
+  T* Dt = reinterpret_cast<T*>(smraw);       // nfull
+  T* X = Dt + nfull;                          // 2 * nfull
+  T* Y = X + 2 * nfull;                       // 4 * nfull (D == 3)
+  T* tab = Y + (D == 3 ? 4 * nfull : 0);      // 2 x (p+1): (-+1/4)^e / e!
   int bc[3];
   double cp[3], s;
   box_center<D>(g, l, b, bc, cp, &s);
-  for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = lcp[(size_t)b * nj + q];
+  for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = (T)lcp[(size_t)b * nj + q];
   if (threadIdx.x <= p) {
     double v = 1.0;
     for (int e = 1; e <= (int)threadIdx.x; ++e) v *= 0.25 / (double)e;
-    tab[threadIdx.x] = (threadIdx.x & 1) ? -v : v;  // child bit 0: h/S = -1/4
-    tab[(p + 1) + threadIdx.x] = v;                  // child bit 1: h/S = +1/4
+    tab[threadIdx.x] = (T)((threadIdx.x & 1) ? -v : v);  // child bit 0: h/S = -1/4
+    tab[(p + 1) + threadIdx.x] = (T)v;                    // child bit 1: h/S = +1/4
   }
   __syncthreads();
-  decompress_smem<double>(pd, Dt, s);
+  decompress_smem<T>(pd, Dt, s);
   // x shift: X[v][q] = sum_{t >= 0} g_v[t] Dt[q + t] along the row of q
   for (int e = threadIdx.x; e < 2 * nfull; e += blockDim.x) {
     const int v = e / nfull, q = e % nfull;
     const char4 m = pd.mi[q];
     const int qs = D == 3 ? m.z : m.y, q1 = D == 3 ? m.y : 0;
     const int len = p - qs - q1 - m.x + 1;
-    const double* gv = tab + v * (p + 1);
-    double acc = 0.0;
+    const T* gv = tab + v * (p + 1);
+    T acc = 0;
     for (int t = 0; t < len; ++t) acc += gv[t] * Dt[q + t];
     X[e] = acc;
   }
   __syncthreads();
-  const double* Zin = X;
+  const T* Zin = X;
   if (D == 3) {
     for (int e = threadIdx.x; e < 4 * nfull; e += blockDim.x) {
       const int v = e / nfull, q = e % nfull;  // v = sx + 2 sy
       const char4 m = pd.mi[q];
-      const double* gv = tab + (v >> 1) * (p + 1);
-      const double* Xv = X + (v & 1) * nfull;
-      double acc = 0.0;
+      const T* gv = tab + (v >> 1) * (p + 1);
+      const T* Xv = X + (v & 1) * nfull;
+      T acc = 0;
       for (int t = 0; t <= p - m.z - m.x - m.y; ++t)
         acc += gv[t] * Xv[pd.frow[m.z * (p + 1) + m.y + t] + m.x];
       Y[e] = acc;
@@ -487,16 +487,16 @@ __global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __rest
     const int ci = e / nj, i = e % nj;
     const char4 m = pd.mi[i];
     const int i0 = m.x, i1 = D == 3 ? m.y : 0, is = D == 3 ? m.z : m.y;
-    const double* gv = tab + ((ci >> (D - 1)) & 1) * (p + 1);
-    const double* Zv = Zin + (ci & (NC / 2 - 1)) * nfull;
-    double acc = 0.0;
+    const T* gv = tab + ((ci >> (D - 1)) & 1) * (p + 1);
+    const T* Zv = Zin + (ci & (NC / 2 - 1)) * nfull;
+    T acc = 0;
     for (int qs = is; qs <= p - i0 - i1; ++qs) {
       const int src = D == 3 ? pd.frow[qs * (p + 1) + i1] + i0 : pd.frow[qs] + i0;
       acc += gv[qs - is] * Zv[src];
     }
     int64_t cb = 0;
     for (int k = D - 1; k >= 0; --k) cb = cb * nlc + (2 * bc[k] + ((ci >> k) & 1));
-    lcc[(size_t)cb * nj + i] += ldexp(acc, -(int)m.w);
+    lcc[(size_t)cb * nj + i] += ldexp((double)acc, -(int)m.w);
   }
 }
 
@@ -507,9 +507,13 @@ cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaSt
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels;
   const size_t smem = sizeof(double) * pd.nh * 2;
+  // the tensor-core M2L of a homogeneous kernel reads only level 2's table
+  const int prec = P->desc.precision;
+  const bool tc = prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3;
+  const int nlev = (tc && pd.d == 3 && pd.kernel != FMM_KERNEL_YUKAWA) ? 1 : L - 1;
   if (pd.d == 3) {
     set_smem(k_deriv_tables<3>, smem);
-    k_deriv_tables<3><<<(L - 1) * 343, 128, smem, st>>>(pd, ws.geom, ws.htab);
+    k_deriv_tables<3><<<nlev * 343, 128, smem, st>>>(pd, ws.geom, ws.htab);
   } else {
     set_smem(k_deriv_tables<2>, smem);
     k_deriv_tables<2><<<(L - 1) * 49, 128, smem, st>>>(pd, ws.geom, ws.htab);
@@ -575,17 +579,26 @@ cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
 cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels, d = pd.d;
-  const size_t smem = sizeof(double) * (3 * (1 << d) * pd.nj + pd.nfull + 2 * (pd.p + 1));
+  // In the mixed modes the leaf multipoles come from the float P2M, so their
+  // first shift runs in float too; shifts higher in the tree stay FP64.
+  const bool mixed = P->desc.precision != FMM_PREC_FP64;
   for (int l = L - 1; l >= 2; --l) {
     const double* mpc = ws.mp + ws.lev_off[l + 1] * pd.nj;
     double* mpp = ws.mp + ws.lev_off[l] * pd.nj;
+    const bool f32 = mixed && l == L - 1;
+    const size_t tsz = f32 ? 4 : 8;
+    const size_t smem = tsz * (3 * (1 << d) * pd.nj + pd.nfull + 2 * (pd.p + 1));
+#define M2M_GO(DD, TT)                                                                     \
+  do {                                                                                     \
+    set_smem(k_m2m<DD, TT>, smem);                                                         \
+    k_m2m<DD, TT><<<(unsigned)nbox_at(DD, l), kThreads, smem, st>>>(pd, ws.geom, l, mpc, mpp); \
+  } while (0)
     if (d == 3) {
-      set_smem(k_m2m<3>, smem);
-      k_m2m<3><<<(unsigned)nbox_at(3, l), kThreads, smem, st>>>(pd, ws.geom, l, mpc, mpp);
+      if (f32) M2M_GO(3, float); else M2M_GO(3, double);
     } else {
-      set_smem(k_m2m<2>, smem);
-      k_m2m<2><<<(unsigned)nbox_at(2, l), kThreads, smem, st>>>(pd, ws.geom, l, mpc, mpp);
+      if (f32) M2M_GO(2, float); else M2M_GO(2, double);
     }
+#undef M2M_GO
     ++*nl;
   }
   return cudaGetLastError();
@@ -594,17 +607,26 @@ cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
 cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels, d = pd.d;
-  const size_t smem = sizeof(double) * (7 * pd.nfull + 2 * (pd.p + 1));
+  // In the mixed modes the leaf locals feed the float L2P, so the last shift
+  // (to the leaves) runs in float; shifts higher in the tree stay FP64.
+  const bool mixed = P->desc.precision != FMM_PREC_FP64;
   for (int l = 2; l < L; ++l) {
     const double* lcp = ws.lc + ws.lev_off[l] * pd.nj;
     double* lcc = ws.lc + ws.lev_off[l + 1] * pd.nj;
+    const bool f32 = mixed && l == L - 1;
+    const size_t tsz = f32 ? 4 : 8;
+    const size_t smem = tsz * (7 * pd.nfull + 2 * (pd.p + 1));
+#define L2L_GO(DD, TT)                                                                     \
+  do {                                                                                     \
+    set_smem(k_l2l<DD, TT>, smem);                                                         \
+    k_l2l<DD, TT><<<(unsigned)nbox_at(DD, l), kThreads, smem, st>>>(pd, ws.geom, l, lcp, lcc); \
+  } while (0)
     if (d == 3) {
-      set_smem(k_l2l<3>, smem);
-      k_l2l<3><<<(unsigned)nbox_at(3, l), kThreads, smem, st>>>(pd, ws.geom, l, lcp, lcc);
+      if (f32) L2L_GO(3, float); else L2L_GO(3, double);
     } else {
-      set_smem(k_l2l<2>, smem);
-      k_l2l<2><<<(unsigned)nbox_at(2, l), kThreads, smem, st>>>(pd, ws.geom, l, lcp, lcc);
+      if (f32) L2L_GO(2, float); else L2L_GO(2, double);
     }
+#undef L2L_GO
     ++*nl;
   }
   return cudaGetLastError();

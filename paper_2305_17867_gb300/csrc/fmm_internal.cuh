@@ -28,7 +28,9 @@
 struct Geom {
   double lo[3];
   double size;
-  int flag;  // device-side status bits (1: domain)
+  double s_leaf;      // size / 2^L
+  double inv_s_leaf;  // 1 / s_leaf
+  int flag;  // device-side status bits (1: domain, 2: timeout)
   int pad;
 };
 

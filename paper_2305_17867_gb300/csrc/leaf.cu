@@ -257,28 +257,30 @@ __global__ void __launch_bounds__(32 * kCoefWarps) k_leaf_coef(PlanDev pd, const
                                                                int L, int64_t nleaf,
                                                                const double* __restrict__ lc,
                                                                float* __restrict__ coef) {
+  // the coefficients feed float arithmetic, so the (short, O(1)-coefficient)
+  // decompression recurrence runs in float as well
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t b = (int64_t)blockIdx.x * kCoefWarps + warp;
   if (b >= nleaf) return;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* Dt = reinterpret_cast<double*>(smraw) + (size_t)warp * pd.nfull;
-  const double s = __ddiv_rn(g->size, (double)(1 << L));
+  float* Dt = reinterpret_cast<float*>(smraw) + (size_t)warp * pd.nfull;
+  const double s = g->s_leaf;
   const int nt = pd.nterms > 0 ? pd.nterms : 1;
-  double cf[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) cf[t] = scaled_coef(pd, t, s);
-  for (int q = lane; q < pd.nj; q += 32) Dt[q] = lc[(size_t)b * pd.nj + q];
+  float cf[FMM_MAX_TERMS];
+  for (int t = 0; t < pd.nterms; ++t) cf[t] = (float)scaled_coef(pd, t, s);
+  for (int q = lane; q < pd.nj; q += 32) Dt[q] = (float)lc[(size_t)b * pd.nj + q];
   __syncwarp();
   for (int ms = pd.c; ms <= pd.p; ++ms) {
     const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
     for (int i = b0 + lane; i < b1; i += 32) {
-      double v = 0.0;
+      float v = 0.f;
       for (int t = 0; t < pd.nterms; ++t) v += cf[t] * Dt[pd.rec_src[i * nt + t]];
       Dt[i] = v;
     }
     __syncwarp();
   }
   for (int q = lane; q < pd.nfull; q += 32)
-    coef[(size_t)b * pd.nfull + q] = (float)(Dt[q] * pd.inv_fact[q]);
+    coef[(size_t)b * pd.nfull + q] = Dt[q] * (float)pd.inv_fact[q];
 }
 
 constexpr int kFastWarps = 4;   // target leaves per block (one warp each)
@@ -314,6 +316,97 @@ __device__ __forceinline__ void pair_masked(float r2, float lam, float& v, float
     v = r2 * ri;
     f1 = ri;
   }
+}
+
+// Pair without the x == y guard: used for source leaves other than the
+// target's own, where no coincident point can exist.
+template <int K>
+__device__ __forceinline__ void pair_plain(float r2, float lam, float& v, float& f1) {
+  // distinct points of adjacent leaves closer than the float resolution of the
+  // box-relative coordinates would round to r2 = 0; keep the result finite
+  const float ri = rsqrt_fast(fmaxf(r2, 1e-30f));
+  if (K == FMM_KERNEL_LAPLACE) {
+    v = ri;
+    f1 = -ri * ri * ri;
+  } else if (K == FMM_KERNEL_YUKAWA) {
+    const float r = r2 * ri;
+    const float e = exp_fast(-lam * r);
+    v = e * ri;
+    f1 = e * (-lam * ri * ri - ri * ri * ri);
+  } else {
+    v = r2 * ri;
+    f1 = ri;
+  }
+}
+
+template <int K, bool MASK>
+__device__ __forceinline__ void pair_sel(float r2, float lam, float& v, float& f1) {
+  if (MASK) pair_masked<K>(r2, lam, v, f1);
+  else pair_plain<K>(r2, lam, v, f1);
+}
+
+// One sweep over n staged sources for one or two target slots per lane.
+template <int K, bool GRAD, bool MASK, bool TWO>
+__device__ __forceinline__ void sweep(const float4* __restrict__ src, int n, float lam,
+                                      const float* ua, const float* ub, float& na, float& nb,
+                                      float* ga, float* gb) {
+  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+  int q = 0;
+  for (; q + 1 < n; q += 2) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 v = src[q + h];
+      const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
+      float pv, f1;
+      pair_sel<K, MASK>(fmaf(dzv, dzv, fmaf(dyv, dyv, dx * dx)), lam, pv, f1);
+      if (h == 0) a0 = fmaf(v.w, pv, a0); else a1 = fmaf(v.w, pv, a1);
+      if (GRAD) {
+        const float fw = v.w * f1;
+        ga[0] = fmaf(fw, dx, ga[0]);
+        ga[1] = fmaf(fw, dyv, ga[1]);
+        ga[2] = fmaf(fw, dzv, ga[2]);
+      }
+      if (TWO) {
+        const float ex = ub[0] - v.x, eyv = ub[1] - v.y, ezv = ub[2] - v.z;
+        float pw, f2;
+        pair_sel<K, MASK>(fmaf(ezv, ezv, fmaf(eyv, eyv, ex * ex)), lam, pw, f2);
+        if (h == 0) b0 = fmaf(v.w, pw, b0); else b1 = fmaf(v.w, pw, b1);
+        if (GRAD) {
+          const float fw = v.w * f2;
+          gb[0] = fmaf(fw, ex, gb[0]);
+          gb[1] = fmaf(fw, eyv, gb[1]);
+          gb[2] = fmaf(fw, ezv, gb[2]);
+        }
+      }
+    }
+  }
+  for (; q < n; ++q) {
+    const float4 v = src[q];
+    const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
+    float pv, f1;
+    pair_sel<K, MASK>(fmaf(dzv, dzv, fmaf(dyv, dyv, dx * dx)), lam, pv, f1);
+    a0 = fmaf(v.w, pv, a0);
+    if (GRAD) {
+      const float fw = v.w * f1;
+      ga[0] = fmaf(fw, dx, ga[0]);
+      ga[1] = fmaf(fw, dyv, ga[1]);
+      ga[2] = fmaf(fw, dzv, ga[2]);
+    }
+    if (TWO) {
+      const float ex = ub[0] - v.x, eyv = ub[1] - v.y, ezv = ub[2] - v.z;
+      float pw, f2;
+      pair_sel<K, MASK>(fmaf(ezv, ezv, fmaf(eyv, eyv, ex * ex)), lam, pw, f2);
+      b0 = fmaf(v.w, pw, b0);
+      if (GRAD) {
+        const float fw = v.w * f2;
+        gb[0] = fmaf(fw, ex, gb[0]);
+        gb[1] = fmaf(fw, eyv, gb[1]);
+        gb[2] = fmaf(fw, ezv, gb[2]);
+      }
+    }
+  }
+  na += a0 + a1;
+  if (TWO) nb += b0 + b1;
 }
 
 template <int K, bool GRAD>
@@ -392,42 +485,13 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
           src[q] = v;
         }
         __syncwarp();
-        if (!two) {
-#pragma unroll 4
-          for (int q = 0; q < n; ++q) {
-            const float4 v = src[q];
-            const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
-            float pv, f1;
-            pair_masked<K>(dx * dx + dyv * dyv + dzv * dzv, lam, pv, f1);
-            na += v.w * pv;
-            if (GRAD) {
-              const float fw = v.w * f1;
-              ga[0] += fw * dx;
-              ga[1] += fw * dyv;
-              ga[2] += fw * dzv;
-            }
-          }
+        const bool center = (dy == 0 && dz == 0);  // only the own leaf can hold x == y
+        if (center) {
+          if (two) sweep<K, GRAD, true, true>(src, n, lam, ua, ub, na, nb, ga, gb);
+          else sweep<K, GRAD, true, false>(src, n, lam, ua, ub, na, nb, ga, gb);
         } else {
-#pragma unroll 2
-          for (int q = 0; q < n; ++q) {
-            const float4 v = src[q];
-            const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
-            const float ex = ub[0] - v.x, eyv = ub[1] - v.y, ezv = ub[2] - v.z;
-            float pv, f1, pw, f2;
-            pair_masked<K>(dx * dx + dyv * dyv + dzv * dzv, lam, pv, f1);
-            pair_masked<K>(ex * ex + eyv * eyv + ezv * ezv, lam, pw, f2);
-            na += v.w * pv;
-            nb += v.w * pw;
-            if (GRAD) {
-              const float fa = v.w * f1, fb = v.w * f2;
-              ga[0] += fa * dx;
-              ga[1] += fa * dyv;
-              ga[2] += fa * dzv;
-              gb[0] += fb * ex;
-              gb[1] += fb * eyv;
-              gb[2] += fb * ezv;
-            }
-          }
+          if (two) sweep<K, GRAD, false, true>(src, n, lam, ua, ub, na, nb, ga, gb);
+          else sweep<K, GRAD, false, false>(src, n, lam, ua, ub, na, nb, ga, gb);
         }
       }
     }
@@ -484,7 +548,7 @@ void leaf_fast_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, dou
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels;
   const int64_t nleaf = nbox_at(3, L);
-  const size_t sm = sizeof(double) * pd.nfull * kCoefWarps;
+  const size_t sm = sizeof(float) * pd.nfull * kCoefWarps;
   set_smem(k_leaf_coef, sm);
   k_leaf_coef<<<(unsigned)((nleaf + kCoefWarps - 1) / kCoefWarps), 32 * kCoefWarps, sm, st>>>(
       pd, ws.geom, L, nleaf, ws.lc + ws.lev_off[L] * pd.nj, ws.lcoef);

@@ -13,12 +13,18 @@ namespace {
 
 constexpr int kRsBlock = 1024;
 
-__global__ void k_geom_fixed(Geom* g, double lo0, double lo1, double lo2, double size) {
+__device__ void set_leaf_side(Geom* g, int L) {
+  g->s_leaf = __ddiv_rn(g->size, (double)(1 << L));
+  g->inv_s_leaf = 1.0 / g->s_leaf;
+}
+
+__global__ void k_geom_fixed(Geom* g, double lo0, double lo1, double lo2, double size, int L) {
   g->lo[0] = lo0;
   g->lo[1] = lo1;
   g->lo[2] = lo2;
   g->size = size;
   g->flag = 0;
+  set_leaf_side(g, L);
 }
 
 // per-block min/max over the sources and targets (bounding cube of the root)
@@ -62,7 +68,7 @@ __global__ void k_bbox_partial(int64_t ns, const double* __restrict__ src, int64
 
 // root = cube with corner at the minimum and side = the largest extent
 template <int D>
-__global__ void k_bbox_final(int nblk, const double* part, Geom* g) {
+__global__ void k_bbox_final(int nblk, const double* part, Geom* g, int L) {
   if (threadIdx.x != 0) return;
   double mn[3] = {0, 0, 0}, mx[3] = {0, 0, 0};
   for (int k = 0; k < D; ++k) {
@@ -80,6 +86,7 @@ __global__ void k_bbox_final(int nblk, const double* part, Geom* g) {
   for (int k = 0; k < 3; ++k) g->lo[k] = (k < D && isfinite(mn[k])) ? mn[k] : 0.0;
   g->size = size;
   g->flag = 0;
+  set_leaf_side(g, L);
 }
 
 }  // namespace
@@ -105,13 +112,23 @@ __global__ void k_bin(int64_t n, const double* __restrict__ x, const Geom* __res
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int nl = 1 << L;
-  const double s = __ddiv_rn(g->size, (double)nl), inv_s = 1.0 / s;
+  const double s = g->s_leaf, inv_s = g->inv_s_leaf;
+  const float inv_sf = (float)inv_s;
   uint32_t key = 0;
   bool bad = false;
   for (int k = D - 1; k >= 0; --k) {
-    const double t = leaf_coord(x[i * D + k], g->lo[k], s, inv_s);
-    if (!(t >= 0.0) || t > (double)nl) bad = true;
-    int b = (t >= 0.0) ? (int)fmin(floor(t), (double)(nl - 1)) : 0;  // NaN -> 0
+    const double xv = x[i * D + k];
+    // float estimate, off by far less than 1e-3 box widths; only points that
+    // close to a box face take the FP64 path (identical to the division)
+    const float tf = ((float)xv - (float)g->lo[k]) * inv_sf;
+    int b;
+    if (tf >= 0.001f && tf <= (float)nl - 0.001f && fabsf(tf - rintf(tf)) > 0.001f) {
+      b = min((int)tf, nl - 1);
+    } else {
+      const double t = leaf_coord(xv, g->lo[k], s, inv_s);
+      if (!(t >= 0.0) || t > (double)nl) bad = true;
+      b = (t >= 0.0) ? (int)fmin(floor(t), (double)(nl - 1)) : 0;  // NaN -> 0
+    }
     key = key * (uint32_t)nl + (uint32_t)b;
   }
   if (bad) atomicOr(&gflag->flag, 1);
@@ -241,22 +258,24 @@ __global__ void k_gather(int n, const int* __restrict__ order, const double* __r
 
 // FP32 path (d = 3): sorted points as float4 (x - c_own)/s and weight, c_own
 // the centre of the point's own leaf.
-__global__ void k_gather_rel(int n, const int* __restrict__ order, const double* __restrict__ x,
+// The leaf of sorted point i is its sorted key; (x - c)/s = (x - lo)/s - (b + 1/2).
+__global__ void k_gather_rel(int n, const int* __restrict__ order,
+                             const uint32_t* __restrict__ keys, const double* __restrict__ x,
                              const double* __restrict__ w, const Geom* __restrict__ g, int L,
                              float4* __restrict__ out, int* __restrict__ perm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int j = order[i];
   perm[i] = j;
-  const int nl = 1 << L;
-  const double s = __ddiv_rn(g->size, (double)nl), inv_s = 1.0 / s;
+  const uint32_t nl = 1u << L;
+  uint32_t key = keys[i];
+  const double inv_s = g->inv_s_leaf;
   float u[3];
   for (int k = 0; k < 3; ++k) {
-    const double xv = x[(int64_t)j * 3 + k];
-    const double t = leaf_coord(xv, g->lo[k], s, inv_s);
-    const int b = (t >= 0.0) ? (int)fmin(floor(t), (double)(nl - 1)) : 0;
-    const double c = __dadd_rn(g->lo[k], __dmul_rn((double)b + 0.5, s));
-    u[k] = (float)((xv - c) * inv_s);
+    const uint32_t b = key % nl;
+    key /= nl;
+    const double t = (x[(int64_t)j * 3 + k] - g->lo[k]) * inv_s;
+    u[k] = (float)(t - ((double)b + 0.5));
   }
   out[i] = make_float4(u[0], u[1], u[2], w ? (float)w[j] : 0.f);
 }
@@ -311,8 +330,8 @@ cudaError_t sort_points(const fmm_plan_s* P, const Workspace& ws, int64_t n, con
     std::swap(va, vb);
   }
   if (rel)
-    k_gather_rel<<<nblocks(n, 256), 256, 0, st>>>((int)n, va, x, w, ws.geom, P->desc.levels, rel,
-                                                  perm);
+    k_gather_rel<<<nblocks(n, 256), 256, 0, st>>>((int)n, va, ka, x, w, ws.geom, P->desc.levels,
+                                                  rel, perm);
   else
     k_gather<D><<<nblocks(n, 256), 256, 0, st>>>((int)n, va, x, w, ox[0], ox[1],
                                                  D == 3 ? ox[2] : ox[0], ow, perm);
@@ -328,17 +347,17 @@ cudaError_t launch_set_geom(const fmm_plan_s* P, const Workspace& ws, int64_t n_
   const fmm_plan_desc& d = P->desc;
   if (d.root_size > 0.0) {
     k_geom_fixed<<<1, 1, 0, st>>>(ws.geom, d.root_lo[0], d.root_lo[1], d.d == 3 ? d.root_lo[2] : 0.0,
-                                  d.root_size);
+                                  d.root_size, d.levels);
     ++*nl;
     return cudaGetLastError();
   }
   const int nb = ws.nbbox_blocks;
   if (P->pd.d == 3) {
     k_bbox_partial<3><<<nb, 256, 0, st>>>(n_src, src, n_tgt, tgt, ws.bbox);
-    k_bbox_final<3><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom);
+    k_bbox_final<3><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom, d.levels);
   } else {
     k_bbox_partial<2><<<nb, 256, 0, st>>>(n_src, src, n_tgt, tgt, ws.bbox);
-    k_bbox_final<2><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom);
+    k_bbox_final<2><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom, d.levels);
   }
   *nl += 2;
   return cudaGetLastError();
