@@ -120,7 +120,7 @@ __global__ void k_bin(int64_t n, const double* __restrict__ x, const Geom* __res
     const double xv = x[i * D + k];
     // float estimate, off by far less than 1e-3 box widths; only points that
     // close to a box face take the FP64 path (identical to the division)
-    const float tf = ((float)xv - (float)g->lo[k]) * inv_sf;
+    const float tf = (float)(xv - g->lo[k]) * inv_sf;  // relative error ~2^-23 of t <= 2^L
     int b;
     if (tf >= 0.001f && tf <= (float)nl - 0.001f && fabsf(tf - rintf(tf)) > 0.001f) {
       b = min((int)tf, nl - 1);
