@@ -153,16 +153,18 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
     w.txr = carve<float4>(cur, std::max<int64_t>(n_tgt, 1));
     w.lcoef = carve<float>(cur, (size_t)nleaf * P->pd.nfull);
   }
-  if (d == 3 && (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3)) {
-    w.tc_jp = (nj + 31) / 32 * 32;
+  if (d == 3 && (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3)) {
+    const int esz = prec == FMM_PREC_BF16X3 ? 2 : 4;  // bytes per operand element
+    const int row = 128 / esz;                         // elements per 128-byte K chunk
+    w.tc_jp = (nj + row - 1) / row * row;
     w.tc_mp = (nj + 127) / 128 * 128;
-    const int halves = prec == FMM_PREC_TF32X3 ? 2 : 1;
+    const int halves = prec == FMM_PREC_TF32 ? 1 : 2;
     // homogeneous kernels (3D Laplace, biharmonic) share one set of offset
     // matrices across levels (exact power-of-two scale per level)
     const int tlev = (P->pd.kernel == FMM_KERNEL_YUKAWA) ? (L - 1) : 1;
     for (int h = 0; h < halves; ++h) {
-      w.tc_bpar[h] = carve<float>(cur, (size_t)off * w.tc_jp);
-      w.tc_tmat[h] = carve<float>(cur, (size_t)tlev * 343 * w.tc_mp * w.tc_jp);
+      w.tc_bpar[h] = carve<char>(cur, (size_t)off * w.tc_jp * esz);
+      w.tc_tmat[h] = carve<char>(cur, (size_t)tlev * 343 * w.tc_mp * w.tc_jp * esz);
     }
   }
   w.bytes = (size_t)(cur - static_cast<char*>(base));
@@ -182,7 +184,6 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   if (p < 1 || p > FMM_MAXP) return FMM_ERR_ARG;
   if (L < 2 || L > (d == 3 ? 7 : 8)) return FMM_ERR_ARG;
   if (desc->precision < FMM_PREC_FP64 || desc->precision > FMM_PREC_BF16X3) return FMM_ERR_ARG;
-  if (desc->precision == FMM_PREC_BF16X3) return FMM_ERR_UNSUPPORTED;
   const int kernel = desc->kernel;
   if (kernel == FMM_KERNEL_LAPLACE) {
   } else if (kernel == FMM_KERNEL_YUKAWA || kernel == FMM_KERNEL_BIHARMONIC) {

@@ -509,7 +509,7 @@ cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaSt
   const size_t smem = sizeof(double) * pd.nh * 2;
   // the tensor-core M2L of a homogeneous kernel reads only level 2's table
   const int prec = P->desc.precision;
-  const bool tc = prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3;
+  const bool tc = prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3;
   const int nlev = (tc && pd.d == 3 && pd.kernel != FMM_KERNEL_YUKAWA) ? 1 : L - 1;
   if (pd.d == 3) {
     set_smem(k_deriv_tables<3>, smem);

@@ -99,10 +99,10 @@ struct Workspace {
   int nbbox_blocks;
   // tensor-core M2L operands (tf32 hi / lo): parity-split multipoles of the
   // finest level and the dense offset matrices of one level
-  int tc_jp;        // |j| padded to a multiple of 32 (K)
+  int tc_jp;        // |j| padded to one 128-byte row of the operand format (K)
   int tc_mp;        // |j| padded to a multiple of 128 (M)
-  float* tc_bpar[2];
-  float* tc_tmat[2];
+  void* tc_bpar[2];
+  void* tc_tmat[2];
   // FP32 leaf path: box-relative coordinates (x - c_own)/s and weight, and the
   // decompressed far-field coefficients M Lt / m! of every leaf
   float4* sxr;

@@ -21,6 +21,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <cuda_bf16.h>
+
 #include "expansions.cuh"
 #include "tc_ptx.cuh"
 
@@ -34,6 +36,30 @@ constexpr int kRowBytes = 128;  // one K chunk: 32 fp32
 constexpr int kTileBytesA = kBM * kRowBytes;
 constexpr int kMaxN = 128;
 constexpr int kTileBytesB = kMaxN * kRowBytes;
+
+// Operand formats: tf32 (fp32 storage, 32 per 128-byte row, kind::tf32) and
+// bf16 (64 per row, kind::f16).  Both split a value into hi + lo.
+struct FmtTF32 {
+  using T = float;
+  static constexpr int kRow = 32;
+  static constexpr int kIdesc = 2;
+  static constexpr bool kF16 = false;
+  static __device__ __forceinline__ void split(double v, T& hi, T& lo) {
+    const float h = tc::tf32_rna((float)v);
+    hi = h;
+    lo = tc::tf32_rna((float)(v - (double)h));
+  }
+};
+struct FmtBF16 {
+  using T = __nv_bfloat16;
+  static constexpr int kRow = 64;
+  static constexpr int kIdesc = 1;
+  static constexpr bool kF16 = true;
+  static __device__ __forceinline__ void split(double v, T& hi, T& lo) {
+    hi = __float2bfloat16_rn((float)v);
+    lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
+  }
+};
 
 template <int NPASS>
 struct Cfg {
@@ -51,15 +77,16 @@ struct LevOff {
   int64_t o[FMM_MAX_LEVELS + 1];
 };
 
+template <typename F>
 __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off, int nj, int JP,
-                            float* __restrict__ bhi, float* __restrict__ blo) {
+                            typename F::T* __restrict__ bhi, typename F::T* __restrict__ blo) {
   const int l = blockIdx.y + 2;
   const int nl = 1 << l, H = nl >> 1;
   const int64_t nbox = (int64_t)nl * nl * nl;
   const int64_t tot = nbox * JP;
   const double* mpl = mp + lev_off.o[l] * nj;
-  float* bh = bhi + lev_off.o[l] * JP;
-  float* bl = blo ? blo + lev_off.o[l] * JP : nullptr;
+  typename F::T* bh = bhi + lev_off.o[l] * JP;
+  typename F::T* bl = blo ? blo + lev_off.o[l] * JP : nullptr;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(e % JP);
@@ -68,16 +95,17 @@ __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off,
     const int sg = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
     const int64_t dst = ((((int64_t)sg * H + (z >> 1)) * H + (y >> 1)) * H + (x >> 1)) * JP + q;
     const double v = q < nj ? mpl[b * nj + q] : 0.0;
-    const float hi = tc::tf32_rna((float)v);
+    typename F::T hi, lo;
+    F::split(v, hi, lo);
     bh[dst] = hi;
-    if (bl) bl[dst] = tc::tf32_rna((float)(v - (double)hi));
+    if (bl) bl[dst] = lo;
   }
 }
 
 // dense offset matrices A_h[i][q] = Ht_h[i + q] for the 343 offsets of a level
-template <int D>
+template <int D, typename F>
 __global__ void k_build_tmat(PlanDev pd, const double* __restrict__ htab, int MP, int JP,
-                             float* __restrict__ thi, float* __restrict__ tlo) {
+                             typename F::T* __restrict__ thi, typename F::T* __restrict__ tlo) {
   const int o = blockIdx.x;
   htab += (size_t)blockIdx.z * 343 * pd.nh;
   thi += (size_t)blockIdx.z * 343 * MP * JP;
@@ -106,9 +134,10 @@ __global__ void k_build_tmat(PlanDev pd, const double* __restrict__ htab, int MP
       v = H[idx];
     }
     const size_t dst = ((size_t)o * MP + i) * JP + q;
-    const float hi = tc::tf32_rna((float)v);
+    typename F::T hi, lo;
+    F::split(v, hi, lo);
     thi[dst] = hi;
-    if (tlo) tlo[dst] = tc::tf32_rna((float)(v - (double)hi));
+    if (tlo) tlo[dst] = lo;
   }
 }
 
@@ -155,7 +184,7 @@ struct TcParams {
   int* err;
 };
 
-template <int NPASS>
+template <typename F, int NPASS>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const __grid_constant__ TcParams prm) {
   int li = 0;
@@ -229,12 +258,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         unsigned char* st = sm + s * C::kStage;
         tc::mbar_expect_tx(&full[s], stage_tx);
         last_round[s] = r;
-        tc::tma_load_2d(st, tmA, &full[s], ch * 32, hidx * MP + mt * kBM);
-        tc::tma_load_5d(st + kTileBytesA, tmB, &full[s], ch * 32, X0 + dx, Y0 + dy, Z0 + dz, sg);
+        const int kc = ch * F::kRow;  // element offset of this 128-byte K chunk
+        tc::tma_load_2d(st, tmA, &full[s], kc, hidx * MP + mt * kBM);
+        tc::tma_load_5d(st + kTileBytesA, tmB, &full[s], kc, X0 + dx, Y0 + dy, Z0 + dz, sg);
         if (NPASS == 3) {
-          tc::tma_load_2d(st + kTileBytesA + kTileBytesB, tmAlo, &full[s], ch * 32,
+          tc::tma_load_2d(st + kTileBytesA + kTileBytesB, tmAlo, &full[s], kc,
                           hidx * MP + mt * kBM);
-          tc::tma_load_5d(st + 2 * kTileBytesA + kTileBytesB, tmBlo, &full[s], ch * 32, X0 + dx,
+          tc::tma_load_5d(st + 2 * kTileBytesA + kTileBytesB, tmBlo, &full[s], kc, X0 + dx,
                           Y0 + dy, Z0 + dz, sg);
         }
       }
@@ -250,7 +280,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else if (warp == kEpiWarps + 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    const uint32_t id = tc::idesc(2, kBM, Nmma);
+    const uint32_t id = tc::idesc(F::kIdesc, kBM, Nmma);
     int kk = 0, g = 0;
     bool ok = true;
     for (int c = 0; c < 216 && ok; ++c) {
@@ -276,11 +306,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint64_t blo = tc::desc_sw128(st + 2 * kTileBytesA + kTileBytesB);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const uint64_t adv = (uint64_t)(k * 32) >> 4;  // 8 tf32 = 32 bytes along K
-          tc::mma_tf32(dacc, a + adv, b + adv, id, (ch | k) != 0);
-          if (NPASS == 3) {
-            tc::mma_tf32(dacc, a + adv, blo + adv, id, 1);
-            tc::mma_tf32(dacc, alo + adv, b + adv, id, 1);
+          // one MMA consumes 32 bytes of K (8 tf32 or 16 bf16) inside the swizzle atom
+          const uint64_t adv = (uint64_t)(k * 32) >> 4;
+          if (F::kF16) {
+            tc::mma_f16(dacc, a + adv, b + adv, id, (ch | k) != 0);
+            if (NPASS == 3) {
+              tc::mma_f16(dacc, a + adv, blo + adv, id, 1);
+              tc::mma_f16(dacc, alo + adv, b + adv, id, 1);
+            }
+          } else {
+            tc::mma_tf32(dacc, a + adv, b + adv, id, (ch | k) != 0);
+            if (NPASS == 3) {
+              tc::mma_tf32(dacc, a + adv, blo + adv, id, 1);
+              tc::mma_tf32(dacc, alo + adv, b + adv, id, 1);
+            }
           }
         }
         tc::mma_commit(&empty[s]);
@@ -369,17 +408,17 @@ EncodeTiledFn encode_fn() {
 }
 
 bool make_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims,
-              const cuuint64_t* strides, const cuuint32_t* box) {
+              const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapDataType dt) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, base, dims, strides, box, es,
+  return fn(m, dt, (cuuint32_t)rank, base, dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
 
-template <int NPASS>
+template <typename F, int NPASS>
 cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st) {
   using C = Cfg<NPASS>;
   const PlanDev& pd = P->pd;
@@ -388,17 +427,22 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
   const int noff = 343;
   const bool shared_t = pd.kernel != FMM_KERNEL_YUKAWA;  // homogeneous G
   const int tlev = shared_t ? 1 : (L - 1);
-  float* blo = NPASS == 3 ? ws.tc_bpar[1] : nullptr;
-  float* tlo = NPASS == 3 ? ws.tc_tmat[1] : nullptr;
+  using T = typename F::T;
+  const size_t esz = sizeof(T);
+  const CUtensorMapDataType dt =
+      F::kF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  T* bhi0 = static_cast<T*>(ws.tc_bpar[0]);
+  T* thi0 = static_cast<T*>(ws.tc_tmat[0]);
+  T* blo = NPASS == 3 ? static_cast<T*>(ws.tc_bpar[1]) : nullptr;
+  T* tlo = NPASS == 3 ? static_cast<T*>(ws.tc_tmat[1]) : nullptr;
   LevOff lo;
   for (int l = 0; l <= FMM_MAX_LEVELS; ++l) lo.o[l] = l <= L + 1 ? ws.lev_off[l] : 0;
-  k_pack_beta<<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, ws.tc_bpar[0], blo);
-  k_build_tmat<3><<<dim3(noff, MP / 8, tlev), 256, 0, st>>>(pd, ws.htab, MP, JP, ws.tc_tmat[0],
-                                                            tlo);
+  k_pack_beta<F><<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, bhi0, blo);
+  k_build_tmat<3, F><<<dim3(noff, MP / 8, tlev), 256, 0, st>>>(pd, ws.htab, MP, JP, thi0, tlo);
   TcParams prm;
   std::memset(&prm, 0, sizeof(prm));
   prm.nj = nj;
-  prm.jchunks = JP / 32;
+  prm.jchunks = JP / F::kRow;
   prm.MP = MP;
   prm.err = &ws.geom->flag;
   int nb = 0;
@@ -417,36 +461,38 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
     nb += v.ntx * v.nty * ntz * 8;
     v.lc = ws.lc + ws.lev_off[l] * nj;
     const int ti = shared_t ? 0 : l - 2;
-    float* th = ws.tc_tmat[0] + (size_t)ti * noff * MP * JP;
-    float* bh = ws.tc_bpar[0] + ws.lev_off[l] * JP;
+    T* th = thi0 + (size_t)ti * noff * MP * JP;
+    T* bh = bhi0 + ws.lev_off[l] * JP;
     v.scale = 1.0f;
     if (shared_t) {  // Ht_l = Ht_2 * (s_2/s_l)^{-deg}: deg -1 (Laplace), +1 (biharmonic)
       const int k = l - 2;
       v.scale = pd.kernel == FMM_KERNEL_LAPLACE ? std::ldexp(1.0f, k) : std::ldexp(1.0f, -k);
     }
     cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
-    cuuint64_t sA[1] = {(cuuint64_t)JP * 4};
-    cuuint32_t bA[2] = {32, (cuuint32_t)kBM};
+    cuuint64_t sA[1] = {(cuuint64_t)JP * esz};
+    cuuint32_t bA[2] = {(cuuint32_t)F::kRow, (cuuint32_t)kBM};
     cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)H, 8};
-    cuuint64_t sB[4] = {(cuuint64_t)JP * 4, (cuuint64_t)JP * 4 * H, (cuuint64_t)JP * 4 * H * H,
-                        (cuuint64_t)JP * 4 * H * H * H};
-    cuuint32_t bB[5] = {32, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ, 1};
-    if (!make_map(&v.A, th, 2, dA, sA, bA)) return cudaErrorInvalidValue;
-    if (!make_map(&v.B, bh, 5, dB, sB, bB)) return cudaErrorInvalidValue;
+    cuuint64_t sB[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * H,
+                        (cuuint64_t)JP * esz * H * H, (cuuint64_t)JP * esz * H * H * H};
+    cuuint32_t bB[5] = {(cuuint32_t)F::kRow, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ,
+                        1};
+    if (!make_map(&v.A, th, 2, dA, sA, bA, dt)) return cudaErrorInvalidValue;
+    if (!make_map(&v.B, bh, 5, dB, sB, bB, dt)) return cudaErrorInvalidValue;
     v.Alo = v.A;
     v.Blo = v.B;
     if (NPASS == 3) {
-      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA))
+      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt))
         return cudaErrorInvalidValue;
-      if (!make_map(&v.Blo, blo + ws.lev_off[l] * JP, 5, dB, sB, bB)) return cudaErrorInvalidValue;
+      if (!make_map(&v.Blo, blo + ws.lev_off[l] * JP, 5, dB, sB, bB, dt))
+        return cudaErrorInvalidValue;
     }
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_m2l_tc<NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     attr = true;
   }
-  k_m2l_tc<NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
+  k_m2l_tc<F, NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
   return cudaGetLastError();
 }
 
@@ -455,8 +501,10 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
 cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
   const int L = P->desc.levels;
   if (P->pd.d != 3) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
-  const bool split = P->desc.precision == FMM_PREC_TF32X3;
-  const cudaError_t e = split ? run_all_levels<3>(P, ws, st) : run_all_levels<1>(P, ws, st);
+  const int prec = P->desc.precision;
+  const cudaError_t e = prec == FMM_PREC_BF16X3   ? run_all_levels<FmtBF16, 3>(P, ws, st)
+                        : prec == FMM_PREC_TF32X3 ? run_all_levels<FmtTF32, 3>(P, ws, st)
+                                                  : run_all_levels<FmtTF32, 1>(P, ws, st);
   *nl += 3;
   return e;
 }

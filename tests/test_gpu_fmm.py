@@ -98,11 +98,12 @@ def test_full_size_laplace3d_sampled(torch_cuda, oracle):
 # Mixed-precision tolerances (relative L2 against the FP64 oracle on the same
 # tree).  fp32 and tf32x3 keep ~22-24 significant bits per product, so the
 # result carries ~1e-7 relative error amplified by the cancellation of the
-# sums; tf32 keeps 11 bits (unit roundoff 2^-11 ~ 4.9e-4 per operand).
-MIXED_TOL = {"fp32": 2e-6, "tf32x3": 2e-6, "tf32": 2e-3}
+# sums; bf16x3 keeps ~16 bits (hi + lo bf16, unit roundoff ~2^-17 per
+# operand); tf32 keeps 11 bits (unit roundoff 2^-11 ~ 4.9e-4 per operand).
+MIXED_TOL = {"fp32": 2e-6, "tf32x3": 2e-6, "bf16x3": 5e-5, "tf32": 2e-3}
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "tf32"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3", "bf16x3", "tf32"])
 @pytest.mark.parametrize("L,n", [(3, 20000), (4, 30011)])
 def test_mixed_precision_error(torch_cuda, oracle, precision, L, n):
     wl = W.WORKLOADS["laplace3d_p10_L5_n1m"]
@@ -112,7 +113,7 @@ def test_mixed_precision_error(torch_cuda, oracle, precision, L, n):
     assert rel_l2(got, ref) < MIXED_TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3", "tf32"])
 def test_tensor_m2l_full_size_sampled(torch_cuda, oracle, precision):
     wl = W.WORKLOADS["laplace3d_p10_L5_n1m"]
     src, w, _ = W.make_inputs(wl)
@@ -122,15 +123,16 @@ def test_tensor_m2l_full_size_sampled(torch_cuda, oracle, precision):
     assert rel_l2(got[idx], ref) < MIXED_TOL[precision]
 
 
+@pytest.mark.parametrize("precision,tol", [("tf32x3", 1e-5), ("bf16x3", 2e-4)])
 @pytest.mark.parametrize("kernel,p,lam", [("yukawa", 12, 1.0), ("biharmonic", 8, 0.0)])
-def test_tensor_m2l_other_kernels(torch_cuda, oracle, kernel, p, lam):
+def test_tensor_m2l_other_kernels(torch_cuda, oracle, kernel, p, lam, precision, tol):
     # |j| = 169 (Yukawa p=12) and 130 (biharmonic p=8): two 128-row M tiles
     rng = np.random.default_rng(17)
     src = rng.random((20000, 3))
     w = rng.uniform(-1, 1, 20000)
     ref = oracle.fmm_uniform(kernel, 3, p, 4, src, w, src, lam=lam)
-    got = gpu_fmm(torch_cuda, kernel, 3, p, 4, src, w, lam=lam, precision="tf32x3")
-    assert rel_l2(got, ref) < 1e-5
+    got = gpu_fmm(torch_cuda, kernel, 3, p, 4, src, w, lam=lam, precision=precision)
+    assert rel_l2(got, ref) < tol
 
 
 # ---- edge cases -------------------------------------------------------------
