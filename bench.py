@@ -34,7 +34,7 @@ WORKLOAD = "laplace3d_p10_L5_n1m"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default=os.environ.get("FMM_BENCH_PRECISION", "tf32x3"))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--cpu-leaves", type=int, default=48)
+    ap.add_argument("--points", type=int, default=0,
+                    help="override the point count (profiling captures: the same L=5 tree and "
+                         "the identical M2L launch on less memory)")
     return ap.parse_args()
 
 
@@ -72,8 +75,12 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
+            # start timing only once the sampler is producing rows
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
         return self
@@ -129,6 +136,42 @@ def m2l_count(d: int, L: int) -> int:
     return tot
 
 
+M2L_SOURCES = ["paper_2305_17867_gb300/csrc/m2l_tc.cu", "paper_2305_17867_gb300/csrc/tc_ptx.cuh",
+               "paper_2305_17867_gb300/csrc/m2l_simt.cu"]
+
+
+def m2l_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in M2L_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(prec: str):
+    """DRAM bytes per launch of the M2L contraction from the committed ncu summary.
+
+    The summary carries one line per precision,
+    ``traffic: <precision> <bytes per launch> sources <hash>``; the figure is
+    reported only while the kernel sources still hash to the captured value.
+    """
+    path = os.path.join(ROOT, "profiles", "m2l_tc_laplace3d_p10_L5.md")
+    if not os.path.exists(path):
+        return None, "no capture"
+    want = m2l_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            f = line.strip().strip("`").split()
+            if len(f) == 5 and f[0] == "traffic:" and f[1] == prec and f[3] == "sources":
+                if f[4] != want:
+                    return None, "kernel changed since the capture"
+                return int(f[2]), ("ncu dram__bytes.sum.per_second x gpu__time_duration.sum of one "
+                                   "launch, " + path[len(ROOT) + 1:])
+    return None, "no capture for this precision"
+
+
 def leaf_of(x, L):
     n = 1 << L
     b = np.minimum(np.floor(x / (1.0 / n)).astype(np.int64), n - 1)
@@ -175,7 +218,8 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     # every rank runs an independent replica of the workload (weak scaling)
-    src, w, _ = Wk.make_inputs(wl, seed=wl.seed + 1000 * rank if rank else None)
+    src, w, _ = Wk.make_inputs(wl, n_src=args.points or None,
+                               seed=wl.seed + 1000 * rank if rank else None)
     n = src.shape[0]
     t_plan = time.perf_counter()
     plan = FMM("laplace", d=3, p=wl.p, levels=wl.levels, precision=args.precision, device=dev)
@@ -192,13 +236,11 @@ def main():
         phi = step()
     torch.cuda.synchronize()
     launches = plan.last_launch_count()
-    # per-phase timing (one extra untimed pass with the plan's phase events)
+    # the plan's own phase events and the events around the M2L contraction are
+    # recorded on the launching stream inside every timed step
     plan.set_timing(True)
-    step()
-    phases = plan.phase_times()
-    plan.set_timing(False)
 
-    times = []
+    times, ph_steps, k_steps = [], [], []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -212,10 +254,15 @@ def main():
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
+            ph_steps.append(plan.phase_times())
+            k_steps.append(plan.m2l_kernel_time())
     torch.cuda.synchronize()
+    plan.set_timing(False)
     if dist:
         dist.barrier()
     ms = sum(times) / len(times)
+    phases = {k: sum(p[k] for p in ph_steps) / len(ph_steps) for k in ph_steps[0]}
+    m2l_kernel_ms = sum(k_steps) / len(k_steps)
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -238,7 +285,7 @@ def main():
     # M2L work and roofline
     nm2l = m2l_count(3, wl.levels)
     flops_m2l = 2.0 * plan.nj * plan.nj * nm2l
-    m2l_ms = phases["m2l"]
+    m2l_ms = m2l_kernel_ms
     peaks, peak_src = load_peaks()
     prec = args.precision
     tf32_dense = peaks["bf16_tflops"] * 1.1 / 2.25
@@ -260,18 +307,21 @@ def main():
         peak = 1.25
         bound, unit, pname = "alu", "TFLOP/s", "fp64 nominal 1.25 TFLOP/s (GB300)"
     achieved = flops_m2l / (m2l_ms * 1e-3) / 1e12
-    roof = {"kernel": "m2l", "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "peak_source": pname,
+    traffic, traffic_src = profiled_traffic(prec)
+    roof = {"kernel": "m2l contraction", "bound": bound, "achieved": achieved, "peak": peak,
+            "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+            "kernel_ms": m2l_ms, "peak_source": pname,
             "frac_vs_tf32_dense": achieved / tf32_dense,
             "algorithmic": f"2*|j|^2 = {2 * plan.nj ** 2} FLOP/translation x {nm2l} translations"}
 
+    wname = WORKLOAD if not args.points else f"{WORKLOAD} with n={args.points} (profiling case)"
     result = {
         "metric": "full-FMM targets/sec (3D Laplace, compressed Taylor p=10, uniform octree L=5, "
                   "N=1e6) with M2L translations/sec",
         "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_src": n, "n_tgt": n, "p": wl.p, "levels": wl.levels,
+        "config": {"workload": wname, "n_src": n, "n_tgt": n, "p": wl.p, "levels": wl.levels,
                    "precision": prec, "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "m2l_translations_per_s": nm2l * world / (ms * 1e-3),

@@ -170,6 +170,12 @@ int fmm_last_status(fmm_plan_t plan);
 int fmm_set_timing(fmm_plan_t plan, int enable);
 int fmm_phase_times(fmm_plan_t plan, float* ms_out /* FMM_NUM_PHASES */);
 
+/* Device time (ms, CUDA events on the evaluation's stream) of the M2L
+ * contraction alone -- the tensor-core launch, or the per-level SIMT launches
+ * -- in the last evaluation made with timing enabled; excludes the zeroing of
+ * the local expansions and the operand packing.  Synchronises. */
+int fmm_m2l_kernel_time(fmm_plan_t plan, float* ms_out);
+
 /* Number of kernel launches the last fmm_eval enqueued. */
 int fmm_last_launch_count(fmm_plan_t plan);
 

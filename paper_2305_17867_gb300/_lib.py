@@ -44,7 +44,7 @@ _LIB = None
 EXPORTS = [
     "fmm_plan_create", "fmm_plan_destroy", "fmm_plan_info", "fmm_workspace_size", "fmm_eval",
     "fmm_eval_backward", "fmm_last_status", "fmm_set_timing", "fmm_phase_times",
-    "fmm_last_launch_count", "fmm_status_string", "fmm_eval_noalloc",
+    "fmm_last_launch_count", "fmm_status_string", "fmm_eval_noalloc", "fmm_m2l_kernel_time",
 ]
 
 
@@ -82,6 +82,8 @@ def load(build: bool = True):
     L.fmm_set_timing.restype = i32
     L.fmm_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.fmm_phase_times.restype = i32
+    L.fmm_m2l_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.fmm_m2l_kernel_time.restype = i32
     L.fmm_last_launch_count.argtypes = [vp]
     L.fmm_last_launch_count.restype = i32
     L.fmm_status_string.argtypes = [i32]

@@ -330,6 +330,8 @@ extern "C" int fmm_plan_destroy(fmm_plan_t P) {
   cudaDeviceSynchronize();
   if (P->events_made)
     for (auto& e : P->ev) cudaEventDestroy(e);
+  if (P->events_made)
+    for (auto& e : P->evk) cudaEventDestroy(e);
   cudaFree(P->dev_tables);
   delete P;
   return FMM_OK;
@@ -357,6 +359,8 @@ extern "C" int fmm_set_timing(fmm_plan_t P, int enable) {
   if (enable && !P->events_made) {
     for (auto& e : P->ev)
       if (cudaEventCreate(&e) != cudaSuccess) return FMM_ERR_CUDA;
+    for (auto& e : P->evk)
+      if (cudaEventCreate(&e) != cudaSuccess) return FMM_ERR_CUDA;
     P->events_made = true;
   }
   P->timing = enable ? 1 : 0;
@@ -368,6 +372,13 @@ extern "C" int fmm_phase_times(fmm_plan_t P, float* ms) {
   if (cudaEventSynchronize(P->ev[FMM_NUM_PHASES]) != cudaSuccess) return FMM_ERR_CUDA;
   for (int i = 0; i < FMM_NUM_PHASES; ++i)
     if (cudaEventElapsedTime(&ms[i], P->ev[i], P->ev[i + 1]) != cudaSuccess) return FMM_ERR_CUDA;
+  return FMM_OK;
+}
+
+extern "C" int fmm_m2l_kernel_time(fmm_plan_t P, float* ms) {
+  if (!P || !ms || !P->events_made) return FMM_ERR_ARG;
+  if (cudaEventSynchronize(P->evk[1]) != cudaSuccess) return FMM_ERR_CUDA;
+  if (cudaEventElapsedTime(ms, P->evk[0], P->evk[1]) != cudaSuccess) return FMM_ERR_CUDA;
   return FMM_OK;
 }
 

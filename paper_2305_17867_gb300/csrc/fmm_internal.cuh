@@ -61,11 +61,17 @@ struct fmm_plan_s {
   void* dev_tables;
   int timing;
   cudaEvent_t ev[FMM_NUM_PHASES + 1];
+  cudaEvent_t evk[2];  // around the M2L contraction launch(es)
   bool events_made;
   cudaStream_t last_stream;
   Geom* last_geom;  // device geometry of the last evaluation (in its workspace)
   int launches;
 };
+
+// record the start (i = 0) or end (i = 1) of the M2L contraction when timing
+inline void mark_contraction(const fmm_plan_s* P, int i, cudaStream_t st) {
+  if (P->timing) cudaEventRecord(P->evk[i], st);
+}
 
 // ---------------------------------------------------------------------------
 // Workspace layout of one evaluation.

@@ -115,6 +115,7 @@ cudaError_t launch_m2l_simt_levels(const fmm_plan_s* P, const Workspace& ws, int
   const size_t tsz = f64 ? 8 : 4;
   const size_t smem = tsz * (pd.nh + pd.nj);
   const int noff = d == 3 ? 343 : 49;
+  mark_contraction(P, 0, st);
   for (int l = l0; l <= l1; ++l) {
     const double* mpl = ws.mp + ws.lev_off[l] * pd.nj;
     double* lcl = ws.lc + ws.lev_off[l] * pd.nj;
@@ -133,6 +134,7 @@ cudaError_t launch_m2l_simt_levels(const fmm_plan_s* P, const Workspace& ws, int
 #undef M2L_LAUNCH
     ++*nl;
   }
+  mark_contraction(P, 1, st);
   return cudaGetLastError();
 }
 

@@ -492,7 +492,9 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
     cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     attr = true;
   }
+  mark_contraction(P, 0, st);
   k_m2l_tc<F, NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
+  mark_contraction(P, 1, st);
   return cudaGetLastError();
 }
 

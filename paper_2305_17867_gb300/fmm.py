@@ -99,6 +99,12 @@ class FMM:
         check(self.L.fmm_phase_times(self._h, out), "fmm_phase_times")
         return dict(zip(_lib.PHASES, list(out)))
 
+    def m2l_kernel_time(self) -> float:
+        """Milliseconds of the M2L contraction launch(es) of the last timed evaluation."""
+        out = ctypes.c_float()
+        check(self.L.fmm_m2l_kernel_time(self._h, ctypes.byref(out)), "fmm_m2l_kernel_time")
+        return float(out.value)
+
     def last_status(self) -> int:
         return self.L.fmm_last_status(self._h)
 
