@@ -38,6 +38,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--precision", default=os.environ.get("FMM_BENCH_PRECISION", "tf32x3"))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m2l", default="dense", choices=["dense", "fft"],
+                    help="M2L form: dense products or the FFT convolution form")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison line")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
@@ -222,7 +224,8 @@ def main():
                                seed=wl.seed + 1000 * rank if rank else None)
     n = src.shape[0]
     t_plan = time.perf_counter()
-    plan = FMM("laplace", d=3, p=wl.p, levels=wl.levels, precision=args.precision, device=dev)
+    plan = FMM("laplace", d=3, p=wl.p, levels=wl.levels, precision=args.precision, device=dev,
+               m2l=args.m2l)
     t_plan = (time.perf_counter() - t_plan) * 1e3
     s = torch.tensor(src, device=dev)
     wt = torch.tensor(w, device=dev)
@@ -285,6 +288,13 @@ def main():
     # M2L work and roofline
     nm2l = m2l_count(3, wl.levels)
     flops_m2l = 2.0 * plan.nj * plan.nj * nm2l
+    # FFT form: one complex multiply-add (8 flop) per kept frequency and translation
+    kf = (wl.p + 1) * (2 * wl.p + 1) * (2 * min(plan.c, wl.p + 1) - 1)
+    algo = f"2*|j|^2 = {2 * plan.nj ** 2} FLOP/translation x {nm2l} translations"
+    if args.m2l == "fft":
+        flops_m2l = 8.0 * kf * nm2l
+        algo = (f"8 * {kf} (complex multiply-add per kept frequency) FLOP/translation x "
+                f"{nm2l} translations")
     m2l_ms = m2l_kernel_ms
     peaks, peak_src = load_peaks()
     prec = args.precision
@@ -304,15 +314,16 @@ def main():
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         bound, unit, pname = "alu", "TFLOP/s", "fp32 FMA: 152 SMs x 128 lanes x 2 x max clock"
     else:
-        peak = 1.25
-        bound, unit, pname = "alu", "TFLOP/s", "fp64 nominal 1.25 TFLOP/s (GB300)"
+        peak = 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound, unit, pname = ("alu", "TFLOP/s",
+                              "fp64 FMA: 152 SMs x 2 lanes x 2 x max clock (nominal 1.25 TFLOP/s)")
     achieved = flops_m2l / (m2l_ms * 1e-3) / 1e12
-    traffic, traffic_src = profiled_traffic(prec)
-    roof = {"kernel": "m2l contraction", "bound": bound, "achieved": achieved, "peak": peak,
+    traffic, traffic_src = profiled_traffic(prec) if args.m2l == "dense" else (None, "no capture")
+    roof = {"kernel": "m2l contraction" if args.m2l == "dense" else "m2l fft stencil", "bound": bound, "achieved": achieved, "peak": peak,
             "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
             "kernel_ms": m2l_ms, "peak_source": pname,
             "frac_vs_tf32_dense": achieved / tf32_dense,
-            "algorithmic": f"2*|j|^2 = {2 * plan.nj ** 2} FLOP/translation x {nm2l} translations"}
+            "algorithmic": algo}
 
     wname = WORKLOAD if not args.points else f"{WORKLOAD} with n={args.points} (profiling case)"
     result = {
@@ -322,7 +333,7 @@ def main():
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
         "config": {"workload": wname, "n_src": n, "n_tgt": n, "p": wl.p, "levels": wl.levels,
-                   "precision": prec, "l2": "flushed (256 MiB write) between timed steps",
+                   "precision": prec, "m2l": args.m2l, "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "m2l_translations_per_s": nm2l * world / (ms * 1e-3),
         "m2l_translations": nm2l,

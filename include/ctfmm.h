@@ -71,6 +71,18 @@ enum {
   FMM_PREC_BF16X3 = 4
 };
 
+/* How M2L applies the translation of eq. (m2l_toeplitz).
+ *  DENSE  as a dense |j| x |j| product per (target, source) pair: the CUDA
+ *         cores for FP64/FP32, the tensor cores for TF32/TF32X3/BF16X3.
+ *  FFT    in its convolution form (eq. (convolution_m2l)): every box's
+ *         multipole is transformed once to a (2p+1)^{d-1} (2c-1) spectrum,
+ *         each target accumulates sum_h Hhat_h * Bhat_{t-h} over its
+ *         interaction list frequency by frequency, and one inverse transform
+ *         per target yields its local coefficients.  Coefficients are scaled
+ *         by g^{|q|} before the transform (g = 3p/8 in units of the box side;
+ *         Sec. 4.1.1).  FP64 (complex double) and FP32 (complex float) only. */
+enum { FMM_M2L_DENSE = 0, FMM_M2L_FFT = 1 };
+
 /* A constant-coefficient PDE L = sum_t coeff[t] d^{multi_idx[t]}  (eq.
  * (define_pde_op)).  multi_idx is n_terms x d exponents.  The PDE must have
  * a nonzero coefficient on c*e_d, c its order (Property 1 on the last axis). */
@@ -91,6 +103,7 @@ typedef struct {
   double root_size;    /* side of the root box; <= 0: bounding cube of the
                           sources and targets, found on the device per call */
   int precision;       /* FMM_PREC_* */
+  int m2l;             /* FMM_M2L_*; FFT requires precision FP64 or FP32 */
 } fmm_plan_desc;
 
 /* Create a plan: validates the description, builds the stored set j, the

@@ -17,6 +17,7 @@ STATUS = {
 }
 KERNELS = {"laplace": 0, "yukawa": 1, "biharmonic": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4}
+M2L_PATHS = {"dense": 0, "fft": 1}
 NUM_PHASES = 7
 PHASES = ["tree", "derivatives", "p2m", "m2m", "m2l", "l2l", "leaf"]
 
@@ -36,7 +37,7 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("lam", ctypes.c_double), ("d", ctypes.c_int),
                 ("p", ctypes.c_int), ("levels", ctypes.c_int), ("pde", ctypes.POINTER(Pde)),
                 ("root_lo", ctypes.c_double * 3), ("root_size", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("m2l", ctypes.c_int)]
 
 
 _LIB = None

@@ -167,6 +167,13 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
       w.tc_tmat[h] = carve<char>(cur, (size_t)tlev * 343 * w.tc_mp * w.tc_jp * esz);
     }
   }
+  if (P->desc.m2l == FMM_M2L_FFT) {
+    const size_t csz = prec == FMM_PREC_FP64 ? 16 : 8;  // complex double / float
+    const int tl = m2l_shared_tables(P) ? 1 : L - 1;
+    w.fft_b = carve<char>(cur, (size_t)off * P->fft.kfp * csz);
+    w.fft_g = carve<char>(cur, (size_t)off * P->fft.kfp * csz);
+    w.fft_h = carve<char>(cur, (size_t)tl * noff * P->fft.kfp * csz);
+  }
   w.bytes = (size_t)(cur - static_cast<char*>(base));
   if (ws) *ws = w;
   return FMM_OK;
@@ -184,6 +191,10 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   if (p < 1 || p > FMM_MAXP) return FMM_ERR_ARG;
   if (L < 2 || L > (d == 3 ? 7 : 8)) return FMM_ERR_ARG;
   if (desc->precision < FMM_PREC_FP64 || desc->precision > FMM_PREC_BF16X3) return FMM_ERR_ARG;
+  if (desc->m2l != FMM_M2L_DENSE && desc->m2l != FMM_M2L_FFT) return FMM_ERR_ARG;
+  if (desc->m2l == FMM_M2L_FFT && desc->precision != FMM_PREC_FP64 &&
+      desc->precision != FMM_PREC_FP32)
+    return FMM_ERR_UNSUPPORTED;
   const int kernel = desc->kernel;
   if (kernel == FMM_KERNEL_LAPLACE) {
   } else if (kernel == FMM_KERNEL_YUKAWA || kernel == FMM_KERNEL_BIHARMONIC) {
@@ -289,7 +300,31 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   const size_t n_rc = align_up(sizeof(int16_t) * pd.nfull * nt);
   const size_t n_fr = align_up(sizeof(int) * full.row.size());
   const size_t n_hr = align_up(sizeof(int) * hank.row.size());
-  const size_t total = n_mi + n_if + 2 * n_rc + n_fr + n_hr;
+  // FFT form of M2L: transform lengths, twiddles and the scaling g^{+-n}
+  FftDev fft{};
+  fft.n1 = 2 * p + 1;
+  fft.n2 = d == 3 ? 2 * p + 1 : 1;
+  fft.n3 = 2 * std::min(c, p + 1) - 1;  // M_s = max m_s over j
+  fft.k1 = p + 1;
+  fft.kf = fft.k1 * fft.n2 * fft.n3;
+  fft.kfp = (fft.kf + 31) / 32 * 32;
+  std::vector<double> ftab;
+  const double kPi = 3.14159265358979323846;
+  for (int n = 0; n < fft.n1; ++n) {
+    ftab.push_back(std::cos(2.0 * kPi * n / fft.n1));
+    ftab.push_back(std::sin(2.0 * kPi * n / fft.n1));
+  }
+  for (int n = 0; n < fft.n3; ++n) {
+    ftab.push_back(std::cos(2.0 * kPi * n / fft.n3));
+    ftab.push_back(std::sin(2.0 * kPi * n / fft.n3));
+  }
+  // scaling of Sec. 4.1.1 in units of the box side: g = 3p/8 (at least 1)
+  // balances the magnitudes of the scaled multipoles and derivatives
+  const double g = std::max(1.0, 0.375 * p);
+  for (int n = 0; n <= 2 * p; ++n) ftab.push_back(std::pow(g, n));
+  for (int n = 0; n <= 2 * p; ++n) ftab.push_back(std::pow(g, -n));
+  const size_t n_ft = align_up(sizeof(double) * ftab.size());
+  const size_t total = n_mi + n_if + 2 * n_rc + n_fr + n_hr + n_ft;
   std::vector<char> host(total, 0);
   char* h = host.data();
   std::memcpy(h, mi.data(), sizeof(char4) * pd.nfull);
@@ -298,6 +333,7 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   std::memcpy(h + n_mi + n_if + n_rc, cmp.data(), sizeof(int16_t) * cmp.size());
   std::memcpy(h + n_mi + n_if + 2 * n_rc, full.row.data(), sizeof(int) * full.row.size());
   std::memcpy(h + n_mi + n_if + 2 * n_rc + n_fr, hank.row.data(), sizeof(int) * hank.row.size());
+  std::memcpy(h + n_mi + n_if + 2 * n_rc + n_fr + n_hr, ftab.data(), sizeof(double) * ftab.size());
   void* dt = nullptr;
   if (cudaMalloc(&dt, total) != cudaSuccess) return FMM_ERR_NOMEM;
   if (cudaMemcpy(dt, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -311,6 +347,12 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   pd.cmp_src = reinterpret_cast<const int16_t*>(db + n_mi + n_if + n_rc);
   pd.frow = reinterpret_cast<const int*>(db + n_mi + n_if + 2 * n_rc);
   pd.hrow = reinterpret_cast<const int*>(db + n_mi + n_if + 2 * n_rc + n_fr);
+  {
+    const double* ft = reinterpret_cast<const double*>(db + n_mi + n_if + 2 * n_rc + n_fr + n_hr);
+    fft.tw1 = ft;
+    fft.tw3 = ft + 2 * fft.n1;
+    fft.gpow = ft + 2 * fft.n1 + 2 * fft.n3;
+  }
 
   fmm_plan_s* P = new (std::nothrow) fmm_plan_s();
   if (!P) {
@@ -320,6 +362,7 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   P->desc = *desc;
   P->desc.pde = nullptr;
   P->pd = pd;
+  P->fft = fft;
   P->dev_tables = dt;
   *out = P;
   return FMM_OK;

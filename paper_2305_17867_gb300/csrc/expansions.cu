@@ -502,15 +502,21 @@ __global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __rest
 
 }  // namespace
 
+bool m2l_shared_tables(const fmm_plan_s* P) {
+  const int prec = P->desc.precision;
+  const bool tc = prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3;
+  const bool fft = P->desc.m2l == FMM_M2L_FFT;
+  return (tc || fft) && P->pd.d == 3 && P->pd.kernel != FMM_KERNEL_YUKAWA;
+}
+
 cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
                                 int* nl) {
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels;
   const size_t smem = sizeof(double) * pd.nh * 2;
-  // the tensor-core M2L of a homogeneous kernel reads only level 2's table
-  const int prec = P->desc.precision;
-  const bool tc = prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3;
-  const int nlev = (tc && pd.d == 3 && pd.kernel != FMM_KERNEL_YUKAWA) ? 1 : L - 1;
+  // the tensor-core and FFT forms of M2L read only level 2's table for a
+  // homogeneous kernel
+  const int nlev = m2l_shared_tables(P) ? 1 : L - 1;
   if (pd.d == 3) {
     set_smem(k_deriv_tables<3>, smem);
     k_deriv_tables<3><<<nlev * 343, 128, smem, st>>>(pd, ws.geom, ws.htab);

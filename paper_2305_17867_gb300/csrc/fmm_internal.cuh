@@ -55,9 +55,24 @@ struct PlanDev {
   const int* hrow;         // Hankel layout row bases: [m_s*(2p+1) + m_1]  (d=2: [m_s])
 };
 
+// Transform sizes and tables of the FFT form of M2L (eq. (convolution_m2l)).
+// Axis a of the coefficient grid (a = 0: m_0, 1: m_1 (d = 3), 2: m_s) has
+// length n_a = 2 M_a + 1 with M = (p, p, c - 1) (d = 2: (p, 1, c - 1)); the
+// spectra keep the Hermitian half k_0 = 0..p of the m_0 axis.
+struct FftDev {
+  int n1, n2, n3;      // transform lengths along m_0, m_1 (1 when d = 2), m_s
+  int k1;              // p + 1 stored frequencies along m_0
+  int kf;              // k1 * n2 * n3 complex values per spectrum
+  int kfp;             // kf rounded up to a multiple of 32 (row stride)
+  const double* tw1;   // n1 x (cos, sin)(2 pi n / n1); also serves axis 1 (n2 = n1 or 1)
+  const double* tw3;   // n3 x (cos, sin)(2 pi n / n3)
+  const double* gpow;  // g^n and g^-n, n = 0..2p (2 x (2p + 1))
+};
+
 struct fmm_plan_s {
   fmm_plan_desc desc;
   PlanDev pd;
+  FftDev fft;
   void* dev_tables;
   int timing;
   cudaEvent_t ev[FMM_NUM_PHASES + 1];
@@ -109,6 +124,11 @@ struct Workspace {
   int tc_mp;        // |j| padded to a multiple of 128 (M)
   void* tc_bpar[2];
   void* tc_tmat[2];
+  // FFT form of M2L: spectra of the multipoles and of the local sums of every
+  // box of levels 2..L (kfp complex each) and of the offset tables
+  void* fft_b;
+  void* fft_g;
+  void* fft_h;
   // FP32 leaf path: box-relative coordinates (x - c_own)/s and weight, and the
   // decompressed far-field coefficients M Lt / m! of every leaf
   float4* sxr;
@@ -135,6 +155,11 @@ cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaSt
 cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
 cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
 cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
+cudaError_t launch_m2l_fft(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
+                           int* nlaunch);
+// offset tables of the M2L derivative tables: one level suffices when the
+// kernel is homogeneous (3D Laplace, biharmonic) and the M2L path rescales
+bool m2l_shared_tables(const fmm_plan_s* P);
 cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
 cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* phi,
                              double* grad, cudaStream_t st, int* nlaunch);

@@ -146,6 +146,7 @@ cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   const int L = P->desc.levels;
   cudaMemsetAsync(ws.lc, 0, sizeof(double) * (size_t)ws.lev_off[L + 1] * P->pd.nj, st);
   const int prec = P->desc.precision;
+  if (P->desc.m2l == FMM_M2L_FFT) return launch_m2l_fft(P, ws, st, nl);
   if (prec == FMM_PREC_FP64 || prec == FMM_PREC_FP32) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
   return launch_m2l_tc(P, ws, st, nl);
 }

@@ -13,7 +13,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import KERNELS, PRECISIONS, PlanDesc, Pde, check
+from ._lib import KERNELS, M2L_PATHS, PRECISIONS, PlanDesc, Pde, check
 
 
 def _ptr(t):
@@ -27,16 +27,19 @@ class FMM:
     p          expansion order;  levels: leaf depth L of the uniform tree
     root_lo, root_size  root box; root_size <= 0 picks the bounding cube per call
     precision  "fp64" | "fp32" | "tf32" | "tf32x3" | "bf16x3"
+    m2l        "dense" (eq. (m2l_toeplitz) as dense products) | "fft" (its
+               convolution form, eq. (convolution_m2l); fp64 and fp32 only)
     pde        optional (multi_idx [n,d] ints, coeff [n] floats) overriding the
                kernel's own PDE (eq. (define_pde_op))
     """
 
     def __init__(self, kernel: str = "laplace", d: int = 3, p: int = 10, levels: int = 5,
                  lam: float = 0.0, root_lo=None, root_size: float = 1.0,
-                 precision: str = "fp64", pde=None, device=None):
+                 precision: str = "fp64", pde=None, device=None, m2l: str = "dense"):
         self.L = _lib.load()
         self.kernel, self.d, self.p, self.levels, self.lam = kernel, d, p, levels, lam
         self.precision = precision
+        self.m2l = m2l
         self.device = torch.device("cuda" if device is None else device)
         desc = PlanDesc()
         desc.kernel = KERNELS[kernel]
@@ -46,6 +49,7 @@ class FMM:
         desc.root_lo = (ctypes.c_double * 3)(*lo)
         desc.root_size = float(root_size)
         desc.precision = PRECISIONS[precision]
+        desc.m2l = M2L_PATHS[m2l]
         self._pde_keep = None
         if pde is not None:
             mi, co = pde

@@ -41,3 +41,29 @@ def test_status_strings_without_gpu():
     L = _lib.load()
     assert L.fmm_status_string(0) == b"ok"
     assert L.fmm_status_string(-6).startswith(b"point outside")
+
+
+def test_plan_validation_without_gpu():
+    # descriptions that fmm_plan_create rejects before any CUDA call
+    from paper_2305_17867_gb300 import _lib
+
+    L = _lib.load()
+
+    def create(**kw):
+        d = _lib.PlanDesc()
+        d.kernel, d.d, d.p, d.levels, d.root_size = 0, 3, 8, 3, 1.0
+        for k, v in kw.items():
+            setattr(d, k, v)
+        h = ctypes.c_void_p()
+        rc = L.fmm_plan_create(ctypes.byref(h), ctypes.byref(d))
+        assert not h.value
+        return rc
+
+    for prec in (2, 3, 4):  # tensor-core formats have no FFT form
+        assert create(precision=prec, m2l=1) == -2
+    assert create(m2l=2) == -1
+    assert create(precision=7) == -1
+    assert create(p=0) == -1
+    assert create(levels=1) == -1
+    assert create(kernel=1, lam=0.0) == -1  # Yukawa needs lambda > 0
+    assert create(kernel=2, d=2) == -2      # biharmonic only in 3D
