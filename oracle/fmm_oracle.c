@@ -33,6 +33,10 @@
  *  R7  Uniform tree: leaf depth L, root = level 0; M2L at levels 2..L over
  *      the interaction list (List 2): children of the parent's neighbours
  *      (parent included) that are not adjacent to the box.
+ *  R15 Adaptive tree: a box splits while it holds more than max_leaf points
+ *      (sources plus targets) and is above max_depth; empty children are not
+ *      created; lists U, V, W, X as defined above or_fmm_adaptive (the paper
+ *      only cites the adaptive FMM it builds on).
  */
 #define _GNU_SOURCE
 #include <math.h>
@@ -973,6 +977,373 @@ int or_fmm_uniform(int kernel, int d, double lam, int p, int L, int compressed,
   free(tbox);
   free(sstart);
   free(sidx);
+  or_expansion_free(e);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adaptive-tree FMM (reading R15).  The tree refines a box of the root cube  */
+/* while it holds more than max_leaf points (sources plus targets) and its    */
+/* level is below max_depth; children that would hold no point are not       */
+/* created.  "Adjacent" means the closed boxes touch or coincide.  For a box  */
+/* B of level l with parent P(B), the interaction lists are, by definition    */
+/* (the classical adaptive FMM; the paper's List 2 is V):                     */
+/*   U(B), B a leaf: the leaves adjacent to B, B included         -> P2P      */
+/*   V(B), l >= 2:   boxes C of level l with P(C) adjacent to P(B) and C not  */
+/*                   adjacent to B                                -> M2L      */
+/*   W(B), B a leaf: boxes C with level(C) > l, P(C) adjacent to B and C not  */
+/*                   adjacent to B                                -> M2P      */
+/*   X(B), l >= 2:   leaves A with level(A) < l, A adjacent to P(B) and A not */
+/*                   adjacent to B (exactly the A with B in W(A)) -> P2L      */
+/* Local expansions live at levels >= 2: L2L from the parent, plus M2L over V */
+/* and P2L over X.  Every leaf evaluates L2P, P2P over U and M2P over W.      */
+/* The lists are found by testing their definitions against every box.       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int level, leaf;
+  int64_t c[OR_MAXD];
+  int64_t parent;
+  int64_t s0, s1, t0, t1; /* ranges in the Morton-sorted source / target orders */
+} or_abox;
+
+static int or_abox_adjacent(int d, const or_abox* A, const or_abox* B) {
+  int m = A->level > B->level ? A->level : B->level;
+  for (int k = 0; k < d; ++k) {
+    int64_t a0 = A->c[k] << (m - A->level), a1 = (A->c[k] + 1) << (m - A->level);
+    int64_t b0 = B->c[k] << (m - B->level), b1 = (B->c[k] + 1) << (m - B->level);
+    if (a0 > b1 || b0 > a1) return 0;
+  }
+  return 1;
+}
+
+static void or_abox_center(int d, const double* lo, double size, const or_abox* B, double* c) {
+  double s = size / (double)((int64_t)1 << B->level);
+  for (int k = 0; k < d; ++k) c[k] = lo[k] + (B->c[k] + 0.5) * s;
+}
+
+/* Morton key of a point at depth D (per level, the bit of axis k at position k). */
+static int or_morton(int d, int D, const double* lo, double size, const double* x,
+                     uint64_t* key) {
+  int64_t n = (int64_t)1 << D;
+  double s = size / (double)n;
+  int64_t kc[OR_MAXD];
+  for (int k = 0; k < d; ++k) {
+    double t = (x[k] - lo[k]) / s;
+    if (!(t >= 0.0) || t > (double)n) return OR_ERR_DOMAIN;
+    int64_t b = (int64_t)floor(t);
+    if (b >= n) b = n - 1;
+    kc[k] = b;
+  }
+  uint64_t m = 0;
+  for (int b = D - 1; b >= 0; --b) {
+    uint64_t dig = 0;
+    for (int k = 0; k < d; ++k) dig |= (uint64_t)((kc[k] >> b) & 1) << k;
+    m = (m << d) | dig;
+  }
+  *key = m;
+  return OR_OK;
+}
+
+typedef struct {
+  uint64_t key;
+  int64_t idx;
+} or_keyed;
+
+static int or_keyed_cmp(const void* a, const void* b) {
+  const or_keyed* x = (const or_keyed*)a;
+  const or_keyed* y = (const or_keyed*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static int or_sort_points(int d, int D, const double* lo, double size, int64_t n,
+                          const double* x, or_keyed* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    out[i].idx = i;
+    if (or_morton(d, D, lo, size, x + i * d, &out[i].key) != OR_OK) return OR_ERR_DOMAIN;
+  }
+  qsort(out, (size_t)n, sizeof(or_keyed), or_keyed_cmp);
+  return OR_OK;
+}
+
+/* Adaptive FMM (3D and 2D).  If nsample > 0 only the listed targets are
+ * evaluated (outputs in sample order).  stats (optional, 8 entries): boxes,
+ * leaves, deepest level, then |U|, |V|, |W|, |X| summed over the boxes that
+ * the evaluated targets use.  cover (optional, one per evaluated target):
+ * the number of sources the lists of that target's leaf and ancestors reach,
+ * with multiplicity (exactly n_src when every pair is covered once and no
+ * source coincides with the target). */
+int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_depth,
+                    const double* lo, double size, int64_t nsrc, const double* src,
+                    const double* w, int64_t ntgt, const double* tgt, int64_t nsample,
+                    const int64_t* sample, double* phi, int64_t* stats, double* cover) {
+  if (d < 2 || d > 3 || p < 0 || max_leaf < 1 || max_depth < 0 || max_depth > 20 ||
+      size <= 0.0)
+    return OR_ERR_ARG;
+  double acoef[64];
+  int c = or_pde_for_kernel(kernel, d, lam, acoef);
+  if (c < 0) return OR_ERR_UNSUPPORTED;
+  const int D = max_depth, nch = 1 << d;
+  or_keyed* ss = (or_keyed*)malloc(sizeof(or_keyed) * (nsrc > 0 ? nsrc : 1));
+  or_keyed* ts = (or_keyed*)malloc(sizeof(or_keyed) * (ntgt > 0 ? ntgt : 1));
+  if (or_sort_points(d, D, lo, size, nsrc, src, ss) != OR_OK ||
+      or_sort_points(d, D, lo, size, ntgt, tgt, ts) != OR_OK) {
+    free(ss);
+    free(ts);
+    return OR_ERR_DOMAIN;
+  }
+
+  /* tree, breadth first (children appended in Morton order) */
+  int64_t cap = 1024, nbox = 1;
+  or_abox* bx = (or_abox*)malloc(sizeof(or_abox) * cap);
+  memset(&bx[0], 0, sizeof(or_abox));
+  bx[0].parent = -1;
+  bx[0].s1 = nsrc;
+  bx[0].t1 = ntgt;
+  int maxlev = 0;
+  for (int64_t b = 0; b < nbox; ++b) {
+    int64_t npt = (bx[b].s1 - bx[b].s0) + (bx[b].t1 - bx[b].t0);
+    if (npt <= max_leaf || bx[b].level >= D) {
+      bx[b].leaf = 1;
+      continue;
+    }
+    const int shift = d * (D - bx[b].level - 1);
+    int64_t si = bx[b].s0, ti = bx[b].t0;
+    for (int ci = 0; ci < nch; ++ci) {
+      int64_t s0 = si, t0 = ti;
+      while (si < bx[b].s1 && (int)((ss[si].key >> shift) & (uint64_t)(nch - 1)) == ci) ++si;
+      while (ti < bx[b].t1 && (int)((ts[ti].key >> shift) & (uint64_t)(nch - 1)) == ci) ++ti;
+      if (si == s0 && ti == t0) continue;
+      if (nbox == cap) {
+        cap *= 2;
+        bx = (or_abox*)realloc(bx, sizeof(or_abox) * cap);
+      }
+      or_abox* ch = &bx[nbox++];
+      memset(ch, 0, sizeof(or_abox));
+      ch->level = bx[b].level + 1;
+      for (int k = 0; k < d; ++k) ch->c[k] = 2 * bx[b].c[k] + ((ci >> k) & 1);
+      ch->parent = b;
+      ch->s0 = s0;
+      ch->s1 = si;
+      ch->t0 = t0;
+      ch->t1 = ti;
+      if (ch->level > maxlev) maxlev = ch->level;
+    }
+  }
+  /* leaf of every sorted target position */
+  int64_t* tleaf = (int64_t*)malloc(sizeof(int64_t) * (ntgt > 0 ? ntgt : 1));
+  int64_t* tpos = (int64_t*)malloc(sizeof(int64_t) * (ntgt > 0 ? ntgt : 1));
+  for (int64_t b = 0; b < nbox; ++b)
+    if (bx[b].leaf)
+      for (int64_t t = bx[b].t0; t < bx[b].t1; ++t) tleaf[t] = b;
+  for (int64_t t = 0; t < ntgt; ++t) tpos[ts[t].idx] = t;
+
+  or_expansion* e = or_expansion_new(d, p, c, acoef, 1);
+  const int nj = e->nj;
+  const size_t nbx = (size_t)(nbox > 0 ? nbox : 1);
+  double* mp = (double*)calloc(nbx * nj, sizeof(double));
+  double* lc = (double*)calloc(nbx * nj, sizeof(double));
+  char* need = (char*)calloc(nbx, 1);
+  double* vxcov = (double*)calloc(nbx, sizeof(double));
+  int64_t cnt[4] = {0, 0, 0, 0};
+
+  const int64_t neval = nsample > 0 ? nsample : ntgt;
+  for (int64_t t = 0; t < neval; ++t) {
+    int64_t it = nsample > 0 ? sample[t] : t;
+    for (int64_t b = tleaf[tpos[it]]; b >= 0; b = bx[b].parent) need[b] = 1;
+  }
+
+  /* P2M at the leaves of level >= 2 (Sec. 3.4) */
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t b = 0; b < nbox; ++b) {
+    if (!bx[b].leaf || bx[b].level < 2 || bx[b].s1 == bx[b].s0) continue;
+    int64_t n = bx[b].s1 - bx[b].s0;
+    double* ys = (double*)malloc(sizeof(double) * n * d);
+    double* ws = (double*)malloc(sizeof(double) * n);
+    for (int64_t q = 0; q < n; ++q) {
+      int64_t i = ss[bx[b].s0 + q].idx;
+      for (int k = 0; k < d; ++k) ys[q * d + k] = src[i * d + k];
+      ws[q] = w[i];
+    }
+    double cb[OR_MAXD];
+    or_abox_center(d, lo, size, &bx[b], cb);
+    or_p2m(e, cb, n, ys, ws, mp + (size_t)b * nj);
+    free(ys);
+    free(ws);
+  }
+  /* M2M, deepest level first (Sec. 4.3); a parent sums its children */
+  for (int l = maxlev; l >= 3; --l) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t b = 0; b < nbox; ++b) {
+      if (bx[b].level != l) continue;
+      int64_t pb = bx[b].parent;
+      double cp[OR_MAXD], cb[OR_MAXD], h[OR_MAXD];
+      or_abox_center(d, lo, size, &bx[pb], cp);
+      or_abox_center(d, lo, size, &bx[b], cb);
+      for (int k = 0; k < d; ++k) h[k] = cp[k] - cb[k];
+      double* psi = (double*)malloc(sizeof(double) * nj);
+      or_m2m(e, h, mp + (size_t)b * nj, psi);
+#pragma omp critical
+      for (int t = 0; t < nj; ++t) mp[(size_t)pb * nj + t] += psi[t];
+      free(psi);
+    }
+  }
+
+  /* M2L derivative tables per level and offset in [-3,3]^d (Sec. 4.1) */
+  int noff = 1;
+  for (int k = 0; k < d; ++k) noff *= 7;
+  const int n2 = or_num_terms(d, 2 * p);
+  double* D2 = (double*)calloc((size_t)(maxlev + 1) * noff * n2, sizeof(double));
+  for (int l = 2; l <= maxlev; ++l) {
+    double s = size / (double)((int64_t)1 << l);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int o = 0; o < noff; ++o) {
+      int t = o, far = 0;
+      double hv[OR_MAXD];
+      for (int k = 0; k < d; ++k) {
+        int oc = t % 7 - 3;
+        t /= 7;
+        if (oc > 1 || oc < -1) far = 1;
+        hv[k] = oc * s;
+      }
+      if (far) or_derivatives(kernel, d, lam, 2 * p, hv, D2 + ((size_t)l * noff + o) * n2);
+    }
+  }
+
+  /* local expansions, coarse to fine: L2L + M2L over V + P2L over X */
+  for (int l = 2; l <= maxlev; ++l) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t b = 0; b < nbox; ++b) {
+      if (bx[b].level != l || !need[b]) continue;
+      double cb[OR_MAXD];
+      or_abox_center(d, lo, size, &bx[b], cb);
+      double* Lb = lc + (size_t)b * nj;
+      const int64_t pb = bx[b].parent;
+      if (bx[pb].level >= 2) {
+        double cp[OR_MAXD], h[OR_MAXD];
+        or_abox_center(d, lo, size, &bx[pb], cp);
+        for (int k = 0; k < d; ++k) h[k] = cb[k] - cp[k];
+        or_l2l(e, h, lc + (size_t)pb * nj, Lb);
+      }
+      int64_t nv = 0, nx = 0;
+      double cov = 0.0;
+      for (int64_t a = 0; a < nbox; ++a) {
+        const or_abox* A = &bx[a];
+        if (A->level == l && a != b && A->parent >= 0 &&
+            or_abox_adjacent(d, &bx[A->parent], &bx[pb]) && !or_abox_adjacent(d, A, &bx[b])) {
+          /* V: M2L (eq. (m2l_toeplitz)) */
+          int o = 0;
+          for (int k = d - 1; k >= 0; --k) o = o * 7 + (int)(bx[b].c[k] - A->c[k] + 3);
+          or_m2l(e, D2 + ((size_t)l * noff + o) * n2, mp + (size_t)a * nj, Lb);
+          cov += (double)(A->s1 - A->s0);
+          ++nv;
+        } else if (A->leaf && A->level < l && or_abox_adjacent(d, A, &bx[pb]) &&
+                   !or_abox_adjacent(d, A, &bx[b])) {
+          /* X: P2L (eq. (stored_local_coeffs)) */
+          int64_t n = A->s1 - A->s0;
+          if (n > 0) {
+            double* ys = (double*)malloc(sizeof(double) * n * d);
+            double* ws = (double*)malloc(sizeof(double) * n);
+            for (int64_t q = 0; q < n; ++q) {
+              int64_t i = ss[A->s0 + q].idx;
+              for (int k = 0; k < d; ++k) ys[q * d + k] = src[i * d + k];
+              ws[q] = w[i];
+            }
+            or_p2l(e, kernel, lam, cb, n, ys, ws, Lb);
+            free(ys);
+            free(ws);
+          }
+          cov += (double)n;
+          ++nx;
+        }
+      }
+      vxcov[b] = cov + vxcov[pb];
+#pragma omp atomic
+      cnt[1] += nv;
+#pragma omp atomic
+      cnt[3] += nx;
+    }
+  }
+
+  /* leaves: L2P + P2P over U + M2P over W */
+  char* leafdone = (char*)calloc(nbx, 1);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t t = 0; t < neval; ++t) {
+    int64_t it = nsample > 0 ? sample[t] : t;
+    const int64_t b = tleaf[tpos[it]];
+    const or_abox* B = &bx[b];
+    const double* x = tgt + it * d;
+    double cb[OR_MAXD];
+    or_abox_center(d, lo, size, B, cb);
+    double acc = B->level >= 2 ? or_l2p(e, cb, lc + (size_t)b * nj, x, NULL) : 0.0;
+    double cov = B->level >= 2 ? vxcov[b] : 0.0;
+    int64_t nu = 0, nw = 0;
+    for (int64_t a = 0; a < nbox; ++a) {
+      const or_abox* A = &bx[a];
+      if (A->leaf && or_abox_adjacent(d, A, B)) {
+        for (int64_t q = A->s0; q < A->s1; ++q) {
+          int64_t is = ss[q].idx;
+          double r[OR_MAXD];
+          int same = 1;
+          for (int k = 0; k < d; ++k) {
+            r[k] = x[k] - src[is * d + k];
+            same &= (r[k] == 0.0);
+          }
+          if (same) continue;
+          acc += or_green(kernel, d, lam, r) * w[is];
+          cov += 1.0;
+        }
+        ++nu;
+      } else if (A->level > B->level && A->parent >= 0 &&
+                 or_abox_adjacent(d, &bx[A->parent], B) && !or_abox_adjacent(d, A, B)) {
+        double ca[OR_MAXD];
+        or_abox_center(d, lo, size, A, ca);
+        acc += or_m2p(e, kernel, lam, ca, mp + (size_t)a * nj, x);
+        cov += (double)(A->s1 - A->s0);
+        ++nw;
+      }
+    }
+    phi[t] = acc;
+    if (cover) cover[t] = cov;
+    int first = 0;
+#pragma omp critical
+    {
+      if (!leafdone[b]) {
+        leafdone[b] = 1;
+        first = 1;
+      }
+    }
+    if (first) {
+#pragma omp atomic
+      cnt[0] += nu;
+#pragma omp atomic
+      cnt[2] += nw;
+    }
+  }
+  if (stats) {
+    int64_t nleaf = 0;
+    for (int64_t b = 0; b < nbox; ++b) nleaf += bx[b].leaf;
+    stats[0] = nbox;
+    stats[1] = nleaf;
+    stats[2] = maxlev;
+    stats[3] = cnt[0];
+    stats[4] = cnt[1];
+    stats[5] = cnt[2];
+    stats[6] = cnt[3];
+    stats[7] = 0;
+  }
+  free(leafdone);
+  free(D2);
+  free(mp);
+  free(lc);
+  free(need);
+  free(vxcov);
+  free(tleaf);
+  free(tpos);
+  free(bx);
+  free(ss);
+  free(ts);
   or_expansion_free(e);
   return OR_OK;
 }

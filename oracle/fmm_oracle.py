@@ -87,6 +87,9 @@ def lib():
             L.or_fmm_uniform.argtypes = [i32, i32, f64, i32, i32, i32, vp, f64,
                                          i64, vp, vp, i64, vp, i64, vp, vp, vp]
             L.or_fmm_uniform.restype = i32
+            L.or_fmm_adaptive.argtypes = [i32, i32, f64, i32, i32, i32, vp, f64,
+                                          i64, vp, vp, i64, vp, i64, vp, vp, vp, vp]
+            L.or_fmm_adaptive.restype = i32
             L.or_num_threads.restype = i32
             L.or_set_num_threads.argtypes = [i32]
             _LIB = L
@@ -263,6 +266,31 @@ def fmm_uniform(kernel: str, d: int, p: int, L: int, src, w, tgt, lo=None,
     if rc != 0:
         raise ValueError(f"oracle FMM failed with status {rc}")
     return (phi, g) if grad else phi
+
+
+def fmm_adaptive(kernel: str, d: int, p: int, src, w, tgt, max_leaf: int = 64,
+                 max_depth: int = 10, lo=None, size: float = 1.0, lam: float = 0.0,
+                 sample=None, want_stats: bool = False):
+    """Adaptive-tree FMM (U/V/W/X lists).  Returns phi, or (phi, stats, cover)
+    with stats = dict(boxes, leaves, depth, U, V, W, X) and cover = sources
+    reached per evaluated target (with multiplicity)."""
+    src, w, tgt = _f64(src), _f64(w), _f64(tgt)
+    lo = _f64(np.zeros(d) if lo is None else lo)
+    ns = 0 if sample is None else len(sample)
+    samp = None if sample is None else np.ascontiguousarray(sample, dtype=np.int64)
+    nout = ns if ns else tgt.shape[0]
+    phi = np.zeros(nout)
+    st = np.zeros(8, dtype=np.int64)
+    cov = np.zeros(nout)
+    rc = lib().or_fmm_adaptive(KERNELS[kernel], d, lam, p, max_leaf, max_depth, _p(lo),
+                               float(size), src.shape[0], _p(src), _p(w), tgt.shape[0],
+                               _p(tgt), ns, _p(samp), _p(phi), _p(st), _p(cov))
+    if rc != 0:
+        raise ValueError(f"oracle adaptive FMM failed with status {rc}")
+    if not want_stats:
+        return phi
+    keys = ["boxes", "leaves", "depth", "U", "V", "W", "X"]
+    return phi, dict(zip(keys, [int(v) for v in st[:7]])), cov
 
 
 def num_threads() -> int:
