@@ -97,13 +97,17 @@ typedef struct {
   double lambda;       /* Yukawa screening; ignored otherwise */
   int d;               /* 2 or 3 */
   int p;               /* expansion order, 1..24 */
-  int levels;          /* leaf depth L of the uniform tree, 2..7 (root = 0) */
+  int levels;          /* > 0: leaf depth L of the uniform tree, 2..7 (root = 0);
+                          < 0: adaptive tree (3D, FP64) refined down to at most
+                          level -levels (1..10) */
   const fmm_pde* pde;  /* NULL: the kernel's own PDE */
   double root_lo[3];   /* lower corner of the root box */
   double root_size;    /* side of the root box; <= 0: bounding cube of the
                           sources and targets, found on the device per call */
   int precision;       /* FMM_PREC_* */
   int m2l;             /* FMM_M2L_*; FFT requires precision FP64 or FP32 */
+  int max_leaf;        /* adaptive tree: a box holding more than max_leaf points
+                          (sources plus targets) is split; ignored when levels > 0 */
 } fmm_plan_desc;
 
 /* Create a plan: validates the description, builds the stored set j, the
@@ -123,7 +127,14 @@ int fmm_plan_info(fmm_plan_t plan, int* nfull, int* nj, int* c);
  * point counts.  The workspace must be 256-byte aligned. */
 int fmm_workspace_size(fmm_plan_t plan, int64_t n_src, int64_t n_tgt, size_t* bytes);
 
-/* Evaluate phi (and, if grad_dev != NULL, grad phi) at the targets:
+/* Evaluate phi (and, if grad_dev != NULL, grad phi) at the targets.
+ * Adaptive plans (levels < 0) build the tree on the device level by level
+ * and synchronise `stream` once per level to size the next one (so the call
+ * returns after the tree is built); they compute phi only (grad_dev must be
+ * NULL, else FMM_ERR_UNSUPPORTED) and return FMM_ERR_WORKSPACE if the tree
+ * outgrows the workspace (it cannot when the workspace has the size
+ * fmm_workspace_size reports, which bounds the number of boxes).
+ * Arguments:
  *   src_dev  n_src x d   source positions        (device, float64)
  *   w_dev    n_src       source weights          (device, float64)
  *   tgt_dev  n_tgt x d   target positions        (device, float64); may equal src_dev
@@ -188,6 +199,10 @@ int fmm_phase_times(fmm_plan_t plan, float* ms_out /* FMM_NUM_PHASES */);
  * -- in the last evaluation made with timing enabled; excludes the zeroing of
  * the local expansions and the operand packing.  Synchronises. */
 int fmm_m2l_kernel_time(fmm_plan_t plan, float* ms_out);
+
+/* Tree of the last evaluation: number of boxes (all levels) and deepest
+ * level.  Uniform plans report their fixed tree.  Any pointer may be NULL. */
+int fmm_last_tree(fmm_plan_t plan, int64_t* boxes_out, int* depth_out);
 
 /* Number of kernel launches the last fmm_eval enqueued. */
 int fmm_last_launch_count(fmm_plan_t plan);

@@ -37,7 +37,8 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("lam", ctypes.c_double), ("d", ctypes.c_int),
                 ("p", ctypes.c_int), ("levels", ctypes.c_int), ("pde", ctypes.POINTER(Pde)),
                 ("root_lo", ctypes.c_double * 3), ("root_size", ctypes.c_double),
-                ("precision", ctypes.c_int), ("m2l", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("m2l", ctypes.c_int),
+                ("max_leaf", ctypes.c_int)]
 
 
 _LIB = None
@@ -46,6 +47,7 @@ EXPORTS = [
     "fmm_plan_create", "fmm_plan_destroy", "fmm_plan_info", "fmm_workspace_size", "fmm_eval",
     "fmm_eval_backward", "fmm_last_status", "fmm_set_timing", "fmm_phase_times",
     "fmm_last_launch_count", "fmm_status_string", "fmm_eval_noalloc", "fmm_m2l_kernel_time",
+    "fmm_last_tree",
 ]
 
 
@@ -85,6 +87,8 @@ def load(build: bool = True):
     L.fmm_phase_times.restype = i32
     L.fmm_m2l_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.fmm_m2l_kernel_time.restype = i32
+    L.fmm_last_tree.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    L.fmm_last_tree.restype = i32
     L.fmm_last_launch_count.argtypes = [vp]
     L.fmm_last_launch_count.restype = i32
     L.fmm_status_string.argtypes = [i32]

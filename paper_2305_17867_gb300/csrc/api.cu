@@ -15,6 +15,7 @@
 #include <map>
 #include <vector>
 
+#include "adaptive.cuh"
 #include "fmm_internal.cuh"
 
 namespace {
@@ -110,8 +111,57 @@ int to_status(cudaError_t e) { return e == cudaSuccess ? FMM_OK : FMM_ERR_CUDA; 
 // ---------------------------------------------------------------------------
 // Workspace layout
 // ---------------------------------------------------------------------------
+// adaptive plans (levels < 0, 3D, FP64): points, sort scratch, Morton codes,
+// box arrays sized by the bound on the number of boxes, expansions per box
+static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt,
+                                     void* base, Workspace* ws) {
+  const int D = -P->desc.levels, nj = P->pd.nj, nh = P->pd.nh;
+  const int64_t nmax = std::max<int64_t>(std::max(n_src, n_tgt), 1);
+  const int64_t nblk = (nmax + 1023) / 1024;
+  const int64_t nb = adaptive_box_bound(n_src + n_tgt, P->desc.max_leaf, D);
+  char* cur = static_cast<char*>(base);
+  Workspace w{};
+  w.geom = carve<Geom>(cur, 1);
+  for (int k = 0; k < 3; ++k) w.sx[k] = carve<double>(cur, std::max<int64_t>(n_src, 1));
+  w.sw = carve<double>(cur, std::max<int64_t>(n_src, 1));
+  w.sperm = carve<int>(cur, std::max<int64_t>(n_src, 1));
+  for (int k = 0; k < 3; ++k) w.tx[k] = carve<double>(cur, std::max<int64_t>(n_tgt, 1));
+  w.tperm = carve<int>(cur, std::max<int64_t>(n_tgt, 1));
+  w.keys_a = carve<uint32_t>(cur, nmax);
+  w.keys_b = carve<uint32_t>(cur, nmax);
+  w.vals_a = carve<int>(cur, nmax);
+  w.vals_b = carve<int>(cur, nmax);
+  w.skey = carve<uint32_t>(cur, std::max<int64_t>(n_src, 1));
+  w.tkey = carve<uint32_t>(cur, std::max<int64_t>(n_tgt, 1));
+  const int64_t nhist = 256 * nblk;
+  const int64_t nscan = std::max<int64_t>(nhist, nb + 1);
+  w.hist = carve<int>(cur, nhist);
+  w.hist_sums = carve<int>(cur, (nscan + 1023) / 1024 + 1);
+  w.anb_cap = nb;
+  w.akey = carve<uint32_t>(cur, nb);
+  w.alev = carve<int>(cur, nb);
+  w.apar = carve<int>(cur, nb);
+  w.achild = carve<int>(cur, 8 * nb);
+  w.as0 = carve<int>(cur, nb);
+  w.as1 = carve<int>(cur, nb);
+  w.at0 = carve<int>(cur, nb);
+  w.at1 = carve<int>(cur, nb);
+  w.aleaf = carve<int>(cur, nb);
+  w.anch = carve<int>(cur, nb);
+  w.ascan = carve<int>(cur, nb + 1);
+  w.mp = carve<double>(cur, (size_t)nb * nj);
+  w.lc = carve<double>(cur, (size_t)nb * nj);
+  w.htab = carve<double>(cur, (size_t)std::max(D - 1, 1) * 343 * nh);
+  w.nbbox_blocks = (int)std::min<int64_t>(1024, (std::max(n_src, n_tgt) + 255) / 256 + 1);
+  w.bbox = carve<double>(cur, (size_t)2 * 3 * 2 * w.nbbox_blocks);
+  w.bytes = (size_t)(cur - static_cast<char*>(base));
+  if (ws) *ws = w;
+  return FMM_OK;
+}
+
 int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void* base,
                          Workspace* ws) {
+  if (P->desc.levels < 0) return workspace_layout_adaptive(P, n_src, n_tgt, base, ws);
   const int d = P->pd.d, L = P->desc.levels, nj = P->pd.nj, nh = P->pd.nh;
   const int64_t nleaf = nbox_at(d, L);
   const int64_t nmax = std::max<int64_t>(std::max(n_src, n_tgt), 1);
@@ -189,7 +239,13 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   const int d = desc->d, p = desc->p, L = desc->levels;
   if (d != 2 && d != 3) return FMM_ERR_ARG;
   if (p < 1 || p > FMM_MAXP) return FMM_ERR_ARG;
-  if (L < 2 || L > (d == 3 ? 7 : 8)) return FMM_ERR_ARG;
+  if (L < 0) {  // adaptive tree
+    if (-L > FMM_MAX_ADEPTH || desc->max_leaf < 1) return FMM_ERR_ARG;
+    if (d != 3 || desc->precision != FMM_PREC_FP64 || desc->m2l != FMM_M2L_DENSE)
+      return FMM_ERR_UNSUPPORTED;
+  } else if (L < 2 || L > (d == 3 ? 7 : 8)) {
+    return FMM_ERR_ARG;
+  }
   if (desc->precision < FMM_PREC_FP64 || desc->precision > FMM_PREC_BF16X3) return FMM_ERR_ARG;
   if (desc->m2l != FMM_M2L_DENSE && desc->m2l != FMM_M2L_FFT) return FMM_ERR_ARG;
   if (desc->m2l == FMM_M2L_FFT && desc->precision != FMM_PREC_FP64 &&
@@ -425,6 +481,17 @@ extern "C" int fmm_m2l_kernel_time(fmm_plan_t P, float* ms) {
   return FMM_OK;
 }
 
+extern "C" int fmm_last_tree(fmm_plan_t P, int64_t* boxes, int* depth) {
+  if (!P) return FMM_ERR_ARG;
+  const int L = P->desc.levels;
+  int64_t nb = 0;
+  if (L > 0)
+    for (int l = 0; l <= L; ++l) nb += nbox_at(P->pd.d, l);
+  if (boxes) *boxes = L > 0 ? nb : P->last_boxes;
+  if (depth) *depth = L > 0 ? L : P->last_depth;
+  return FMM_OK;
+}
+
 extern "C" int fmm_last_launch_count(fmm_plan_t P) { return P ? P->launches : -1; }
 
 // ---------------------------------------------------------------------------
@@ -446,6 +513,42 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
   auto mark = [&](int i) {
     if (P->timing) cudaEventRecord(P->ev[i], st);
   };
+  if (P->desc.levels < 0) {
+    if (grad) return FMM_ERR_UNSUPPORTED;
+    mark(0);
+    if ((e = launch_set_geom(P, ws, n_src, src, n_tgt, tgt, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+    ATree tree;
+    int overflow = 0;
+    if ((e = launch_build_adaptive(P, ws, n_src, src, w, n_tgt, tgt, st, &nl, &tree, &overflow)) !=
+        cudaSuccess)
+      return FMM_ERR_CUDA;
+    if (overflow) return FMM_ERR_WORKSPACE;
+    const int nbox = tree.loff[tree.maxlev + 1];
+    cudaMemsetAsync(ws.mp, 0, sizeof(double) * (size_t)nbox * P->pd.nj, st);
+    cudaMemsetAsync(ws.lc, 0, sizeof(double) * (size_t)nbox * P->pd.nj, st);
+    mark(1);
+    if (tree.maxlev >= 2) {
+      set_deriv_levels(P, tree.maxlev);
+      if ((e = launch_deriv_tables(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+    }
+    mark(2);
+    if ((e = launch_adaptive_upward(P, ws, tree, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+    mark(3);
+    mark(4);
+    if ((e = launch_adaptive_m2l(P, ws, tree, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+    mark(5);
+    if ((e = launch_adaptive_p2l_l2l(P, ws, tree, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+    mark(6);
+    if (n_tgt > 0 && (e = launch_adaptive_leaf(P, ws, tree, phi, st, &nl)) != cudaSuccess)
+      return FMM_ERR_CUDA;
+    mark(7);
+    P->last_stream = st;
+    P->last_geom = ws.geom;
+    P->launches = first ? nl : P->launches + nl;
+    P->last_boxes = nbox;
+    P->last_depth = tree.maxlev;
+    return FMM_OK;
+  }
   mark(0);
   if ((e = launch_set_geom(P, ws, n_src, src, n_tgt, tgt, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   if ((e = launch_build_tree(P, ws, n_src, src, w, n_tgt, tgt, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
@@ -487,6 +590,7 @@ extern "C" int fmm_eval_backward(fmm_plan_t P, int64_t n_src, const double* src,
                                  double* grad_tgt, void* workspace, size_t wbytes,
                                  void* stream) {
   if (!P) return FMM_ERR_ARG;
+  if (P->desc.levels < 0) return FMM_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int d = P->pd.d;
   int rc = FMM_OK;

@@ -1,6 +1,7 @@
 // Derivative tables (Sec. 4.4), P2M (Sec. 3.4), M2M (Sec. 4.3), L2L (Sec. 4.2).
 #include <algorithm>
 
+#include "adaptive.cuh"
 #include "expansions.cuh"
 
 namespace {
@@ -251,28 +252,16 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
 constexpr int kWarpTerms = 32;
 constexpr int kP2mWarps = 4;
 
+// body of the warp P2M for a box of centre c and side s with sources i0..i1
+// of the sorted arrays; writes the compressed box-scaled multipole to out
 template <int D, typename T, int NT>
-__global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
-    PlanDev pd, const Geom* __restrict__ g, int L, int64_t nleaf, const int* __restrict__ start,
-    const double* __restrict__ x0, const double* __restrict__ x1, const double* __restrict__ x2,
-    const double* __restrict__ w, const float4* __restrict__ rel, double* __restrict__ mp) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * kP2mWarps + warp;
-  if (b >= nleaf) return;
+__device__ void p2m_warp_body(const PlanDev& pd, const double* c, double s, int i0, int i1,
+                              const double* __restrict__ x0, const double* __restrict__ x1,
+                              const double* __restrict__ x2, const double* __restrict__ w,
+                              const float4* __restrict__ rel, T* pw, T* alpha, int lane,
+                              double* __restrict__ out) {
   const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
   const int P1 = p + 1;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const size_t per_warp = align_bytes<T>(sizeof(T) * (32 * D * P1 + nfull));
-  T* pw = reinterpret_cast<T*>(smraw + warp * per_warp);  // [32][D][p+1]
-  T* alpha = pw + 32 * D * P1;                            // [nfull]
-  const int i0 = start[b], i1 = start[b + 1];
-  if (i0 == i1) {
-    for (int q = lane; q < nj; q += 32) mp[(size_t)b * nj + q] = 0.0;
-    return;
-  }
-  int bc[3];
-  double c[3], s;
-  box_center<D>(g, L, b, bc, c, &s);
   const double inv_s = 1.0 / s;
   const int nt = (nfull + 31) / 32;
   T acc[NT];
@@ -336,7 +325,54 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
   }
   __syncwarp();
   compress_warp<T>(pd, alpha, s, lane);
-  for (int q = lane; q < nj; q += 32) mp[(size_t)b * nj + q] = (double)alpha[q];
+  for (int q = lane; q < nj; q += 32) out[q] = (double)alpha[q];
+}
+
+template <int D, typename T, int NT>
+__global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
+    PlanDev pd, const Geom* __restrict__ g, int L, int64_t nleaf, const int* __restrict__ start,
+    const double* __restrict__ x0, const double* __restrict__ x1, const double* __restrict__ x2,
+    const double* __restrict__ w, const float4* __restrict__ rel, double* __restrict__ mp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kP2mWarps + warp;
+  if (b >= nleaf) return;
+  const int nj = pd.nj;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const size_t per_warp = align_bytes<T>(sizeof(T) * (32 * D * (pd.p + 1) + pd.nfull));
+  T* pw = reinterpret_cast<T*>(smraw + warp * per_warp);  // [32][D][p+1]
+  T* alpha = pw + 32 * D * (pd.p + 1);                    // [nfull]
+  const int i0 = start[b], i1 = start[b + 1];
+  if (i0 == i1) {
+    for (int q = lane; q < nj; q += 32) mp[(size_t)b * nj + q] = 0.0;
+    return;
+  }
+  int bc[3];
+  double c[3], s;
+  box_center<D>(g, L, b, bc, c, &s);
+  p2m_warp_body<D, T, NT>(pd, c, s, i0, i1, x0, x1, x2, w, rel, pw, alpha, lane,
+                          mp + (size_t)b * nj);
+}
+
+// adaptive tree: one warp per leaf of level >= 2 with sources (FP64 inputs)
+template <typename T, int NT>
+__global__ void __launch_bounds__(32 * kP2mWarps) k_ap2m_warp(
+    PlanDev pd, const Geom* __restrict__ g, ATree t, const double* __restrict__ x0,
+    const double* __restrict__ x1, const double* __restrict__ x2, const double* __restrict__ w,
+    double* __restrict__ mp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = t.loff[2] + blockIdx.x * kP2mWarps + warp;
+  if (b >= t.loff[t.maxlev + 1]) return;
+  if (!t.leaf[b] || t.s1[b] == t.s0[b]) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const size_t per_warp = align_bytes<T>(sizeof(T) * (32 * 3 * (pd.p + 1) + pd.nfull));
+  T* pw = reinterpret_cast<T*>(smraw + warp * per_warp);
+  T* alpha = pw + 32 * 3 * (pd.p + 1);
+  int l, bc[3];
+  abox(t, b, &l, bc);
+  double c[3], s;
+  abox_center(g, l, bc, c, &s);
+  p2m_warp_body<3, T, NT>(pd, c, s, t.s0[b], t.s1[b], x0, x1, x2, w, nullptr, pw, alpha, lane,
+                          mp + (size_t)b * pd.nj);
 }
 
 // ---------------------------------------------------------------------------
@@ -349,12 +385,12 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
 // once with the parent's recurrence (M^T is linear).  One block per parent;
 // the 2^d children are shifted concurrently.
 // ---------------------------------------------------------------------------
+// body of M2M for a parent of side s: child ci's multipole is the row
+// crow[ci] of mpc (-1: no child, taken as zero); the result goes to out
 template <int D, typename T>
-__global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __restrict__ g, int l,
-                                                  const double* __restrict__ mpc,
-                                                  double* __restrict__ mpp) {
+__device__ void m2m_body(const PlanDev& pd, double s, const int64_t* crow,
+                         const double* __restrict__ mpc, double* __restrict__ out) {
   constexpr int NC = 1 << D;
-  const int b = blockIdx.x;
   const int p = pd.p, c = pd.c, nfull = pd.nfull, nj = pd.nj;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* bet = reinterpret_cast<T*>(smraw);  // NC * nj
@@ -362,21 +398,15 @@ __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __rest
   T* Y = X + NC * nj;                     // NC * nj  (D == 3)
   T* sig = Y + NC * nj;                   // nfull
   T* tab = sig + nfull;                   // 2 (sign) x (p+1): (+-1/2)^e / e!
-  int bc[3];
-  double cp[3], s;
-  box_center<D>(g, l, b, bc, cp, &s);
   if (threadIdx.x <= p) {
     double v = 1.0;
     for (int e = 1; e <= (int)threadIdx.x; ++e) v *= 0.5 / (double)e;
     tab[threadIdx.x] = (T)v;                                      // h = +1/2 (child bit 0)
     tab[(p + 1) + threadIdx.x] = (T)((threadIdx.x & 1) ? -v : v);  // h = -1/2 (child bit 1)
   }
-  const int nlc = 1 << (l + 1);
   for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
     const int ci = e / nj, q = e % nj;
-    int64_t cb = 0;
-    for (int k = D - 1; k >= 0; --k) cb = cb * nlc + (2 * bc[k] + ((ci >> k) & 1));
-    bet[e] = (T)mpc[(size_t)cb * nj + q];
+    bet[e] = crow[ci] >= 0 ? (T)mpc[(size_t)crow[ci] * nj + q] : (T)0;
   }
   __syncthreads();
   // x shift on the stored slabs: X[q] = sum_{t <= q0} f[t] bet[q - t]
@@ -421,7 +451,38 @@ __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __rest
   }
   __syncthreads();
   compress_smem<T>(pd, sig, s);
-  for (int q = threadIdx.x; q < nj; q += blockDim.x) mpp[(size_t)b * nj + q] = (double)sig[q];
+  for (int q = threadIdx.x; q < nj; q += blockDim.x) out[q] = (double)sig[q];
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __restrict__ g, int l,
+                                                  const double* __restrict__ mpc,
+                                                  double* __restrict__ mpp) {
+  constexpr int NC = 1 << D;
+  const int b = blockIdx.x;
+  int bc[3];
+  double cp[3], s;
+  box_center<D>(g, l, b, bc, cp, &s);
+  const int nlc = 1 << (l + 1);
+  int64_t crow[NC];
+  for (int ci = 0; ci < NC; ++ci) {
+    int64_t cb = 0;
+    for (int k = D - 1; k >= 0; --k) cb = cb * nlc + (2 * bc[k] + ((ci >> k) & 1));
+    crow[ci] = cb;
+  }
+  m2m_body<D, T>(pd, s, crow, mpc, mpp + (size_t)b * pd.nj);
+}
+
+// adaptive tree: one block per box of level l with children
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_am2m(PlanDev pd, const Geom* __restrict__ g,
+                                                   ATree t, int l, double* __restrict__ mp) {
+  const int b = t.loff[l] + blockIdx.x;
+  if (t.leaf[b]) return;
+  const double s = __ddiv_rn(g->size, (double)(1 << l));
+  int64_t crow[8];
+  for (int ci = 0; ci < 8; ++ci) crow[ci] = t.child[8 * b + ci];
+  m2m_body<3, T>(pd, s, crow, mp, mp + (size_t)b * pd.nj);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,21 +492,18 @@ __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __rest
 // (two sign variants), y (four variants) and the slow axis (eight children,
 // stored slabs only); the x and y partial shifts are shared by the children.
 // ---------------------------------------------------------------------------
+// body of L2L for a parent of side s with local row `par`: child ci receives
+// into row crow[ci] of lcc (-1: no child)
 template <int D, typename T>
-__global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __restrict__ g, int l,
-                                                  const double* __restrict__ lcp,
-                                                  double* __restrict__ lcc) {
-  const int b = blockIdx.x;
+__device__ void l2l_body(const PlanDev& pd, double s, const double* __restrict__ par,
+                         const int64_t* crow, double* __restrict__ lcc) {
   const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Dt = reinterpret_cast<T*>(smraw);       // nfull
   T* X = Dt + nfull;                          // 2 * nfull
   T* Y = X + 2 * nfull;                       // 4 * nfull (D == 3)
   T* tab = Y + (D == 3 ? 4 * nfull : 0);      // 2 x (p+1): (-+1/4)^e / e!
-  int bc[3];
-  double cp[3], s;
-  box_center<D>(g, l, b, bc, cp, &s);
-  for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = (T)lcp[(size_t)b * nj + q];
+  for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = (T)par[q];
   if (threadIdx.x <= p) {
     double v = 1.0;
     for (int e = 1; e <= (int)threadIdx.x; ++e) v *= 0.25 / (double)e;
@@ -482,9 +540,9 @@ __global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __rest
     Zin = Y;
   }
   constexpr int NC = 1 << D;
-  const int nlc = 1 << (l + 1);
   for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
     const int ci = e / nj, i = e % nj;
+    if (crow[ci] < 0) continue;
     const char4 m = pd.mi[i];
     const int i0 = m.x, i1 = D == 3 ? m.y : 0, is = D == 3 ? m.z : m.y;
     const T* gv = tab + ((ci >> (D - 1)) & 1) * (p + 1);
@@ -494,10 +552,42 @@ __global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __rest
       const int src = D == 3 ? pd.frow[qs * (p + 1) + i1] + i0 : pd.frow[qs] + i0;
       acc += gv[qs - is] * Zv[src];
     }
+    lcc[(size_t)crow[ci] * nj + i] += ldexp((double)acc, -(int)m.w);
+  }
+}
+
+template <int D, typename T>
+__global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __restrict__ g, int l,
+                                                  const double* __restrict__ lcp,
+                                                  double* __restrict__ lcc) {
+  constexpr int NC = 1 << D;
+  const int b = blockIdx.x;
+  int bc[3];
+  double cp[3], s;
+  box_center<D>(g, l, b, bc, cp, &s);
+  const int nlc = 1 << (l + 1);
+  int64_t crow[NC];
+  for (int ci = 0; ci < NC; ++ci) {
     int64_t cb = 0;
     for (int k = D - 1; k >= 0; --k) cb = cb * nlc + (2 * bc[k] + ((ci >> k) & 1));
-    lcc[(size_t)cb * nj + i] += ldexp((double)acc, -(int)m.w);
+    crow[ci] = cb;
   }
+  l2l_body<D, T>(pd, s, lcp + (size_t)b * pd.nj, crow, lcc);
+}
+
+// adaptive tree: one block per box of level l (>= 2) with children and targets
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_al2l(PlanDev pd, const Geom* __restrict__ g,
+                                                   ATree t, int l, double* __restrict__ lc) {
+  const int b = t.loff[l] + blockIdx.x;
+  if (t.leaf[b] || t.t1[b] == t.t0[b]) return;
+  const double s = __ddiv_rn(g->size, (double)(1 << l));
+  int64_t crow[8];
+  for (int ci = 0; ci < 8; ++ci) {
+    const int cb = t.child[8 * b + ci];
+    crow[ci] = (cb >= 0 && t.t1[cb] > t.t0[cb]) ? cb : -1;
+  }
+  l2l_body<3, T>(pd, s, lc + (size_t)b * pd.nj, crow, lc);
 }
 
 }  // namespace
@@ -516,7 +606,8 @@ cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaSt
   const size_t smem = sizeof(double) * pd.nh * 2;
   // the tensor-core and FFT forms of M2L read only level 2's table for a
   // homogeneous kernel
-  const int nlev = m2l_shared_tables(P) ? 1 : L - 1;
+  // adaptive plans: levels 2..deepest level of the current tree
+  const int nlev = L < 0 ? P->deriv_levels - 1 : (m2l_shared_tables(P) ? 1 : L - 1);
   if (pd.d == 3) {
     set_smem(k_deriv_tables<3>, smem);
     k_deriv_tables<3><<<nlev * 343, 128, smem, st>>>(pd, ws.geom, ws.htab);
@@ -633,6 +724,124 @@ cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
       if (f32) L2L_GO(2, float); else L2L_GO(2, double);
     }
 #undef L2L_GO
+    ++*nl;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive tree: P2L over X (eq. (stored_local_coeffs)) into every box of
+// level >= 2 that holds targets.  X(B) = the leaves coarser than B that are
+// adjacent to P(B) but not to B; each is a neighbour of B's ancestor at its
+// own level, so the block walks the 27 neighbours of every ancestor.  Threads
+// share the sources of each X leaf; every source adds w * Ht((c_B - y)/s)
+// to the box's local expansion (shared-memory atomics).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kAThreads = 64;
+
+__global__ void __launch_bounds__(kAThreads) k_ap2l(PlanDev pd, const Geom* __restrict__ g,
+                                                    ATree t, const double* __restrict__ sx0,
+                                                    const double* __restrict__ sx1,
+                                                    const double* __restrict__ sx2,
+                                                    const double* __restrict__ sw,
+                                                    double* __restrict__ lc) {
+  const int b = t.loff[2] + blockIdx.x;
+  if (b >= t.loff[t.maxlev + 1] || t.t1[b] == t.t0[b]) return;
+  const int nj = pd.nj;
+  int l, bc[3];
+  abox(t, b, &l, bc);
+  double cb[3], s;
+  abox_center(g, l, bc, cb, &s);
+  extern __shared__ __align__(16) double smd[];
+  double* Lacc = smd;
+  const int sl = min(pd.c, pd.p + 1) * (pd.p + 1);
+  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  double* S = smd + ((nj + 1) & ~1) + threadIdx.x * per;
+  for (int i = threadIdx.x; i < nj; i += blockDim.x) Lacc[i] = 0.0;
+  __syncthreads();
+  const double inv_s = 1.0 / s, lam = pd.lam * s, scale = deriv_scale(pd, s);
+  const int pc[3] = {bc[0] >> 1, bc[1] >> 1, bc[2] >> 1};
+  bool any = false;
+  for (int lp = l - 1; lp >= 0; --lp) {
+    const int a[3] = {bc[0] >> (l - lp), bc[1] >> (l - lp), bc[2] >> (l - lp)};
+    for (int nb = 0; nb < 27; ++nb) {
+      const int nc[3] = {a[0] + nb % 3 - 1, a[1] + (nb / 3) % 3 - 1, a[2] + nb / 9 - 1};
+      const int A = alookup(t, lp, nc);
+      if (A < 0 || !t.leaf[A]) continue;
+      if (!aadjacent(lp, nc, l - 1, pc) || aadjacent(lp, nc, l, bc)) continue;
+      any = true;
+      for (int q = t.s0[A] + threadIdx.x; q < t.s1[A]; q += blockDim.x) {
+        const double x[3] = {(cb[0] - sx0[q]) * inv_s, (cb[1] - sx1[q]) * inv_s,
+                             (cb[2] - sx2[q]) * inv_s};
+        deriv_point(pd, x, lam, scale * sw[q], S, sl,
+                    [&](int pos, double v) { atomicAdd(&Lacc[pos], v); });
+      }
+    }
+  }
+  if (!any) return;  // block-uniform
+  __syncthreads();
+  for (int i = threadIdx.x; i < nj; i += blockDim.x) lc[(size_t)b * nj + i] += Lacc[i];
+}
+
+}  // namespace
+
+cudaError_t launch_adaptive_upward(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                   cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  const int nbox = t.loff[t.maxlev + 1];
+  if (t.maxlev < 2) return cudaGetLastError();
+  // P2M at the leaves of level >= 2 (warp per leaf)
+  {
+    const int n = nbox - t.loff[2];
+    const size_t pwb = align_bytes<double>(sizeof(double) * (32 * 3 * (pd.p + 1) + pd.nfull));
+    const size_t sm2 = pwb * kP2mWarps;
+    const unsigned nb = (unsigned)((n + kP2mWarps - 1) / kP2mWarps);
+    const int ntl = (pd.nfull + 31) / 32;
+#define AP2M(NTT)                                                                          \
+  do {                                                                                     \
+    set_smem(k_ap2m_warp<double, NTT>, sm2);                                               \
+    k_ap2m_warp<double, NTT><<<nb, 32 * kP2mWarps, sm2, st>>>(pd, ws.geom, t, ws.sx[0],    \
+                                                              ws.sx[1], ws.sx[2], ws.sw, ws.mp); \
+  } while (0)
+    if (ntl <= 4) AP2M(4);
+    else if (ntl <= 10) AP2M(10);
+    else if (ntl <= 16) AP2M(16);
+    else AP2M(32);
+#undef AP2M
+    ++*nl;
+  }
+  // M2M, deepest parents first
+  const size_t smem = sizeof(double) * (3 * 8 * pd.nj + pd.nfull + 2 * (pd.p + 1));
+  set_smem(k_am2m<double>, smem);
+  for (int l = t.maxlev - 1; l >= 2; --l) {
+    const int n = t.loff[l + 1] - t.loff[l];
+    k_am2m<double><<<(unsigned)n, kThreads, smem, st>>>(pd, ws.geom, t, l, ws.mp);
+    ++*nl;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                    cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  if (t.maxlev < 2) return cudaGetLastError();
+  const int nbox = t.loff[t.maxlev + 1];
+  {
+    const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
+    const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+    const size_t smem = sizeof(double) * (((pd.nj + 1) & ~1) + (size_t)per * kAThreads);
+    set_smem(k_ap2l, smem);
+    k_ap2l<<<(unsigned)(nbox - t.loff[2]), kAThreads, smem, st>>>(
+        pd, ws.geom, t, ws.sx[0], ws.sx[1], ws.sx[2], ws.sw, ws.lc);
+    ++*nl;
+  }
+  const size_t smem = sizeof(double) * (7 * pd.nfull + 2 * (pd.p + 1));
+  set_smem(k_al2l<double>, smem);
+  for (int l = 2; l < t.maxlev; ++l) {
+    const int n = t.loff[l + 1] - t.loff[l];
+    k_al2l<double><<<(unsigned)n, kThreads, smem, st>>>(pd, ws.geom, t, l, ws.lc);
     ++*nl;
   }
   return cudaGetLastError();

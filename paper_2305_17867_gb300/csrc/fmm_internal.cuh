@@ -81,7 +81,14 @@ struct fmm_plan_s {
   cudaStream_t last_stream;
   Geom* last_geom;  // device geometry of the last evaluation (in its workspace)
   int launches;
+  int deriv_levels;  // adaptive plans: M2L table levels of the current tree
+  int last_boxes;    // adaptive plans: boxes and depth of the last tree
+  int last_depth;
 };
+
+inline void set_deriv_levels(const fmm_plan_s* P, int maxlev) {
+  const_cast<fmm_plan_s*>(P)->deriv_levels = maxlev;
+}
 
 // record the start (i = 0) or end (i = 1) of the M2L contraction when timing
 inline void mark_contraction(const fmm_plan_s* P, int i, cudaStream_t st) {
@@ -134,6 +141,22 @@ struct Workspace {
   float4* sxr;
   float4* txr;
   float* lcoef;
+  // adaptive tree (plans with levels < 0): box arrays of capacity anb_cap and
+  // the points' Morton codes in sorted order
+  int64_t anb_cap;
+  uint32_t* akey;
+  int* alev;
+  int* apar;
+  int* achild;
+  int* as0;
+  int* as1;
+  int* at0;
+  int* at1;
+  int* aleaf;
+  int* anch;
+  int* ascan;
+  uint32_t* skey;
+  uint32_t* tkey;
   size_t bytes;
 };
 
@@ -163,3 +186,19 @@ bool m2l_shared_tables(const fmm_plan_s* P);
 cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
 cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* phi,
                              double* grad, cudaStream_t st, int* nlaunch);
+
+// adaptive tree (adaptive.cuh): the build synchronises the stream once per
+// level to size the next level; *tree receives the level offsets
+struct ATree;
+cudaError_t launch_build_adaptive(const fmm_plan_s* P, const Workspace& ws, int64_t n_src,
+                                  const double* src, const double* w, int64_t n_tgt,
+                                  const double* tgt, cudaStream_t st, int* nlaunch,
+                                  ATree* tree, int* overflow);
+cudaError_t launch_adaptive_upward(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                   cudaStream_t st, int* nlaunch);
+cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                cudaStream_t st, int* nlaunch);
+cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                    cudaStream_t st, int* nlaunch);
+cudaError_t launch_adaptive_leaf(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                 double* phi, cudaStream_t st, int* nlaunch);

@@ -9,6 +9,7 @@
 // written straight to the caller's order through the target permutation.
 #include <algorithm>
 
+#include "adaptive.cuh"
 #include "expansions.cuh"
 
 namespace {
@@ -570,6 +571,132 @@ void leaf_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, double* 
   else leaf_launch_g<K, D, T, false>(P, ws, phi, grad, st);
 }
 
+// ---------------------------------------------------------------------------
+// Adaptive tree, FP64: one block per leaf holding targets; each thread owns
+// targets and walks the leaf's lists itself (the walk is identical across
+// the block):
+//   L2P from the leaf's local expansion (levels >= 2);
+//   U: coarser adjacent leaves (neighbours of each ancestor at its level),
+//      the leaf's colleagues that are leaves, and the finer adjacent leaves
+//      found by descending the non-leaf colleagues -> P2P (eq. (1));
+//   W: the boxes met in that descent that are not adjacent to the leaf
+//      (their parent is) -> M2P, sum_q Ht_q((x - c_C)/s_C) bt_C[q].
+// ---------------------------------------------------------------------------
+constexpr int kAThreads = 64;
+constexpr int kAStack = 8 * (FMM_MAX_ADEPTH + 1);
+
+__device__ __forceinline__ double green3(int kern, double lam, double r2) {
+  const double ri = rsqrt(r2);
+  if (kern == FMM_KERNEL_LAPLACE) return ri * (1.0 / (4.0 * 3.14159265358979323846));
+  if (kern == FMM_KERNEL_YUKAWA) return exp(-lam * r2 * ri) * ri;
+  return r2 * ri;  // biharmonic: r
+}
+
+__global__ void __launch_bounds__(kAThreads) k_aleaf(
+    PlanDev pd, const Geom* __restrict__ g, ATree t, const double* __restrict__ lc,
+    const double* __restrict__ mp, const double* __restrict__ tx0, const double* __restrict__ tx1,
+    const double* __restrict__ tx2, const int* __restrict__ tperm, const double* __restrict__ sx0,
+    const double* __restrict__ sx1, const double* __restrict__ sx2, const double* __restrict__ sw,
+    double* __restrict__ phi, int* __restrict__ err) {
+  const int b = blockIdx.x;
+  if (b >= t.loff[t.maxlev + 1] || !t.leaf[b] || t.t1[b] == t.t0[b]) return;
+  const int p = pd.p, nfull = pd.nfull;
+  int l, bc[3];
+  abox(t, b, &l, bc);
+  double cb[3], s;
+  abox_center(g, l, bc, cb, &s);
+  extern __shared__ __align__(16) double smd[];
+  double* a = smd;  // decompressed local / m!
+  const int sl = min(pd.c, p + 1) * (p + 1);
+  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  double* S = smd + ((nfull + 1) & ~1) + threadIdx.x * per;
+  const bool has_local = l >= 2;
+  if (has_local) {
+    for (int q = threadIdx.x; q < pd.nj; q += blockDim.x) a[q] = lc[(size_t)b * pd.nj + q];
+    __syncthreads();
+    decompress_smem<double>(pd, a, s);
+    for (int q = threadIdx.x; q < nfull; q += blockDim.x) a[q] *= pd.inv_fact[q];
+    __syncthreads();
+  }
+  const double inv_s = 1.0 / s, lam = pd.lam;
+  const int kern = pd.kernel;
+  for (int ti = t.t0[b] + threadIdx.x; ti < t.t1[b]; ti += blockDim.x) {
+    const double x[3] = {tx0[ti], tx1[ti], tx2[ti]};
+    double acc = 0.0;
+    if (has_local) {  // L2P, Sec. 3.3
+      double pw[3][FMM_MAXP + 1];
+      for (int k = 0; k < 3; ++k) {
+        const double u = (x[k] - cb[k]) * inv_s;
+        pw[k][0] = 1.0;
+        for (int e = 1; e <= p; ++e) pw[k][e] = pw[k][e - 1] * u;
+      }
+      for (int q = 0; q < nfull; ++q) {
+        const char4 m = pd.mi[q];
+        acc += a[q] * pw[0][m.x] * pw[1][m.y] * pw[2][m.z];
+      }
+    }
+    auto p2p = [&](int A) {
+      for (int q = t.s0[A]; q < t.s1[A]; ++q) {
+        const double d0 = x[0] - sx0[q], d1 = x[1] - sx1[q], d2 = x[2] - sx2[q];
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        if (r2 > 0.0) acc += sw[q] * green3(kern, lam, r2);
+      }
+    };
+    auto m2p = [&](int C, int lc_, const int* cc) {
+      double c2[3], s2;
+      abox_center(g, lc_, cc, c2, &s2);
+      const double is2 = 1.0 / s2;
+      const double y[3] = {(x[0] - c2[0]) * is2, (x[1] - c2[1]) * is2, (x[2] - c2[2]) * is2};
+      const double* bt = mp + (size_t)C * pd.nj;
+      double v = 0.0;
+      deriv_point(pd, y, lam * s2, deriv_scale(pd, s2), S, sl,
+                  [&](int pos, double h) { v += h * bt[pos]; });
+      acc += v;
+    };
+    // U: coarser adjacent leaves
+    for (int lp = l - 1; lp >= 0; --lp) {
+      const int an[3] = {bc[0] >> (l - lp), bc[1] >> (l - lp), bc[2] >> (l - lp)};
+      for (int nb = 0; nb < 27; ++nb) {
+        const int nc[3] = {an[0] + nb % 3 - 1, an[1] + (nb / 3) % 3 - 1, an[2] + nb / 9 - 1};
+        const int A = alookup(t, lp, nc);
+        if (A >= 0 && t.leaf[A] && aadjacent(lp, nc, l, bc)) p2p(A);
+      }
+    }
+    // colleagues: leaves -> U; others -> descend (adjacent: deeper, else W)
+    for (int nb = 0; nb < 27; ++nb) {
+      const int nc[3] = {bc[0] + nb % 3 - 1, bc[1] + (nb / 3) % 3 - 1, bc[2] + nb / 9 - 1};
+      const int C = alookup(t, l, nc);
+      if (C < 0) continue;
+      if (t.leaf[C]) {
+        p2p(C);
+        continue;
+      }
+      int stack[kAStack];
+      int sp = 0;
+      for (int ci = 0; ci < 8; ++ci)
+        if (t.child[8 * C + ci] >= 0) stack[sp++] = t.child[8 * C + ci];
+      while (sp > 0) {
+        const int E = stack[--sp];
+        int le, ce[3];
+        abox(t, E, &le, ce);
+        if (!aadjacent(le, ce, l, bc)) {
+          m2p(E, le, ce);
+        } else if (t.leaf[E]) {
+          p2p(E);
+        } else {
+          for (int ci = 0; ci < 8; ++ci) {
+            const int F = t.child[8 * E + ci];
+            if (F < 0) continue;
+            if (sp < kAStack) stack[sp++] = F;
+            else atomicOr(err, 4);  // cannot happen: depth-first, 7 siblings per level
+          }
+        }
+      }
+    }
+    phi[tperm[ti]] = acc;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
@@ -600,3 +727,19 @@ cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* p
   return cudaGetLastError();
 }
 
+
+cudaError_t launch_adaptive_leaf(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                 double* phi, cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  const int nbox = t.loff[t.maxlev + 1];
+  const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
+  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  const size_t smem = sizeof(double) * (((pd.nfull + 1) & ~1) + (size_t)per * kAThreads);
+  set_smem(k_aleaf, smem);
+  k_aleaf<<<(unsigned)nbox, kAThreads, smem, st>>>(pd, ws.geom, t, ws.lc, ws.mp, ws.tx[0],
+                                                   ws.tx[1], ws.tx[2], ws.tperm, ws.sx[0],
+                                                   ws.sx[1], ws.sx[2], ws.sw, phi,
+                                                   &ws.geom->flag);
+  ++*nl;
+  return cudaGetLastError();
+}

@@ -8,6 +8,7 @@
 // One block per target box; used for the FP64 and FP32 configurations.
 #include <algorithm>
 
+#include "adaptive.cuh"
 #include "expansions.cuh"
 
 namespace {
@@ -21,14 +22,62 @@ void set_smem(K kernel, size_t bytes) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Accumulates one source box: stage its table row Ht (nh) and multipole
+// bt (nj) in shared memory, then acc[k] += sum_q Ht[i_k + q] bt[q].
+template <int D, typename T>
+__device__ __forceinline__ void m2l_one_source(const PlanDev& pd, const double* __restrict__ hsrc,
+                                               const double* __restrict__ bsrc, T* H, T* bs,
+                                               T (&acc)[kMaxI], const int (&ii0)[kMaxI],
+                                               const int (&ii1)[kMaxI], const int (&iis)[kMaxI]) {
+  const int p = pd.p, c = pd.c, nj = pd.nj, nh = pd.nh, P2 = 2 * p;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nh; i += blockDim.x) H[i] = (T)hsrc[i];
+  for (int i = threadIdx.x; i < nj; i += blockDim.x) bs[i] = (T)bsrc[i];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kMaxI; ++k) {
+    if (threadIdx.x + k * blockDim.x >= nj) continue;
+    T sum = 0;
+    for (int qs = 0; qs < c; ++qs) {
+      if (D == 3) {
+        for (int q1 = 0; q1 <= p - qs; ++q1) {
+          const T* hrow = H + pd.hrow[(iis[k] + qs) * (P2 + 1) + ii1[k] + q1] + ii0[k];
+          const T* brow = bs + pd.frow[qs * (p + 1) + q1];
+          const int len = p - qs - q1 + 1;
+          for (int q0 = 0; q0 < len; ++q0) sum += hrow[q0] * brow[q0];
+        }
+      } else {
+        const T* hrow = H + pd.hrow[iis[k] + qs] + ii0[k];
+        const T* brow = bs + pd.frow[qs];
+        const int len = p - qs + 1;
+        for (int q0 = 0; q0 < len; ++q0) sum += hrow[q0] * brow[q0];
+      }
+    }
+    acc[k] += sum;
+  }
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void m2l_init(const PlanDev& pd, T (&acc)[kMaxI], int (&ii0)[kMaxI],
+                                         int (&ii1)[kMaxI], int (&iis)[kMaxI]) {
+#pragma unroll
+  for (int k = 0; k < kMaxI; ++k) {
+    acc[k] = 0;
+    const int i = threadIdx.x + k * blockDim.x;
+    const char4 m = i < pd.nj ? pd.mi[i] : make_char4(0, 0, 0, 0);
+    ii0[k] = m.x;
+    ii1[k] = D == 3 ? m.y : 0;
+    iis[k] = D == 3 ? m.z : m.y;
+  }
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(kThreads) k_m2l_simt(PlanDev pd, int l,
                                                        const double* __restrict__ mp,
                                                        double* __restrict__ lc,
                                                        const double* __restrict__ htab) {
-  constexpr int NOFF = D == 3 ? 343 : 49;
   const int b = blockIdx.x;
-  const int p = pd.p, c = pd.c, nj = pd.nj, nh = pd.nh, P2 = 2 * p;
+  const int nj = pd.nj, nh = pd.nh;
   const int nl = 1 << l;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* H = reinterpret_cast<T*>(smraw);
@@ -44,15 +93,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_simt(PlanDev pd, int l,
   }
   T acc[kMaxI];
   int ii0[kMaxI], ii1[kMaxI], iis[kMaxI];
-#pragma unroll
-  for (int k = 0; k < kMaxI; ++k) {
-    acc[k] = 0;
-    const int i = threadIdx.x + k * blockDim.x;
-    const char4 m = i < nj ? pd.mi[i] : make_char4(0, 0, 0, 0);
-    ii0[k] = m.x;
-    ii1[k] = D == 3 ? m.y : 0;
-    iis[k] = D == 3 ? m.z : m.y;
-  }
+  m2l_init<D, T>(pd, acc, ii0, ii1, iis);
   int nn = 1;
   for (int k = 0; k < D; ++k) nn *= 6;
   for (int a = 0; a < nn; ++a) {
@@ -70,31 +111,51 @@ __global__ void __launch_bounds__(kThreads) k_m2l_simt(PlanDev pd, int l,
     if (!ok || adj) continue;
     int64_t sb = 0;
     for (int k = D - 1; k >= 0; --k) sb = sb * nl + sc[k];
-    __syncthreads();
-    const double* hsrc = htab + (size_t)o * nh;
-    for (int i = threadIdx.x; i < nh; i += blockDim.x) H[i] = (T)hsrc[i];
-    for (int i = threadIdx.x; i < nj; i += blockDim.x) bs[i] = (T)mp[(size_t)sb * nj + i];
-    __syncthreads();
+    m2l_one_source<D, T>(pd, htab + (size_t)o * nh, mp + (size_t)sb * nj, H, bs, acc, ii0, ii1,
+                         iis);
+  }
 #pragma unroll
-    for (int k = 0; k < kMaxI; ++k) {
-      if (threadIdx.x + k * blockDim.x >= nj) continue;
-      T sum = 0;
-      for (int qs = 0; qs < c; ++qs) {
-        if (D == 3) {
-          for (int q1 = 0; q1 <= p - qs; ++q1) {
-            const T* hrow = H + pd.hrow[(iis[k] + qs) * (P2 + 1) + ii1[k] + q1] + ii0[k];
-            const T* brow = bs + pd.frow[qs * (p + 1) + q1];
-            const int len = p - qs - q1 + 1;
-            for (int q0 = 0; q0 < len; ++q0) sum += hrow[q0] * brow[q0];
-          }
-        } else {
-          const T* hrow = H + pd.hrow[iis[k] + qs] + ii0[k];
-          const T* brow = bs + pd.frow[qs];
-          const int len = p - qs + 1;
-          for (int q0 = 0; q0 < len; ++q0) sum += hrow[q0] * brow[q0];
-        }
-      }
-      acc[k] += sum;
+  for (int k = 0; k < kMaxI; ++k) {
+    const int i = threadIdx.x + k * blockDim.x;
+    if (i < nj) lc[(size_t)b * nj + i] += (double)acc[k];
+  }
+}
+
+// Adaptive tree: one block per box of level >= 2 holding targets.  V(B) =
+// children of the boxes adjacent to P(B) that are not adjacent to B, found by
+// looking up the 27 neighbours of the parent; their offsets lie in [-3,3]^3.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
+                                                   const double* __restrict__ mp,
+                                                   double* __restrict__ lc,
+                                                   const double* __restrict__ htab) {
+  const int b = t.loff[2] + blockIdx.x;
+  if (b >= t.loff[t.maxlev + 1] || t.t1[b] == t.t0[b]) return;
+  const int nj = pd.nj, nh = pd.nh;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* H = reinterpret_cast<T*>(smraw);
+  T* bs = H + nh;
+  int l, bc[3];
+  abox(t, b, &l, bc);
+  const int pc[3] = {bc[0] >> 1, bc[1] >> 1, bc[2] >> 1};
+  const double* ht = htab + (size_t)(l - 2) * 343 * nh;
+  T acc[kMaxI];
+  int ii0[kMaxI], ii1[kMaxI], iis[kMaxI];
+  m2l_init<3, T>(pd, acc, ii0, ii1, iis);
+  for (int nb = 0; nb < 27; ++nb) {
+    const int nc[3] = {pc[0] + nb % 3 - 1, pc[1] + (nb / 3) % 3 - 1, pc[2] + nb / 9 - 1};
+    const int Pn = alookup(t, l - 1, nc);
+    if (Pn < 0 || t.leaf[Pn]) continue;
+    for (int ci = 0; ci < 8; ++ci) {
+      const int C = t.child[8 * Pn + ci];
+      if (C < 0) continue;
+      const int cc[3] = {2 * nc[0] + (ci & 1), 2 * nc[1] + ((ci >> 1) & 1),
+                         2 * nc[2] + ((ci >> 2) & 1)};
+      const int d0 = bc[0] - cc[0], d1 = bc[1] - cc[1], d2 = bc[2] - cc[2];
+      if (d0 >= -1 && d0 <= 1 && d1 >= -1 && d1 <= 1 && d2 >= -1 && d2 <= 1) continue;
+      const int o = (d0 + 3) + 7 * (d1 + 3) + 49 * (d2 + 3);
+      m2l_one_source<3, T>(pd, ht + (size_t)o * nh, mp + (size_t)C * nj, H, bs, acc, ii0, ii1,
+                           iis);
     }
   }
 #pragma unroll
@@ -102,7 +163,6 @@ __global__ void __launch_bounds__(kThreads) k_m2l_simt(PlanDev pd, int l,
     const int i = threadIdx.x + k * blockDim.x;
     if (i < nj) lc[(size_t)b * nj + i] += (double)acc[k];
   }
-  (void)NOFF;
 }
 
 }  // namespace
@@ -149,4 +209,18 @@ cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   if (P->desc.m2l == FMM_M2L_FFT) return launch_m2l_fft(P, ws, st, nl);
   if (prec == FMM_PREC_FP64 || prec == FMM_PREC_FP32) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
   return launch_m2l_tc(P, ws, st, nl);
+}
+
+cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  if (t.maxlev < 2) return cudaGetLastError();
+  const size_t smem = sizeof(double) * (pd.nh + pd.nj);
+  set_smem(k_am2l<double>, smem);
+  mark_contraction(P, 0, st);
+  k_am2l<double><<<(unsigned)(t.loff[t.maxlev + 1] - t.loff[2]), kThreads, smem, st>>>(
+      pd, t, ws.mp, ws.lc, ws.htab);
+  mark_contraction(P, 1, st);
+  ++*nl;
+  return cudaGetLastError();
 }

@@ -7,6 +7,7 @@
 // round-to-nearest operations only, so the binning is reproducible.
 #include <algorithm>
 
+#include "adaptive.cuh"
 #include "fmm_internal.cuh"
 
 namespace {
@@ -280,6 +281,114 @@ __global__ void k_gather_rel(int n, const int* __restrict__ order,
   out[i] = make_float4(u[0], u[1], u[2], w ? (float)w[j] : 0.f);
 }
 
+// ---- adaptive octree (adaptive.cuh) ----------------------------------------
+// Morton code of every point at the deepest level D, from the same leaf
+// coordinates as the uniform binning (leaf side = root / 2^D).
+__global__ void k_amorton(int64_t n, const double* __restrict__ x, const Geom* __restrict__ g,
+                          int D, uint32_t* __restrict__ keys, int* __restrict__ vals, Geom* gflag) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nl = 1 << D;
+  const double s = g->s_leaf, inv_s = g->inv_s_leaf;
+  int bc[3];
+  bool bad = false;
+  for (int k = 0; k < 3; ++k) {
+    const double t = leaf_coord(x[i * 3 + k], g->lo[k], s, inv_s);
+    if (!(t >= 0.0) || t > (double)nl) bad = true;
+    bc[k] = (t >= 0.0) ? (int)fmin(floor(t), (double)(nl - 1)) : 0;  // NaN -> 0
+  }
+  if (bad) atomicOr(&gflag->flag, 1);
+  keys[i] = morton3(bc[0], bc[1], bc[2], D);
+  vals[i] = (int)i;
+}
+
+__global__ void k_atree_root(int* lev, int* par, uint32_t* key, int* s0, int* s1, int* t0,
+                             int* t1, int ns, int nt) {
+  lev[0] = 0;
+  par[0] = -1;
+  key[0] = 0;
+  s0[0] = 0;
+  s1[0] = ns;
+  t0[0] = 0;
+  t1[0] = nt;
+}
+
+// first position in sorted[lo, hi) whose code is >= v
+__device__ inline int lower_bound_u32(const uint32_t* a, int lo, int hi, uint32_t v) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// child ranges of box b (level l): boundaries of octants 0..8 in the sorted codes
+__device__ inline void child_bounds(const uint32_t* skey, const uint32_t* tkey, uint32_t key,
+                                    int l, int D, int s0, int s1, int t0, int t1, int* sb,
+                                    int* tb) {
+  const int shift = 3 * (D - l - 1);
+  sb[0] = s0;
+  tb[0] = t0;
+  for (int ci = 1; ci < 8; ++ci) {
+    const uint32_t v = ((key << 3) | (uint32_t)ci) << shift;
+    sb[ci] = lower_bound_u32(skey, s0, s1, v);
+    tb[ci] = lower_bound_u32(tkey, t0, t1, v);
+  }
+  sb[8] = s1;
+  tb[8] = t1;
+}
+
+// split decision and number of non-empty children of every box of one level
+__global__ void k_atree_split(int b0, int b1, int l, int D, int max_leaf,
+                              const uint32_t* __restrict__ key, const int* __restrict__ s0,
+                              const int* __restrict__ s1, const int* __restrict__ t0,
+                              const int* __restrict__ t1, const uint32_t* __restrict__ skey,
+                              const uint32_t* __restrict__ tkey, int* __restrict__ leaf,
+                              int* __restrict__ child, int* __restrict__ nch) {
+  const int b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= b1) return;
+  for (int ci = 0; ci < 8; ++ci) child[8 * b + ci] = -1;
+  const int npt = (s1[b] - s0[b]) + (t1[b] - t0[b]);
+  if (npt <= max_leaf || l >= D) {
+    leaf[b] = 1;
+    nch[b - b0] = 0;
+    return;
+  }
+  leaf[b] = 0;
+  int sb[9], tb[9];
+  child_bounds(skey, tkey, key[b], l, D, s0[b], s1[b], t0[b], t1[b], sb, tb);
+  int n = 0;
+  for (int ci = 0; ci < 8; ++ci) n += (sb[ci + 1] > sb[ci] || tb[ci + 1] > tb[ci]) ? 1 : 0;
+  nch[b - b0] = n;
+}
+
+// create the children of the level's split boxes at next + scan[b - b0]
+__global__ void k_atree_emit(int b0, int b1, int l, int D, int next, const int* __restrict__ scan,
+                             uint32_t* __restrict__ key, int* __restrict__ lev,
+                             int* __restrict__ par, int* __restrict__ s0, int* __restrict__ s1,
+                             int* __restrict__ t0, int* __restrict__ t1,
+                             const uint32_t* __restrict__ skey, const uint32_t* __restrict__ tkey,
+                             const int* __restrict__ leaf, int* __restrict__ child) {
+  const int b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= b1 || leaf[b]) return;
+  int sb[9], tb[9];
+  child_bounds(skey, tkey, key[b], l, D, s0[b], s1[b], t0[b], t1[b], sb, tb);
+  int pos = next + scan[b - b0];
+  for (int ci = 0; ci < 8; ++ci) {
+    if (sb[ci + 1] == sb[ci] && tb[ci + 1] == tb[ci]) continue;
+    key[pos] = (key[b] << 3) | (uint32_t)ci;
+    lev[pos] = l + 1;
+    par[pos] = b;
+    s0[pos] = sb[ci];
+    s1[pos] = sb[ci + 1];
+    t0[pos] = tb[ci];
+    t1[pos] = tb[ci + 1];
+    child[8 * b + ci] = pos;
+    ++pos;
+  }
+}
+
 unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // exclusive scan of in[0..n) into out[0..n], out[n] = total
@@ -345,19 +454,20 @@ cudaError_t launch_set_geom(const fmm_plan_s* P, const Workspace& ws, int64_t n_
                             const double* src, int64_t n_tgt, const double* tgt,
                             cudaStream_t st, int* nl) {
   const fmm_plan_desc& d = P->desc;
+  const int depth = d.levels > 0 ? d.levels : -d.levels;  // adaptive: deepest level
   if (d.root_size > 0.0) {
     k_geom_fixed<<<1, 1, 0, st>>>(ws.geom, d.root_lo[0], d.root_lo[1], d.d == 3 ? d.root_lo[2] : 0.0,
-                                  d.root_size, d.levels);
+                                  d.root_size, depth);
     ++*nl;
     return cudaGetLastError();
   }
   const int nb = ws.nbbox_blocks;
   if (P->pd.d == 3) {
     k_bbox_partial<3><<<nb, 256, 0, st>>>(n_src, src, n_tgt, tgt, ws.bbox);
-    k_bbox_final<3><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom, d.levels);
+    k_bbox_final<3><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom, depth);
   } else {
     k_bbox_partial<2><<<nb, 256, 0, st>>>(n_src, src, n_tgt, tgt, ws.bbox);
-    k_bbox_final<2><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom, d.levels);
+    k_bbox_final<2><<<1, 32, 0, st>>>(nb, ws.bbox, ws.geom, depth);
   }
   *nl += 2;
   return cudaGetLastError();
@@ -380,4 +490,95 @@ cudaError_t launch_build_tree(const fmm_plan_s* P, const Workspace& ws, int64_t 
                        st, nl);
   }
   return e;
+}
+
+namespace {
+
+// sort one point set by Morton code at depth D into the FP64 SoA arrays,
+// keeping the sorted codes
+cudaError_t asort_points(const Workspace& ws, int64_t n, const double* x, const double* w,
+                         double* const* ox, double* ow, int* perm, uint32_t* okey, int D,
+                         cudaStream_t st, int* nl) {
+  if (n == 0) return cudaGetLastError();
+  k_amorton<<<nblocks(n, 256), 256, 0, st>>>(n, x, ws.geom, D, ws.keys_a, ws.vals_a, ws.geom);
+  ++*nl;
+  const int bits = 3 * D;
+  const int nblk = (int)nblocks(n, kRsBlock);
+  uint32_t* ka = ws.keys_a;
+  uint32_t* kb = ws.keys_b;
+  int* va = ws.vals_a;
+  int* vb = ws.vals_b;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_hist<<<nblk, kRsBlock, 0, st>>>(ka, (int)n, shift, ws.hist, nblk);
+    const int64_t nh = 256LL * nblk;
+    const unsigned nb = nblocks(nh, 1024);
+    k_scan_chunks<<<nb, 1024, 0, st>>>(ws.hist, ws.hist, nh, ws.hist_sums);
+    k_scan_top<<<1, 1024, 0, st>>>(ws.hist_sums, (int)nb);
+    k_scan_add<<<nb, 1024, 0, st>>>(ws.hist, nh, ws.hist_sums, nullptr, nullptr);
+    k_rs_scatter<<<nblk, kRsBlock, 0, st>>>(ka, va, kb, vb, (int)n, shift, ws.hist, nblk);
+    *nl += 5;
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  cudaMemcpyAsync(okey, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+  k_gather<3><<<nblocks(n, 256), 256, 0, st>>>((int)n, va, x, w, ox[0], ox[1], ox[2], ow, perm);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_build_adaptive(const fmm_plan_s* P, const Workspace& ws, int64_t n_src,
+                                  const double* src, const double* w, int64_t n_tgt,
+                                  const double* tgt, cudaStream_t st, int* nl, ATree* t,
+                                  int* overflow) {
+  const int D = -P->desc.levels;
+  *overflow = 0;
+  cudaError_t e = asort_points(ws, n_src, src, w, ws.sx, ws.sw, ws.sperm, ws.skey, D, st, nl);
+  if (e != cudaSuccess) return e;
+  e = asort_points(ws, n_tgt, tgt, nullptr, ws.tx, nullptr, ws.tperm, ws.tkey, D, st, nl);
+  if (e != cudaSuccess) return e;
+  k_atree_root<<<1, 1, 0, st>>>(ws.alev, ws.apar, ws.akey, ws.as0, ws.as1, ws.at0, ws.at1,
+                                (int)n_src, (int)n_tgt);
+  ++*nl;
+  int loff[FMM_MAX_ADEPTH + 2];
+  loff[0] = 0;
+  loff[1] = 1;
+  int maxlev = 0;
+  for (int l = 0; l <= D; ++l) {
+    const int b0 = loff[l], b1 = loff[l + 1], n = b1 - b0;
+    k_atree_split<<<nblocks(n, 128), 128, 0, st>>>(b0, b1, l, D, P->desc.max_leaf, ws.akey,
+                                                   ws.as0, ws.as1, ws.at0, ws.at1, ws.skey,
+                                                   ws.tkey, ws.aleaf, ws.achild, ws.anch);
+    ++*nl;
+    if (l == D) break;
+    e = scan_ints(ws.anch, ws.ascan, n, ws.hist_sums, st, nl);
+    if (e != cudaSuccess) return e;
+    int total = 0;
+    cudaMemcpyAsync(&total, ws.ascan + n, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    if (total == 0) break;
+    if ((int64_t)b1 + total > ws.anb_cap) {
+      *overflow = 1;
+      return cudaSuccess;
+    }
+    k_atree_emit<<<nblocks(n, 128), 128, 0, st>>>(b0, b1, l, D, b1, ws.ascan, ws.akey, ws.alev,
+                                                  ws.apar, ws.as0, ws.as1, ws.at0, ws.at1,
+                                                  ws.skey, ws.tkey, ws.aleaf, ws.achild);
+    ++*nl;
+    loff[l + 2] = b1 + total;
+    maxlev = l + 1;
+  }
+  t->key = ws.akey;
+  t->lev = ws.alev;
+  t->par = ws.apar;
+  t->child = ws.achild;
+  t->s0 = ws.as0;
+  t->s1 = ws.as1;
+  t->t0 = ws.at0;
+  t->t1 = ws.at1;
+  t->leaf = ws.aleaf;
+  for (int l = 0; l <= FMM_MAX_ADEPTH + 1; ++l) t->loff[l] = l <= maxlev + 1 ? loff[l] : loff[maxlev + 1];
+  t->maxlev = maxlev;
+  return cudaGetLastError();
 }

@@ -24,7 +24,9 @@ class FMM:
     """A compressed-Taylor FMM plan on a uniform tree.
 
     kernel     "laplace" (d = 2, 3), "yukawa" (d = 3), "biharmonic" (d = 3)
-    p          expansion order;  levels: leaf depth L of the uniform tree
+    p          expansion order;  levels: leaf depth L of the uniform tree, or
+               -D for an adaptive tree (3D, fp64) refined to at most level D,
+               splitting boxes that hold more than ``max_leaf`` points
     root_lo, root_size  root box; root_size <= 0 picks the bounding cube per call
     precision  "fp64" | "fp32" | "tf32" | "tf32x3" | "bf16x3"
     m2l        "dense" (eq. (m2l_toeplitz) as dense products) | "fft" (its
@@ -35,7 +37,8 @@ class FMM:
 
     def __init__(self, kernel: str = "laplace", d: int = 3, p: int = 10, levels: int = 5,
                  lam: float = 0.0, root_lo=None, root_size: float = 1.0,
-                 precision: str = "fp64", pde=None, device=None, m2l: str = "dense"):
+                 precision: str = "fp64", pde=None, device=None, m2l: str = "dense",
+                 max_leaf: int = 64):
         self.L = _lib.load()
         self.kernel, self.d, self.p, self.levels, self.lam = kernel, d, p, levels, lam
         self.precision = precision
@@ -50,6 +53,7 @@ class FMM:
         desc.root_size = float(root_size)
         desc.precision = PRECISIONS[precision]
         desc.m2l = M2L_PATHS[m2l]
+        desc.max_leaf = int(max_leaf)
         self._pde_keep = None
         if pde is not None:
             mi, co = pde
@@ -111,6 +115,12 @@ class FMM:
 
     def last_status(self) -> int:
         return self.L.fmm_last_status(self._h)
+
+    def last_tree(self):
+        """(boxes, deepest level) of the last evaluation's tree."""
+        nb, dp = ctypes.c_int64(), ctypes.c_int()
+        check(self.L.fmm_last_tree(self._h, ctypes.byref(nb), ctypes.byref(dp)), "fmm_last_tree")
+        return nb.value, dp.value
 
     def last_launch_count(self) -> int:
         return self.L.fmm_last_launch_count(self._h)

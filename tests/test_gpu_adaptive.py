@@ -1,0 +1,117 @@
+"""GPU parity of the adaptive-tree FMM (U, V, W, X lists) against the oracle.
+
+The tree (boxes and depth) must match the oracle's exactly; potentials must
+match the oracle's adaptive FMM with the same tree and p to 1e-12 (FP64).
+"""
+import numpy as np
+import pytest
+
+from paper_2305_17867_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def gpu_adaptive(torch, kernel, p, src, w, tgt=None, lam=0.0, max_leaf=64, depth=10):
+    from paper_2305_17867_gb300.fmm import FMM
+
+    plan = FMM(kernel, d=3, p=p, levels=-depth, lam=lam, max_leaf=max_leaf)
+    s = torch.tensor(src, device="cuda")
+    wt = torch.tensor(w, device="cuda")
+    t = None if tgt is None else torch.tensor(tgt, device="cuda")
+    out = plan.eval(s, wt, t, check_status=True)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), plan.last_tree()
+
+
+def plummer_case(n_src, n_tgt, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    src = W.plummer_points(rng, n_src)
+    w = rng.normal(size=n_src)
+    tgt = rng.random((n_tgt, 3))
+    return src, w, tgt
+
+
+def test_complete_tree_matches_uniform(torch_cuda, oracle):
+    rng = np.random.default_rng(41)
+    src = rng.random((12000, 3))
+    w = rng.uniform(-1, 1, 12000)
+    got, (nb, depth) = gpu_adaptive(torch_cuda, "laplace", 8, src, w, max_leaf=200)
+    assert depth == 3 and nb == 1 + 8 + 64 + 512
+    ref = oracle.fmm_uniform("laplace", 3, 8, 3, src, w, src)
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+@pytest.mark.parametrize("kernel,p,lam,n", [("laplace", 8, 0.0, 20000), ("laplace", 12, 0.0, 6000),
+                                            ("yukawa", 8, 1.0, 20000), ("yukawa", 12, 1.0, 5000),
+                                            ("biharmonic", 6, 0.0, 20000)])
+def test_plummer_matches_oracle(torch_cuda, oracle, kernel, p, lam, n):
+    src, w, tgt = plummer_case(n, n // 5, 42)
+    ref, st, _ = oracle.fmm_adaptive(kernel, 3, p, src, w, tgt, max_leaf=32, lam=lam,
+                                     want_stats=True)
+    assert st["W"] > 0 and st["X"] > 0
+    got, (nb, depth) = gpu_adaptive(torch_cuda, kernel, p, src, w, tgt, lam=lam, max_leaf=32)
+    assert (nb, depth) == (st["boxes"], st["depth"])
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+def test_sources_are_targets(torch_cuda, oracle):
+    src, w, _ = plummer_case(15000, 1, 43)
+    ref = oracle.fmm_adaptive("laplace", 3, 8, src, w, src, max_leaf=40)
+    got, _ = gpu_adaptive(torch_cuda, "laplace", 8, src, w, max_leaf=40)
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+def test_depth_cap(torch_cuda, oracle):
+    rng = np.random.default_rng(44)
+    src = np.concatenate([0.3 + 1e-4 * rng.random((2000, 3)), rng.random((3000, 3))])
+    w = rng.normal(size=5000)
+    tgt = rng.random((2000, 3))
+    ref, st, _ = oracle.fmm_adaptive("laplace", 3, 6, src, w, tgt, max_leaf=8, max_depth=5,
+                                     want_stats=True)
+    got, (nb, depth) = gpu_adaptive(torch_cuda, "laplace", 6, src, w, tgt, max_leaf=8, depth=5)
+    assert depth == 5 and nb == st["boxes"]
+    assert rel_l2(got, ref) < FP64_TOL
+
+
+def test_tiny_and_empty(torch_cuda, oracle):
+    rng = np.random.default_rng(45)
+    src = rng.random((50, 3))
+    w = rng.normal(size=50)
+    tgt = rng.random((30, 3))
+    ref = oracle.direct("laplace", 3, src, w, tgt)  # one leaf: all direct
+    got, (nb, depth) = gpu_adaptive(torch_cuda, "laplace", 6, src, w, tgt, max_leaf=100)
+    assert (nb, depth) == (1, 0)
+    assert rel_l2(got, ref) < 1e-14
+    z = np.zeros((0, 3))
+    got, _ = gpu_adaptive(torch_cuda, "laplace", 6, z, np.zeros(0), tgt, max_leaf=8)
+    assert np.all(got == 0.0)
+
+
+def test_yukawa_plummer_full_size_sampled(torch_cuda, oracle):
+    # the adaptive Yukawa workload: 2e6 Plummer sources, 2e6 uniform targets,
+    # p = 12, at most 64 points per leaf; the oracle evaluates 16 seeded
+    # targets on the same tree
+    wl = W.WORKLOADS["yukawa3d_p12_adaptive_n2m"]
+    src, w, tgt = W.make_inputs(wl)
+    got, (nb, depth) = gpu_adaptive(torch_cuda, "yukawa", 12, src, w, tgt, lam=wl.lam,
+                                    max_leaf=wl.max_leaf)
+    idx = np.random.default_rng(96).choice(len(tgt), 16, replace=False)
+    ref, st, _ = oracle.fmm_adaptive("yukawa", 3, 12, src, w, tgt, max_leaf=wl.max_leaf,
+                                     lam=wl.lam, sample=idx, want_stats=True)
+    assert (nb, depth) == (st["boxes"], st["depth"])
+    assert rel_l2(got[idx], ref) < FP64_TOL
