@@ -1,9 +1,12 @@
 """Benchmark of the GB300 compressed-Taylor FMM.
 
-Workload (one "step" = one full evaluation: tree build, M2L derivative
-tables, P2M, M2M, M2L, L2L, L2P + P2P): 3D Laplace G = 1/(4 pi r),
-compressed Taylor p = 10, uniform octree of 5 levels, N = 1,000,000 sources =
-targets uniform in [0,1]^3, weights uniform[-1,1] (seeded synthetic data).
+Default workload (one "step" = one full evaluation: tree build, M2L
+derivative tables, P2M, M2M, M2L, L2L, L2P + P2P): 3D Laplace
+G = 1/(4 pi r), compressed Taylor p = 10, uniform octree of 5 levels,
+N = 1,000,000 sources = targets uniform in [0,1]^3, weights uniform[-1,1]
+(seeded synthetic data).  `--workload` selects the other particle sets of
+paper_2305_17867_gb300/workloads.py (2D Laplace, adaptive Yukawa/Plummer,
+the backward step, 3D biharmonic with `--p`).
 
 Prints ONE JSON line.  value = targets/s of the whole job (all ranks);
 inputs are resident in HBM when the timed region starts; L2 is flushed
@@ -11,7 +14,8 @@ between timed steps (each step is timed alone with CUDA events on the
 launching stream).  `e2e` repeats the measurement through the public API
 with host buffers (pinned), the host<->device copies inside the timed region.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--p P]
+                  [--precision P] [--m2l dense|fft] [--impl reference]
 """
 from __future__ import annotations
 
@@ -28,7 +32,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "laplace3d_p10_L5_n1m"
+DEFAULT_WORKLOAD = "laplace3d_p10_L5_n1m"
+METRIC = "full-FMM targets/sec and M2L translations/sec at stated rel. error, % of roofline"
+ADAPTIVE_DEPTH = 10
 
 
 def parse():
@@ -36,7 +42,11 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default=os.environ.get("FMM_BENCH_PRECISION", "tf32x3"))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--p", type=int, default=0, help="override the expansion order")
+    ap.add_argument("--precision", default=os.environ.get("FMM_BENCH_PRECISION", "auto"),
+                    help="fp64|fp32|tf32|tf32x3|bf16x3; auto = tf32x3 on uniform 3D trees, "
+                         "else fp64")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m2l", default="dense", choices=["dense", "fft"],
                     help="M2L form: dense products or the FFT convolution form")
@@ -44,9 +54,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--cpu-leaves", type=int, default=48)
+    ap.add_argument("--cpu-targets", type=int, default=16,
+                    help="adaptive workloads: targets the CPU oracle evaluates")
     ap.add_argument("--points", type=int, default=0,
-                    help="override the point count (profiling captures: the same L=5 tree and "
-                         "the identical M2L launch on less memory)")
+                    help="override the point count (profiling captures: the same tree depth and, "
+                         "for uniform trees, the identical M2L launch on less memory)")
     return ap.parse_args()
 
 
@@ -123,17 +135,13 @@ def m2l_count(d: int, L: int) -> int:
     tot = 0
     for l in range(2, L + 1):
         n = 1 << l
-        # per dimension: for target t, sources s with parent(s) adjacent to
-        # parent(t), s not adjacent to t (count by brute force on 1D factors
-        # is not separable because of the 'not adjacent' condition) -> count
-        # pairs directly with numpy on the box grid.
         t = np.arange(n)
         pt = t >> 1
         par_adj = np.abs(pt[:, None] - pt[None, :]) <= 1
         adj = np.abs(t[:, None] - t[None, :]) <= 1
         A = par_adj.astype(np.int64)
         B = (par_adj & adj).astype(np.int64)
-        # pairs with all dims parent-adjacent minus those adjacent in all dims
+        # pairs with all axes parent-adjacent minus those adjacent on all axes
         tot += int(A.sum() ** d - B.sum() ** d)
     return tot
 
@@ -176,24 +184,109 @@ def profiled_traffic(prec: str):
 
 def leaf_of(x, L):
     n = 1 << L
+    d = x.shape[1]
     b = np.minimum(np.floor(x / (1.0 / n)).astype(np.int64), n - 1)
-    return (b[:, 2] * n + b[:, 1]) * n + b[:, 0]
+    key = np.zeros(len(x), dtype=np.int64)
+    for k in range(d - 1, -1, -1):
+        key = key * n + b[:, k]
+    return key
 
 
-def run_cpu_oracle(src, w, L, p, nleaves, seed=12345):
-    """Oracle on a bounded sample: every target of `nleaves` random leaves."""
+def max_over_ranks(ms: float, dist, device) -> float:
+    """Step time of the job: the slowest rank's (replicas run concurrently)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank: int, world: int, ms: float) -> float:
+    """Targets per second of the whole job: every rank's targets in the job's step time."""
+    return n_per_rank * world / (ms * 1e-3)
+
+
+def precision_of(args, wl):
+    if args.precision != "auto":
+        return args.precision
+    return "tf32x3" if (wl.d == 3 and wl.levels > 0) else "fp64"
+
+
+def make_plan(wl, p, prec, m2l, dev):
+    from paper_2305_17867_gb300.fmm import FMM
+
+    levels = wl.levels if wl.levels > 0 else -ADAPTIVE_DEPTH
+    return FMM(wl.kernel, d=wl.d, p=p, levels=levels, lam=wl.lam, precision=prec, device=dev,
+               m2l=m2l, max_leaf=wl.max_leaf or 64)
+
+
+def run_cpu_oracle(wl, p, src, w, tgt, args, seed=12345):
+    """The oracle on a bounded sample of the same workload: every target of
+    a few random leaves (uniform trees) or a few random targets (adaptive)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import fmm_oracle
 
     fmm_oracle.lib()
-    leaves = leaf_of(src, L)
     rng = np.random.default_rng(seed)
-    pick = rng.choice(1 << (3 * L), nleaves, replace=False)
-    idx = np.nonzero(np.isin(leaves, pick))[0]
     t0 = time.perf_counter()
-    ref = fmm_oracle.fmm_uniform("laplace", 3, p, L, src, w, src, sample=idx)
+    if wl.levels > 0:
+        leaves = leaf_of(tgt, wl.levels)
+        pick = rng.choice(1 << (wl.d * wl.levels), args.cpu_leaves, replace=False)
+        idx = np.nonzero(np.isin(leaves, pick))[0]
+        t0 = time.perf_counter()
+        ref = fmm_oracle.fmm_uniform(wl.kernel, wl.d, p, wl.levels, src, w, tgt, lam=wl.lam,
+                                     sample=idx)
+        what = (f"every target of {args.cpu_leaves} random leaves ({len(idx)} targets) of the "
+                f"same tree; upward pass over all sources included")
+    else:
+        idx = rng.choice(len(tgt), args.cpu_targets, replace=False)
+        ref = fmm_oracle.fmm_adaptive(wl.kernel, wl.d, p, src, w, tgt, max_leaf=wl.max_leaf,
+                                      max_depth=ADAPTIVE_DEPTH, lam=wl.lam, sample=idx)
+        what = (f"{len(idx)} random targets of the same adaptive tree; tree build and upward "
+                f"pass over all sources included")
     dt = time.perf_counter() - t0
-    return idx, ref, dt, fmm_oracle.num_threads()
+    return idx, ref, dt, fmm_oracle.num_threads(), what
+
+
+def roofline(plan, prec, m2l, m2l_ms, nm2l, p, c):
+    peaks, peak_src = load_peaks()
+    tf32_dense = peaks["bf16_tflops"] * 1.1 / 2.25
+    clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    if m2l == "fft":
+        kf = (p + 1) * (2 * p + 1) ** (plan.d - 2) * (2 * min(c, p + 1) - 1)
+        flops = 8.0 * kf * nm2l
+        algo = (f"8 * {kf} (complex multiply-add per kept frequency) FLOP/translation x "
+                f"{nm2l} translations")
+    else:
+        flops = 2.0 * plan.nj * plan.nj * nm2l
+        algo = f"2*|j|^2 = {2 * plan.nj ** 2} FLOP/translation x {nm2l} translations"
+    tensor = m2l == "dense" and plan.d == 3 and prec in ("tf32", "tf32x3", "bf16x3")
+    if tensor and prec == "tf32":
+        peak, bound, pname = tf32_dense, "tensor", f"tf32 dense = bf16 {peak_src} x 1.1/2.25"
+    elif tensor and prec == "tf32x3":
+        # the split contraction issues three tf32 products per algorithmic multiply-add
+        peak, bound = tf32_dense / 3.0, "tensor"
+        pname = f"tf32x3 = (bf16 {peak_src} x 1.1/2.25) / 3 passes"
+    elif tensor and prec == "bf16x3":
+        peak, bound = peaks["bf16_tflops"] / 3.0, "tensor"
+        pname = f"bf16x3 = bf16 dense {peak_src} / 3 passes"
+    elif prec == "fp64":
+        peak, bound = 152 * 2 * 2 * clock / 1e12, "alu"
+        pname = "fp64 FMA: 152 SMs x 2 lanes x 2 x max clock (nominal 1.25 TFLOP/s)"
+    else:
+        peak, bound = 152 * 128 * 2 * clock / 1e12, "alu"
+        pname = "fp32 FMA: 152 SMs x 128 lanes x 2 x max clock"
+    achieved = flops / (m2l_ms * 1e-3) / 1e12
+    traffic, traffic_src = (profiled_traffic(prec) if (tensor and plan.levels == 5 and p == 10)
+                            else (None, "no capture"))
+    kname = {"dense": "m2l tensor-core contraction" if tensor else "m2l simt contraction",
+             "fft": "m2l fft stencil"}[m2l]
+    return {"kernel": kname, "bound": bound, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_source": traffic_src, "kernel_ms": m2l_ms, "peak_source": pname,
+            "frac_vs_tf32_dense": achieved / tf32_dense, "algorithmic": algo}
 
 
 def main():
@@ -211,29 +304,37 @@ def main():
         dist.init_process_group("nccl")
     from paper_2305_17867_gb300 import workloads as Wk
 
-    wl = Wk.WORKLOADS[WORKLOAD]
+    wl = Wk.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl, rank)
 
-    from paper_2305_17867_gb300.fmm import FMM
-
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    p = args.p or wl.p
+    prec = precision_of(args, wl)
+    backward = "bwd" in wl.name
     # every rank runs an independent replica of the workload (weak scaling)
-    src, w, _ = Wk.make_inputs(wl, n_src=args.points or None,
-                               seed=wl.seed + 1000 * rank if rank else None)
-    n = src.shape[0]
+    src, w, tgt = Wk.make_inputs(wl, n_src=args.points or None,
+                                 n_tgt=(args.points or None) if wl.n_tgt else None,
+                                 seed=wl.seed + 1000 * rank if rank else None)
+    same = tgt is src
+    u = Wk.cotangent(len(tgt), wl.seed) if backward else None
+    n_t = tgt.shape[0]
     t_plan = time.perf_counter()
-    plan = FMM("laplace", d=3, p=wl.p, levels=wl.levels, precision=args.precision, device=dev,
-               m2l=args.m2l)
+    plan = make_plan(wl, p, prec, args.m2l, dev)
     t_plan = (time.perf_counter() - t_plan) * 1e3
     s = torch.tensor(src, device=dev)
     wt = torch.tensor(w, device=dev)
+    t = None if same else torch.tensor(tgt, device=dev)
+    ut = torch.tensor(u, device=dev) if backward else None
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        return plan.eval(s, wt)
+        phi = plan.eval(s, wt, t)
+        if backward:
+            plan.backward(s, wt, s if t is None else t, ut)
+        return phi
 
     for _ in range(max(args.warmup, 3)):
         phi = step()
@@ -257,94 +358,70 @@ def main():
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-            ph_steps.append(plan.phase_times())
-            k_steps.append(plan.m2l_kernel_time())
+            if not backward:
+                ph_steps.append(plan.phase_times())
+                k_steps.append(plan.m2l_kernel_time())
     torch.cuda.synchronize()
     plan.set_timing(False)
     if dist:
         dist.barrier()
-    ms = sum(times) / len(times)
-    phases = {k: sum(p[k] for p in ph_steps) / len(ph_steps) for k in ph_steps[0]}
+    ms = max_over_ranks(sum(times) / len(times), dist, dev)
+    value = job_throughput(n_t, world, ms)
+    if backward:  # phases of a forward evaluation alone
+        plan.set_timing(True)
+        plan.eval(s, wt, t)
+        ph_steps = [plan.phase_times()]
+        k_steps = [plan.m2l_kernel_time()]
+        plan.set_timing(False)
+    phases = {k: sum(q[k] for q in ph_steps) / len(ph_steps) for k in ph_steps[0]}
     m2l_kernel_ms = sum(k_steps) / len(k_steps)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n * world / (ms * 1e-3)
+    nm2l = plan.last_m2l_count()
+    boxes, depth = plan.last_tree()
 
     # end to end through the public API from pinned host buffers
     hs = torch.tensor(src).pin_memory()
     hw = torch.tensor(w).pin_memory()
+    ht = None if same else torch.tensor(tgt).pin_memory()
+    hu = torch.tensor(u).pin_memory() if backward else None
     e2e_times = []
+    d2h = n_t * 8
     for _ in range(0 if args.no_e2e else max(2, min(args.steps, 5))):
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = plan.eval(hs, hw)
+        out = plan.eval(hs, hw, ht)
+        if backward:
+            gw, gs, gt = plan.backward(hs, hw, hs if ht is None else ht, hu)
+            gw, gs, gt = gw.cpu(), gs.cpu(), gt.cpu()
         e2e_times.append((time.perf_counter() - t0) * 1e3)
         assert out.device.type == "cpu"
+    if backward:
+        d2h += (len(w) + len(w) * wl.d + n_t * wl.d) * 8
     e2e_ms = statistics.median(e2e_times) if e2e_times else float("nan")
+    h2d = int(src.nbytes + w.nbytes + (0 if same else tgt.nbytes) + (u.nbytes if backward else 0))
 
-    # M2L work and roofline
-    nm2l = m2l_count(3, wl.levels)
-    flops_m2l = 2.0 * plan.nj * plan.nj * nm2l
-    # FFT form: one complex multiply-add (8 flop) per kept frequency and translation
-    kf = (wl.p + 1) * (2 * wl.p + 1) * (2 * min(plan.c, wl.p + 1) - 1)
-    algo = f"2*|j|^2 = {2 * plan.nj ** 2} FLOP/translation x {nm2l} translations"
-    if args.m2l == "fft":
-        flops_m2l = 8.0 * kf * nm2l
-        algo = (f"8 * {kf} (complex multiply-add per kept frequency) FLOP/translation x "
-                f"{nm2l} translations")
-    m2l_ms = m2l_kernel_ms
-    peaks, peak_src = load_peaks()
-    prec = args.precision
-    tf32_dense = peaks["bf16_tflops"] * 1.1 / 2.25
-    if prec == "tf32":
-        peak = tf32_dense
-        bound, unit, pname = "tensor", "TFLOP/s", f"tf32 dense = bf16 {peak_src} x 1.1/2.25"
-    elif prec == "tf32x3":
-        # the split contraction issues three tf32 products per algorithmic multiply-add
-        peak = tf32_dense / 3.0
-        bound, unit, pname = ("tensor", "TFLOP/s",
-                              f"tf32x3 = (bf16 {peak_src} x 1.1/2.25) / 3 passes")
-    elif prec == "bf16x3":
-        peak = peaks["bf16_tflops"] / 3.0
-        bound, unit, pname = "tensor", "TFLOP/s", f"bf16x3 = bf16 dense {peak_src} / 3 passes"
-    elif prec == "fp32":
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound, unit, pname = "alu", "TFLOP/s", "fp32 FMA: 152 SMs x 128 lanes x 2 x max clock"
-    else:
-        peak = 152 * 2 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound, unit, pname = ("alu", "TFLOP/s",
-                              "fp64 FMA: 152 SMs x 2 lanes x 2 x max clock (nominal 1.25 TFLOP/s)")
-    achieved = flops_m2l / (m2l_ms * 1e-3) / 1e12
-    traffic, traffic_src = profiled_traffic(prec) if args.m2l == "dense" else (None, "no capture")
-    roof = {"kernel": "m2l contraction" if args.m2l == "dense" else "m2l fft stencil", "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": unit, "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
-            "kernel_ms": m2l_ms, "peak_source": pname,
-            "frac_vs_tf32_dense": achieved / tf32_dense,
-            "algorithmic": algo}
-
-    wname = WORKLOAD if not args.points else f"{WORKLOAD} with n={args.points} (profiling case)"
+    roof = roofline(plan, prec, args.m2l, m2l_kernel_ms, nm2l, p, plan.c)
+    wname = wl.name if p == wl.p else f"{wl.name} with p={p}"
+    if args.points:
+        wname += f" with n={args.points} (profiling case)"
+    config = {"workload": wname, "kernel": wl.kernel, "d": wl.d, "n_src": len(w), "n_tgt": n_t,
+              "p": p, "tree": (f"uniform, {wl.levels} levels" if wl.levels > 0 else
+                               f"adaptive, <= {wl.max_leaf} points per leaf, depth <= "
+                               f"{ADAPTIVE_DEPTH}"),
+              "boxes": boxes, "depth": depth, "precision": prec, "m2l": args.m2l,
+              "step": "forward + backward" if backward else "forward",
+              "l2": "flushed (256 MiB write) between timed steps",
+              "parallelism": "replicas" if world > 1 else "single"}
     result = {
-        "metric": "full-FMM targets/sec (3D Laplace, compressed Taylor p=10, uniform octree L=5, "
-                  "N=1e6) with M2L translations/sec",
-        "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
-        "config": {"workload": wname, "n_src": n, "n_tgt": n, "p": wl.p, "levels": wl.levels,
-                   "precision": prec, "m2l": args.m2l, "l2": "flushed (256 MiB write) between timed steps",
-                   "parallelism": "replicas" if world > 1 else "single"},
-        "m2l_translations_per_s": nm2l * world / (ms * 1e-3),
-        "m2l_translations": nm2l,
-        "phases_ms": phases,
-        "plan_create_ms": t_plan,
-        "roofline": roof,
-        "gpu_launches": launches * args.steps,
-        "clocks": clk.summary(),
-        "e2e": {"value": n * world / (e2e_ms * 1e-3), "unit": "targets/s",
-                "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(src.nbytes + w.nbytes),
-                "d2h_bytes_per_step": int(n * 8)},
+        "metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+        "data": "synthetic", "config": config,
+        "m2l_translations_per_s": nm2l * world / (ms * 1e-3), "m2l_translations": nm2l,
+        "phases_ms": phases, "plan_create_ms": t_plan, "roofline": roof,
+        "gpu_launches": launches * args.steps, "clocks": clk.summary(),
+        "e2e": {"value": n_t * world / (e2e_ms * 1e-3), "unit": "targets/s",
+                "ms_per_step": e2e_ms, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
     }
     if rank != 0:
         if dist:
@@ -354,9 +431,9 @@ def main():
 
     phi_np = phi.cpu().numpy()
     if not args.no_fp64 and prec != "fp64":
-        plan64 = FMM("laplace", d=3, p=wl.p, levels=wl.levels, precision="fp64", device=dev)
+        plan64 = make_plan(wl, p, "fp64", "dense", dev)
         for _ in range(2):
-            phi64 = plan64.eval(s, wt)
+            phi64 = plan64.eval(s, wt, t)
         torch.cuda.synchronize()
         t64 = []
         for _ in range(2):
@@ -364,31 +441,30 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            phi64 = plan64.eval(s, wt)
+            phi64 = plan64.eval(s, wt, t)
             e1.record(stream)
             e1.synchronize()
             t64.append(e0.elapsed_time(e1))
         plan64.set_timing(True)
-        plan64.eval(s, wt)
+        plan64.eval(s, wt, t)
         ph64 = plan64.phase_times()
+        k64 = plan64.m2l_kernel_time()
         p64 = phi64.cpu().numpy()
-        result["fp64"] = {"value": n / (statistics.median(t64) * 1e-3), "unit": "targets/s",
+        result["fp64"] = {"value": n_t / (statistics.median(t64) * 1e-3), "unit": "targets/s",
                           "ms_per_step": statistics.median(t64), "phases_ms": ph64,
-                          "m2l_tflops": flops_m2l / (ph64["m2l"] * 1e-3) / 1e12}
+                          "m2l_tflops": 2.0 * plan.nj ** 2 * nm2l / (k64 * 1e-3) / 1e12}
         result["rel_err_vs_fp64_gpu"] = float(np.linalg.norm(phi_np - p64) / np.linalg.norm(p64))
 
     if not args.no_cpu:
-        idx, ref, dt, cores = run_cpu_oracle(src, w, wl.levels, wl.p, args.cpu_leaves)
+        idx, ref, dt, cores, what = run_cpu_oracle(wl, p, src, w, tgt, args)
         result["rel_err_vs_oracle"] = float(np.linalg.norm(phi_np[idx] - ref) / np.linalg.norm(ref))
-        result["cpu_baseline"] = {
-            "value": len(idx) / dt, "unit": "targets/s", "cores": cores, "kind": "oracle",
-            "sample": f"every target of {args.cpu_leaves} random leaves ({len(idx)} targets) of the "
-                      f"same 1e6-point tree; upward pass over all sources included; {dt:.1f} s"}
-        sys.path.insert(0, os.path.join(ROOT, "oracle"))
+        result["cpu_baseline"] = {"value": len(idx) / dt, "unit": "targets/s", "cores": cores,
+                                  "kind": "oracle", "sample": f"{what}; {dt:.1f} s"}
         import fmm_oracle
 
-        dref = fmm_oracle.direct("laplace", 3, src, w, src[idx[:200]])
-        result["rel_err_vs_direct"] = float(np.linalg.norm(phi_np[idx[:200]] - dref) /
+        k = idx[:200]
+        dref = fmm_oracle.direct(wl.kernel, wl.d, src, w, tgt[k], lam=wl.lam)
+        result["rel_err_vs_direct"] = float(np.linalg.norm(phi_np[k] - dref) /
                                             np.linalg.norm(dref))
     print(json.dumps(result))
     if dist:
@@ -400,26 +476,35 @@ def run_reference(args, wl, rank):
     """The reference arm: the CPU oracle, timed on the host cores."""
     if rank != 0:
         return
-    src, w, _ = __import__("paper_2305_17867_gb300.workloads", fromlist=["x"]).make_inputs(wl)
-    times, n_t, cores = [], 0, 1
-    for k in range(max(args.warmup, 0) + args.steps):
-        idx, ref, dt, cores = run_cpu_oracle(src, w, wl.levels, wl.p, max(4, args.cpu_leaves // 4),
-                                             seed=777 + k)
-        if k >= args.warmup:
+    from paper_2305_17867_gb300 import workloads as Wk
+
+    src, w, tgt = Wk.make_inputs(wl)
+    p = args.p or wl.p
+    times, n_t, cores, what = [], 0, 1, ""
+    args.cpu_leaves = max(4, args.cpu_leaves // 4)
+    args.cpu_targets = max(2, args.cpu_targets // 4)
+    # every oracle step repeats the whole upward pass (seconds), so the run
+    # stops after the time budget even if fewer than --steps steps were timed
+    budget_s, spent = 150.0, 0.0
+    warm = min(max(args.warmup, 0), 1)
+    for k in range(warm + args.steps):
+        idx, ref, dt, cores, what = run_cpu_oracle(wl, p, src, w, tgt, args, seed=777 + k)
+        spent += dt
+        if k >= warm:
             times.append(dt)
             n_t += len(idx)
+            if spent > budget_s:
+                break
     value = n_t / sum(times)
     line = {
-        "impl": "reference", "metric": "full-FMM targets/sec (3D Laplace, compressed Taylor p=10, "
-        "uniform octree L=5, N=1e6) with M2L translations/sec",
-        "value": value, "unit": "targets/s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n_src": len(w), "p": wl.p,
-                                        "levels": wl.levels},
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "targets/s",
+        "n_gpus": args.gpus, "steps": len(times), "steps_requested": args.steps,
+        "warmup": warm, "time_budget_s": budget_s,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_src": len(w), "n_tgt": len(tgt), "p": p},
         "cpu_baseline": {"value": value, "unit": "targets/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: every target of a few random leaves of the 1e6-point "
-                                   "tree (upward pass over all sources included)"},
+                         "sample": f"per step: {what}"},
         "e2e": {"value": value, "unit": "targets/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

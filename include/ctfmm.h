@@ -200,9 +200,12 @@ int fmm_phase_times(fmm_plan_t plan, float* ms_out /* FMM_NUM_PHASES */);
  * the local expansions and the operand packing.  Synchronises. */
 int fmm_m2l_kernel_time(fmm_plan_t plan, float* ms_out);
 
-/* Tree of the last evaluation: number of boxes (all levels) and deepest
- * level.  Uniform plans report their fixed tree.  Any pointer may be NULL. */
-int fmm_last_tree(fmm_plan_t plan, int64_t* boxes_out, int* depth_out);
+/* Tree of the last evaluation: number of boxes (all levels), deepest level
+ * and number of M2L translations (interaction-list entries, List 2, summed
+ * over the boxes that received them).  Uniform plans report their fixed tree;
+ * for adaptive plans the count is read from the device (synchronises the
+ * evaluation's stream).  Any pointer may be NULL. */
+int fmm_last_tree(fmm_plan_t plan, int64_t* boxes_out, int* depth_out, int64_t* m2l_out);
 
 /* Number of kernel launches the last fmm_eval enqueued. */
 int fmm_last_launch_count(fmm_plan_t plan);

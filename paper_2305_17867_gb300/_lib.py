@@ -87,7 +87,7 @@ def load(build: bool = True):
     L.fmm_phase_times.restype = i32
     L.fmm_m2l_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.fmm_m2l_kernel_time.restype = i32
-    L.fmm_last_tree.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
+    L.fmm_last_tree.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.fmm_last_tree.restype = i32
     L.fmm_last_launch_count.argtypes = [vp]
     L.fmm_last_launch_count.restype = i32

@@ -481,7 +481,32 @@ extern "C" int fmm_m2l_kernel_time(fmm_plan_t P, float* ms) {
   return FMM_OK;
 }
 
-extern "C" int fmm_last_tree(fmm_plan_t P, int64_t* boxes, int* depth) {
+// M2L translations of a uniform tree: per level, the (target, source) pairs
+// whose parents are adjacent minus those that are adjacent themselves; the
+// count factorises over the axes.
+static int64_t uniform_m2l_count(int d, int L) {
+  int64_t tot = 0;
+  for (int l = 2; l <= L; ++l) {
+    const int64_t n = (int64_t)1 << l;
+    int64_t A = 0, B = 0;
+    for (int64_t t = 0; t < n; ++t)
+      for (int64_t s = std::max<int64_t>(0, t - 3); s <= std::min<int64_t>(n - 1, t + 3); ++s) {
+        const int64_t dp = (t >> 1) - (s >> 1);
+        if (dp < -1 || dp > 1) continue;
+        ++A;
+        if (t - s >= -1 && t - s <= 1) ++B;
+      }
+    int64_t Ad = 1, Bd = 1;
+    for (int k = 0; k < d; ++k) {
+      Ad *= A;
+      Bd *= B;
+    }
+    tot += Ad - Bd;
+  }
+  return tot;
+}
+
+extern "C" int fmm_last_tree(fmm_plan_t P, int64_t* boxes, int* depth, int64_t* m2l) {
   if (!P) return FMM_ERR_ARG;
   const int L = P->desc.levels;
   int64_t nb = 0;
@@ -489,6 +514,20 @@ extern "C" int fmm_last_tree(fmm_plan_t P, int64_t* boxes, int* depth) {
     for (int l = 0; l <= L; ++l) nb += nbox_at(P->pd.d, l);
   if (boxes) *boxes = L > 0 ? nb : P->last_boxes;
   if (depth) *depth = L > 0 ? L : P->last_depth;
+  if (m2l) {
+    if (L > 0) {
+      *m2l = uniform_m2l_count(P->pd.d, L);
+    } else {
+      *m2l = 0;
+      if (P->last_geom) {
+        Geom g;
+        if (cudaStreamSynchronize(P->last_stream) != cudaSuccess) return FMM_ERR_CUDA;
+        if (cudaMemcpy(&g, P->last_geom, sizeof(Geom), cudaMemcpyDeviceToHost) != cudaSuccess)
+          return FMM_ERR_CUDA;
+        *m2l = (int64_t)g.m2l_count;
+      }
+    }
+  }
   return FMM_OK;
 }
 

@@ -32,6 +32,7 @@ struct Geom {
   double inv_s_leaf;  // 1 / s_leaf
   int flag;  // device-side status bits (1: domain, 2: timeout)
   int pad;
+  unsigned long long m2l_count;  // adaptive trees: M2L translations performed
 };
 
 // Read-only plan data passed by value to kernels.

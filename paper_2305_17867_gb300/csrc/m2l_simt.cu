@@ -128,7 +128,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
                                                    const double* __restrict__ mp,
                                                    double* __restrict__ lc,
-                                                   const double* __restrict__ htab) {
+                                                   const double* __restrict__ htab,
+                                                   unsigned long long* __restrict__ count) {
   const int b = t.loff[2] + blockIdx.x;
   if (b >= t.loff[t.maxlev + 1] || t.t1[b] == t.t0[b]) return;
   const int nj = pd.nj, nh = pd.nh;
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
   T acc[kMaxI];
   int ii0[kMaxI], ii1[kMaxI], iis[kMaxI];
   m2l_init<3, T>(pd, acc, ii0, ii1, iis);
+  unsigned long long nv = 0;
   for (int nb = 0; nb < 27; ++nb) {
     const int nc[3] = {pc[0] + nb % 3 - 1, pc[1] + (nb / 3) % 3 - 1, pc[2] + nb / 9 - 1};
     const int Pn = alookup(t, l - 1, nc);
@@ -156,8 +158,10 @@ __global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
       const int o = (d0 + 3) + 7 * (d1 + 3) + 49 * (d2 + 3);
       m2l_one_source<3, T>(pd, ht + (size_t)o * nh, mp + (size_t)C * nj, H, bs, acc, ii0, ii1,
                            iis);
+      ++nv;
     }
   }
+  if (threadIdx.x == 0 && nv) atomicAdd(count, nv);
 #pragma unroll
   for (int k = 0; k < kMaxI; ++k) {
     const int i = threadIdx.x + k * blockDim.x;
@@ -219,7 +223,7 @@ cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const 
   set_smem(k_am2l<double>, smem);
   mark_contraction(P, 0, st);
   k_am2l<double><<<(unsigned)(t.loff[t.maxlev + 1] - t.loff[2]), kThreads, smem, st>>>(
-      pd, t, ws.mp, ws.lc, ws.htab);
+      pd, t, ws.mp, ws.lc, ws.htab, &ws.geom->m2l_count);
   mark_contraction(P, 1, st);
   ++*nl;
   return cudaGetLastError();

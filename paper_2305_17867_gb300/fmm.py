@@ -119,8 +119,15 @@ class FMM:
     def last_tree(self):
         """(boxes, deepest level) of the last evaluation's tree."""
         nb, dp = ctypes.c_int64(), ctypes.c_int()
-        check(self.L.fmm_last_tree(self._h, ctypes.byref(nb), ctypes.byref(dp)), "fmm_last_tree")
+        check(self.L.fmm_last_tree(self._h, ctypes.byref(nb), ctypes.byref(dp), None),
+              "fmm_last_tree")
         return nb.value, dp.value
+
+    def last_m2l_count(self) -> int:
+        """M2L translations of the last evaluation (uniform: exact count of the lists)."""
+        n = ctypes.c_int64()
+        check(self.L.fmm_last_tree(self._h, None, None, ctypes.byref(n)), "fmm_last_tree")
+        return n.value
 
     def last_launch_count(self) -> int:
         return self.L.fmm_last_launch_count(self._h)

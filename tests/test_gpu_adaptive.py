@@ -26,7 +26,8 @@ def torch_cuda():
     return torch
 
 
-def gpu_adaptive(torch, kernel, p, src, w, tgt=None, lam=0.0, max_leaf=64, depth=10):
+def gpu_adaptive(torch, kernel, p, src, w, tgt=None, lam=0.0, max_leaf=64, depth=10,
+                 counts=False):
     from paper_2305_17867_gb300.fmm import FMM
 
     plan = FMM(kernel, d=3, p=p, levels=-depth, lam=lam, max_leaf=max_leaf)
@@ -35,6 +36,8 @@ def gpu_adaptive(torch, kernel, p, src, w, tgt=None, lam=0.0, max_leaf=64, depth
     t = None if tgt is None else torch.tensor(tgt, device="cuda")
     out = plan.eval(s, wt, t, check_status=True)
     torch.cuda.synchronize()
+    if counts:
+        return out.cpu().numpy(), plan.last_tree(), plan.last_m2l_count()
     return out.cpu().numpy(), plan.last_tree()
 
 
@@ -64,8 +67,10 @@ def test_plummer_matches_oracle(torch_cuda, oracle, kernel, p, lam, n):
     ref, st, _ = oracle.fmm_adaptive(kernel, 3, p, src, w, tgt, max_leaf=32, lam=lam,
                                      want_stats=True)
     assert st["W"] > 0 and st["X"] > 0
-    got, (nb, depth) = gpu_adaptive(torch_cuda, kernel, p, src, w, tgt, lam=lam, max_leaf=32)
+    got, (nb, depth), nv = gpu_adaptive(torch_cuda, kernel, p, src, w, tgt, lam=lam,
+                                        max_leaf=32, counts=True)
     assert (nb, depth) == (st["boxes"], st["depth"])
+    assert nv == st["V"]  # interaction-list entries of the boxes holding targets
     assert rel_l2(got, ref) < FP64_TOL
 
 

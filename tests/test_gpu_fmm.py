@@ -247,3 +247,14 @@ def test_autograd_against_direct_gradients(torch_cuda, oracle):
         g = {"s": s.grad, "t": t.grad, "w": wt.grad}[which].cpu().numpy()
         an = g[i] if k is None else g[i, k]
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (which, fd, an)
+
+
+@pytest.mark.parametrize("d,L", [(3, 5), (2, 4), (3, 3)])
+def test_uniform_m2l_translation_count(torch_cuda, d, L):
+    # the library's count of interaction-list entries against an independent
+    # count over the box grid
+    import bench
+    from paper_2305_17867_gb300.fmm import FMM
+
+    plan = FMM("laplace", d=d, p=4, levels=L)
+    assert plan.last_m2l_count() == bench.m2l_count(d, L)
