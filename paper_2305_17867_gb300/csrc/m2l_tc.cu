@@ -142,13 +142,16 @@ __global__ void k_build_tmat(PlanDev pd, const double* __restrict__ htab, int MP
 }
 
 // ---- the contraction --------------------------------------------------------
-// Warp roles: warps 0-3 drain TMEM (TMEM lanes 32w..32w+31 = rows i), warp 4
-// lane 0 issues TMA, warp 5 lane 0 issues MMA.  The tensor cores truncate when
-// they accumulate, so a long K loop in one accumulator drifts; each offset's
-// partial product (|j|/32 K-chunks) therefore goes to one of two TMEM buffers,
-// and the draining warps add it into float registers (round-to-nearest)
-// while the MMA warp fills the other buffer.
-constexpr int kEpiWarps = 4;
+// Warp roles: warps 0-7 drain TMEM (warp w reads TMEM lanes 32(w%4).. = rows
+// i, columns 64(w/4)..+63 = targets), warp 8 lane 0 issues TMA, warp 9 lane 0
+// issues MMA.  The tensor cores truncate when they accumulate, so a long K
+// loop in one accumulator drifts; each offset's partial product (|j|/32
+// K-chunks) therefore goes to one of four TMEM buffers (the whole 512
+// columns), and the draining warps add it into float registers
+// (round-to-nearest) while the MMA warp fills the next buffers: a drain may
+// lag three offsets behind the tensor cores.
+constexpr int kEpiWarps = 8;
+constexpr int kNBuf = 4;
 constexpr int kTcThreads = (kEpiWarps + 2) * 32;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -204,9 +207,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::kStages * C::kStage);
   uint64_t* empty = full + C::kStages;
-  uint64_t* accf = empty + C::kStages;  // [2] accumulator filled (MMA commit)
-  uint64_t* acce = accf + 2;            // [2] accumulator drained (4 warp arrivals)
-  uint64_t* drainb = acce + 2;          // all MMAs of this CTA finished
+  uint64_t* accf = empty + C::kStages;  // [kNBuf] accumulator filled (MMA commit)
+  uint64_t* acce = accf + kNBuf;        // [kNBuf] accumulator drained (warp arrivals)
+  uint64_t* drainb = acce + kNBuf;      // all MMAs of this CTA finished
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drainb + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -227,14 +230,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    for (int bf = 0; bf < 2; ++bf) {
+    for (int bf = 0; bf < kNBuf; ++bf) {
       tc::mbar_init(&accf[bf], 1);
       tc::mbar_init(&acce[bf], kEpiWarps);
     }
     tc::mbar_init(drainb, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tslot, 256);
+  if (warp == 0) tc::tmem_alloc(tslot, 128 * kNBuf);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -286,8 +289,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int c = 0; c < 216 && ok; ++c) {
       int sg, dx, dy, dz, hidx;
       if (!combo(c, px, py, pz, sg, dx, dy, dz, hidx)) continue;
-      const int bf = g & 1;
-      if (g >= 2 && !tc::mbar_wait(&acce[bf], ((g >> 1) - 1) & 1, err)) {
+      const int bf = g % kNBuf;
+      if (g >= kNBuf && !tc::mbar_wait(&acce[bf], ((g / kNBuf) - 1) & 1, err)) {
         ok = false;
         break;
       }
@@ -339,28 +342,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else if (warp < kEpiWarps) {
     // ---------------- drain TMEM into float registers ----------------
-    float sum[128];
+    const int quad = warp & 3, c0 = (warp >> 2) * 64;  // TMEM lanes / first column
+    float sum[64];
 #pragma unroll
-    for (int j = 0; j < 128; ++j) sum[j] = 0.f;
+    for (int j = 0; j < 64; ++j) sum[j] = 0.f;
     bool ok = true;
     int g = 0;
     for (int c = 0; c < 216; ++c) {
       int sg, dx, dy, dz, hidx;
       if (!combo(c, px, py, pz, sg, dx, dy, dz, hidx)) continue;
-      const int bf = g & 1;
-      if (!tc::mbar_wait(&accf[bf], (g >> 1) & 1, err)) {
+      const int bf = g % kNBuf;
+      if (!tc::mbar_wait(&accf[bf], (g / kNBuf) & 1, err)) {
         ok = false;
         break;
       }
       tc::fence_after();
-      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(bf * 128);
+      const uint32_t base =
+          tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bf * 128 + c0);
+      if (c0 < N) {
+        uint32_t r0[32], r1[32];
+        tc::tmem_ld32_nowait(base, r0);
+        if (c0 + 32 < N) tc::tmem_ld32_nowait(base + 32u, r1);
+        tc::tmem_wait();
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        if (cc * 32 < N) {
-          uint32_t r[32];
-          tc::tmem_ld32(base + (uint32_t)(cc * 32), r);
+        for (int j = 0; j < 32; ++j) sum[j] += __uint_as_float(r0[j]);
+        if (c0 + 32 < N) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) sum[cc * 32 + j] += __uint_as_float(r[j]);
+          for (int j = 0; j < 32; ++j) sum[32 + j] += __uint_as_float(r1[j]);
         }
       }
       tc::fence_before();
@@ -370,14 +378,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     ok = ok && !(*(volatile int*)err & 2);
     if (ok) {
-      const int i = mt * kBM + warp * 32 + lane;
+      const int i = mt * kBM + quad * 32 + lane;
 #pragma unroll
-      for (int n = 0; n < 128; ++n) {
+      for (int jn = 0; jn < 64; ++jn) {
+        const int n = c0 + jn;
+        const float sv = sum[jn];
         if (n < N) {
           const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
           if (x < H && y < H && z < H && i < nj) {
             const int64_t t = ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
-            lc[t * nj + i] += (double)(sum[n] * LV.scale);
+            lc[t * nj + i] += (double)(sv * LV.scale);
           }
         }
       }
@@ -385,7 +395,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, 128 * kNBuf);
 }
 
 // ---- host side: tensor maps ---------------------------------------------------
