@@ -87,7 +87,7 @@ __device__ inline void abox(const ATree& t, int b, int* l, int* c) {
 // centre and side of a box, in the same operations as the uniform tree:
 // s = size / 2^l, c_k = lo_k + (coord_k + 1/2) s
 __device__ inline void abox_center(const Geom* g, int l, const int* bc, double* c, double* s) {
-  const double sl = __ddiv_rn(g->size, (double)(1 << l));
+  const double sl = __dmul_rn(g->size, __longlong_as_double((long long)(1023 - l) << 52));
   for (int k = 0; k < 3; ++k) c[k] = __dadd_rn(g->lo[k], __dmul_rn((double)bc[k] + 0.5, sl));
   *s = sl;
 }

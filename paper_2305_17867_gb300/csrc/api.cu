@@ -547,6 +547,14 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
   Workspace ws;
   fmm_workspace_layout(P, n_src, n_tgt, workspace, &ws);
   if (ws.bytes > wbytes) return FMM_ERR_WORKSPACE;
+  if (tgt == src && n_tgt == n_src) {
+    // targets are the sources: one sort serves both (same keys, same stable order)
+    for (int k = 0; k < 3; ++k) ws.tx[k] = ws.sx[k];
+    ws.tperm = ws.sperm;
+    ws.tstart = ws.sstart;
+    ws.txr = ws.sxr;
+    ws.tkey = ws.skey;
+  }
   int nl = 0;
   cudaError_t e = cudaSuccess;
   auto mark = [&](int i) {

@@ -57,10 +57,16 @@ __global__ void __launch_bounds__(128) k_deriv_tables(PlanDev pd, const Geom* __
   extern __shared__ double sm[];
   double* G = sm;
   double* B = sm + pd.nh;
+  __shared__ double sh_r, sh_rinv2;  // one square root and division per block
   const int P2 = 2 * pd.p, nslab = 2 * pd.c - 1;
-  const double s = __ddiv_rn(g->size, (double)(1 << l));
-  const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-  const double r = sqrt(r2), rinv2 = 1.0 / r2;
+  const double s = __dmul_rn(g->size, pow2_neg<double>(l));
+  if (threadIdx.x == 0) {
+    const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    sh_r = sqrt(r2);
+    sh_rinv2 = 1.0 / r2;
+  }
+  __syncthreads();
+  const double r = sh_r, rinv2 = sh_rinv2;
   const int kern = pd.kernel;
   const double lam = pd.lam * s;
   // nu for the r^nu family; log / Yukawa flagged separately
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
   int bc[3];
   double c[3], s;
   box_center<D>(g, L, b, bc, c, &s);
-  const double inv_s = 1.0 / s;
+  const double inv_s = rel ? 0.0 : 1.0 / s;  // only the FP64-input path divides
   T acc[kMaxT];
   char4 mt[kMaxT];
 #pragma unroll
@@ -262,7 +268,7 @@ __device__ void p2m_warp_body(const PlanDev& pd, const double* c, double s, int 
                               double* __restrict__ out) {
   const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
   const int P1 = p + 1;
-  const double inv_s = 1.0 / s;
+  const double inv_s = rel ? 0.0 : 1.0 / s;  // only the FP64-input path divides
   const int nt = (nfull + 31) / 32;
   T acc[NT];
   int qoff[NT];
@@ -399,8 +405,8 @@ __device__ void m2m_body(const PlanDev& pd, double s, const int64_t* crow,
   T* sig = Y + NC * nj;                   // nfull
   T* tab = sig + nfull;                   // 2 (sign) x (p+1): (+-1/2)^e / e!
   if (threadIdx.x <= p) {
-    double v = 1.0;
-    for (int e = 1; e <= (int)threadIdx.x; ++e) v *= 0.5 / (double)e;
+    // (1/2)^e / e!: inv_fact[e] is 1/e! (multi-index (e,0,0) sits at position e)
+    const double v = pow2_neg<double>((int)threadIdx.x) * pd.inv_fact[threadIdx.x];
     tab[threadIdx.x] = (T)v;                                      // h = +1/2 (child bit 0)
     tab[(p + 1) + threadIdx.x] = (T)((threadIdx.x & 1) ? -v : v);  // h = -1/2 (child bit 1)
   }
@@ -447,7 +453,7 @@ __device__ void m2m_body(const PlanDev& pd, double s, const int64_t* crow,
         acc += f[qs - is] * Zc[src];
       }
     }
-    sig[q] = acc * (T)ldexp(1.0, -(int)m.w);
+    sig[q] = acc * pow2_neg<T>((int)m.w);
   }
   __syncthreads();
   compress_smem<T>(pd, sig, s);
@@ -479,7 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_am2m(PlanDev pd, const Geom* __res
                                                    ATree t, int l, double* __restrict__ mp) {
   const int b = t.loff[l] + blockIdx.x;
   if (t.leaf[b]) return;
-  const double s = __ddiv_rn(g->size, (double)(1 << l));
+  const double s = __dmul_rn(g->size, pow2_neg<double>(l));
   int64_t crow[8];
   for (int ci = 0; ci < 8; ++ci) crow[ci] = t.child[8 * b + ci];
   m2m_body<3, T>(pd, s, crow, mp, mp + (size_t)b * pd.nj);
@@ -505,8 +511,8 @@ __device__ void l2l_body(const PlanDev& pd, double s, const double* __restrict__
   T* tab = Y + (D == 3 ? 4 * nfull : 0);      // 2 x (p+1): (-+1/4)^e / e!
   for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = (T)par[q];
   if (threadIdx.x <= p) {
-    double v = 1.0;
-    for (int e = 1; e <= (int)threadIdx.x; ++e) v *= 0.25 / (double)e;
+    // (1/4)^e / e!
+    const double v = pow2_neg<double>(2 * (int)threadIdx.x) * pd.inv_fact[threadIdx.x];
     tab[threadIdx.x] = (T)((threadIdx.x & 1) ? -v : v);  // child bit 0: h/S = -1/4
     tab[(p + 1) + threadIdx.x] = (T)v;                    // child bit 1: h/S = +1/4
   }
@@ -552,7 +558,7 @@ __device__ void l2l_body(const PlanDev& pd, double s, const double* __restrict__
       const int src = D == 3 ? pd.frow[qs * (p + 1) + i1] + i0 : pd.frow[qs] + i0;
       acc += gv[qs - is] * Zv[src];
     }
-    lcc[(size_t)crow[ci] * nj + i] += ldexp((double)acc, -(int)m.w);
+    lcc[(size_t)crow[ci] * nj + i] += (double)(acc * pow2_neg<T>((int)m.w));
   }
 }
 
@@ -581,7 +587,7 @@ __global__ void __launch_bounds__(kThreads) k_al2l(PlanDev pd, const Geom* __res
                                                    ATree t, int l, double* __restrict__ lc) {
   const int b = t.loff[l] + blockIdx.x;
   if (t.leaf[b] || t.t1[b] == t.t0[b]) return;
-  const double s = __ddiv_rn(g->size, (double)(1 << l));
+  const double s = __dmul_rn(g->size, pow2_neg<double>(l));
   int64_t crow[8];
   for (int ci = 0; ci < 8; ++ci) {
     const int cb = t.child[8 * b + ci];

@@ -10,13 +10,26 @@ __device__ __forceinline__ int slab_begin(const PlanDev& pd, int ms) {
   return pd.d == 3 ? pd.frow[ms * (pd.p + 1)] : pd.frow[ms];
 }
 
+// 2^-e for 0 <= e <= 126, exact, from the exponent field (no FP64 work in
+// float kernels)
+template <typename T>
+__device__ __forceinline__ T pow2_neg(int e);
+template <>
+__device__ __forceinline__ float pow2_neg<float>(int e) {
+  return __int_as_float((127 - e) << 23);
+}
+template <>
+__device__ __forceinline__ double pow2_neg<double>(int e) {
+  return __longlong_as_double((long long)(1023 - e) << 52);
+}
+
 // Box centre at level l (lexicographic index b, x fastest), round-to-nearest
 // operations in the same order as lo + (b + 1/2) * s.
 template <int D>
 __device__ __forceinline__ void box_center(const Geom* g, int l, int64_t b, int* bc, double* c,
                                            double* s_out) {
   const int nl = 1 << l;
-  const double s = __ddiv_rn(g->size, (double)nl);
+  const double s = __dmul_rn(g->size, pow2_neg<double>(l));  // size / 2^l, exact
   for (int k = 0; k < D; ++k) {
     bc[k] = (int)(b % nl);
     b /= nl;

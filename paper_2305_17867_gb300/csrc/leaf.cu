@@ -323,9 +323,10 @@ __device__ __forceinline__ void pair_masked(float r2, float lam, float& v, float
 // target's own, where no coincident point can exist.
 template <int K>
 __device__ __forceinline__ void pair_plain(float r2, float lam, float& v, float& f1) {
+  // r2 carries +1e-30 (added by the caller inside the fused multiply-adds):
   // distinct points of adjacent leaves closer than the float resolution of the
-  // box-relative coordinates would round to r2 = 0; keep the result finite
-  const float ri = rsqrt_fast(fmaxf(r2, 1e-30f));
+  // box-relative coordinates would otherwise round to r2 = 0
+  const float ri = rsqrt_fast(r2);
   if (K == FMM_KERNEL_LAPLACE) {
     v = ri;
     f1 = -ri * ri * ri;
@@ -346,32 +347,41 @@ __device__ __forceinline__ void pair_sel(float r2, float lam, float& v, float& f
   else pair_plain<K>(r2, lam, v, f1);
 }
 
+// squared distance; pairs without the x == y guard carry +1e-30 so that
+// r2 > 0 without an extra instruction
+template <bool MASK>
+__device__ __forceinline__ float dist2(float dx, float dy, float dz) {
+  return fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, MASK ? 0.f : 1e-30f)));
+}
+
 // One sweep over n staged sources for one or two target slots per lane.
 template <int K, bool GRAD, bool MASK, bool TWO>
 __device__ __forceinline__ void sweep(const float4* __restrict__ src, int n, float lam,
                                       const float* ua, const float* ub, float& na, float& nb,
                                       float* ga, float* gb) {
-  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+  float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
   int q = 0;
-  for (; q + 1 < n; q += 2) {
+  for (; q + 3 < n; q += 4) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < 4; ++h) {
       const float4 v = src[q + h];
-      const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
-      float pv, f1;
-      pair_sel<K, MASK>(fmaf(dzv, dzv, fmaf(dyv, dyv, dx * dx)), lam, pv, f1);
-      if (h == 0) a0 = fmaf(v.w, pv, a0); else a1 = fmaf(v.w, pv, a1);
-      if (GRAD) {
-        const float fw = v.w * f1;
-        ga[0] = fmaf(fw, dx, ga[0]);
-        ga[1] = fmaf(fw, dyv, ga[1]);
-        ga[2] = fmaf(fw, dzv, ga[2]);
+      {
+        const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
+        float pv, f1;
+        pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
+        a[h] = fmaf(v.w, pv, a[h]);
+        if (GRAD) {
+          const float fw = v.w * f1;
+          ga[0] = fmaf(fw, dx, ga[0]);
+          ga[1] = fmaf(fw, dyv, ga[1]);
+          ga[2] = fmaf(fw, dzv, ga[2]);
+        }
       }
       if (TWO) {
         const float ex = ub[0] - v.x, eyv = ub[1] - v.y, ezv = ub[2] - v.z;
         float pw, f2;
-        pair_sel<K, MASK>(fmaf(ezv, ezv, fmaf(eyv, eyv, ex * ex)), lam, pw, f2);
-        if (h == 0) b0 = fmaf(v.w, pw, b0); else b1 = fmaf(v.w, pw, b1);
+        pair_sel<K, MASK>(dist2<MASK>(ex, eyv, ezv), lam, pw, f2);
+        b[h] = fmaf(v.w, pw, b[h]);
         if (GRAD) {
           const float fw = v.w * f2;
           gb[0] = fmaf(fw, ex, gb[0]);
@@ -385,8 +395,8 @@ __device__ __forceinline__ void sweep(const float4* __restrict__ src, int n, flo
     const float4 v = src[q];
     const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
     float pv, f1;
-    pair_sel<K, MASK>(fmaf(dzv, dzv, fmaf(dyv, dyv, dx * dx)), lam, pv, f1);
-    a0 = fmaf(v.w, pv, a0);
+    pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
+    a[0] = fmaf(v.w, pv, a[0]);
     if (GRAD) {
       const float fw = v.w * f1;
       ga[0] = fmaf(fw, dx, ga[0]);
@@ -396,8 +406,8 @@ __device__ __forceinline__ void sweep(const float4* __restrict__ src, int n, flo
     if (TWO) {
       const float ex = ub[0] - v.x, eyv = ub[1] - v.y, ezv = ub[2] - v.z;
       float pw, f2;
-      pair_sel<K, MASK>(fmaf(ezv, ezv, fmaf(eyv, eyv, ex * ex)), lam, pw, f2);
-      b0 = fmaf(v.w, pw, b0);
+      pair_sel<K, MASK>(dist2<MASK>(ex, eyv, ezv), lam, pw, f2);
+      b[0] = fmaf(v.w, pw, b[0]);
       if (GRAD) {
         const float fw = v.w * f2;
         gb[0] = fmaf(fw, ex, gb[0]);
@@ -406,8 +416,93 @@ __device__ __forceinline__ void sweep(const float4* __restrict__ src, int n, flo
       }
     }
   }
-  na += a0 + a1;
-  if (TWO) nb += b0 + b1;
+  na += (a[0] + a[1]) + (a[2] + a[3]);
+  if (TWO) nb += (b[0] + b[1]) + (b[2] + b[3]);
+}
+
+// Remainder targets (at most 16 after the full 32-lane passes): lane group
+// of gs lanes per target, each lane taking every gs-th staged source; the
+// group's partial sums are combined by shuffles at the end.
+template <int K, bool GRAD, bool MASK>
+__device__ __forceinline__ void sweep_split(const float4* __restrict__ src, int n, float lam,
+                                            const float* uc, int sub, int gs, float& nc,
+                                            float* gc) {
+  float a0 = 0.f, a1 = 0.f;
+  int q = sub;
+  for (; q + gs < n; q += 2 * gs) {
+    const float4 v = src[q], v2 = src[q + gs];
+    {
+      const float dx = uc[0] - v.x, dyv = uc[1] - v.y, dzv = uc[2] - v.z;
+      float pv, f1;
+      pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
+      a0 = fmaf(v.w, pv, a0);
+      if (GRAD) {
+        const float fw = v.w * f1;
+        gc[0] = fmaf(fw, dx, gc[0]);
+        gc[1] = fmaf(fw, dyv, gc[1]);
+        gc[2] = fmaf(fw, dzv, gc[2]);
+      }
+    }
+    {
+      const float dx = uc[0] - v2.x, dyv = uc[1] - v2.y, dzv = uc[2] - v2.z;
+      float pv, f1;
+      pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
+      a1 = fmaf(v2.w, pv, a1);
+      if (GRAD) {
+        const float fw = v2.w * f1;
+        gc[0] = fmaf(fw, dx, gc[0]);
+        gc[1] = fmaf(fw, dyv, gc[1]);
+        gc[2] = fmaf(fw, dzv, gc[2]);
+      }
+    }
+  }
+  if (q < n) {
+    const float4 v = src[q];
+    const float dx = uc[0] - v.x, dyv = uc[1] - v.y, dzv = uc[2] - v.z;
+    float pv, f1;
+    pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
+    a0 = fmaf(v.w, pv, a0);
+    if (GRAD) {
+      const float fw = v.w * f1;
+      gc[0] = fmaf(fw, dx, gc[0]);
+      gc[1] = fmaf(fw, dyv, gc[1]);
+      gc[2] = fmaf(fw, dzv, gc[2]);
+    }
+  }
+  nc += a0 + a1;
+}
+
+// far field (L2P) at box-relative u: sum_m Dt_m/m! u^m by rows of the full
+// layout (Horner along m_0), with the analytic gradient
+template <bool GRAD>
+__device__ __forceinline__ float far_field(const PlanDev& pd, const float* __restrict__ cb,
+                                           float u0, float u1, float u2, float* gf) {
+  const int p = pd.p;
+  float far = 0.f;
+  float pz = 1.f, pzm = 0.f;
+  for (int ms = 0; ms <= p; ++ms) {
+    float py = 1.f, pym = 0.f;
+    for (int m1 = 0; m1 <= p - ms; ++m1) {
+      const int base = pd.frow[ms * (p + 1) + m1];
+      const int len = p - ms - m1 + 1;
+      float v = cb[base + len - 1], dv = 0.f;
+      for (int k = len - 2; k >= 0; --k) {
+        if (GRAD) dv = dv * u0 + v;
+        v = v * u0 + cb[base + k];
+      }
+      far += v * py * pz;
+      if (GRAD) {
+        gf[0] += dv * py * pz;
+        gf[1] += v * pym * pz;
+        gf[2] += v * py * pzm;
+      }
+      pym = pym * u1 + py;
+      py *= u1;
+    }
+    pzm = pzm * u2 + pz;
+    pz *= u2;
+  }
+  return far;
 }
 
 template <int K, bool GRAD>
@@ -432,26 +527,38 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
       t /= nl;
     }
   }
-  const double s = __ddiv_rn(g->size, (double)nl);
+  // leaf side and its reciprocal from the geometry record (no FP64 division)
+  const double s = g->s_leaf, inv_s = g->inv_s_leaf;
   const float lam = (float)(pd.lam * s);
   const float* cb = coef + (size_t)b * pd.nfull;
   double phi_scale, grad_scale;
   if (K == FMM_KERNEL_LAPLACE) {
-    phi_scale = 1.0 / (4.0 * 3.14159265358979323846 * s);
-    grad_scale = phi_scale / s;
+    phi_scale = inv_s * (1.0 / (4.0 * 3.14159265358979323846));
+    grad_scale = phi_scale * inv_s;
   } else if (K == FMM_KERNEL_YUKAWA) {
-    phi_scale = 1.0 / s;
-    grad_scale = 1.0 / (s * s);
+    phi_scale = inv_s;
+    grad_scale = inv_s * inv_s;
   } else {
     phi_scale = s;
     grad_scale = 1.0;
   }
-  // lanes own targets tb + lane and tb + 32 + lane (up to 64 per sweep)
+  // Per block of up to 64 targets: nfull full slots (lane = target; 0, 1 or
+  // 2 of them) and r <= 16 remainder targets split over lane groups of gs.
   for (int tb = t0; tb < t1; tb += 64) {
-    const int ta = tb + lane, tb2 = tb + 32 + lane;
-    const bool va = ta < t1, vb = tb2 < t1;
-    const bool two = (t1 - tb) > 32;  // warp-uniform
-    float ua[3] = {0.f, 0.f, 0.f}, ub[3] = {0.f, 0.f, 0.f};
+    const int m = min(64, t1 - tb);
+    int nfull = m >> 5, r = m & 31;
+    if (r > 16) {
+      ++nfull;
+      r = 0;
+    }
+    int rp = 1;
+    while (rp < r) rp <<= 1;
+    const int gs = r ? 32 / rp : 32;
+    const int tr = lane / gs, sub = lane % gs;
+    const bool two = nfull == 2, one = nfull >= 1;  // warp-uniform
+    const int ta = tb + lane, tb2 = tb + 32 + lane, tc = tb + 32 * nfull + tr;
+    const bool va = one && ta < t1, vb = two && tb2 < t1, vc = r > 0 && tr < r;
+    float ua[3] = {0.f, 0.f, 0.f}, ub[3] = {0.f, 0.f, 0.f}, uc[3] = {0.f, 0.f, 0.f};
     if (va) {
       const float4 q = txr[ta];
       ua[0] = q.x;
@@ -464,7 +571,14 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
       ub[1] = q.y;
       ub[2] = q.z;
     }
-    float na = 0.f, nb = 0.f, ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f};
+    if (vc) {
+      const float4 q = txr[tc];
+      uc[0] = q.x;
+      uc[1] = q.y;
+      uc[2] = q.z;
+    }
+    float na = 0.f, nb = 0.f, nc = 0.f;
+    float ga[3] = {0.f, 0.f, 0.f}, gb[3] = {0.f, 0.f, 0.f}, gc[3] = {0.f, 0.f, 0.f};
     for (int rr = 0; rr < 9; ++rr) {
       const int dy = rr % 3 - 1, dz = rr / 3 - 1;
       const int by = bc[1] + dy, bz = bc[2] + dz;
@@ -489,54 +603,40 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
         const bool center = (dy == 0 && dz == 0);  // only the own leaf can hold x == y
         if (center) {
           if (two) sweep<K, GRAD, true, true>(src, n, lam, ua, ub, na, nb, ga, gb);
-          else sweep<K, GRAD, true, false>(src, n, lam, ua, ub, na, nb, ga, gb);
+          else if (one) sweep<K, GRAD, true, false>(src, n, lam, ua, ub, na, nb, ga, gb);
+          if (r) sweep_split<K, GRAD, true>(src, n, lam, uc, sub, gs, nc, gc);
         } else {
           if (two) sweep<K, GRAD, false, true>(src, n, lam, ua, ub, na, nb, ga, gb);
-          else sweep<K, GRAD, false, false>(src, n, lam, ua, ub, na, nb, ga, gb);
+          else if (one) sweep<K, GRAD, false, false>(src, n, lam, ua, ub, na, nb, ga, gb);
+          if (r) sweep_split<K, GRAD, false>(src, n, lam, uc, sub, gs, nc, gc);
         }
       }
     }
-    // far field for both target slots, each lane on its own targets
-    for (int slot = 0; slot < (two ? 2 : 1); ++slot) {
-      const bool valid = slot == 0 ? va : vb;
-      const float u0 = slot == 0 ? ua[0] : ub[0];
-      const float u1 = slot == 0 ? ua[1] : ub[1];
-      const float u2 = slot == 0 ? ua[2] : ub[2];
-      float far = 0.f, gf[3] = {0.f, 0.f, 0.f};
-      float pz = 1.f, pzm = 0.f;
-      for (int ms = 0; ms <= p; ++ms) {
-        float py = 1.f, pym = 0.f;
-        for (int m1 = 0; m1 <= p - ms; ++m1) {
-          const int base = pd.frow[ms * (p + 1) + m1];
-          const int len = p - ms - m1 + 1;
-          float v = cb[base + len - 1], dv = 0.f;
-          for (int k = len - 2; k >= 0; --k) {
-            if (GRAD) dv = dv * u0 + v;
-            v = v * u0 + cb[base + k];
-          }
-          far += v * py * pz;
-          if (GRAD) {
-            gf[0] += dv * py * pz;
-            gf[1] += v * pym * pz;
-            gf[2] += v * py * pzm;
-          }
-          pym = pym * u1 + py;
-          py *= u1;
-        }
-        pzm = pzm * u2 + pz;
-        pz *= u2;
+    if (r) {  // combine the remainder groups (groups are aligned runs of gs lanes)
+      for (int off = gs >> 1; off > 0; off >>= 1) {
+        nc += __shfl_xor_sync(0xffffffffu, nc, off);
+        if (GRAD)
+          for (int k = 0; k < 3; ++k) gc[k] += __shfl_xor_sync(0xffffffffu, gc[k], off);
       }
+    }
+    // far field for the slots in use, each lane on its own targets
+    const int nslot = nfull + (r ? 1 : 0);
+    for (int slot = 0; slot < nslot; ++slot) {
+      const bool split = slot == nfull;  // the remainder slot
+      const bool valid = split ? (vc && sub == 0) : (slot == 0 ? va : vb);
+      const float* u = split ? uc : (slot == 0 ? ua : ub);
+      float gf[3] = {0.f, 0.f, 0.f};
+      const float far = far_field<GRAD>(pd, cb, u[0], u[1], u[2], gf);
       if (valid) {
-        const int t = slot == 0 ? ta : tb2;
+        const int t = split ? tc : (slot == 0 ? ta : tb2);
         const int orig = tperm[t];
-        const float nv = slot == 0 ? na : nb;
+        const float nv = split ? nc : (slot == 0 ? na : nb);
         if (phi) phi[orig] = (double)far + phi_scale * (double)nv;
         if (GRAD && grad) {
-          const float gn0 = slot == 0 ? ga[0] : gb[0], gn1 = slot == 0 ? ga[1] : gb[1],
-                      gn2 = slot == 0 ? ga[2] : gb[2];
-          grad[(size_t)orig * 3 + 0] = (double)gf[0] / s + grad_scale * (double)gn0;
-          grad[(size_t)orig * 3 + 1] = (double)gf[1] / s + grad_scale * (double)gn1;
-          grad[(size_t)orig * 3 + 2] = (double)gf[2] / s + grad_scale * (double)gn2;
+          const float* gn = split ? gc : (slot == 0 ? ga : gb);
+          grad[(size_t)orig * 3 + 0] = (double)gf[0] * inv_s + grad_scale * (double)gn[0];
+          grad[(size_t)orig * 3 + 1] = (double)gf[1] * inv_s + grad_scale * (double)gn[1];
+          grad[(size_t)orig * 3 + 2] = (double)gf[2] * inv_s + grad_scale * (double)gn[2];
         }
       }
     }

@@ -478,15 +478,16 @@ cudaError_t launch_build_tree(const fmm_plan_s* P, const Workspace& ws, int64_t 
                               const double* src, const double* w, int64_t n_tgt,
                               const double* tgt, cudaStream_t st, int* nl) {
   cudaError_t e;
+  const bool shared = ws.tstart == ws.sstart;  // targets are the sources: sorted once
   if (P->pd.d == 3) {
     // the FP32 path keeps only the box-relative float4 copies
     e = sort_points<3>(P, ws, n_src, src, w, ws.sstart, ws.sx, ws.sw, ws.sperm, ws.sxr, st, nl);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || shared) return e;
     e = sort_points<3>(P, ws, n_tgt, tgt, nullptr, ws.tstart, ws.tx, nullptr, ws.tperm, ws.txr,
                        st, nl);
   } else {
     e = sort_points<2>(P, ws, n_src, src, w, ws.sstart, ws.sx, ws.sw, ws.sperm, nullptr, st, nl);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || shared) return e;
     e = sort_points<2>(P, ws, n_tgt, tgt, nullptr, ws.tstart, ws.tx, nullptr, ws.tperm, nullptr,
                        st, nl);
   }
@@ -537,8 +538,10 @@ cudaError_t launch_build_adaptive(const fmm_plan_s* P, const Workspace& ws, int6
   *overflow = 0;
   cudaError_t e = asort_points(ws, n_src, src, w, ws.sx, ws.sw, ws.sperm, ws.skey, D, st, nl);
   if (e != cudaSuccess) return e;
-  e = asort_points(ws, n_tgt, tgt, nullptr, ws.tx, nullptr, ws.tperm, ws.tkey, D, st, nl);
-  if (e != cudaSuccess) return e;
+  if (ws.tkey != ws.skey) {  // else the targets are the sources, sorted once
+    e = asort_points(ws, n_tgt, tgt, nullptr, ws.tx, nullptr, ws.tperm, ws.tkey, D, st, nl);
+    if (e != cudaSuccess) return e;
+  }
   k_atree_root<<<1, 1, 0, st>>>(ws.alev, ws.apar, ws.akey, ws.as0, ws.as1, ws.at0, ws.at1,
                                 (int)n_src, (int)n_tgt);
   ++*nl;
