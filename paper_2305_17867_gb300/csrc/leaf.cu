@@ -295,181 +295,112 @@ __device__ __forceinline__ float rsqrt_fast(float x) {  // hardware approximatio
   return y;
 }
 
-__device__ __forceinline__ float exp_fast(float x) {  // 2^(x log2 e) on the SFU
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x * 1.4426950408889634f));
-  return y;
+
+// ---- packed pairs: two sources per instruction (f32x2 arithmetic) ----------
+// Staged sources come in pairs: A = (x0, x1, y0, y1), B = (z0, z1, w0, w1)
+// in box units relative to the target leaf; an odd count is padded with a
+// far, weightless source.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2pack(float lo, float hi) {
+  f2_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(f2_t a, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+__device__ __forceinline__ f2_t f2sub(f2_t a, f2_t b) {
+  f2_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2mul(f2_t a, f2_t b) {
+  f2_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2_t f2fma(f2_t a, f2_t b, f2_t c) {
+  f2_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
 }
 
+// Accumulates one source pair into (acc, g) for the target u = (UX, UY, UZ)
+// (each coordinate broadcast into both halves).  g collects sum w |f1| (u - y)
+// with f1 = (1/r) dG/dr; pair_sign<K>() restores the sign of f1.
 template <int K>
-__device__ __forceinline__ void pair_masked(float r2, float lam, float& v, float& f1) {
-  const bool ok = r2 > 0.f;
-  const float ri = ok ? rsqrt_fast(r2) : 0.f;
-  if (K == FMM_KERNEL_LAPLACE) {
-    v = ri;
-    f1 = -ri * ri * ri;
-  } else if (K == FMM_KERNEL_YUKAWA) {
-    const float r = r2 * ri;
-    const float e = ok ? exp_fast(-lam * r) : 0.f;
-    v = e * ri;
-    f1 = e * (-lam * ri * ri - ri * ri * ri);
-  } else {
-    v = r2 * ri;
-    f1 = ri;
-  }
+__host__ __device__ constexpr float pair_sign() {
+  return K == FMM_KERNEL_BIHARMONIC ? 1.f : -1.f;
 }
 
-// Pair without the x == y guard: used for source leaves other than the
-// target's own, where no coincident point can exist.
-template <int K>
-__device__ __forceinline__ void pair_plain(float r2, float lam, float& v, float& f1) {
-  // r2 carries +1e-30 (added by the caller inside the fused multiply-adds):
-  // distinct points of adjacent leaves closer than the float resolution of the
-  // box-relative coordinates would otherwise round to r2 = 0
-  const float ri = rsqrt_fast(r2);
-  if (K == FMM_KERNEL_LAPLACE) {
-    v = ri;
-    f1 = -ri * ri * ri;
-  } else if (K == FMM_KERNEL_YUKAWA) {
-    const float r = r2 * ri;
-    const float e = exp_fast(-lam * r);
-    v = e * ri;
-    f1 = e * (-lam * ri * ri - ri * ri * ri);
-  } else {
-    v = r2 * ri;
-    f1 = ri;
-  }
-}
-
-template <int K, bool MASK>
-__device__ __forceinline__ void pair_sel(float r2, float lam, float& v, float& f1) {
-  if (MASK) pair_masked<K>(r2, lam, v, f1);
-  else pair_plain<K>(r2, lam, v, f1);
-}
-
-// squared distance; pairs without the x == y guard carry +1e-30 so that
-// r2 > 0 without an extra instruction
-template <bool MASK>
-__device__ __forceinline__ float dist2(float dx, float dy, float dz) {
-  return fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, MASK ? 0.f : 1e-30f)));
-}
-
-// One sweep over n staged sources for one or two target slots per lane.
-template <int K, bool GRAD, bool MASK, bool TWO>
-__device__ __forceinline__ void sweep(const float4* __restrict__ src, int n, float lam,
-                                      const float* ua, const float* ub, float& na, float& nb,
-                                      float* ga, float* gb) {
-  float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
-  int q = 0;
-  for (; q + 3 < n; q += 4) {
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const float4 v = src[q + h];
-      {
-        const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
-        float pv, f1;
-        pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
-        a[h] = fmaf(v.w, pv, a[h]);
-        if (GRAD) {
-          const float fw = v.w * f1;
-          ga[0] = fmaf(fw, dx, ga[0]);
-          ga[1] = fmaf(fw, dyv, ga[1]);
-          ga[2] = fmaf(fw, dzv, ga[2]);
-        }
-      }
-      if (TWO) {
-        const float ex = ub[0] - v.x, eyv = ub[1] - v.y, ezv = ub[2] - v.z;
-        float pw, f2;
-        pair_sel<K, MASK>(dist2<MASK>(ex, eyv, ezv), lam, pw, f2);
-        b[h] = fmaf(v.w, pw, b[h]);
-        if (GRAD) {
-          const float fw = v.w * f2;
-          gb[0] = fmaf(fw, ex, gb[0]);
-          gb[1] = fmaf(fw, eyv, gb[1]);
-          gb[2] = fmaf(fw, ezv, gb[2]);
-        }
-      }
-    }
-  }
-  for (; q < n; ++q) {
-    const float4 v = src[q];
-    const float dx = ua[0] - v.x, dyv = ua[1] - v.y, dzv = ua[2] - v.z;
-    float pv, f1;
-    pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
-    a[0] = fmaf(v.w, pv, a[0]);
-    if (GRAD) {
-      const float fw = v.w * f1;
-      ga[0] = fmaf(fw, dx, ga[0]);
-      ga[1] = fmaf(fw, dyv, ga[1]);
-      ga[2] = fmaf(fw, dzv, ga[2]);
-    }
-    if (TWO) {
-      const float ex = ub[0] - v.x, eyv = ub[1] - v.y, ezv = ub[2] - v.z;
-      float pw, f2;
-      pair_sel<K, MASK>(dist2<MASK>(ex, eyv, ezv), lam, pw, f2);
-      b[0] = fmaf(v.w, pw, b[0]);
-      if (GRAD) {
-        const float fw = v.w * f2;
-        gb[0] = fmaf(fw, ex, gb[0]);
-        gb[1] = fmaf(fw, eyv, gb[1]);
-        gb[2] = fmaf(fw, ezv, gb[2]);
-      }
-    }
-  }
-  na += (a[0] + a[1]) + (a[2] + a[3]);
-  if (TWO) nb += (b[0] + b[1]) + (b[2] + b[3]);
-}
-
-// Remainder targets (at most 16 after the full 32-lane passes): lane group
-// of gs lanes per target, each lane taking every gs-th staged source; the
-// group's partial sums are combined by shuffles at the end.
 template <int K, bool GRAD, bool MASK>
-__device__ __forceinline__ void sweep_split(const float4* __restrict__ src, int n, float lam,
-                                            const float* uc, int sub, int gs, float& nc,
-                                            float* gc) {
-  float a0 = 0.f, a1 = 0.f;
-  int q = sub;
-  for (; q + gs < n; q += 2 * gs) {
-    const float4 v = src[q], v2 = src[q + gs];
-    {
-      const float dx = uc[0] - v.x, dyv = uc[1] - v.y, dzv = uc[2] - v.z;
-      float pv, f1;
-      pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
-      a0 = fmaf(v.w, pv, a0);
-      if (GRAD) {
-        const float fw = v.w * f1;
-        gc[0] = fmaf(fw, dx, gc[0]);
-        gc[1] = fmaf(fw, dyv, gc[1]);
-        gc[2] = fmaf(fw, dzv, gc[2]);
-      }
-    }
-    {
-      const float dx = uc[0] - v2.x, dyv = uc[1] - v2.y, dzv = uc[2] - v2.z;
-      float pv, f1;
-      pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
-      a1 = fmaf(v2.w, pv, a1);
-      if (GRAD) {
-        const float fw = v2.w * f1;
-        gc[0] = fmaf(fw, dx, gc[0]);
-        gc[1] = fmaf(fw, dyv, gc[1]);
-        gc[2] = fmaf(fw, dzv, gc[2]);
-      }
-    }
+__device__ __forceinline__ void pair2(const float4 A, const float4 B, f2_t UX, f2_t UY, f2_t UZ,
+                                      f2_t LAM, f2_t NL2E, f2_t& acc, f2_t* g) {
+  const f2_t dx = f2sub(UX, f2pack(A.x, A.y));
+  const f2_t dy = f2sub(UY, f2pack(A.z, A.w));
+  const f2_t dz = f2sub(UZ, f2pack(B.x, B.y));
+  const f2_t W = f2pack(B.z, B.w);
+  const f2_t eps = MASK ? 0ull : f2pack(1e-30f, 1e-30f);
+  const f2_t r2 = f2fma(dz, dz, f2fma(dy, dy, f2fma(dx, dx, eps)));
+  float r2l, r2h;
+  f2unpack(r2, r2l, r2h);
+  float ril = rsqrt_fast(r2l), rih = rsqrt_fast(r2h);
+  if (MASK) {  // x == y contributes nothing
+    ril = r2l > 0.f ? ril : 0.f;
+    rih = r2h > 0.f ? rih : 0.f;
   }
-  if (q < n) {
-    const float4 v = src[q];
-    const float dx = uc[0] - v.x, dyv = uc[1] - v.y, dzv = uc[2] - v.z;
-    float pv, f1;
-    pair_sel<K, MASK>(dist2<MASK>(dx, dyv, dzv), lam, pv, f1);
-    a0 = fmaf(v.w, pv, a0);
-    if (GRAD) {
-      const float fw = v.w * f1;
-      gc[0] = fmaf(fw, dx, gc[0]);
-      gc[1] = fmaf(fw, dyv, gc[1]);
-      gc[2] = fmaf(fw, dzv, gc[2]);
-    }
+  const f2_t ri = f2pack(ril, rih);
+  f2_t v, f1 = 0ull;
+  if (K == FMM_KERNEL_LAPLACE) {
+    v = ri;
+    if (GRAD) f1 = f2mul(f2mul(ri, ri), ri);  // |f1| = 1/r^3
+  } else if (K == FMM_KERNEL_YUKAWA) {
+    float al, ah, el, eh;
+    f2unpack(f2mul(f2mul(r2, ri), NL2E), al, ah);  // -lam r log2(e)
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(el) : "f"(al));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(eh) : "f"(ah));
+    v = f2mul(f2pack(el, eh), ri);                          // e^{-lam r} / r (0 if masked)
+    if (GRAD) f1 = f2mul(v, f2fma(ri, ri, f2mul(LAM, ri)));  // |f1| = v (lam/r + 1/r^2)
+  } else {  // biharmonic: G = r, f1 = 1/r
+    v = f2mul(r2, ri);
+    if (GRAD) f1 = ri;
   }
-  nc += a0 + a1;
+  acc = f2fma(W, v, acc);
+  if (GRAD) {
+    const f2_t fw = f2mul(W, f1);
+    g[0] = f2fma(fw, dx, g[0]);
+    g[1] = f2fma(fw, dy, g[1]);
+    g[2] = f2fma(fw, dz, g[2]);
+  }
+}
+
+// One target per lane over source pairs k0, k0 + step, ... < npair.
+template <int K, bool GRAD, bool MASK>
+__device__ __forceinline__ void sweep2(const float4* __restrict__ pa, const float4* __restrict__ pb,
+                                       int npair, int k0, int step, const float* u, float lam,
+                                       float& acc_out, float* g_out) {
+  const f2_t UX = f2pack(u[0], u[0]), UY = f2pack(u[1], u[1]), UZ = f2pack(u[2], u[2]);
+  const f2_t LAM = f2pack(lam, lam);
+  const float nl = -lam * 1.4426950408889634f;
+  const f2_t NL2E = f2pack(nl, nl);
+  f2_t acc0 = 0ull, acc1 = 0ull;
+  f2_t g[3] = {0ull, 0ull, 0ull};
+  int k = k0;
+  for (; k + step < npair; k += 2 * step) {
+    pair2<K, GRAD, MASK>(pa[k], pb[k], UX, UY, UZ, LAM, NL2E, acc0, g);
+    pair2<K, GRAD, MASK>(pa[k + step], pb[k + step], UX, UY, UZ, LAM, NL2E, acc1, g);
+  }
+  if (k < npair) pair2<K, GRAD, MASK>(pa[k], pb[k], UX, UY, UZ, LAM, NL2E, acc0, g);
+  float a, b, c, d;
+  f2unpack(acc0, a, b);
+  f2unpack(acc1, c, d);
+  acc_out += (a + b) + (c + d);
+  if (GRAD)
+    for (int j = 0; j < 3; ++j) {
+      float lo, hi;
+      f2unpack(g[j], lo, hi);
+      g_out[j] += pair_sign<K>() * (lo + hi);
+    }
 }
 
 // far field (L2P) at box-relative u: sum_m Dt_m/m! u^m by rows of the full
@@ -513,12 +444,13 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
     double* __restrict__ grad) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t b = (int64_t)blockIdx.x * kFastWarps + warp;
-  __shared__ float4 stage[kFastWarps][kStageSrc];
+  __shared__ float4 stage[kFastWarps][kStageSrc];  // kStageSrc/2 source pairs: A then B
   if (b >= nleaf) return;
   const int t0 = tstart[b], t1 = tstart[b + 1];
   if (t0 == t1) return;
-  float4* src = stage[warp];
-  const int p = pd.p, nl = 1 << L;
+  float4* pa = stage[warp];
+  float4* pb = stage[warp] + kStageSrc / 2;
+  const int nl = 1 << L;
   int bc[3];
   {
     int64_t t = b;
@@ -589,26 +521,37 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
       const int e1 = sstart[rowb + bx0 + 1], e2 = sstart[rowb + min(bx0 + 2, bx1 + 1)];
       for (int jb = j0; jb < j1; jb += kStageSrc) {
         const int n = min(kStageSrc, j1 - jb);
+        const int npair = (n + 1) >> 1;
         __syncwarp();
-        for (int q = lane; q < n; q += 32) {
-          const int j = jb + q;
-          float4 v = sxr[j];
-          const int bx = bx0 + (j >= e1) + (j >= e2);
-          v.x += (float)(bx - bc[0]);
-          v.y += (float)dy;
-          v.z += (float)dz;
-          src[q] = v;
+        for (int k = lane; k < npair; k += 32) {
+          float4 v[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int q = 2 * k + h;
+            if (q < n) {
+              const int j = jb + q;
+              v[h] = sxr[j];
+              const int bx = bx0 + (j >= e1) + (j >= e2);
+              v[h].x += (float)(bx - bc[0]);
+              v[h].y += (float)dy;
+              v[h].z += (float)dz;
+            } else {
+              v[h] = make_float4(1e4f, 0.f, 0.f, 0.f);  // far and weightless
+            }
+          }
+          pa[k] = make_float4(v[0].x, v[1].x, v[0].y, v[1].y);
+          pb[k] = make_float4(v[0].z, v[1].z, v[0].w, v[1].w);
         }
         __syncwarp();
         const bool center = (dy == 0 && dz == 0);  // only the own leaf can hold x == y
         if (center) {
-          if (two) sweep<K, GRAD, true, true>(src, n, lam, ua, ub, na, nb, ga, gb);
-          else if (one) sweep<K, GRAD, true, false>(src, n, lam, ua, ub, na, nb, ga, gb);
-          if (r) sweep_split<K, GRAD, true>(src, n, lam, uc, sub, gs, nc, gc);
+          if (one) sweep2<K, GRAD, true>(pa, pb, npair, 0, 1, ua, lam, na, ga);
+          if (two) sweep2<K, GRAD, true>(pa, pb, npair, 0, 1, ub, lam, nb, gb);
+          if (r) sweep2<K, GRAD, true>(pa, pb, npair, sub, gs, uc, lam, nc, gc);
         } else {
-          if (two) sweep<K, GRAD, false, true>(src, n, lam, ua, ub, na, nb, ga, gb);
-          else if (one) sweep<K, GRAD, false, false>(src, n, lam, ua, ub, na, nb, ga, gb);
-          if (r) sweep_split<K, GRAD, false>(src, n, lam, uc, sub, gs, nc, gc);
+          if (one) sweep2<K, GRAD, false>(pa, pb, npair, 0, 1, ua, lam, na, ga);
+          if (two) sweep2<K, GRAD, false>(pa, pb, npair, 0, 1, ub, lam, nb, gb);
+          if (r) sweep2<K, GRAD, false>(pa, pb, npair, sub, gs, uc, lam, nc, gc);
         }
       }
     }
@@ -624,19 +567,24 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
     for (int slot = 0; slot < nslot; ++slot) {
       const bool split = slot == nfull;  // the remainder slot
       const bool valid = split ? (vc && sub == 0) : (slot == 0 ? va : vb);
-      const float* u = split ? uc : (slot == 0 ? ua : ub);
+      // select values, not pointers, so the per-slot arrays stay in registers
+      const float u0 = split ? uc[0] : (slot == 0 ? ua[0] : ub[0]);
+      const float u1 = split ? uc[1] : (slot == 0 ? ua[1] : ub[1]);
+      const float u2 = split ? uc[2] : (slot == 0 ? ua[2] : ub[2]);
       float gf[3] = {0.f, 0.f, 0.f};
-      const float far = far_field<GRAD>(pd, cb, u[0], u[1], u[2], gf);
+      const float far = far_field<GRAD>(pd, cb, u0, u1, u2, gf);
       if (valid) {
         const int t = split ? tc : (slot == 0 ? ta : tb2);
         const int orig = tperm[t];
         const float nv = split ? nc : (slot == 0 ? na : nb);
         if (phi) phi[orig] = (double)far + phi_scale * (double)nv;
         if (GRAD && grad) {
-          const float* gn = split ? gc : (slot == 0 ? ga : gb);
-          grad[(size_t)orig * 3 + 0] = (double)gf[0] * inv_s + grad_scale * (double)gn[0];
-          grad[(size_t)orig * 3 + 1] = (double)gf[1] * inv_s + grad_scale * (double)gn[1];
-          grad[(size_t)orig * 3 + 2] = (double)gf[2] * inv_s + grad_scale * (double)gn[2];
+          const float g0 = split ? gc[0] : (slot == 0 ? ga[0] : gb[0]);
+          const float g1 = split ? gc[1] : (slot == 0 ? ga[1] : gb[1]);
+          const float g2 = split ? gc[2] : (slot == 0 ? ga[2] : gb[2]);
+          grad[(size_t)orig * 3 + 0] = (double)gf[0] * inv_s + grad_scale * (double)g0;
+          grad[(size_t)orig * 3 + 1] = (double)gf[1] * inv_s + grad_scale * (double)g1;
+          grad[(size_t)orig * 3 + 2] = (double)gf[2] * inv_s + grad_scale * (double)g2;
         }
       }
     }

@@ -82,19 +82,17 @@ __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off,
                             typename F::T* __restrict__ bhi, typename F::T* __restrict__ blo) {
   const int l = blockIdx.y + 2;
   const int nl = 1 << l, H = nl >> 1;
-  const int64_t nbox = (int64_t)nl * nl * nl;
-  const int64_t tot = nbox * JP;
+  const unsigned tot = (unsigned)JP << (3 * l);  // boxes of the level x JP (< 2^32)
   const double* mpl = mp + lev_off.o[l] * nj;
   typename F::T* bh = bhi + lev_off.o[l] * JP;
   typename F::T* bl = blo ? blo + lev_off.o[l] * JP : nullptr;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(e % JP);
-    const int64_t b = e / JP;
-    const int x = (int)(b % nl), y = (int)((b / nl) % nl), z = (int)(b / ((int64_t)nl * nl));
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    const unsigned b = e / (unsigned)JP;  // 32-bit division (JP need not be a power of two)
+    const int q = (int)(e - b * (unsigned)JP);
+    const int x = (int)(b & (nl - 1)), y = (int)((b >> l) & (nl - 1)), z = (int)(b >> (2 * l));
     const int sg = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
-    const int64_t dst = ((((int64_t)sg * H + (z >> 1)) * H + (y >> 1)) * H + (x >> 1)) * JP + q;
-    const double v = q < nj ? mpl[b * nj + q] : 0.0;
+    const size_t dst = ((((size_t)sg * H + (z >> 1)) * H + (y >> 1)) * H + (x >> 1)) * JP + q;
+    const double v = q < nj ? mpl[(size_t)b * nj + q] : 0.0;
     typename F::T hi, lo;
     F::split(v, hi, lo);
     bh[dst] = hi;

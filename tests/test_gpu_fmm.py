@@ -258,3 +258,21 @@ def test_uniform_m2l_translation_count(torch_cuda, d, L):
 
     plan = FMM("laplace", d=d, p=4, levels=L)
     assert plan.last_m2l_count() == bench.m2l_count(d, L)
+
+
+@pytest.mark.parametrize("kernel,p,lam", [("laplace", 8, 0.0), ("yukawa", 8, 1.0),
+                                          ("biharmonic", 6, 0.0)])
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+def test_mixed_precision_gradient(torch_cuda, oracle, kernel, p, lam, precision):
+    # the float leaf kernel with the analytic gradient (packed pair arithmetic),
+    # separate targets and sources = targets
+    rng = np.random.default_rng(31)
+    src = rng.random((20000, 3))
+    w = rng.uniform(-1, 1, 20000)
+    for tgt in (rng.random((9000, 3)), None):
+        t = src if tgt is None else tgt
+        ref, gref = oracle.fmm_uniform(kernel, 3, p, 4, src, w, t, lam=lam, grad=True)
+        got, g = gpu_fmm(torch_cuda, kernel, 3, p, 4, src, w, tgt, lam=lam,
+                         precision=precision, grad=True)
+        assert rel_l2(got, ref) < 5e-6
+        assert rel_l2(g, gref) < 5e-5
