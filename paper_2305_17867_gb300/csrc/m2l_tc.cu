@@ -39,15 +39,18 @@ constexpr int kTileBytesB = kMaxN * kRowBytes;
 
 // Operand formats: tf32 (fp32 storage, 32 per 128-byte row, kind::tf32) and
 // bf16 (64 per row, kind::f16).  Both split a value into hi + lo.
+// The split works on the float rounding of the value (one conversion from
+// FP64): lo = f - hi is exact in float, and keeps the bits the tf32/bf16
+// format drops from hi.
 struct FmtTF32 {
   using T = float;
   static constexpr int kRow = 32;
   static constexpr int kIdesc = 2;
   static constexpr bool kF16 = false;
-  static __device__ __forceinline__ void split(double v, T& hi, T& lo) {
-    const float h = tc::tf32_rna((float)v);
+  static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
+    const float h = tc::tf32_rna(f);
     hi = h;
-    lo = tc::tf32_rna((float)(v - (double)h));
+    lo = tc::tf32_rna(f - h);
   }
 };
 struct FmtBF16 {
@@ -55,9 +58,9 @@ struct FmtBF16 {
   static constexpr int kRow = 64;
   static constexpr int kIdesc = 1;
   static constexpr bool kF16 = true;
-  static __device__ __forceinline__ void split(double v, T& hi, T& lo) {
-    hi = __float2bfloat16_rn((float)v);
-    lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
+  static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
+    hi = __float2bfloat16_rn(f);
+    lo = __float2bfloat16_rn(f - __bfloat162float(hi));
   }
 };
 
@@ -92,7 +95,7 @@ __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off,
     const int x = (int)(b & (nl - 1)), y = (int)((b >> l) & (nl - 1)), z = (int)(b >> (2 * l));
     const int sg = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
     const size_t dst = ((((size_t)sg * H + (z >> 1)) * H + (y >> 1)) * H + (x >> 1)) * JP + q;
-    const double v = q < nj ? mpl[(size_t)b * nj + q] : 0.0;
+    const float v = q < nj ? (float)mpl[(size_t)b * nj + q] : 0.f;
     typename F::T hi, lo;
     F::split(v, hi, lo);
     bh[dst] = hi;
@@ -100,14 +103,19 @@ __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off,
   }
 }
 
-// dense offset matrices A_h[i][q] = Ht_h[i + q] for the 343 offsets of a level
+// dense offset matrices A_h[i][q] = Ht_h[i + q] for the 343 offsets of a level:
+// one block per (offset, table level); the offset's Hankel row is split into
+// hi/lo once in shared memory, then expanded to the MP x JP matrix
 template <int D, typename F>
-__global__ void k_build_tmat(PlanDev pd, const double* __restrict__ htab, int MP, int JP,
-                             typename F::T* __restrict__ thi, typename F::T* __restrict__ tlo) {
+__global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const double* __restrict__ htab,
+                                                    int MP, int JP,
+                                                    typename F::T* __restrict__ thi,
+                                                    typename F::T* __restrict__ tlo) {
+  using T = typename F::T;
   const int o = blockIdx.x;
-  htab += (size_t)blockIdx.z * 343 * pd.nh;
-  thi += (size_t)blockIdx.z * 343 * MP * JP;
-  if (tlo) tlo += (size_t)blockIdx.z * 343 * MP * JP;
+  htab += (size_t)blockIdx.y * 343 * pd.nh;
+  thi += (size_t)blockIdx.y * 343 * MP * JP;
+  if (tlo) tlo += (size_t)blockIdx.y * 343 * MP * JP;
   {
     int t = o;
     bool far = false;
@@ -118,24 +126,28 @@ __global__ void k_build_tmat(PlanDev pd, const double* __restrict__ htab, int MP
     }
     if (!far) return;
   }
+  extern __shared__ __align__(16) unsigned char smtm[];
+  T* hh = reinterpret_cast<T*>(smtm);
+  T* hl = hh + pd.nh;
   const double* H = htab + (size_t)o * pd.nh;
+  for (int e = threadIdx.x; e < pd.nh; e += blockDim.x) F::split((float)H[e], hh[e], hl[e]);
+  __syncthreads();
   const int P2 = 2 * pd.p;
-  const int rows = 8;
-  const int i0 = blockIdx.y * rows;
-  for (int e = threadIdx.x; e < rows * JP; e += blockDim.x) {
-    const int i = i0 + e / JP, q = e % JP;
-    double v = 0.0;
+  T* dh = thi + (size_t)o * MP * JP;
+  T* dl = tlo ? tlo + (size_t)o * MP * JP : nullptr;
+  const T zero = T(0.f);
+  for (int e = threadIdx.x; e < MP * JP; e += blockDim.x) {
+    const int i = e / JP, q = e - i * JP;
+    T vh = zero, vl = zero;
     if (i < pd.nj && q < pd.nj) {
       const char4 a = pd.mi[i], b = pd.mi[q];
       const int m0 = a.x + b.x, m1 = a.y + b.y, m2 = a.z + b.z;
       const int idx = D == 3 ? pd.hrow[m2 * (P2 + 1) + m1] + m0 : pd.hrow[m1] + m0;
-      v = H[idx];
+      vh = hh[idx];
+      vl = hl[idx];
     }
-    const size_t dst = ((size_t)o * MP + i) * JP + q;
-    typename F::T hi, lo;
-    F::split(v, hi, lo);
-    thi[dst] = hi;
-    if (tlo) tlo[dst] = lo;
+    dh[e] = vh;
+    if (dl) dl[e] = vl;
   }
 }
 
@@ -446,7 +458,12 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
   LevOff lo;
   for (int l = 0; l <= FMM_MAX_LEVELS; ++l) lo.o[l] = l <= L + 1 ? ws.lev_off[l] : 0;
   k_pack_beta<F><<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, bhi0, blo);
-  k_build_tmat<3, F><<<dim3(noff, MP / 8, tlev), 256, 0, st>>>(pd, ws.htab, MP, JP, thi0, tlo);
+  {
+    const size_t sm = 2 * sizeof(T) * pd.nh;
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_build_tmat<3, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_build_tmat<3, F><<<dim3(noff, tlev), 256, sm, st>>>(pd, ws.htab, MP, JP, thi0, tlo);
+  }
   TcParams prm;
   std::memset(&prm, 0, sizeof(prm));
   prm.nj = nj;
