@@ -177,7 +177,7 @@ def profiled_traffic(prec: str):
             if len(f) == 5 and f[0] == "traffic:" and f[1] == prec and f[3] == "sources":
                 if f[4] != want:
                     return None, "kernel changed since the capture"
-                return int(f[2]), ("ncu dram__bytes.sum.per_second x gpu__time_duration.sum of one "
+                return int(f[2]), ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                    "launch, " + path[len(ROOT) + 1:])
     return None, "no capture for this precision"
 
