@@ -98,8 +98,8 @@ typedef struct {
   int d;               /* 2 or 3 */
   int p;               /* expansion order, 1..24 */
   int levels;          /* > 0: leaf depth L of the uniform tree, 2..7 (root = 0);
-                          < 0: adaptive tree (3D, FP64) refined down to at most
-                          level -levels (1..10) */
+                          < 0: adaptive tree (3D; precision FP64 or FP32)
+                          refined down to at most level -levels (1..10) */
   const fmm_pde* pde;  /* NULL: the kernel's own PDE */
   double root_lo[3];   /* lower corner of the root box */
   double root_size;    /* side of the root box; <= 0: bounding cube of the

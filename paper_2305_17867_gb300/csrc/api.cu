@@ -241,7 +241,8 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   if (p < 1 || p > FMM_MAXP) return FMM_ERR_ARG;
   if (L < 0) {  // adaptive tree
     if (-L > FMM_MAX_ADEPTH || desc->max_leaf < 1) return FMM_ERR_ARG;
-    if (d != 3 || desc->precision != FMM_PREC_FP64 || desc->m2l != FMM_M2L_DENSE)
+    if (d != 3 || desc->m2l != FMM_M2L_DENSE) return FMM_ERR_UNSUPPORTED;
+    if (desc->precision != FMM_PREC_FP64 && desc->precision != FMM_PREC_FP32)
       return FMM_ERR_UNSUPPORTED;
   } else if (L < 2 || L > (d == 3 ? 7 : 8)) {
     return FMM_ERR_ARG;

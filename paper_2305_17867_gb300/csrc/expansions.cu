@@ -791,6 +791,67 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l(PlanDev pd, const Geom* __re
   for (int i = threadIdx.x; i < nj; i += blockDim.x) lc[(size_t)b * nj + i] += Lacc[i];
 }
 
+// Float form of k_ap2l (mixed-precision modes): the X leaf's sources are
+// staged as float (c_B - y)/s_B (FP64 subtraction once per source), each
+// thread runs the float derivative recurrence for its sources and adds
+// w * Ht into a float accumulator in shared memory.
+constexpr int kAFStage = 256;
+
+__global__ void __launch_bounds__(kAThreads) k_ap2l_f32(PlanDev pd, const Geom* __restrict__ g,
+                                                        ATree t, const double* __restrict__ sx0,
+                                                        const double* __restrict__ sx1,
+                                                        const double* __restrict__ sx2,
+                                                        const double* __restrict__ sw,
+                                                        double* __restrict__ lc) {
+  const int b = t.loff[2] + blockIdx.x;
+  if (b >= t.loff[t.maxlev + 1] || t.t1[b] == t.t0[b]) return;
+  const int nj = pd.nj;
+  int l, bc[3];
+  abox(t, b, &l, bc);
+  double cb[3], s;
+  abox_center(g, l, bc, cb, &s);
+  extern __shared__ __align__(16) float smp[];
+  float4* stage = reinterpret_cast<float4*>(smp);  // kAFStage
+  float* Lacc = smp + 4 * kAFStage;
+  const int sl = min(pd.c, pd.p + 1) * (pd.p + 1);
+  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  float* S = Lacc + ((nj + 3) & ~3) + threadIdx.x * per;
+  for (int i = threadIdx.x; i < nj; i += blockDim.x) Lacc[i] = 0.f;
+  const double inv_s = 1.0 / s;
+  const float lam = (float)(pd.lam * s), scale = (float)deriv_scale(pd, s);
+  const int pc[3] = {bc[0] >> 1, bc[1] >> 1, bc[2] >> 1};
+  bool any = false;
+  for (int lp = l - 1; lp >= 0; --lp) {
+    const int an[3] = {bc[0] >> (l - lp), bc[1] >> (l - lp), bc[2] >> (l - lp)};
+    for (int nb = 0; nb < 27; ++nb) {
+      const int nc[3] = {an[0] + nb % 3 - 1, an[1] + (nb / 3) % 3 - 1, an[2] + nb / 9 - 1};
+      const int A = alookup(t, lp, nc);
+      if (A < 0 || !t.leaf[A]) continue;
+      if (!aadjacent(lp, nc, l - 1, pc) || aadjacent(lp, nc, l, bc)) continue;
+      any = true;
+      for (int jb = t.s0[A]; jb < t.s1[A]; jb += kAFStage) {
+        const int n = min(kAFStage, t.s1[A] - jb);
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+          const int j = jb + q;
+          stage[q] = make_float4((float)((cb[0] - sx0[j]) * inv_s), (float)((cb[1] - sx1[j]) * inv_s),
+                                 (float)((cb[2] - sx2[j]) * inv_s), (float)sw[j]);
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+          const float4 v = stage[q];
+          const float x[3] = {v.x, v.y, v.z};
+          deriv_point<float>(pd, x, lam, scale * v.w, S, sl,
+                             [&](int pos, float h) { atomicAdd(&Lacc[pos], h); });
+        }
+      }
+    }
+  }
+  if (!any) return;  // block-uniform
+  __syncthreads();
+  for (int i = threadIdx.x; i < nj; i += blockDim.x) lc[(size_t)b * nj + i] += (double)Lacc[i];
+}
+
 }  // namespace
 
 cudaError_t launch_adaptive_upward(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
@@ -805,16 +866,22 @@ cudaError_t launch_adaptive_upward(const fmm_plan_s* P, const Workspace& ws, con
     const size_t sm2 = pwb * kP2mWarps;
     const unsigned nb = (unsigned)((n + kP2mWarps - 1) / kP2mWarps);
     const int ntl = (pd.nfull + 31) / 32;
-#define AP2M(NTT)                                                                          \
+#define AP2M(TT, NTT)                                                                      \
   do {                                                                                     \
-    set_smem(k_ap2m_warp<double, NTT>, sm2);                                               \
-    k_ap2m_warp<double, NTT><<<nb, 32 * kP2mWarps, sm2, st>>>(pd, ws.geom, t, ws.sx[0],    \
-                                                              ws.sx[1], ws.sx[2], ws.sw, ws.mp); \
+    set_smem(k_ap2m_warp<TT, NTT>, sm2);                                                   \
+    k_ap2m_warp<TT, NTT><<<nb, 32 * kP2mWarps, sm2, st>>>(pd, ws.geom, t, ws.sx[0],        \
+                                                          ws.sx[1], ws.sx[2], ws.sw, ws.mp); \
   } while (0)
-    if (ntl <= 4) AP2M(4);
-    else if (ntl <= 10) AP2M(10);
-    else if (ntl <= 16) AP2M(16);
-    else AP2M(32);
+#define AP2MN(TT)                                                                          \
+  do {                                                                                     \
+    if (ntl <= 4) AP2M(TT, 4);                                                             \
+    else if (ntl <= 10) AP2M(TT, 10);                                                      \
+    else if (ntl <= 16) AP2M(TT, 16);                                                      \
+    else AP2M(TT, 32);                                                                     \
+  } while (0)
+    if (P->desc.precision == FMM_PREC_FP64) AP2MN(double);
+    else AP2MN(float);  // float sums from FP64 inputs in the mixed modes
+#undef AP2MN
 #undef AP2M
     ++*nl;
   }
@@ -837,10 +904,18 @@ cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, co
   {
     const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
     const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
-    const size_t smem = sizeof(double) * (((pd.nj + 1) & ~1) + (size_t)per * kAThreads);
-    set_smem(k_ap2l, smem);
-    k_ap2l<<<(unsigned)(nbox - t.loff[2]), kAThreads, smem, st>>>(
-        pd, ws.geom, t, ws.sx[0], ws.sx[1], ws.sx[2], ws.sw, ws.lc);
+    if (P->desc.precision == FMM_PREC_FP64) {
+      const size_t smem = sizeof(double) * (((pd.nj + 1) & ~1) + (size_t)per * kAThreads);
+      set_smem(k_ap2l, smem);
+      k_ap2l<<<(unsigned)(nbox - t.loff[2]), kAThreads, smem, st>>>(
+          pd, ws.geom, t, ws.sx[0], ws.sx[1], ws.sx[2], ws.sw, ws.lc);
+    } else {
+      const size_t smem =
+          sizeof(float) * (4 * kAFStage + ((pd.nj + 3) & ~3) + (size_t)per * kAThreads);
+      set_smem(k_ap2l_f32, smem);
+      k_ap2l_f32<<<(unsigned)(nbox - t.loff[2]), kAThreads, smem, st>>>(
+          pd, ws.geom, t, ws.sx[0], ws.sx[1], ws.sx[2], ws.sw, ws.lc);
+    }
     ++*nl;
   }
   const size_t smem = sizeof(double) * (7 * pd.nfull + 2 * (pd.p + 1));

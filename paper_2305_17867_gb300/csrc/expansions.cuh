@@ -113,34 +113,35 @@ __device__ void compress_warp(const PlanDev& pd, T* a, double s, int lane) {
 // the stored set j (order p, slabs m_s < c), degree by degree, from the same
 // r^2-led recurrences as the M2L derivative tables (Sec. 4.4; 3D Laplace,
 // Yukawa, biharmonic).  Only the last two degrees are kept: S holds 3 * sl
-// doubles (6 * sl for Yukawa), sl = min(c, p+1) * (p+1), private to the
+// values (6 * sl for Yukawa), sl = min(c, p+1) * (p+1), private to the
 // caller.  emit(pos, value) receives value * scale for the multi-index at
-// position pos of the stored layout.  lam is lambda * s.
-template <typename F>
-__device__ void deriv_point(const PlanDev& pd, const double* x, double lam, double scale,
-                            double* S, int sl, F&& emit) {
+// position pos of the stored layout.  lam is lambda * s.  T = double, or
+// float for the mixed-precision modes.
+template <typename T, typename F>
+__device__ void deriv_point(const PlanDev& pd, const T* x, T lam, T scale, T* S, int sl,
+                            F&& emit) {
   const int p = pd.p, ce = pd.c < p + 1 ? pd.c : p + 1;
   const bool yuk = pd.kernel == FMM_KERNEL_YUKAWA;
-  const double nu = pd.kernel == FMM_KERNEL_BIHARMONIC ? 1.0 : -1.0;
-  const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-  const double r = sqrt(r2), rinv2 = 1.0 / r2;
-  double* G3[3] = {S, S + sl, S + 2 * sl};
-  double* B3[3] = {S + 3 * sl, S + 4 * sl, S + 5 * sl};
+  const T nu = pd.kernel == FMM_KERNEL_BIHARMONIC ? T(1) : T(-1);
+  const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+  const T r = sqrt(r2), rinv2 = T(1) / r2;
+  T* G3[3] = {S, S + sl, S + 2 * sl};
+  T* B3[3] = {S + 3 * sl, S + 4 * sl, S + 5 * sl};
   if (yuk) {
-    const double e = exp(-lam * r);
+    const T e = exp(-lam * r);
     G3[0][0] = e / r;
     B3[0][0] = e;
   } else {
-    G3[0][0] = pd.kernel == FMM_KERNEL_BIHARMONIC ? r : 1.0 / r;
+    G3[0][0] = pd.kernel == FMM_KERNEL_BIHARMONIC ? r : T(1) / r;
   }
   emit(0, G3[0][0] * scale);
   for (int n = 1; n <= p; ++n) {
-    double* cur = G3[n % 3];
-    const double* g1s = G3[(n + 2) % 3];  // degree n-1
-    const double* g2s = G3[(n + 1) % 3];  // degree n-2
-    double* bcur = B3[n % 3];
-    const double* b1s = B3[(n + 2) % 3];
-    const double* b2s = B3[(n + 1) % 3];
+    T* cur = G3[n % 3];
+    const T* g1s = G3[(n + 2) % 3];  // degree n-1
+    const T* g2s = G3[(n + 1) % 3];  // degree n-2
+    T* bcur = B3[n % 3];
+    const T* b1s = B3[(n + 2) % 3];
+    const T* b2s = B3[(n + 1) % 3];
     for (int ms = 0; ms < ce && ms <= n; ++ms) {
       for (int m1 = 0; m1 <= n - ms; ++m1) {
         const int m[3] = {n - ms - m1, m1, ms};
@@ -151,8 +152,8 @@ __device__ void deriv_point(const PlanDev& pd, const double* x, double lam, doub
         auto pos = [](int dq, int qs, int q1) { return qs * (dq + 1) - qs * (qs - 1) / 2 + q1; };
         int q1[3] = {m[0], m[1], m[2]};
         q1[a] -= 1;
-        const double g1 = g1s[pos(n - 1, q1[2], q1[1])];
-        double g2 = 0.0, b1 = 0.0, b2 = 0.0;
+        const T g1 = g1s[pos(n - 1, q1[2], q1[1])];
+        T g2 = 0, b1 = 0, b2 = 0;
         if (yuk) b1 = b1s[pos(n - 1, q1[2], q1[1])];
         if (ma >= 2) {
           int q2[3] = {m[0], m[1], m[2]};
@@ -160,26 +161,26 @@ __device__ void deriv_point(const PlanDev& pd, const double* x, double lam, doub
           g2 = g2s[pos(n - 2, q2[2], q2[1])];
           if (yuk) b2 = b2s[pos(n - 2, q2[2], q2[1])];
         }
-        double v;
+        T v;
         if (yuk)
-          v = -(2.0 * ma - 1.0) * x[a] * g1 - (double)(ma - 1) * (ma - 1) * g2 - lam * x[a] * b1 -
-              lam * (ma - 1) * b2;
+          v = -(T(2) * ma - T(1)) * x[a] * g1 - T((ma - 1) * (ma - 1)) * g2 - lam * x[a] * b1 -
+              lam * T(ma - 1) * b2;
         else
-          v = (nu - 2.0 * (ma - 1)) * x[a] * g1 + (double)(ma - 1) * (nu - (ma - 2)) * g2;
+          v = (nu - T(2 * (ma - 1))) * x[a] * g1 + T(ma - 1) * (nu - T(ma - 2)) * g2;
         for (int bax = a + 1; bax < 3; ++bax) {
           const int mb = m[bax];
           if (mb == 0) continue;
           int qb[3] = {m[0], m[1], m[2]};
           qb[bax] -= 1;
-          v -= 2.0 * mb * x[bax] * g1s[pos(n - 1, qb[2], qb[1])];
+          v -= T(2 * mb) * x[bax] * g1s[pos(n - 1, qb[2], qb[1])];
           if (mb >= 2) {
             qb[bax] -= 1;
-            v -= (double)mb * (mb - 1) * g2s[pos(n - 2, qb[2], qb[1])];
+            v -= T(mb * (mb - 1)) * g2s[pos(n - 2, qb[2], qb[1])];
           }
         }
         const int pm = pos(n, ms, m1);
         cur[pm] = v * rinv2;
-        if (yuk) bcur[pm] = -lam * (x[a] * g1 + (ma - 1) * g2);
+        if (yuk) bcur[pm] = -lam * (x[a] * g1 + T(ma - 1) * g2);
         emit(pd.frow[ms * (p + 1) + m1] + m[0], cur[pm] * scale);
       }
     }

@@ -219,11 +219,17 @@ cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const 
                                 cudaStream_t st, int* nl) {
   const PlanDev& pd = P->pd;
   if (t.maxlev < 2) return cudaGetLastError();
-  const size_t smem = sizeof(double) * (pd.nh + pd.nj);
-  set_smem(k_am2l<double>, smem);
+  const unsigned nb = (unsigned)(t.loff[t.maxlev + 1] - t.loff[2]);
   mark_contraction(P, 0, st);
-  k_am2l<double><<<(unsigned)(t.loff[t.maxlev + 1] - t.loff[2]), kThreads, smem, st>>>(
-      pd, t, ws.mp, ws.lc, ws.htab, &ws.geom->m2l_count);
+  if (P->desc.precision == FMM_PREC_FP64) {
+    const size_t smem = sizeof(double) * (pd.nh + pd.nj);
+    set_smem(k_am2l<double>, smem);
+    k_am2l<double><<<nb, kThreads, smem, st>>>(pd, t, ws.mp, ws.lc, ws.htab, &ws.geom->m2l_count);
+  } else {
+    const size_t smem = sizeof(float) * (pd.nh + pd.nj);
+    set_smem(k_am2l<float>, smem);
+    k_am2l<float><<<nb, kThreads, smem, st>>>(pd, t, ws.mp, ws.lc, ws.htab, &ws.geom->m2l_count);
+  }
   mark_contraction(P, 1, st);
   ++*nl;
   return cudaGetLastError();

@@ -25,7 +25,7 @@ class FMM:
 
     kernel     "laplace" (d = 2, 3), "yukawa" (d = 3), "biharmonic" (d = 3)
     p          expansion order;  levels: leaf depth L of the uniform tree, or
-               -D for an adaptive tree (3D, fp64) refined to at most level D,
+               -D for an adaptive tree (3D, fp64 or fp32) refined to at most level D,
                splitting boxes that hold more than ``max_leaf`` points
     root_lo, root_size  root box; root_size <= 0 picks the bounding cube per call
     precision  "fp64" | "fp32" | "tf32" | "tf32x3" | "bf16x3"

@@ -27,10 +27,10 @@ def torch_cuda():
 
 
 def gpu_adaptive(torch, kernel, p, src, w, tgt=None, lam=0.0, max_leaf=64, depth=10,
-                 counts=False):
+                 counts=False, precision="fp64"):
     from paper_2305_17867_gb300.fmm import FMM
 
-    plan = FMM(kernel, d=3, p=p, levels=-depth, lam=lam, max_leaf=max_leaf)
+    plan = FMM(kernel, d=3, p=p, levels=-depth, lam=lam, max_leaf=max_leaf, precision=precision)
     s = torch.tensor(src, device="cuda")
     wt = torch.tensor(w, device="cuda")
     t = None if tgt is None else torch.tensor(tgt, device="cuda")
@@ -120,3 +120,27 @@ def test_yukawa_plummer_full_size_sampled(torch_cuda, oracle):
                                      lam=wl.lam, sample=idx, want_stats=True)
     assert (nb, depth) == (st["boxes"], st["depth"])
     assert rel_l2(got[idx], ref) < FP64_TOL
+
+
+# Float forms (P2M, M2L, P2L, L2P, P2P, M2P in float; M2M, L2L and the
+# derivative tables in FP64): ~24-bit products with the sums' cancellation.
+FP32_TOL = 2e-5
+
+
+@pytest.mark.parametrize("kernel,p,lam", [("laplace", 8, 0.0), ("yukawa", 8, 1.0),
+                                          ("biharmonic", 6, 0.0), ("yukawa", 12, 1.0)])
+def test_adaptive_fp32_matches_oracle(torch_cuda, oracle, kernel, p, lam):
+    src, w, tgt = plummer_case(20000 if p < 12 else 6000, 4000 if p < 12 else 1200, 42)
+    ref = oracle.fmm_adaptive(kernel, 3, p, src, w, tgt, max_leaf=32, lam=lam)
+    got, _ = gpu_adaptive(torch_cuda, kernel, p, src, w, tgt, lam=lam, max_leaf=32,
+                          precision="fp32")
+    err = rel_l2(got, ref)
+    print(kernel, p, "adaptive fp32 rel err", err)
+    assert err < FP32_TOL
+
+
+def test_adaptive_fp32_sources_are_targets(torch_cuda, oracle):
+    src, w, _ = plummer_case(15000, 1, 43)
+    ref = oracle.fmm_adaptive("laplace", 3, 8, src, w, src, max_leaf=40)
+    got, _ = gpu_adaptive(torch_cuda, "laplace", 8, src, w, max_leaf=40, precision="fp32")
+    assert rel_l2(got, ref) < FP32_TOL
