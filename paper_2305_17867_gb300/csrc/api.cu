@@ -154,6 +154,22 @@ static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t
   w.htab = carve<double>(cur, (size_t)std::max(D - 1, 1) * 343 * nh);
   w.nbbox_blocks = (int)std::min<int64_t>(1024, (std::max(n_src, n_tgt) + 255) / 256 + 1);
   w.bbox = carve<double>(cur, (size_t)2 * 3 * 2 * w.nbbox_blocks);
+  const int prec = P->desc.precision;
+  if (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3) {
+    const int esz = prec == FMM_PREC_BF16X3 ? 2 : 4;
+    const int row = 128 / esz;
+    w.tc_jp = (nj + row - 1) / row * row;
+    w.tc_mp = (nj + 127) / 128 * 128;
+    const int halves = prec == FMM_PREC_TF32 ? 1 : 2;
+    const int tlev = P->pd.kernel == FMM_KERNEL_YUKAWA ? std::max(D - 1, 1) : 1;
+    for (int h = 0; h < halves; ++h)
+      w.tc_tmat[h] = carve<char>(cur, (size_t)tlev * 343 * w.tc_mp * w.tc_jp * esz);
+    // window cells: as many as the bound on boxes (levels the arena cannot
+    // hold fall back to the float CUDA-core M2L)
+    w.tc_arena_bytes = (size_t)nb * ((size_t)w.tc_jp * esz * halves + sizeof(int));
+    w.tc_arena = carve<char>(cur, w.tc_arena_bytes);
+    w.tc_bounds = carve<int>(cur, 6 * (FMM_MAX_ADEPTH + 2));
+  }
   w.bytes = (size_t)(cur - static_cast<char*>(base));
   if (ws) *ws = w;
   return FMM_OK;
@@ -242,8 +258,6 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   if (L < 0) {  // adaptive tree
     if (-L > FMM_MAX_ADEPTH || desc->max_leaf < 1) return FMM_ERR_ARG;
     if (d != 3 || desc->m2l != FMM_M2L_DENSE) return FMM_ERR_UNSUPPORTED;
-    if (desc->precision != FMM_PREC_FP64 && desc->precision != FMM_PREC_FP32)
-      return FMM_ERR_UNSUPPORTED;
   } else if (L < 2 || L > (d == 3 ? 7 : 8)) {
     return FMM_ERR_ARG;
   }

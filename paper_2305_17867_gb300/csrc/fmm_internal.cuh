@@ -132,6 +132,11 @@ struct Workspace {
   int tc_mp;        // |j| padded to a multiple of 128 (M)
   void* tc_bpar[2];
   void* tc_tmat[2];
+  // adaptive trees: arena for the per-level windows (parity-split operands
+  // and cell -> box maps) and the per-level coordinate bounds
+  void* tc_arena;
+  size_t tc_arena_bytes;
+  int* tc_bounds;
   // FFT form of M2L: spectra of the multipoles and of the local sums of every
   // box of levels 2..L (kfp complex each) and of the offset tables
   void* fft_b;
@@ -199,6 +204,11 @@ cudaError_t launch_adaptive_upward(const fmm_plan_s* P, const Workspace& ws, con
                                    cudaStream_t st, int* nlaunch);
 cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
                                 cudaStream_t st, int* nlaunch);
+// tensor-core M2L of an adaptive tree (levels packed into dense windows);
+// levels whose window does not fit the arena are left to the caller
+// (*done_mask bit l set for every level handled)
+cudaError_t launch_adaptive_m2l_tc(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                   cudaStream_t st, int* nlaunch, unsigned* done_mask);
 cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
                                     cudaStream_t st, int* nlaunch);
 cudaError_t launch_adaptive_leaf(const fmm_plan_s* P, const Workspace& ws, const ATree& t,

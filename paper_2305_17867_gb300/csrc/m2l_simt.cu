@@ -124,14 +124,18 @@ __global__ void __launch_bounds__(kThreads) k_m2l_simt(PlanDev pd, int l,
 // Adaptive tree: one block per box of level >= 2 holding targets.  V(B) =
 // children of the boxes adjacent to P(B) that are not adjacent to B, found by
 // looking up the 27 neighbours of the parent; their offsets lie in [-3,3]^3.
-template <typename T>
+template <typename T, bool COUNT_ONLY = false>
 __global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
                                                    const double* __restrict__ mp,
                                                    double* __restrict__ lc,
                                                    const double* __restrict__ htab,
-                                                   unsigned long long* __restrict__ count) {
+                                                   unsigned long long* __restrict__ count,
+                                                   unsigned skip_mask) {
   const int b = t.loff[2] + blockIdx.x;
   if (b >= t.loff[t.maxlev + 1] || t.t1[b] == t.t0[b]) return;
+  // COUNT_ONLY: count the interaction lists of the levels in skip_mask (done
+  // on the tensor cores); otherwise translate the other levels
+  if ((((skip_mask >> t.lev[b]) & 1u) != 0) != COUNT_ONLY) return;
   const int nj = pd.nj, nh = pd.nh;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* H = reinterpret_cast<T*>(smraw);
@@ -156,12 +160,14 @@ __global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
       const int d0 = bc[0] - cc[0], d1 = bc[1] - cc[1], d2 = bc[2] - cc[2];
       if (d0 >= -1 && d0 <= 1 && d1 >= -1 && d1 <= 1 && d2 >= -1 && d2 <= 1) continue;
       const int o = (d0 + 3) + 7 * (d1 + 3) + 49 * (d2 + 3);
-      m2l_one_source<3, T>(pd, ht + (size_t)o * nh, mp + (size_t)C * nj, H, bs, acc, ii0, ii1,
-                           iis);
+      if (!COUNT_ONLY)
+        m2l_one_source<3, T>(pd, ht + (size_t)o * nh, mp + (size_t)C * nj, H, bs, acc, ii0, ii1,
+                             iis);
       ++nv;
     }
   }
   if (threadIdx.x == 0 && nv) atomicAdd(count, nv);
+  if (COUNT_ONLY) return;
 #pragma unroll
   for (int k = 0; k < kMaxI; ++k) {
     const int i = threadIdx.x + k * blockDim.x;
@@ -220,17 +226,34 @@ cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const 
   const PlanDev& pd = P->pd;
   if (t.maxlev < 2) return cudaGetLastError();
   const unsigned nb = (unsigned)(t.loff[t.maxlev + 1] - t.loff[2]);
+  const int prec = P->desc.precision;
+  unsigned done = 0;
   mark_contraction(P, 0, st);
-  if (P->desc.precision == FMM_PREC_FP64) {
-    const size_t smem = sizeof(double) * (pd.nh + pd.nj);
-    set_smem(k_am2l<double>, smem);
-    k_am2l<double><<<nb, kThreads, smem, st>>>(pd, t, ws.mp, ws.lc, ws.htab, &ws.geom->m2l_count);
-  } else {
-    const size_t smem = sizeof(float) * (pd.nh + pd.nj);
-    set_smem(k_am2l<float>, smem);
-    k_am2l<float><<<nb, kThreads, smem, st>>>(pd, t, ws.mp, ws.lc, ws.htab, &ws.geom->m2l_count);
+  if (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3) {
+    const cudaError_t e = launch_adaptive_m2l_tc(P, ws, t, st, nl, &done);
+    if (e != cudaSuccess) return e;
+  }
+  unsigned all = 0;
+  for (int l = 2; l <= t.maxlev; ++l) all |= 1u << l;
+  if (done) {  // interaction-list counts of the tensor-core levels
+    k_am2l<float, true><<<nb, 32, 0, st>>>(pd, t, ws.mp, ws.lc, ws.htab, &ws.geom->m2l_count,
+                                          done);
+    ++*nl;
+  }
+  if ((done & all) != all) {
+    if (prec == FMM_PREC_FP64) {
+      const size_t smem = sizeof(double) * (pd.nh + pd.nj);
+      set_smem(k_am2l<double>, smem);
+      k_am2l<double><<<nb, kThreads, smem, st>>>(pd, t, ws.mp, ws.lc, ws.htab,
+                                                 &ws.geom->m2l_count, done);
+    } else {
+      const size_t smem = sizeof(float) * (pd.nh + pd.nj);
+      set_smem(k_am2l<float>, smem);
+      k_am2l<float><<<nb, kThreads, smem, st>>>(pd, t, ws.mp, ws.lc, ws.htab,
+                                                &ws.geom->m2l_count, done);
+    }
+    ++*nl;
   }
   mark_contraction(P, 1, st);
-  ++*nl;
   return cudaGetLastError();
 }

@@ -23,6 +23,7 @@
 
 #include <cuda_bf16.h>
 
+#include "adaptive.cuh"
 #include "expansions.cuh"
 #include "tc_ptx.cuh"
 
@@ -185,14 +186,20 @@ __device__ __forceinline__ bool combo(int c, int px, int py, int pz, int& sg, in
 
 // One launch covers every level: blocks [first_block, first_block + 8 ntiles)
 // of grid.x belong to level l (block = tile * 8 + pi), grid.y = 128-row block.
+// The parent grid of a level is Hx x Hy x Hz cells: the whole level of a
+// uniform tree (Hx = Hy = Hz = 2^(l-1), boxes lexicographic), or, for an
+// adaptive tree, the window of parents spanned by the level's boxes, with
+// map[(pi, cell)] the box at that position (-1: none).
 struct TcLevel {
   CUtensorMap A, Alo, B, Blo;  // offset matrices and parity-split multipoles
-  double* lc;                  // local expansions of the level
+  double* lc;                  // local expansions (level base, or all boxes with map)
+  const int* map;              // adaptive: window cell -> box; null for uniform levels
   float scale;                 // exact power of two (shared offset matrices)
-  int l, BX, BY, BZ, ntx, nty, first_block;
+  int l, BX, BY, BZ, ntx, nty, first_block, Hx, Hy, Hz;
 };
+constexpr int kTcMaxLevels = 10;
 struct TcParams {
-  TcLevel lev[FMM_MAX_LEVELS];
+  TcLevel lev[kTcMaxLevels];
   int nlev, nj, jchunks, MP;
   int* err;
 };
@@ -230,7 +237,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int X0 = tx * BX, Y0 = ty * BY, Z0 = tz * BZ;
   const int N = BX * BY * BZ;                         // rows the TMA box fills
   const int Nmma = N < 16 ? 16 : (N + 15) / 16 * 16;  // MMA width; extra columns discarded
-  const int nl = 1 << l, H = nl >> 1;
+  const int nl = 1 << l, Hx = LV.Hx, Hy = LV.Hy, Hz = LV.Hz;
+  const int* __restrict__ map = LV.map;
   const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
   const uint32_t bytesA = kTileBytesA, bytesB = (uint32_t)N * kRowBytes;
   const uint32_t stage_tx = (NPASS == 1 ? 1u : 2u) * (bytesA + bytesB);
@@ -395,9 +403,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const float sv = sum[jn];
         if (n < N) {
           const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
-          if (x < H && y < H && z < H && i < nj) {
-            const int64_t t = ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
-            lc[t * nj + i] += (double)(sv * LV.scale);
+          if (x < Hx && y < Hy && z < Hz && i < nj) {
+            const int64_t t =
+                map ? (int64_t)map[(((size_t)pi * Hz + z) * Hy + y) * Hx + x]
+                    : ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
+            if (t >= 0) lc[t * nj + i] += (double)(sv * LV.scale);
           }
         }
       }
@@ -485,6 +495,8 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
     v.first_block = nb;
     nb += v.ntx * v.nty * ntz * 8;
     v.lc = ws.lc + ws.lev_off[l] * nj;
+    v.map = nullptr;
+    v.Hx = v.Hy = v.Hz = H;
     const int ti = shared_t ? 0 : l - 2;
     T* th = thi0 + (size_t)ti * noff * MP * JP;
     T* bh = bhi0 + ws.lev_off[l] * JP;
@@ -523,6 +535,169 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
   return cudaGetLastError();
 }
 
+// ---- adaptive trees: every level packed into a dense window ----------------
+// bounds[6 l + k] / [6 l + 3 + k]: smallest / largest coordinate k of the
+// boxes of level l
+__global__ void k_alevel_bounds_init(int* bounds, int n) {
+  const int i = threadIdx.x;
+  if (i < n) bounds[i] = (i % 6) < 3 ? 0x7fffffff : -1;
+}
+
+__global__ void k_alevel_bounds(ATree t, int* __restrict__ bounds) {
+  const int b = t.loff[2] + blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= t.loff[t.maxlev + 1]) return;
+  int l, c[3];
+  abox(t, b, &l, c);
+  for (int k = 0; k < 3; ++k) {
+    atomicMin(&bounds[6 * l + k], c[k]);
+    atomicMax(&bounds[6 * l + 3 + k], c[k]);
+  }
+}
+
+// the level's boxes into Bpar[sigma][Tz][Ty][Tx][JP] (hi and lo) of a window
+// with parent origin W and size H, and map[sigma][Tz][Ty][Tx] = box
+template <typename F>
+__global__ void k_apack(ATree t, int l, const double* __restrict__ mp, int nj, int JP, int W0x,
+                        int W0y, int W0z, int Hx, int Hy, int Hz, typename F::T* __restrict__ bhi,
+                        typename F::T* __restrict__ blo, int* __restrict__ map) {
+  const int b0 = t.loff[l];
+  const unsigned tot = (unsigned)(t.loff[l + 1] - b0) * (unsigned)JP;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    const unsigned bi = e / (unsigned)JP;
+    const int q = (int)(e - bi * (unsigned)JP);
+    const int b = b0 + (int)bi;
+    int c[3];
+    demorton3(t.key[b], l, c);
+    const int sg = (c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2);
+    const size_t cell =
+        (((size_t)sg * Hz + ((c[2] >> 1) - W0z)) * Hy + ((c[1] >> 1) - W0y)) * Hx + ((c[0] >> 1) - W0x);
+    const float v = q < nj ? (float)mp[(size_t)b * nj + q] : 0.f;
+    typename F::T hi, lo;
+    F::split(v, hi, lo);
+    bhi[cell * JP + q] = hi;
+    if (blo) blo[cell * JP + q] = lo;
+    if (q == 0) map[cell] = b;
+  }
+}
+
+template <typename F, int NPASS>
+cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                         cudaStream_t st, int* nl, unsigned* done) {
+  using C = Cfg<NPASS>;
+  using T = typename F::T;
+  const PlanDev& pd = P->pd;
+  const int nj = pd.nj, JP = ws.tc_jp, MP = ws.tc_mp;
+  const int noff = 343;
+  const bool shared_t = pd.kernel != FMM_KERNEL_YUKAWA;  // homogeneous G
+  const int tlev = shared_t ? 1 : (t.maxlev - 1);
+  const size_t esz = sizeof(T);
+  const CUtensorMapDataType dt =
+      F::kF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  T* thi0 = static_cast<T*>(ws.tc_tmat[0]);
+  T* tlo = NPASS == 3 ? static_cast<T*>(ws.tc_tmat[1]) : nullptr;
+  // coordinate bounds of every level (one synchronisation)
+  const int nbnd = 6 * (t.maxlev + 1);
+  k_alevel_bounds_init<<<1, 128, 0, st>>>(ws.tc_bounds, nbnd);
+  const int nbox2 = t.loff[t.maxlev + 1] - t.loff[2];
+  k_alevel_bounds<<<(nbox2 + 255) / 256, 256, 0, st>>>(t, ws.tc_bounds);
+  *nl += 2;
+  int bnd[6 * (FMM_MAX_ADEPTH + 2)];
+  cudaMemcpyAsync(bnd, ws.tc_bounds, sizeof(int) * nbnd, cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  {
+    const size_t sm = 2 * sizeof(T) * pd.nh;
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_build_tmat<3, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_build_tmat<3, F><<<dim3(noff, tlev), 256, sm, st>>>(pd, ws.htab, MP, JP, thi0, tlo);
+    ++*nl;
+  }
+  TcParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.nj = nj;
+  prm.jchunks = JP / F::kRow;
+  prm.MP = MP;
+  prm.err = &ws.geom->flag;
+  int nb = 0;
+  char* arena = static_cast<char*>(ws.tc_arena);
+  size_t used = 0;
+  const size_t cell_bytes = (size_t)JP * esz;
+  for (int l = t.maxlev; l >= 2; --l) {  // largest (finest) level first
+    if (bnd[6 * l + 3] < 0) continue;    // no box at this level
+    int W0[3], H[3];
+    for (int k = 0; k < 3; ++k) {
+      W0[k] = bnd[6 * l + k] >> 1;
+      H[k] = (bnd[6 * l + 3 + k] >> 1) - W0[k] + 1;
+    }
+    const size_t cells = (size_t)8 * H[0] * H[1] * H[2];
+    auto a256 = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t need = a256(cells * cell_bytes) * (NPASS == 3 ? 2 : 1) + a256(cells * sizeof(int));
+    if (used + need > ws.tc_arena_bytes) continue;  // left to the CUDA cores
+    T* bhi = reinterpret_cast<T*>(arena + used);
+    T* blo = NPASS == 3 ? reinterpret_cast<T*>(arena + used + a256(cells * cell_bytes)) : nullptr;
+    int* map = reinterpret_cast<int*>(arena + used + a256(cells * cell_bytes) * (NPASS == 3 ? 2 : 1));
+    used += need;
+    cudaMemsetAsync(bhi, 0, cells * cell_bytes, st);
+    if (blo) cudaMemsetAsync(blo, 0, cells * cell_bytes, st);
+    cudaMemsetAsync(map, 0xff, cells * sizeof(int), st);
+    const unsigned nbl = (unsigned)(t.loff[l + 1] - t.loff[l]);
+    k_apack<F><<<std::min<unsigned>((nbl * JP + 255) / 256, 152 * 8), 256, 0, st>>>(
+        t, l, ws.mp, nj, JP, W0[0], W0[1], W0[2], H[0], H[1], H[2], bhi, blo, map);
+    ++*nl;
+    TcLevel& v = prm.lev[prm.nlev++];
+    v.l = l;
+    v.Hx = H[0];
+    v.Hy = H[1];
+    v.Hz = H[2];
+    v.BX = std::min(8, H[0]);
+    v.BY = std::min(4, H[1]);
+    v.BZ = std::min(4, H[2]);
+    v.ntx = (H[0] + v.BX - 1) / v.BX;
+    v.nty = (H[1] + v.BY - 1) / v.BY;
+    const int ntz = (H[2] + v.BZ - 1) / v.BZ;
+    v.first_block = nb;
+    nb += v.ntx * v.nty * ntz * 8;
+    v.lc = ws.lc;
+    v.map = map;
+    const int ti = shared_t ? 0 : l - 2;
+    v.scale = 1.0f;
+    if (shared_t) {
+      const int k = l - 2;
+      v.scale = pd.kernel == FMM_KERNEL_LAPLACE ? std::ldexp(1.0f, k) : std::ldexp(1.0f, -k);
+    }
+    cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
+    cuuint64_t sA[1] = {(cuuint64_t)JP * esz};
+    cuuint32_t bA[2] = {(cuuint32_t)F::kRow, (cuuint32_t)kBM};
+    cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H[0], (cuuint64_t)H[1], (cuuint64_t)H[2], 8};
+    cuuint64_t sB[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * H[0],
+                        (cuuint64_t)JP * esz * H[0] * H[1],
+                        (cuuint64_t)JP * esz * H[0] * H[1] * H[2]};
+    cuuint32_t bB[5] = {(cuuint32_t)F::kRow, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ,
+                        1};
+    if (!make_map(&v.A, thi0 + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt))
+      return cudaErrorInvalidValue;
+    if (!make_map(&v.B, bhi, 5, dB, sB, bB, dt)) return cudaErrorInvalidValue;
+    v.Alo = v.A;
+    v.Blo = v.B;
+    if (NPASS == 3) {
+      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt))
+        return cudaErrorInvalidValue;
+      if (!make_map(&v.Blo, blo, 5, dB, sB, bB, dt)) return cudaErrorInvalidValue;
+    }
+    *done |= 1u << l;
+    if (prm.nlev == kTcMaxLevels) break;
+  }
+  if (prm.nlev == 0) return cudaGetLastError();
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    attr = true;
+  }
+  k_m2l_tc<F, NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
+  ++*nl;
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
@@ -534,4 +709,14 @@ cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t
                                                   : run_all_levels<FmtTF32, 1>(P, ws, st);
   *nl += 3;
   return e;
+}
+
+cudaError_t launch_adaptive_m2l_tc(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                   cudaStream_t st, int* nl, unsigned* done) {
+  *done = 0;
+  if (t.maxlev < 2) return cudaGetLastError();
+  const int prec = P->desc.precision;
+  return prec == FMM_PREC_BF16X3   ? run_adaptive<FmtBF16, 3>(P, ws, t, st, nl, done)
+         : prec == FMM_PREC_TF32X3 ? run_adaptive<FmtTF32, 3>(P, ws, t, st, nl, done)
+                                   : run_adaptive<FmtTF32, 1>(P, ws, t, st, nl, done);
 }

@@ -144,3 +144,24 @@ def test_adaptive_fp32_sources_are_targets(torch_cuda, oracle):
     ref = oracle.fmm_adaptive("laplace", 3, 8, src, w, src, max_leaf=40)
     got, _ = gpu_adaptive(torch_cuda, "laplace", 8, src, w, max_leaf=40, precision="fp32")
     assert rel_l2(got, ref) < FP32_TOL
+
+
+# Tensor-core M2L on the adaptive tree (each level packed into a dense window);
+# tolerances as for the uniform tree's mixed-precision forms.
+TC_TOL = {"tf32x3": 2e-5, "bf16x3": 1e-4, "tf32": 3e-3}
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3", "tf32"])
+@pytest.mark.parametrize("kernel,p,lam", [("laplace", 8, 0.0), ("yukawa", 12, 1.0),
+                                          ("biharmonic", 6, 0.0)])
+def test_adaptive_tensor_m2l(torch_cuda, oracle, kernel, p, lam, precision):
+    n = 20000 if p < 12 else 6000
+    src, w, tgt = plummer_case(n, n // 5, 42)
+    ref, st, _ = oracle.fmm_adaptive(kernel, 3, p, src, w, tgt, max_leaf=32, lam=lam,
+                                     want_stats=True)
+    got, (nb, depth), nv = gpu_adaptive(torch_cuda, kernel, p, src, w, tgt, lam=lam,
+                                        max_leaf=32, counts=True, precision=precision)
+    assert nv == st["V"]
+    err = rel_l2(got, ref)
+    print(kernel, p, precision, "adaptive tensor-core rel err", err)
+    assert err < TC_TOL[precision]
