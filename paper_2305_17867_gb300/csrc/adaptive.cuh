@@ -32,9 +32,15 @@ struct ATree {
   const int* t0;
   const int* t1;
   const int* leaf;
+  const int* grid;  // dense index of levels 0..grid_levels: grid[(8^l - 1)/7 + code] = box or -1
+  int grid_levels;
   int loff[FMM_MAX_ADEPTH + 2];  // first box of each level; loff[maxlev+1] = boxes
   int maxlev;
 };
+
+#define FMM_AGRID_LEVELS 7  // dense index down to level 7: sum 8^l = 2,396,745 entries
+
+__host__ __device__ inline int64_t agrid_offset(int l) { return (((int64_t)1 << (3 * l)) - 1) / 7; }
 
 __host__ __device__ inline uint32_t morton3(int x, int y, int z, int l) {
   uint32_t k = 0;
@@ -59,6 +65,7 @@ __device__ inline int alookup(const ATree& t, int l, const int* c) {
   if (c[0] < 0 || c[1] < 0 || c[2] < 0 || c[0] >= n || c[1] >= n || c[2] >= n) return -1;
   if (l > t.maxlev) return -1;
   const uint32_t k = morton3(c[0], c[1], c[2], l);
+  if (l <= t.grid_levels) return t.grid[agrid_offset(l) + k];
   int lo = t.loff[l], hi = t.loff[l + 1];
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;

@@ -151,6 +151,7 @@ static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t
   w.ascan = carve<int>(cur, nb + 1);
   w.mp = carve<double>(cur, (size_t)nb * nj);
   w.lc = carve<double>(cur, (size_t)nb * nj);
+  w.agrid = carve<int>(cur, (size_t)agrid_offset(std::min(D, FMM_AGRID_LEVELS) + 1));
   w.htab = carve<double>(cur, (size_t)std::max(D - 1, 1) * 343 * nh);
   w.nbbox_blocks = (int)std::min<int64_t>(1024, (std::max(n_src, n_tgt) + 255) / 256 + 1);
   w.bbox = carve<double>(cur, (size_t)2 * 3 * 2 * w.nbbox_blocks);

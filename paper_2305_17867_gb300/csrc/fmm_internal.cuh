@@ -163,6 +163,7 @@ struct Workspace {
   int* ascan;
   uint32_t* skey;
   uint32_t* tkey;
+  int* agrid;       // dense box index of the coarse levels (adaptive.cuh)
   size_t bytes;
 };
 

@@ -314,6 +314,14 @@ __global__ void k_atree_root(int* lev, int* par, uint32_t* key, int* s0, int* s1
   t1[0] = nt;
 }
 
+// dense index of the coarse levels: grid[(8^l - 1)/7 + code] = box
+__global__ void k_agrid_fill(int nbox, int glev, const uint32_t* __restrict__ key,
+                             const int* __restrict__ lev, int* __restrict__ grid) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbox || lev[b] > glev) return;
+  grid[agrid_offset(lev[b]) + key[b]] = b;
+}
+
 // first position in sorted[lo, hi) whose code is >= v
 __device__ inline int lower_bound_u32(const uint32_t* a, int lo, int hi, uint32_t v) {
   while (lo < hi) {
@@ -584,5 +592,13 @@ cudaError_t launch_build_adaptive(const fmm_plan_s* P, const Workspace& ws, int6
   t->leaf = ws.aleaf;
   for (int l = 0; l <= FMM_MAX_ADEPTH + 1; ++l) t->loff[l] = l <= maxlev + 1 ? loff[l] : loff[maxlev + 1];
   t->maxlev = maxlev;
+  // dense index of levels 0..glev (one load per lookup there)
+  const int glev = std::min(maxlev, FMM_AGRID_LEVELS);
+  const int nbox = loff[maxlev + 1];
+  cudaMemsetAsync(ws.agrid, 0xff, sizeof(int) * (size_t)agrid_offset(glev + 1), st);
+  k_agrid_fill<<<nblocks(nbox, 256), 256, 0, st>>>(nbox, glev, ws.akey, ws.alev, ws.agrid);
+  ++*nl;
+  t->grid = ws.agrid;
+  t->grid_levels = glev;
   return cudaGetLastError();
 }
