@@ -331,10 +331,11 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        phi = plan.eval(s, wt, t)
-        if backward:
-            plan.backward(s, wt, s if t is None else t, ut)
-        return phi
+        if backward:  # training step: phi and grad phi, then the transposed FMM
+            phi, gphi = plan.eval(s, wt, t, grad=True)
+            plan.backward(s, wt, s if t is None else t, ut, grad_phi=gphi)
+            return phi
+        return plan.eval(s, wt, t)
 
     for _ in range(max(args.warmup, 3)):
         phi = step()
@@ -389,16 +390,20 @@ def main():
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = plan.eval(hs, hw, ht)
         if backward:
-            gw, gs, gt = plan.backward(hs, hw, hs if ht is None else ht, hu)
+            out, gphi = plan.eval(hs, hw, ht, grad=True)
+            gw, gs, gt = plan.backward(hs, hw, hs if ht is None else ht, hu,
+                                       grad_phi=gphi.to(dev))
             gw, gs, gt = gw.cpu(), gs.cpu(), gt.cpu()
+        else:
+            out = plan.eval(hs, hw, ht)
         e2e_times.append((time.perf_counter() - t0) * 1e3)
         assert out.device.type == "cpu"
-    if backward:
-        d2h += (len(w) + len(w) * wl.d + n_t * wl.d) * 8
+    if backward:  # grad phi comes back with phi and returns to the device; three gradients
+        d2h += (n_t * wl.d + len(w) + len(w) * wl.d + n_t * wl.d) * 8
     e2e_ms = statistics.median(e2e_times) if e2e_times else float("nan")
-    h2d = int(src.nbytes + w.nbytes + (0 if same else tgt.nbytes) + (u.nbytes if backward else 0))
+    h2d = int(src.nbytes + w.nbytes + (0 if same else tgt.nbytes) +
+              ((u.nbytes + n_t * wl.d * 8) if backward else 0))
 
     roof = roofline(plan, prec, args.m2l, m2l_kernel_ms, nm2l, p, plan.c)
     wname = wl.name if p == wl.p else f"{wl.name} with p={p}"
@@ -409,7 +414,8 @@ def main():
                                f"adaptive, <= {wl.max_leaf} points per leaf, depth <= "
                                f"{ADAPTIVE_DEPTH}"),
               "boxes": boxes, "depth": depth, "precision": prec, "m2l": args.m2l,
-              "step": "forward + backward" if backward else "forward",
+              "step": ("forward (phi and grad phi) + backward (transposed FMM)" if backward
+                       else "forward"),
               "l2": "flushed (256 MiB write) between timed steps",
               "parallelism": "replicas" if world > 1 else "single"}
     result = {

@@ -152,14 +152,17 @@ int fmm_eval(fmm_plan_t plan, int64_t n_src, const double* src_dev, const double
  *   grad_src_dev n_src x d   d loss/d y_j  = w_j grad psi(y_j)           (or NULL)
  *   grad_tgt_dev n_tgt x d   d loss/d x_i  = u_i grad phi(x_i)           (or NULL)
  * where psi(y) = sum_i u_i G(y - x_i) is the transposed FMM (targets as
- * sources with weights u).  Same buffer conventions as fmm_eval; the
- * workspace must be sized with fmm_workspace_size(plan, max(n_src, n_tgt),
- * max(n_src, n_tgt)). */
+ * sources with weights u).  grad_phi_dev (n_tgt x d, or NULL) is grad phi at
+ * the targets from the forward call (fmm_eval with grad_dev): when given,
+ * grad_tgt is formed from it, otherwise a second FMM evaluates grad phi.
+ * Same buffer conventions as fmm_eval; the workspace must be sized with
+ * fmm_workspace_size(plan, max(n_src, n_tgt), max(n_src, n_tgt)).  Uniform
+ * plans only (FMM_ERR_UNSUPPORTED for adaptive plans). */
 int fmm_eval_backward(fmm_plan_t plan, int64_t n_src, const double* src_dev,
                       const double* w_dev, int64_t n_tgt, const double* tgt_dev,
-                      const double* u_dev, double* grad_w_dev, double* grad_src_dev,
-                      double* grad_tgt_dev, void* workspace_dev, size_t workspace_bytes,
-                      void* stream);
+                      const double* u_dev, const double* grad_phi_dev, double* grad_w_dev,
+                      double* grad_src_dev, double* grad_tgt_dev, void* workspace_dev,
+                      size_t workspace_bytes, void* stream);
 
 /* fmm_eval without any allocation.  The paper has no counterpart; this is a
  * service for callers that may not allocate device memory when they evaluate:

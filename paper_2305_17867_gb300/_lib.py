@@ -75,7 +75,7 @@ def load(build: bool = True):
     L.fmm_workspace_size.restype = i32
     L.fmm_eval.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp, sz, vp]
     L.fmm_eval.restype = i32
-    L.fmm_eval_backward.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.fmm_eval_backward.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.fmm_eval_backward.restype = i32
     L.fmm_eval_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp]
     L.fmm_eval_noalloc.restype = i32

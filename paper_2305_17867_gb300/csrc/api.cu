@@ -647,11 +647,17 @@ __global__ void k_scale_rows(int64_t n, int d, const double* s, double* g) {
   if (i < n * d) g[i] *= s[i / d];
 }
 
+__global__ void k_scale_rows_from(int64_t n, int d, const double* s, const double* g,
+                                  double* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n * d) out[i] = g[i] * s[i / d];
+}
+
 extern "C" int fmm_eval_backward(fmm_plan_t P, int64_t n_src, const double* src,
                                  const double* w, int64_t n_tgt, const double* tgt,
-                                 const double* u, double* grad_w, double* grad_src,
-                                 double* grad_tgt, void* workspace, size_t wbytes,
-                                 void* stream) {
+                                 const double* u, const double* grad_phi, double* grad_w,
+                                 double* grad_src, double* grad_tgt, void* workspace,
+                                 size_t wbytes, void* stream) {
   if (!P) return FMM_ERR_ARG;
   if (P->desc.levels < 0) return FMM_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -673,7 +679,15 @@ extern "C" int fmm_eval_backward(fmm_plan_t P, int64_t n_src, const double* src,
       if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
     }
   }
-  if (grad_tgt) {
+  if (grad_tgt && grad_phi) {  // the forward's gradient: u * grad phi, no second FMM
+    if (n_tgt > 0) {
+      const int64_t tot = n_tgt * d;
+      k_scale_rows_from<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(n_tgt, d, u, grad_phi,
+                                                                        grad_tgt);
+      P->launches = first ? 1 : P->launches + 1;
+      if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
+    }
+  } else if (grad_tgt) {
     rc = eval_internal(P, n_src, src, w, n_tgt, tgt, nullptr, grad_tgt, workspace, wbytes, st,
                        first);
     if (rc != FMM_OK) return rc;

@@ -160,8 +160,12 @@ class FMM:
             g = g.cpu() if g is not None else None
         return (phi, g) if grad else phi
 
-    def backward(self, src, w, tgt, u, need_w=True, need_src=True, need_tgt=True):
+    def backward(self, src, w, tgt, u, need_w=True, need_src=True, need_tgt=True,
+                 grad_phi=None):
+        """Gradients of sum(u * phi); grad_phi (grad phi at tgt from a forward
+        eval with grad=True) saves the second FMM for the target gradient."""
         s, wd, t, ud = self._dev(src), self._dev(w), self._dev(tgt), self._dev(u)
+        gp = None if grad_phi is None else self._dev(grad_phi)
         ns, nt = s.shape[0], t.shape[0]
         gw = torch.empty(ns, dtype=torch.float64, device=self.device) if need_w else None
         gs = torch.empty(ns, self.d, dtype=torch.float64, device=self.device) if need_src else None
@@ -170,7 +174,7 @@ class FMM:
         ws, wb = self._workspace(n, n)
         stream = torch.cuda.current_stream(self.device).cuda_stream
         check(self.L.fmm_eval_backward(self._h, ns, _ptr(s), _ptr(wd), nt, _ptr(t), _ptr(ud),
-                                       _ptr(gw), _ptr(gs), _ptr(gt), ws, wb,
+                                       _ptr(gp), _ptr(gw), _ptr(gs), _ptr(gt), ws, wb,
                                        ctypes.c_void_p(stream)), "fmm_eval_backward")
         return gw, gs, gt
 
@@ -178,8 +182,14 @@ class FMM:
 class _FMMFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, plan, src, w, tgt):
-        phi = plan.eval(src, w, tgt)
+        # when the targets need a gradient, grad phi comes with phi in the
+        # same evaluation and the backward needs only the transposed FMM
+        if ctx.needs_input_grad[3]:
+            phi, gphi = plan.eval(src, w, tgt, grad=True)
+        else:
+            phi, gphi = plan.eval(src, w, tgt), None
         ctx.plan = plan
+        ctx.gphi = gphi
         ctx.save_for_backward(src, w, tgt)
         return phi.to(src.dtype)
 
@@ -189,7 +199,8 @@ class _FMMFunction(torch.autograd.Function):
         plan = ctx.plan
         _, ns, nw, nt = ctx.needs_input_grad
         gw, gs, gt = plan.backward(src, w, tgt, gphi, need_w=bool(nw), need_src=bool(ns),
-                                   need_tgt=bool(nt))
+                                   need_tgt=bool(nt), grad_phi=ctx.gphi)
+        ctx.gphi = None
         cast = lambda g, ref: None if g is None else g.to(ref.dtype)
         return None, cast(gs, src), cast(gw, w), cast(gt, tgt)
 
