@@ -81,7 +81,12 @@ enum {
  *         per target yields its local coefficients.  Coefficients are scaled
  *         by g^{|q|} before the transform (g = 3p/8 in units of the box side;
  *         Sec. 4.1.1).  FP64 (complex double) and FP32 (complex float) only. */
-enum { FMM_M2L_DENSE = 0, FMM_M2L_FFT = 1 };
+enum { FMM_M2L_DENSE = 0, FMM_M2L_FFT = 1, FMM_M2L_AUTO = 2 };
+/* AUTO picks by arithmetic, following measurements on GB300 (3D biharmonic,
+ * L = 6, p = 4..16): FFT for FP64 (its stencil runs at ~95% of the FP64 FMA
+ * rate, 5-6x fewer operations than dense) and for FP32 (CUDA-core dense
+ * products are slower still); DENSE on the tensor cores for TF32, TF32X3 and
+ * BF16X3.  Adaptive plans use DENSE. */
 
 /* A constant-coefficient PDE L = sum_t coeff[t] d^{multi_idx[t]}  (eq.
  * (define_pde_op)).  multi_idx is n_terms x d exponents.  The PDE must have

@@ -258,12 +258,13 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   if (p < 1 || p > FMM_MAXP) return FMM_ERR_ARG;
   if (L < 0) {  // adaptive tree
     if (-L > FMM_MAX_ADEPTH || desc->max_leaf < 1) return FMM_ERR_ARG;
-    if (d != 3 || desc->m2l != FMM_M2L_DENSE) return FMM_ERR_UNSUPPORTED;
+    if (d != 3 || desc->m2l == FMM_M2L_FFT) return FMM_ERR_UNSUPPORTED;
   } else if (L < 2 || L > (d == 3 ? 7 : 8)) {
     return FMM_ERR_ARG;
   }
   if (desc->precision < FMM_PREC_FP64 || desc->precision > FMM_PREC_BF16X3) return FMM_ERR_ARG;
-  if (desc->m2l != FMM_M2L_DENSE && desc->m2l != FMM_M2L_FFT) return FMM_ERR_ARG;
+  if (desc->m2l != FMM_M2L_DENSE && desc->m2l != FMM_M2L_FFT && desc->m2l != FMM_M2L_AUTO)
+    return FMM_ERR_ARG;
   if (desc->m2l == FMM_M2L_FFT && desc->precision != FMM_PREC_FP64 &&
       desc->precision != FMM_PREC_FP32)
     return FMM_ERR_UNSUPPORTED;
@@ -433,6 +434,10 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   }
   P->desc = *desc;
   P->desc.pde = nullptr;
+  if (desc->m2l == FMM_M2L_AUTO) {  // resolved once, by arithmetic (see ctfmm.h)
+    const bool fp = desc->precision == FMM_PREC_FP64 || desc->precision == FMM_PREC_FP32;
+    P->desc.m2l = (fp && desc->levels > 0) ? FMM_M2L_FFT : FMM_M2L_DENSE;
+  }
   P->pd = pd;
   P->fft = fft;
   P->dev_tables = dt;

@@ -30,7 +30,8 @@ class FMM:
     root_lo, root_size  root box; root_size <= 0 picks the bounding cube per call
     precision  "fp64" | "fp32" | "tf32" | "tf32x3" | "bf16x3"
     m2l        "dense" (eq. (m2l_toeplitz) as dense products) | "fft" (its
-               convolution form, eq. (convolution_m2l); fp64 and fp32 only)
+               convolution form, eq. (convolution_m2l); fp64 and fp32 only) |
+               "auto" (fft for fp64/fp32, dense tensor cores otherwise)
     pde        optional (multi_idx [n,d] ints, coeff [n] floats) overriding the
                kernel's own PDE (eq. (define_pde_op))
     """

@@ -61,7 +61,7 @@ def test_plan_validation_without_gpu():
 
     for prec in (2, 3, 4):  # tensor-core formats have no FFT form
         assert create(precision=prec, m2l=1) == -2
-    assert create(m2l=2) == -1
+    assert create(m2l=3) == -1
     assert create(precision=7) == -1
     assert create(p=0) == -1
     assert create(levels=1) == -1

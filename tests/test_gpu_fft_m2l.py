@@ -130,3 +130,15 @@ def test_fft_rejects_tensor_precisions(torch_cuda):
     for prec in ("tf32", "tf32x3", "bf16x3"):
         with pytest.raises(FMMError):
             FMM("laplace", d=3, p=8, levels=3, precision=prec, m2l="fft")
+
+
+@pytest.mark.parametrize("precision,expect", [("fp64", "fft"), ("fp32", "fft"),
+                                               ("tf32x3", "dense")])
+def test_auto_m2l_matches_its_choice(torch_cuda, precision, expect):
+    # AUTO resolves by arithmetic; its results equal the chosen form's bit for bit
+    rng = np.random.default_rng(33)
+    src = rng.random((20000, 3))
+    w = rng.uniform(-1, 1, 20000)
+    a = fft_fmm(torch_cuda, "laplace", 3, 8, 4, src, w, precision=precision, m2l="auto")
+    b = fft_fmm(torch_cuda, "laplace", 3, 8, 4, src, w, precision=precision, m2l=expect)
+    assert np.array_equal(a, b)

@@ -276,3 +276,37 @@ def test_mixed_precision_gradient(torch_cuda, oracle, kernel, p, lam, precision)
                          precision=precision, grad=True)
         assert rel_l2(got, ref) < 5e-6
         assert rel_l2(g, gref) < 5e-5
+
+
+def test_backward_workload_full_size_sampled(torch_cuda, oracle):
+    # 1e6 sources and 1e6 separate targets, p = 8, L = 5: potential and
+    # target gradient on seeded sampled targets (FP64 against the oracle,
+    # tf32x3 within the mixed-precision tolerance)
+    wl = W.WORKLOADS["laplace3d_p8_L5_bwd_n1m"]
+    src, w, tgt = W.make_inputs(wl)
+    idx = np.random.default_rng(95).choice(len(tgt), 24, replace=False)
+    ref, gref = oracle.fmm_uniform("laplace", 3, 8, 5, src, w, tgt, sample=idx, grad=True)
+    got, g = gpu_fmm(torch_cuda, "laplace", 3, 8, 5, src, w, tgt, grad=True)
+    assert rel_l2(got[idx], ref) < FP64_TOL
+    assert rel_l2(g[idx], gref) < FP64_TOL
+    got, g = gpu_fmm(torch_cuda, "laplace", 3, 8, 5, src, w, tgt, grad=True,
+                     precision="tf32x3")
+    assert rel_l2(got[idx], ref) < MIXED_TOL["tf32x3"]
+    assert rel_l2(g[idx], gref) < 2e-5
+
+
+def test_biharmonic_workload_full_size_sampled(torch_cuda, oracle):
+    # 4e6 points, L = 6, p = 8: dense tensor-core M2L and the FFT form
+    from paper_2305_17867_gb300.fmm import FMM
+
+    wl = W.WORKLOADS["biharmonic3d_p8_L6_n4m"]
+    src, w, _ = W.make_inputs(wl)
+    idx = np.random.default_rng(94).choice(len(w), 16, replace=False)
+    ref = oracle.fmm_uniform("biharmonic", 3, 8, 6, src, w, src, sample=idx)
+    s = torch_cuda.tensor(src, device="cuda")
+    wt = torch_cuda.tensor(w, device="cuda")
+    for prec, m2l, tol in (("tf32x3", "dense", 2e-5), ("fp32", "fft", 1e-4),
+                           ("fp64", "fft", 5e-12)):
+        plan = FMM("biharmonic", d=3, p=8, levels=6, precision=prec, m2l=m2l)
+        got = plan.eval(s, wt, check_status=True).cpu().numpy()
+        assert rel_l2(got[idx], ref) < tol, (prec, m2l)
