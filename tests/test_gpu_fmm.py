@@ -310,3 +310,48 @@ def test_biharmonic_workload_full_size_sampled(torch_cuda, oracle):
         plan = FMM("biharmonic", d=3, p=8, levels=6, precision=prec, m2l=m2l)
         got = plan.eval(s, wt, check_status=True).cpu().numpy()
         assert rel_l2(got[idx], ref) < tol, (prec, m2l)
+
+
+# ---- user-supplied PDEs (eq. (define_pde_op)) -------------------------------
+def _plan_eval(torch, kernel, p, L, src, w, pde=None, lam=0.0, precision="fp64"):
+    from paper_2305_17867_gb300.fmm import FMM
+
+    plan = FMM(kernel, d=3, p=p, levels=L, lam=lam, precision=precision, pde=pde)
+    out = plan.eval(torch.tensor(src, device="cuda"), torch.tensor(w, device="cuda"),
+                    check_status=True)
+    return out.cpu().numpy(), plan
+
+
+def test_user_pde_equal_to_the_kernels_own(torch_cuda):
+    # the same operators given explicitly (scaled, reordered) compress identically
+    rng = np.random.default_rng(34)
+    src = rng.random((20000, 3))
+    w = rng.uniform(-1, 1, 20000)
+    lap = ([(0, 0, 2), (2, 0, 0), (0, 2, 0)], [3.0, 3.0, 3.0])
+    a, _ = _plan_eval(torch_cuda, "laplace", 3, 8, 3, src, w)
+    b, _ = _plan_eval(torch_cuda, "laplace", 3, 8, 3, src, w, pde=lap)
+    assert np.array_equal(a, b)
+    yuk = ([(2, 0, 0), (0, 2, 0), (0, 0, 2), (0, 0, 0)], [1.0, 1.0, 1.0, -1.0])
+    a, _ = _plan_eval(torch_cuda, "yukawa", 3, 8, 3, src, w, lam=1.0)
+    b, _ = _plan_eval(torch_cuda, "yukawa", 3, 8, 3, src, w, pde=yuk, lam=1.0)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("kernel,lam", [("laplace", 0.0), ("biharmonic", 0.0),
+                                        ("yukawa", 1.0)])
+def test_uncompressed_taylor_fmm(torch_cuda, oracle, kernel, lam):
+    # PDE d_z^(p+1): every multi-index of M(p) is stored and nothing is
+    # compressed, i.e. the plain Taylor FMM (Sec. 2), held to the oracle's
+    # uncompressed FMM
+    p, L = 6, 3
+    rng = np.random.default_rng(35)
+    src = rng.random((12000, 3))
+    w = rng.uniform(-1, 1, 12000)
+    pde = ([(0, 0, p + 1)], [1.0])
+    got, plan = _plan_eval(torch_cuda, kernel, p, L, src, w, pde=pde, lam=lam)
+    assert plan.nj == plan.nfull == (p + 1) * (p + 2) * (p + 3) // 6
+    ref = oracle.fmm_uniform(kernel, 3, p, L, src, w, src, lam=lam, compressed=False)
+    assert rel_l2(got, ref) < FP64_TOL
+    got, _ = _plan_eval(torch_cuda, kernel, p, L, src, w, pde=pde, lam=lam,
+                        precision="tf32x3")
+    assert rel_l2(got, ref) < 2e-5
