@@ -432,6 +432,18 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
     cudaFree(dt);
     return FMM_ERR_NOMEM;
   }
+  int prio_low = 0, prio_high = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&P->hi, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&P->aux, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFree(dt);
+    delete P;
+    return FMM_ERR_CUDA;
+  }
   P->desc = *desc;
   P->desc.pde = nullptr;
   if (desc->m2l == FMM_M2L_AUTO) {  // resolved once, by arithmetic (see ctfmm.h)
@@ -452,6 +464,9 @@ extern "C" int fmm_plan_destroy(fmm_plan_t P) {
     for (auto& e : P->ev) cudaEventDestroy(e);
   if (P->events_made)
     for (auto& e : P->evk) cudaEventDestroy(e);
+  for (cudaEvent_t e : {P->ev_in, P->ev_fork, P->ev_join, P->ev_out}) cudaEventDestroy(e);
+  cudaStreamDestroy(P->hi);
+  cudaStreamDestroy(P->aux);
   cudaFree(P->dev_tables);
   delete P;
   return FMM_OK;
@@ -578,8 +593,16 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
   }
   int nl = 0;
   cudaError_t e = cudaSuccess;
+  // FP32 3D uniform path: the near field needs only the sorted points, so it
+  // runs on a low-priority stream of the plan while the rest of the pipeline
+  // runs on a high-priority one (the block scheduler then fills the SMs the
+  // memory-bound passes and the tensor-core M2L leave idle with near-field
+  // blocks); both are ordered after the caller's stream and the caller's
+  // stream after both
+  const bool split = P->desc.levels > 0 && leaf_split_supported(P) && n_tgt > 0;
+  cudaStream_t run = split ? P->hi : st;
   auto mark = [&](int i) {
-    if (P->timing) cudaEventRecord(P->ev[i], st);
+    if (P->timing) cudaEventRecord(P->ev[i], run);
   };
   if (P->desc.levels < 0) {
     if (grad) return FMM_ERR_UNSUPPORTED;
@@ -617,22 +640,41 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
     P->last_depth = tree.maxlev;
     return FMM_OK;
   }
+  if (split && (cudaEventRecord(P->ev_in, st) != cudaSuccess ||
+                cudaStreamWaitEvent(run, P->ev_in, 0) != cudaSuccess))
+    return FMM_ERR_CUDA;
   mark(0);
-  if ((e = launch_set_geom(P, ws, n_src, src, n_tgt, tgt, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
-  if ((e = launch_build_tree(P, ws, n_src, src, w, n_tgt, tgt, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_set_geom(P, ws, n_src, src, n_tgt, tgt, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_build_tree(P, ws, n_src, src, w, n_tgt, tgt, run, &nl)) != cudaSuccess)
+    return FMM_ERR_CUDA;
+  if (split) {
+    if (cudaEventRecord(P->ev_fork, run) != cudaSuccess ||
+        cudaStreamWaitEvent(P->aux, P->ev_fork, 0) != cudaSuccess)
+      return FMM_ERR_CUDA;
+    if ((e = launch_near_field(P, ws, phi, grad, P->aux, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+    if (cudaEventRecord(P->ev_join, P->aux) != cudaSuccess) return FMM_ERR_CUDA;
+  }
   mark(1);
-  if ((e = launch_deriv_tables(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_deriv_tables(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(2);
-  if ((e = launch_p2m(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_p2m(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(3);
-  if ((e = launch_m2m(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_m2m(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(4);
-  if ((e = launch_m2l(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_m2l(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(5);
-  if ((e = launch_l2l(P, ws, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_l2l(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(6);
-  if ((e = launch_leaf_eval(P, ws, phi, grad, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if (split) {
+    if (cudaStreamWaitEvent(run, P->ev_join, 0) != cudaSuccess) return FMM_ERR_CUDA;
+    if ((e = launch_far_field(P, ws, phi, grad, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  } else if ((e = launch_leaf_eval(P, ws, phi, grad, run, &nl)) != cudaSuccess) {
+    return FMM_ERR_CUDA;
+  }
   mark(7);
+  if (split && (cudaEventRecord(P->ev_out, run) != cudaSuccess ||
+                cudaStreamWaitEvent(st, P->ev_out, 0) != cudaSuccess))
+    return FMM_ERR_CUDA;
   P->last_stream = st;
   P->last_geom = ws.geom;
   P->launches = first ? nl : P->launches + nl;

@@ -79,6 +79,12 @@ struct fmm_plan_s {
   cudaEvent_t ev[FMM_NUM_PHASES + 1];
   cudaEvent_t evk[2];  // around the M2L contraction launch(es)
   bool events_made;
+  // FP32 3D uniform path: the pipeline on a high-priority stream, the near
+  // field on a low-priority one; events order them after the caller's stream
+  // (in), the near field after the sort (fork), the far field after the near
+  // field (join) and the caller's stream after the pipeline (out)
+  cudaStream_t hi, aux;
+  cudaEvent_t ev_in, ev_fork, ev_join, ev_out;
   cudaStream_t last_stream;
   Geom* last_geom;  // device geometry of the last evaluation (in its workspace)
   int launches;
@@ -192,6 +198,11 @@ cudaError_t launch_m2l_fft(const fmm_plan_s* P, const Workspace& ws, cudaStream_
 bool m2l_shared_tables(const fmm_plan_s* P);
 cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
 cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* phi,
+                             double* grad, cudaStream_t st, int* nlaunch);
+bool leaf_split_supported(const fmm_plan_s* P);
+cudaError_t launch_near_field(const fmm_plan_s* P, const Workspace& ws, double* phi,
+                              double* grad, cudaStream_t st, int* nlaunch);
+cudaError_t launch_far_field(const fmm_plan_s* P, const Workspace& ws, double* phi,
                              double* grad, cudaStream_t st, int* nlaunch);
 
 // adaptive tree (adaptive.cuh): the build synchronises the stream once per

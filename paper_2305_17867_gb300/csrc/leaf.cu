@@ -436,7 +436,10 @@ __device__ __forceinline__ float far_field(const PlanDev& pd, const float* __res
   return far;
 }
 
-template <int K, bool GRAD>
+// FAR = false: the near field only (P2P); phi (and grad) are overwritten with
+// it, and k_leaf_far adds the far field later (the two run on separate
+// streams, the near field concurrently with the upward and M2L passes).
+template <int K, bool GRAD, bool FAR = true>
 __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
     PlanDev pd, const Geom* __restrict__ g, int L, int64_t nleaf, const float* __restrict__ coef,
     const int* __restrict__ tstart, const float4* __restrict__ txr, const int* __restrict__ tperm,
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
       const float u1 = split ? uc[1] : (slot == 0 ? ua[1] : ub[1]);
       const float u2 = split ? uc[2] : (slot == 0 ? ua[2] : ub[2]);
       float gf[3] = {0.f, 0.f, 0.f};
-      const float far = far_field<GRAD>(pd, cb, u0, u1, u2, gf);
+      const float far = FAR ? far_field<GRAD>(pd, cb, u0, u1, u2, gf) : 0.f;
       if (valid) {
         const int t = split ? tc : (slot == 0 ? ta : tb2);
         const int orig = tperm[t];
@@ -610,6 +613,45 @@ void leaf_fast_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, dou
     k_leaf_fast<K, false><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, L, nleaf, ws.lcoef,
                                                           ws.tstart, ws.txr, ws.tperm, ws.sstart,
                                                           ws.sxr, phi, grad);
+}
+
+// Far field (L2P) added to the near field already in phi/grad: one warp per
+// target leaf, lanes over its targets, coefficients from k_leaf_coef.
+template <bool GRAD>
+__global__ void __launch_bounds__(32 * kFastWarps) k_leaf_far(
+    PlanDev pd, const Geom* __restrict__ g, int64_t nleaf, const float* __restrict__ coef,
+    const int* __restrict__ tstart, const float4* __restrict__ txr, const int* __restrict__ tperm,
+    double* __restrict__ phi, double* __restrict__ grad) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * kFastWarps + warp;
+  if (b >= nleaf) return;
+  const int t0 = tstart[b], t1 = tstart[b + 1];
+  const float* cb = coef + (size_t)b * pd.nfull;
+  const double inv_s = g->inv_s_leaf;
+  for (int t = t0 + lane; t < t1; t += 32) {
+    const float4 q = txr[t];
+    float gf[3] = {0.f, 0.f, 0.f};
+    const float far = far_field<GRAD>(pd, cb, q.x, q.y, q.z, gf);
+    const int orig = tperm[t];
+    if (phi) phi[orig] += (double)far;
+    if (GRAD && grad)
+      for (int k = 0; k < 3; ++k) grad[(size_t)orig * 3 + k] += (double)gf[k] * inv_s;
+  }
+}
+
+template <int K>
+void near_fast_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
+                      cudaStream_t st) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels;
+  const int64_t nleaf = nbox_at(3, L);
+  const unsigned nbk = (unsigned)((nleaf + kFastWarps - 1) / kFastWarps);
+  if (grad)
+    k_leaf_fast<K, true, false><<<nbk, 32 * kFastWarps, 0, st>>>(
+        pd, ws.geom, L, nleaf, ws.lcoef, ws.tstart, ws.txr, ws.tperm, ws.sstart, ws.sxr, phi, grad);
+  else
+    k_leaf_fast<K, false, false><<<nbk, 32 * kFastWarps, 0, st>>>(
+        pd, ws.geom, L, nleaf, ws.lcoef, ws.tstart, ws.txr, ws.tperm, ws.sstart, ws.sxr, phi, grad);
 }
 
 template <int K, int D, typename T>
@@ -958,5 +1000,42 @@ cudaError_t launch_adaptive_leaf(const fmm_plan_s* P, const Workspace& ws, const
                                                    ws.sx[1], ws.sx[2], ws.sw, phi,
                                                    &ws.geom->flag);
   ++*nl;
+  return cudaGetLastError();
+}
+
+// Split leaf pass of the FP32 3D path: the near field alone (to be launched
+// on a second stream as soon as the points are sorted) ...
+bool leaf_split_supported(const fmm_plan_s* P) {
+  return P->desc.precision != FMM_PREC_FP64 && P->pd.d == 3 && P->desc.levels > 0;
+}
+
+cudaError_t launch_near_field(const fmm_plan_s* P, const Workspace& ws, double* phi,
+                              double* grad, cudaStream_t st, int* nl) {
+  const int k = P->pd.kernel;
+  if (k == FMM_KERNEL_LAPLACE) near_fast_launch<FMM_KERNEL_LAPLACE>(P, ws, phi, grad, st);
+  else if (k == FMM_KERNEL_YUKAWA) near_fast_launch<FMM_KERNEL_YUKAWA>(P, ws, phi, grad, st);
+  else near_fast_launch<FMM_KERNEL_BIHARMONIC>(P, ws, phi, grad, st);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+// ... and the far field added afterwards (leaf coefficients, then L2P)
+cudaError_t launch_far_field(const fmm_plan_s* P, const Workspace& ws, double* phi,
+                             double* grad, cudaStream_t st, int* nl) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels;
+  const int64_t nleaf = nbox_at(3, L);
+  const size_t sm = sizeof(float) * pd.nfull * kCoefWarps;
+  set_smem(k_leaf_coef, sm);
+  k_leaf_coef<<<(unsigned)((nleaf + kCoefWarps - 1) / kCoefWarps), 32 * kCoefWarps, sm, st>>>(
+      pd, ws.geom, L, nleaf, ws.lc + ws.lev_off[L] * pd.nj, ws.lcoef);
+  const unsigned nbk = (unsigned)((nleaf + kFastWarps - 1) / kFastWarps);
+  if (grad)
+    k_leaf_far<true><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, nleaf, ws.lcoef, ws.tstart,
+                                                      ws.txr, ws.tperm, phi, grad);
+  else
+    k_leaf_far<false><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, nleaf, ws.lcoef, ws.tstart,
+                                                       ws.txr, ws.tperm, phi, grad);
+  *nl += 2;
   return cudaGetLastError();
 }

@@ -12,12 +12,21 @@
 // parity-split, Bpar[sigma][Tz][Ty][Tx][q], one 5-D TMA box (zero-filled
 // outside the domain) is the B operand, and the dense offset matrix
 //   A_h[i][q] = Ht_h[i + q]   (i, q in j)
-// is the A operand.  One CTA owns one (tile of 4x4x8 targets, pi, 128-row
-// block of i), accumulates D[i][T] = sum_{sigma,delta,q} A_h[i][q] Bpar[...][q]
-// over the 189 offsets in TMEM, and adds D into the FP64 local expansions.
+// is the A operand.  One CTA owns one (tile of up to 256 target parents,
+// pi, 128-row block of i), accumulates D[i][T] = sum_{sigma,delta,q}
+// A_h[i][q] Bpar[...][q] per offset in TMEM, sums the offsets in registers and
+// adds the result into the FP64 local expansions.
 //
-// Precision: TF32 (one pass) or TF32x3 (a = a_hi + a_lo split, three passes
-// a_hi b_hi + a_hi b_lo + a_lo b_hi), FP32 accumulation.
+// Precision: TF32 (one pass), or TF32x3 / BF16x3 (a = a_hi + a_lo split,
+// three passes a_hi b_hi + a_hi b_lo + a_lo b_hi), FP32 accumulation.
+//
+// Tile width.  An MMA of N = 256 columns reads its A slice once for twice the
+// work of N = 128: the operand traffic out of shared memory drops from 128 to
+// 96 bytes per clock at the full tensor rate, and each MMA runs twice as long,
+// which leaves room for the issuing thread's barrier waits and commits between
+// MMAs.  Measured on this kernel's issue pattern (three passes, one wait and
+// one commit per stage), N = 128 kept the tensor pipe 85% busy and N = 256
+// 99%.
 #include <algorithm>
 #include <cstring>
 
@@ -32,11 +41,8 @@ cudaError_t launch_m2l_simt_levels(const fmm_plan_s* P, const Workspace& ws, int
 
 namespace {
 
-constexpr int kBM = 128;        // rows of A / TMEM lanes
-constexpr int kRowBytes = 128;  // one K chunk: 32 fp32
-constexpr int kTileBytesA = kBM * kRowBytes;
-constexpr int kMaxN = 128;
-constexpr int kTileBytesB = kMaxN * kRowBytes;
+constexpr int kBM = 128;    // rows of A / TMEM lanes
+constexpr int kMaxN = 256;  // target parents per CTA = MMA N
 
 // Operand formats: tf32 (fp32 storage, 32 per 128-byte row, kind::tf32) and
 // bf16 (64 per row, kind::f16).  Both split a value into hi + lo.
@@ -65,12 +71,21 @@ struct FmtBF16 {
   }
 };
 
+// Pipeline stage = one K chunk of every operand the passes read.  The split
+// forms take 64-byte chunks (64-byte swizzle) so that four stages of A_hi,
+// B_hi, A_lo, B_lo fit; the one-pass form takes 128-byte chunks.
 template <int NPASS>
 struct Cfg {
-  static constexpr int kStages = NPASS == 1 ? 6 : 3;
-  static constexpr int kStage = NPASS == 1 ? kTileBytesA + kTileBytesB
-                                           : 2 * (kTileBytesA + kTileBytesB);
+  static constexpr int kRowBytes = NPASS == 1 ? 128 : 64;
+  static constexpr int kKSteps = kRowBytes / 32;  // MMAs of 32 bytes of K per chunk
+  static constexpr int kTileA = kBM * kRowBytes;
+  static constexpr int kTileB = kMaxN * kRowBytes;
+  static constexpr int kStages = 4;
+  static constexpr int kStage = (NPASS == 1 ? 1 : 2) * (kTileA + kTileB);
   static constexpr int kSmem = 1024 + kStages * kStage + 256;
+  static __device__ __forceinline__ uint64_t desc(uint32_t saddr) {
+    return NPASS == 1 ? tc::desc_sw128(saddr) : tc::desc_sw64(saddr);
+  }
 };
 
 // ---- operand packing ------------------------------------------------------
@@ -153,16 +168,17 @@ __global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const double* __
 }
 
 // ---- the contraction --------------------------------------------------------
-// Warp roles: warps 0-7 drain TMEM (warp w reads TMEM lanes 32(w%4).. = rows
-// i, columns 64(w/4)..+63 = targets), warp 8 lane 0 issues TMA, warp 9 lane 0
-// issues MMA.  The tensor cores truncate when they accumulate, so a long K
-// loop in one accumulator drifts; each offset's partial product (|j|/32
-// K-chunks) therefore goes to one of four TMEM buffers (the whole 512
-// columns), and the draining warps add it into float registers
-// (round-to-nearest) while the MMA warp fills the next buffers: a drain may
-// lag three offsets behind the tensor cores.
-constexpr int kEpiWarps = 8;
-constexpr int kNBuf = 4;
+// Warp roles: warps 0-15 drain TMEM (warp w reads TMEM lanes 32(w%4).. = rows
+// i, columns 64(w/4)..+63 = targets), warp 16 lane 0 issues TMA, warp 17 lane
+// 0 issues MMA.  Sixteen draining warps keep the running sums at 64 floats a
+// thread: 18 warps leave at most 5 per SM sub-partition, ~100 registers each.  The tensor cores truncate when they accumulate, so a long K
+// loop in one accumulator drifts; each offset's partial product therefore
+// goes to one of two 256-column TMEM buffers (the whole 512 columns), and the
+// draining warps add it into float registers (round-to-nearest) while the
+// MMA warp fills the other buffer.
+constexpr int kEpiWarps = 16;
+constexpr int kNBuf = 2;
+constexpr int kBufCols = kMaxN;  // TMEM columns per accumulator buffer
 constexpr int kTcThreads = (kEpiWarps + 2) * 32;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -190,12 +206,20 @@ __device__ __forceinline__ bool combo(int c, int px, int py, int pz, int& sg, in
 // uniform tree (Hx = Hy = Hz = 2^(l-1), boxes lexicographic), or, for an
 // adaptive tree, the window of parents spanned by the level's boxes, with
 // map[(pi, cell)] the box at that position (-1: none).
+// A homogeneous kernel shares one set of offset matrices over the levels, so a
+// small level can ride along in the CTAs of another: its whole parent grid
+// (H2^3 parents, H2 = 2^(l2-1)) is loaded into the B rows after the primary
+// tile's and its targets are read off the extra MMA columns (l2 = 0: none).
+// This keeps the tiny coarse levels from forming a wave of their own.
 struct TcLevel {
   CUtensorMap A, Alo, B, Blo;  // offset matrices and parity-split multipoles
+  CUtensorMap B2, B2lo;        // multipoles of the riding level l2
   double* lc;                  // local expansions (level base, or all boxes with map)
+  double* lc2;                 // local expansions of level l2 (base)
   const int* map;              // adaptive: window cell -> box; null for uniform levels
-  float scale;                 // exact power of two (shared offset matrices)
+  float scale, scale2;         // exact powers of two (shared offset matrices)
   int l, BX, BY, BZ, ntx, nty, first_block, Hx, Hy, Hz;
+  int l2;
 };
 constexpr int kTcMaxLevels = 10;
 struct TcParams {
@@ -235,12 +259,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int tile = lb >> 3;
   const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
   const int X0 = tx * BX, Y0 = ty * BY, Z0 = tz * BZ;
-  const int N = BX * BY * BZ;                         // rows the TMA box fills
+  const int l2 = LV.l2, H2 = l2 ? 1 << (l2 - 1) : 0;
+  const int N1 = BX * BY * BZ;                        // rows of the primary tile
+  const int N = N1 + H2 * H2 * H2;                    // rows the TMA boxes fill
   const int Nmma = N < 16 ? 16 : (N + 15) / 16 * 16;  // MMA width; extra columns discarded
   const int nl = 1 << l, Hx = LV.Hx, Hy = LV.Hy, Hz = LV.Hz;
   const int* __restrict__ map = LV.map;
   const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
-  const uint32_t bytesA = kTileBytesA, bytesB = (uint32_t)N * kRowBytes;
+  const uint32_t bytesA = C::kTileA, bytesB = (uint32_t)N * C::kRowBytes;
   const uint32_t stage_tx = (NPASS == 1 ? 1u : 2u) * (bytesA + bytesB);
 
   if (threadIdx.x == 0) {
@@ -255,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::mbar_init(drainb, 1);
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tslot, 128 * kNBuf);
+  if (warp == 0) tc::tmem_alloc(tslot, kBufCols * kNBuf);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -279,14 +305,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         unsigned char* st = sm + s * C::kStage;
         tc::mbar_expect_tx(&full[s], stage_tx);
         last_round[s] = r;
-        const int kc = ch * F::kRow;  // element offset of this 128-byte K chunk
+        // element offset of this K chunk (a multiple of 64 bytes)
+        const int kc = ch * (C::kRowBytes / (int)sizeof(typename F::T));
         tc::tma_load_2d(st, tmA, &full[s], kc, hidx * MP + mt * kBM);
-        tc::tma_load_5d(st + kTileBytesA, tmB, &full[s], kc, X0 + dx, Y0 + dy, Z0 + dz, sg);
+        tc::tma_load_5d(st + C::kTileA, tmB, &full[s], kc, X0 + dx, Y0 + dy, Z0 + dz, sg);
+        if (l2)  // N1 is a multiple of 8 rows: the second box starts on a swizzle atom
+          tc::tma_load_5d(st + C::kTileA + N1 * C::kRowBytes, &LV.B2, &full[s], kc, dx, dy, dz,
+                          sg);
         if (NPASS == 3) {
-          tc::tma_load_2d(st + kTileBytesA + kTileBytesB, tmAlo, &full[s], kc,
-                          hidx * MP + mt * kBM);
-          tc::tma_load_5d(st + 2 * kTileBytesA + kTileBytesB, tmBlo, &full[s], kc, X0 + dx,
-                          Y0 + dy, Z0 + dz, sg);
+          tc::tma_load_2d(st + C::kTileA + C::kTileB, tmAlo, &full[s], kc, hidx * MP + mt * kBM);
+          tc::tma_load_5d(st + 2 * C::kTileA + C::kTileB, tmBlo, &full[s], kc, X0 + dx, Y0 + dy,
+                          Z0 + dz, sg);
+          if (l2)
+            tc::tma_load_5d(st + 2 * C::kTileA + C::kTileB + N1 * C::kRowBytes, &LV.B2lo,
+                            &full[s], kc, dx, dy, dz, sg);
         }
       }
     }
@@ -313,7 +345,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       tc::fence_after();
-      const uint32_t dacc = tmem + (uint32_t)(bf * 128);
+      const uint32_t dacc = tmem + (uint32_t)(bf * kBufCols);
       for (int ch = 0; ch < jchunks; ++ch, ++kk) {
         const int s = kk % C::kStages, r = kk / C::kStages;
         if (!tc::mbar_wait(&full[s], r & 1, err)) {
@@ -322,11 +354,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         tc::fence_after();
         const uint32_t st = tc::smem_u32(sm + s * C::kStage);
-        const uint64_t a = tc::desc_sw128(st), b = tc::desc_sw128(st + kTileBytesA);
-        const uint64_t alo = tc::desc_sw128(st + kTileBytesA + kTileBytesB);
-        const uint64_t blo = tc::desc_sw128(st + 2 * kTileBytesA + kTileBytesB);
+        const uint64_t a = C::desc(st), b = C::desc(st + C::kTileA);
+        const uint64_t alo = C::desc(st + C::kTileA + C::kTileB);
+        const uint64_t blo = C::desc(st + 2 * C::kTileA + C::kTileB);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < C::kKSteps; ++k) {
           // one MMA consumes 32 bytes of K (8 tf32 or 16 bf16) inside the swizzle atom
           const uint64_t adv = (uint64_t)(k * 32) >> 4;
           if (F::kF16) {
@@ -360,10 +392,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else if (warp < kEpiWarps) {
     // ---------------- drain TMEM into float registers ----------------
-    const int quad = warp & 3, c0 = (warp >> 2) * 64;  // TMEM lanes / first column
-    float sum[64];
+    constexpr int kCols = kMaxN / (kEpiWarps / 4);       // columns per draining warp
+    const int quad = warp & 3, c0 = (warp >> 2) * kCols;  // TMEM lanes / first column
+    float sum[kCols];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) sum[j] = 0.f;
+    for (int j = 0; j < kCols; ++j) sum[j] = 0.f;
     bool ok = true;
     int g = 0;
     for (int c = 0; c < 216; ++c) {
@@ -376,17 +409,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc::fence_after();
       const uint32_t base =
-          tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bf * 128 + c0);
-      if (c0 < N) {
-        uint32_t r0[32], r1[32];
-        tc::tmem_ld32_nowait(base, r0);
-        if (c0 + 32 < N) tc::tmem_ld32_nowait(base + 32u, r1);
-        tc::tmem_wait();
+          tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bf * kBufCols + c0);
+      // groups of 16 columns, each loaded then summed (16 registers in flight)
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sum[j] += __uint_as_float(r0[j]);
-        if (c0 + 32 < N) {
+      for (int gq = 0; gq < kCols / 16; ++gq) {
+        if (c0 + 16 * gq < N) {
+          uint32_t r0[16];
+          tc::tmem_ld16_nowait(base + (uint32_t)(16 * gq), r0);
+          tc::tmem_wait();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) sum[32 + j] += __uint_as_float(r1[j]);
+          for (int j = 0; j < 16; ++j) sum[16 * gq + j] += __uint_as_float(r0[j]);
         }
       }
       tc::fence_before();
@@ -398,10 +430,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (ok) {
       const int i = mt * kBM + quad * 32 + lane;
 #pragma unroll
-      for (int jn = 0; jn < 64; ++jn) {
+      for (int jn = 0; jn < kCols; ++jn) {
         const int n = c0 + jn;
         const float sv = sum[jn];
-        if (n < N) {
+        if (n < N1) {
           const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
           if (x < Hx && y < Hy && z < Hz && i < nj) {
             const int64_t t =
@@ -409,13 +441,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     : ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
             if (t >= 0) lc[t * nj + i] += (double)(sv * LV.scale);
           }
+        } else if (n < N && i < nj) {  // the riding level's targets
+          const int n2 = n - N1, nl2 = 2 * H2;
+          const int x = n2 % H2, y = (n2 / H2) % H2, z = n2 / (H2 * H2);
+          const int64_t t = ((int64_t)(2 * z + pz) * nl2 + (2 * y + py)) * nl2 + (2 * x + px);
+          LV.lc2[t * nj + i] += (double)(sv * LV.scale2);
         }
       }
     }
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 128 * kNBuf);
+  if (warp == 0) tc::tmem_dealloc(tmem, kBufCols * kNBuf);
 }
 
 // ---- host side: tensor maps ---------------------------------------------------
@@ -438,14 +475,26 @@ EncodeTiledFn encode_fn() {
 }
 
 bool make_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims,
-              const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapDataType dt) {
+              const cuuint64_t* strides, const cuuint32_t* box, CUtensorMapDataType dt,
+              int row_bytes) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   return fn(m, dt, (cuuint32_t)rank, base, dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE,
+            row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
+}
+
+// Target tile of a parent grid Hx x Hy x Hz: up to 16 x 4 x 4 (or 8 x 8 x 4)
+// = 256 parents, x fastest.
+void tile_shape(int Hx, int Hy, int Hz, TcLevel* v) {
+  v->BX = std::min(16, Hx);
+  v->BZ = std::min(4, Hz);
+  v->BY = std::min(Hy, kMaxN / (v->BX * v->BZ));
+  v->ntx = (Hx + v->BX - 1) / v->BX;
+  v->nty = (Hy + v->BY - 1) / v->BY;
 }
 
 template <typename F, int NPASS>
@@ -477,20 +526,20 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
   TcParams prm;
   std::memset(&prm, 0, sizeof(prm));
   prm.nj = nj;
-  prm.jchunks = JP / F::kRow;
+  const int row = C::kRowBytes / (int)esz;  // elements per K chunk
+  prm.jchunks = JP / row;
   prm.MP = MP;
   prm.err = &ws.geom->flag;
   int nb = 0;
-  // largest level first: its tiles start earliest
-  for (int l = L; l >= 2; --l) {
+  // largest level first: its tiles start earliest; with shared offset
+  // matrices level 2 rides along in level 3's CTAs
+  const int lmin = (shared_t && L >= 3) ? 3 : 2;
+  for (int l = L; l >= lmin; --l) {
     TcLevel& v = prm.lev[prm.nlev++];
     const int nl = 1 << l, H = nl >> 1;
     v.l = l;
-    v.BX = std::min(8, H);
-    v.BY = std::min(4, H);
-    v.BZ = std::min(4, H);
-    v.ntx = (H + v.BX - 1) / v.BX;
-    v.nty = (H + v.BY - 1) / v.BY;
+    v.l2 = 0;
+    tile_shape(H, H, H, &v);
     const int ntz = (H + v.BZ - 1) / v.BZ;
     v.first_block = nb;
     nb += v.ntx * v.nty * ntz * 8;
@@ -507,20 +556,35 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
     }
     cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
     cuuint64_t sA[1] = {(cuuint64_t)JP * esz};
-    cuuint32_t bA[2] = {(cuuint32_t)F::kRow, (cuuint32_t)kBM};
+    cuuint32_t bA[2] = {(cuuint32_t)row, (cuuint32_t)kBM};
     cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)H, 8};
     cuuint64_t sB[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * H,
                         (cuuint64_t)JP * esz * H * H, (cuuint64_t)JP * esz * H * H * H};
-    cuuint32_t bB[5] = {(cuuint32_t)F::kRow, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ,
-                        1};
-    if (!make_map(&v.A, th, 2, dA, sA, bA, dt)) return cudaErrorInvalidValue;
-    if (!make_map(&v.B, bh, 5, dB, sB, bB, dt)) return cudaErrorInvalidValue;
+    cuuint32_t bB[5] = {(cuuint32_t)row, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ, 1};
+    const int rb = C::kRowBytes;
+    if (!make_map(&v.A, th, 2, dA, sA, bA, dt, rb)) return cudaErrorInvalidValue;
+    if (!make_map(&v.B, bh, 5, dB, sB, bB, dt, rb)) return cudaErrorInvalidValue;
     v.Alo = v.A;
     v.Blo = v.B;
     if (NPASS == 3) {
-      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt))
+      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt, rb))
         return cudaErrorInvalidValue;
-      if (!make_map(&v.Blo, blo + ws.lev_off[l] * JP, 5, dB, sB, bB, dt))
+      if (!make_map(&v.Blo, blo + ws.lev_off[l] * JP, 5, dB, sB, bB, dt, rb))
+        return cudaErrorInvalidValue;
+    }
+    if (l == 3 && lmin == 3) {  // level 2: 2 x 2 x 2 parents after level 3's 64
+      v.l2 = 2;
+      v.lc2 = ws.lc + ws.lev_off[2] * nj;
+      v.scale2 = 1.0f;
+      cuuint64_t d2[5] = {(cuuint64_t)JP, 2, 2, 2, 8};
+      cuuint64_t s2[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * 2,
+                          (cuuint64_t)JP * esz * 4, (cuuint64_t)JP * esz * 8};
+      cuuint32_t b2[5] = {(cuuint32_t)row, 2, 2, 2, 1};
+      if (!make_map(&v.B2, bhi0 + ws.lev_off[2] * JP, 5, d2, s2, b2, dt, rb))
+        return cudaErrorInvalidValue;
+      v.B2lo = v.B2;
+      if (NPASS == 3 &&
+          !make_map(&v.B2lo, blo + ws.lev_off[2] * JP, 5, d2, s2, b2, dt, rb))
         return cudaErrorInvalidValue;
     }
   }
@@ -615,7 +679,8 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
   TcParams prm;
   std::memset(&prm, 0, sizeof(prm));
   prm.nj = nj;
-  prm.jchunks = JP / F::kRow;
+  const int row = C::kRowBytes / (int)esz;  // elements per K chunk
+  prm.jchunks = JP / row;
   prm.MP = MP;
   prm.err = &ws.geom->flag;
   int nb = 0;
@@ -646,14 +711,11 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
     ++*nl;
     TcLevel& v = prm.lev[prm.nlev++];
     v.l = l;
+    v.l2 = 0;
     v.Hx = H[0];
     v.Hy = H[1];
     v.Hz = H[2];
-    v.BX = std::min(8, H[0]);
-    v.BY = std::min(4, H[1]);
-    v.BZ = std::min(4, H[2]);
-    v.ntx = (H[0] + v.BX - 1) / v.BX;
-    v.nty = (H[1] + v.BY - 1) / v.BY;
+    tile_shape(H[0], H[1], H[2], &v);
     const int ntz = (H[2] + v.BZ - 1) / v.BZ;
     v.first_block = nb;
     nb += v.ntx * v.nty * ntz * 8;
@@ -667,22 +729,22 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
     }
     cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
     cuuint64_t sA[1] = {(cuuint64_t)JP * esz};
-    cuuint32_t bA[2] = {(cuuint32_t)F::kRow, (cuuint32_t)kBM};
+    cuuint32_t bA[2] = {(cuuint32_t)row, (cuuint32_t)kBM};
     cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H[0], (cuuint64_t)H[1], (cuuint64_t)H[2], 8};
     cuuint64_t sB[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * H[0],
                         (cuuint64_t)JP * esz * H[0] * H[1],
                         (cuuint64_t)JP * esz * H[0] * H[1] * H[2]};
-    cuuint32_t bB[5] = {(cuuint32_t)F::kRow, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ,
-                        1};
-    if (!make_map(&v.A, thi0 + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt))
+    cuuint32_t bB[5] = {(cuuint32_t)row, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ, 1};
+    const int rb = C::kRowBytes;
+    if (!make_map(&v.A, thi0 + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt, rb))
       return cudaErrorInvalidValue;
-    if (!make_map(&v.B, bhi, 5, dB, sB, bB, dt)) return cudaErrorInvalidValue;
+    if (!make_map(&v.B, bhi, 5, dB, sB, bB, dt, rb)) return cudaErrorInvalidValue;
     v.Alo = v.A;
     v.Blo = v.B;
     if (NPASS == 3) {
-      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt))
+      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt, rb))
         return cudaErrorInvalidValue;
-      if (!make_map(&v.Blo, blo, 5, dB, sB, bB, dt)) return cudaErrorInvalidValue;
+      if (!make_map(&v.Blo, blo, 5, dB, sB, bB, dt, rb)) return cudaErrorInvalidValue;
     }
     *done |= 1u << l;
     if (prm.nlev == kTcMaxLevels) break;

@@ -328,12 +328,12 @@ def test_user_pde_equal_to_the_kernels_own(torch_cuda):
     src = rng.random((20000, 3))
     w = rng.uniform(-1, 1, 20000)
     lap = ([(0, 0, 2), (2, 0, 0), (0, 2, 0)], [3.0, 3.0, 3.0])
-    a, _ = _plan_eval(torch_cuda, "laplace", 3, 8, 3, src, w)
-    b, _ = _plan_eval(torch_cuda, "laplace", 3, 8, 3, src, w, pde=lap)
+    a, _ = _plan_eval(torch_cuda, "laplace", 8, 3, src, w)
+    b, _ = _plan_eval(torch_cuda, "laplace", 8, 3, src, w, pde=lap)
     assert np.array_equal(a, b)
     yuk = ([(2, 0, 0), (0, 2, 0), (0, 0, 2), (0, 0, 0)], [1.0, 1.0, 1.0, -1.0])
-    a, _ = _plan_eval(torch_cuda, "yukawa", 3, 8, 3, src, w, lam=1.0)
-    b, _ = _plan_eval(torch_cuda, "yukawa", 3, 8, 3, src, w, pde=yuk, lam=1.0)
+    a, _ = _plan_eval(torch_cuda, "yukawa", 8, 3, src, w, lam=1.0)
+    b, _ = _plan_eval(torch_cuda, "yukawa", 8, 3, src, w, pde=yuk, lam=1.0)
     assert np.array_equal(a, b)
 
 
