@@ -615,27 +615,86 @@ void leaf_fast_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, dou
                                                           ws.sxr, phi, grad);
 }
 
-// Far field (L2P) added to the near field already in phi/grad: one warp per
-// target leaf, lanes over its targets, coefficients from k_leaf_coef.
+// far_field for two targets at once in packed f32x2 arithmetic (both halves
+// share the coefficients); row bases follow the full layout: rows (ms, m1) in
+// order, m0 contiguous.
+template <bool GRAD>
+__device__ __forceinline__ f2_t far_field2(const PlanDev& pd, const float* __restrict__ cb,
+                                           f2_t U0, f2_t U1, f2_t U2, f2_t* gf) {
+  const int p = pd.p;
+  const f2_t one = f2pack(1.f, 1.f);
+  f2_t far = 0ull, pz = one, pzm = 0ull;
+  int base = 0;
+  for (int ms = 0; ms <= p; ++ms) {
+    f2_t py = one, pym = 0ull;
+    for (int m1 = 0; m1 <= p - ms; ++m1) {
+      const int len = p - ms - m1 + 1;
+      float c = cb[base + len - 1];
+      f2_t v = f2pack(c, c), dv = 0ull;
+      for (int k = len - 2; k >= 0; --k) {
+        if (GRAD) dv = f2fma(dv, U0, v);
+        c = cb[base + k];
+        v = f2fma(v, U0, f2pack(c, c));
+      }
+      const f2_t vy = f2mul(v, py);
+      far = f2fma(vy, pz, far);
+      if (GRAD) {
+        gf[0] = f2fma(f2mul(dv, py), pz, gf[0]);
+        gf[1] = f2fma(f2mul(v, pym), pz, gf[1]);
+        gf[2] = f2fma(vy, pzm, gf[2]);
+      }
+      pym = f2fma(pym, U1, py);
+      py = f2mul(py, U1);
+      base += len;
+    }
+    pzm = f2fma(pzm, U2, pz);
+    pz = f2mul(pz, U2);
+  }
+  return far;
+}
+
+// Far field (L2P) added to the near field already in phi/grad, coefficients
+// from k_leaf_coef.  A warp takes two target leaves, one per half; lane l of
+// a half evaluates targets l and l + 16 of a 32-target block as the two
+// halves of packed f32x2 operations, which halves the instructions a target
+// costs (the evaluation is bound by instruction issue, not memory).
 template <bool GRAD>
 __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_far(
     PlanDev pd, const Geom* __restrict__ g, int64_t nleaf, const float* __restrict__ coef,
     const int* __restrict__ tstart, const float4* __restrict__ txr, const int* __restrict__ tperm,
     double* __restrict__ phi, double* __restrict__ grad) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * kFastWarps + warp;
-  if (b >= nleaf) return;
-  const int t0 = tstart[b], t1 = tstart[b + 1];
-  const float* cb = coef + (size_t)b * pd.nfull;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, l16 = lane & 15;
+  const int64_t b = ((int64_t)blockIdx.x * kFastWarps + warp) * 2 + (lane >> 4);
+  if (b - (lane >> 4) >= nleaf) return;  // warp-uniform: no leaf for either half
+  const bool has = b < nleaf;
+  const int t0 = has ? tstart[b] : 0, t1 = has ? tstart[b + 1] : 0;
+  const float* cb = coef + (size_t)(has ? b : nleaf - 1) * pd.nfull;
   const double inv_s = g->inv_s_leaf;
-  for (int t = t0 + lane; t < t1; t += 32) {
-    const float4 q = txr[t];
-    float gf[3] = {0.f, 0.f, 0.f};
-    const float far = far_field<GRAD>(pd, cb, q.x, q.y, q.z, gf);
-    const int orig = tperm[t];
-    if (phi) phi[orig] += (double)far;
-    if (GRAD && grad)
-      for (int k = 0; k < 3; ++k) grad[(size_t)orig * 3 + k] += (double)gf[k] * inv_s;
+  for (int tb = t0; tb < t1; tb += 32) {
+    const int ta = tb + l16, tc = tb + 16 + l16;
+    const bool va = ta < t1, vc = tc < t1;
+    const float4 qa = va ? txr[ta] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 qc = vc ? txr[tc] : make_float4(0.f, 0.f, 0.f, 0.f);
+    f2_t gf[3] = {0ull, 0ull, 0ull};
+    const f2_t far = far_field2<GRAD>(pd, cb, f2pack(qa.x, qc.x), f2pack(qa.y, qc.y),
+                                      f2pack(qa.z, qc.z), gf);
+    float fa, fc;
+    f2unpack(far, fa, fc);
+    float ga[3], gc[3];
+    if (GRAD)
+      for (int k = 0; k < 3; ++k) f2unpack(gf[k], ga[k], gc[k]);
+    if (va) {
+      const int orig = tperm[ta];
+      if (phi) phi[orig] += (double)fa;
+      if (GRAD && grad)
+        for (int k = 0; k < 3; ++k) grad[(size_t)orig * 3 + k] += (double)ga[k] * inv_s;
+    }
+    if (vc) {
+      const int orig = tperm[tc];
+      if (phi) phi[orig] += (double)fc;
+      if (GRAD && grad)
+        for (int k = 0; k < 3; ++k) grad[(size_t)orig * 3 + k] += (double)gc[k] * inv_s;
+    }
   }
 }
 
@@ -1029,7 +1088,7 @@ cudaError_t launch_far_field(const fmm_plan_s* P, const Workspace& ws, double* p
   set_smem(k_leaf_coef, sm);
   k_leaf_coef<<<(unsigned)((nleaf + kCoefWarps - 1) / kCoefWarps), 32 * kCoefWarps, sm, st>>>(
       pd, ws.geom, L, nleaf, ws.lc + ws.lev_off[L] * pd.nj, ws.lcoef);
-  const unsigned nbk = (unsigned)((nleaf + kFastWarps - 1) / kFastWarps);
+  const unsigned nbk = (unsigned)((nleaf + 2 * kFastWarps - 1) / (2 * kFastWarps));
   if (grad)
     k_leaf_far<true><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, nleaf, ws.lcoef, ws.tstart,
                                                       ws.txr, ws.tperm, phi, grad);
