@@ -18,10 +18,11 @@
  *    NULL = legacy default stream).  Calls return as soon as the work is
  *    enqueued; nothing is synchronised except where stated.  Uniform 3D
  *    plans of the float precisions run the pipeline on two streams the plan
- *    owns (the near field on a low-priority one, concurrently with the rest
- *    on a high-priority one), joined to `stream` by events on both sides: to
- *    the caller the work is still ordered on `stream`, and a call made while
- *    `stream` is being captured into a CUDA graph captures both branches.
+ *    owns (the M2L tables and the near field on a low-priority one,
+ *    concurrently with the rest on a high-priority one), joined to `stream`
+ *    by events on both sides: to the caller the work is still ordered on
+ *    `stream`, and a call made while `stream` is being captured into a CUDA
+ *    graph captures both branches.
  *  - The caller owns every input, output and workspace buffer.  The library
  *    owns the plan and the small read-only tables the plan uploads at
  *    creation (cudaMalloc'd once, freed by fmm_plan_destroy).
@@ -205,7 +206,9 @@ int fmm_last_status(fmm_plan_t plan);
  * 0 tree, 1 derivative tables, 2 P2M, 3 M2M, 4 M2L, 5 L2L, 6 L2P+P2P.
  * Where the near field runs on its own stream (see above), phase 6 is the
  * far field (leaf coefficients and L2P) plus any wait for the near field,
- * and the near field's time is spread over the phases it overlaps. */
+ * the derivative and offset tables are built on that stream too (phase 1 is
+ * empty, phase 4 includes any wait for them), and the side stream's time is
+ * spread over the phases it overlaps. */
 #define FMM_NUM_PHASES 7
 int fmm_set_timing(fmm_plan_t plan, int enable);
 int fmm_phase_times(fmm_plan_t plan, float* ms_out /* FMM_NUM_PHASES */);

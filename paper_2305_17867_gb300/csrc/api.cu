@@ -439,7 +439,8 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
       cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_tab, cudaEventDisableTiming) != cudaSuccess) {
     cudaFree(dt);
     delete P;
     return FMM_ERR_CUDA;
@@ -464,7 +465,8 @@ extern "C" int fmm_plan_destroy(fmm_plan_t P) {
     for (auto& e : P->ev) cudaEventDestroy(e);
   if (P->events_made)
     for (auto& e : P->evk) cudaEventDestroy(e);
-  for (cudaEvent_t e : {P->ev_in, P->ev_fork, P->ev_join, P->ev_out}) cudaEventDestroy(e);
+  for (cudaEvent_t e : {P->ev_in, P->ev_fork, P->ev_join, P->ev_out, P->ev_tab})
+    cudaEventDestroy(e);
   cudaStreamDestroy(P->hi);
   cudaStreamDestroy(P->aux);
   cudaFree(P->dev_tables);
@@ -648,20 +650,26 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
   if ((e = launch_build_tree(P, ws, n_src, src, w, n_tgt, tgt, run, &nl)) != cudaSuccess)
     return FMM_ERR_CUDA;
   if (split) {
+    // the derivative and offset tables depend only on the geometry: they are
+    // built on the side stream while P2M and M2M run, then the near field
     if (cudaEventRecord(P->ev_fork, run) != cudaSuccess ||
         cudaStreamWaitEvent(P->aux, P->ev_fork, 0) != cudaSuccess)
       return FMM_ERR_CUDA;
+    if ((e = launch_deriv_tables(P, ws, P->aux, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+    if ((e = launch_m2l_tables(P, ws, P->aux, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+    if (cudaEventRecord(P->ev_tab, P->aux) != cudaSuccess) return FMM_ERR_CUDA;
     if ((e = launch_near_field(P, ws, phi, grad, P->aux, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
     if (cudaEventRecord(P->ev_join, P->aux) != cudaSuccess) return FMM_ERR_CUDA;
   }
   mark(1);
-  if ((e = launch_deriv_tables(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if (!split && (e = launch_deriv_tables(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(2);
   if ((e = launch_p2m(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(3);
   if ((e = launch_m2m(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(4);
-  if ((e = launch_m2l(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
+  if (split && cudaStreamWaitEvent(run, P->ev_tab, 0) != cudaSuccess) return FMM_ERR_CUDA;
+  if ((e = launch_m2l(P, ws, run, &nl, split)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(5);
   if ((e = launch_l2l(P, ws, run, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
   mark(6);

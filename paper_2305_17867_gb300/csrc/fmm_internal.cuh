@@ -79,12 +79,14 @@ struct fmm_plan_s {
   cudaEvent_t ev[FMM_NUM_PHASES + 1];
   cudaEvent_t evk[2];  // around the M2L contraction launch(es)
   bool events_made;
-  // FP32 3D uniform path: the pipeline on a high-priority stream, the near
-  // field on a low-priority one; events order them after the caller's stream
-  // (in), the near field after the sort (fork), the far field after the near
-  // field (join) and the caller's stream after the pipeline (out)
+  // FP32 3D uniform path: the pipeline on a high-priority stream, the M2L
+  // tables and the near field on a low-priority one; events order them after
+  // the caller's stream (in), the tables and near field after the sort (fork),
+  // the M2L after the tables (tab), the far field after the near field (join)
+  // and the caller's stream after the pipeline (out)
   cudaStream_t hi, aux;
   cudaEvent_t ev_in, ev_fork, ev_join, ev_out;
+  cudaEvent_t ev_tab;  // derivative and offset tables built (on aux)
   cudaStream_t last_stream;
   Geom* last_geom;  // device geometry of the last evaluation (in its workspace)
   int launches;
@@ -190,7 +192,11 @@ cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaSt
                                 int* nlaunch);
 cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
 cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
-cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch);
+// tables_ready: launch_m2l_tables has already been ordered before this call
+cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nlaunch,
+                       bool tables_ready = false);
+cudaError_t launch_m2l_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
+                              int* nlaunch);
 cudaError_t launch_m2l_fft(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
                            int* nlaunch);
 // offset tables of the M2L derivative tables: one level suffices when the

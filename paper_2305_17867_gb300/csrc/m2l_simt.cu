@@ -210,15 +210,29 @@ cudaError_t launch_m2l_simt_levels(const fmm_plan_s* P, const Workspace& ws, int
 
 // M2L dispatcher: zero the local expansions of levels 2..L, then run the
 // configured contraction path.
-cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl);
+cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl,
+                          bool tables_ready);
+cudaError_t launch_m2l_tc_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
+                                 int* nl);
 
-cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+static bool uses_tc_tables(const fmm_plan_s* P) {
+  const int prec = P->desc.precision;
+  return P->desc.m2l != FMM_M2L_FFT && prec != FMM_PREC_FP64 && prec != FMM_PREC_FP32 &&
+         P->pd.d == 3 && P->desc.levels > 0;
+}
+
+cudaError_t launch_m2l_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+  return uses_tc_tables(P) ? launch_m2l_tc_tables(P, ws, st, nl) : cudaGetLastError();
+}
+
+cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl,
+                       bool tables_ready) {
   const int L = P->desc.levels;
   cudaMemsetAsync(ws.lc, 0, sizeof(double) * (size_t)ws.lev_off[L + 1] * P->pd.nj, st);
   const int prec = P->desc.precision;
   if (P->desc.m2l == FMM_M2L_FFT) return launch_m2l_fft(P, ws, st, nl);
   if (prec == FMM_PREC_FP64 || prec == FMM_PREC_FP32) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
-  return launch_m2l_tc(P, ws, st, nl);
+  return launch_m2l_tc(P, ws, st, nl, tables_ready && uses_tc_tables(P));
 }
 
 cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const ATree& t,

@@ -497,8 +497,24 @@ void tile_shape(int Hx, int Hy, int Hz, TcLevel* v) {
   v->nty = (Hy + v->BY - 1) / v->BY;
 }
 
+// offset matrices A_h (hi and lo) of a uniform tree from the derivative tables
 template <typename F, int NPASS>
-cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st) {
+void build_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st) {
+  using T = typename F::T;
+  const PlanDev& pd = P->pd;
+  const bool shared_t = pd.kernel != FMM_KERNEL_YUKAWA;  // homogeneous G
+  const int tlev = shared_t ? 1 : (P->desc.levels - 1);
+  T* thi0 = static_cast<T*>(ws.tc_tmat[0]);
+  T* tlo = NPASS == 3 ? static_cast<T*>(ws.tc_tmat[1]) : nullptr;
+  const size_t sm = 2 * sizeof(T) * pd.nh;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_build_tmat<3, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_build_tmat<3, F><<<dim3(343, tlev), 256, sm, st>>>(pd, ws.htab, ws.tc_mp, ws.tc_jp, thi0, tlo);
+}
+
+template <typename F, int NPASS>
+cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
+                           bool tables_ready) {
   using C = Cfg<NPASS>;
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels;
@@ -517,12 +533,7 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
   LevOff lo;
   for (int l = 0; l <= FMM_MAX_LEVELS; ++l) lo.o[l] = l <= L + 1 ? ws.lev_off[l] : 0;
   k_pack_beta<F><<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, bhi0, blo);
-  {
-    const size_t sm = 2 * sizeof(T) * pd.nh;
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_build_tmat<3, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_build_tmat<3, F><<<dim3(noff, tlev), 256, sm, st>>>(pd, ws.htab, MP, JP, thi0, tlo);
-  }
+  if (!tables_ready) build_tables<F, NPASS>(P, ws, st);
   TcParams prm;
   std::memset(&prm, 0, sizeof(prm));
   prm.nj = nj;
@@ -762,15 +773,29 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
 
 }  // namespace
 
-cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl) {
+cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl,
+                          bool tables_ready) {
   const int L = P->desc.levels;
   if (P->pd.d != 3) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
   const int prec = P->desc.precision;
-  const cudaError_t e = prec == FMM_PREC_BF16X3   ? run_all_levels<FmtBF16, 3>(P, ws, st)
-                        : prec == FMM_PREC_TF32X3 ? run_all_levels<FmtTF32, 3>(P, ws, st)
-                                                  : run_all_levels<FmtTF32, 1>(P, ws, st);
-  *nl += 3;
+  const cudaError_t e =
+      prec == FMM_PREC_BF16X3   ? run_all_levels<FmtBF16, 3>(P, ws, st, tables_ready)
+      : prec == FMM_PREC_TF32X3 ? run_all_levels<FmtTF32, 3>(P, ws, st, tables_ready)
+                                : run_all_levels<FmtTF32, 1>(P, ws, st, tables_ready);
+  *nl += tables_ready ? 2 : 3;
   return e;
+}
+
+// the offset matrices alone (uniform 3D tree, tensor-core precisions), so
+// that they can be built on another stream ahead of the contraction
+cudaError_t launch_m2l_tc_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
+                                 int* nl) {
+  const int prec = P->desc.precision;
+  if (prec == FMM_PREC_BF16X3) build_tables<FmtBF16, 3>(P, ws, st);
+  else if (prec == FMM_PREC_TF32X3) build_tables<FmtTF32, 3>(P, ws, st);
+  else build_tables<FmtTF32, 1>(P, ws, st);
+  ++*nl;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adaptive_m2l_tc(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
