@@ -838,11 +838,19 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l_f32(PlanDev pd, const Geom* 
                                  (float)((cb[2] - sx2[j]) * inv_s), (float)sw[j]);
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < n; q += blockDim.x) {
-          const float4 v = stage[q];
+        // A warp takes 32 sources at a time (lanes past the end take a
+        // weightless point), so every lane emits the same coefficient at the
+        // same step: the warp sums it with shuffles and one lane adds it, in
+        // place of 32 shared-memory atomics on one address.
+        const int lane = threadIdx.x & 31;
+        for (int q0 = threadIdx.x & ~31; q0 < n; q0 += blockDim.x) {  // warp-uniform
+          const int q = q0 + lane;
+          const float4 v = q < n ? stage[q] : make_float4(4.f, 4.f, 4.f, 0.f);
           const float x[3] = {v.x, v.y, v.z};
-          deriv_point<float>(pd, x, lam, scale * v.w, S, sl,
-                             [&](int pos, float h) { atomicAdd(&Lacc[pos], h); });
+          deriv_point<float>(pd, x, lam, scale * v.w, S, sl, [&](int pos, float h) {
+            for (int off = 16; off > 0; off >>= 1) h += __shfl_xor_sync(0xffffffffu, h, off);
+            if (lane == 0) atomicAdd(&Lacc[pos], h);
+          });
         }
       }
     }
