@@ -658,17 +658,42 @@ __device__ __forceinline__ f2_t far_field2(const PlanDev& pd, const float* __res
 // a half evaluates targets l and l + 16 of a 32-target block as the two
 // halves of packed f32x2 operations, which halves the instructions a target
 // costs (the evaluation is bound by instruction issue, not memory).
+// Each half-warp first decompresses its leaf's local expansion into N(p)
+// float coefficients with 1/m! in shared memory (the work k_leaf_coef does,
+// without the round trip through global memory), then evaluates.
 template <bool GRAD>
 __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_far(
-    PlanDev pd, const Geom* __restrict__ g, int64_t nleaf, const float* __restrict__ coef,
+    PlanDev pd, const Geom* __restrict__ g, int64_t nleaf, const double* __restrict__ lc,
     const int* __restrict__ tstart, const float4* __restrict__ txr, const int* __restrict__ tperm,
     double* __restrict__ phi, double* __restrict__ grad) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, l16 = lane & 15;
-  const int64_t b = ((int64_t)blockIdx.x * kFastWarps + warp) * 2 + (lane >> 4);
-  if (b - (lane >> 4) >= nleaf) return;  // warp-uniform: no leaf for either half
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, l16 = lane & 15, half = lane >> 4;
+  const int64_t b = ((int64_t)blockIdx.x * kFastWarps + warp) * 2 + half;
+  if (b - half >= nleaf) return;  // warp-uniform: no leaf for either half
   const bool has = b < nleaf;
+  const int64_t bl = has ? b : nleaf - 1;  // a leaf without targets still runs the sweep
   const int t0 = has ? tstart[b] : 0, t1 = has ? tstart[b + 1] : 0;
-  const float* cb = coef + (size_t)(has ? b : nleaf - 1) * pd.nfull;
+  extern __shared__ __align__(16) float dsm[];
+  const int pitch = (pd.nfull + 1) | 1;  // odd pitch: the halves' rows start in different banks
+  float* Dt = dsm + (size_t)(2 * warp + half) * pitch;
+  {
+    const int nt = pd.nterms > 0 ? pd.nterms : 1;
+    float cf[FMM_MAX_TERMS];
+    for (int t = 0; t < pd.nterms; ++t) cf[t] = (float)scaled_coef(pd, t, g->s_leaf);
+    for (int q = l16; q < pd.nj; q += 16) Dt[q] = (float)lc[(size_t)bl * pd.nj + q];
+    __syncwarp();
+    for (int ms = pd.c; ms <= pd.p; ++ms) {  // the same sweep in both halves
+      const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
+      for (int i = b0 + l16; i < b1; i += 16) {
+        float v = 0.f;
+        for (int t = 0; t < pd.nterms; ++t) v += cf[t] * Dt[pd.rec_src[i * nt + t]];
+        Dt[i] = v;
+      }
+      __syncwarp();
+    }
+    for (int q = l16; q < pd.nfull; q += 16) Dt[q] *= (float)pd.inv_fact[q];
+    __syncwarp();
+  }
+  const float* cb = Dt;
   const double inv_s = g->inv_s_leaf;
   for (int tb = t0; tb < t1; tb += 32) {
     const int ta = tb + l16, tc = tb + 16 + l16;
@@ -1084,17 +1109,18 @@ cudaError_t launch_far_field(const fmm_plan_s* P, const Workspace& ws, double* p
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels;
   const int64_t nleaf = nbox_at(3, L);
-  const size_t sm = sizeof(float) * pd.nfull * kCoefWarps;
-  set_smem(k_leaf_coef, sm);
-  k_leaf_coef<<<(unsigned)((nleaf + kCoefWarps - 1) / kCoefWarps), 32 * kCoefWarps, sm, st>>>(
-      pd, ws.geom, L, nleaf, ws.lc + ws.lev_off[L] * pd.nj, ws.lcoef);
+  const double* lcL = ws.lc + ws.lev_off[L] * pd.nj;
+  const size_t sm = sizeof(float) * (size_t)((pd.nfull + 1) | 1) * 2 * kFastWarps;
   const unsigned nbk = (unsigned)((nleaf + 2 * kFastWarps - 1) / (2 * kFastWarps));
-  if (grad)
-    k_leaf_far<true><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, nleaf, ws.lcoef, ws.tstart,
-                                                      ws.txr, ws.tperm, phi, grad);
-  else
-    k_leaf_far<false><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, nleaf, ws.lcoef, ws.tstart,
+  if (grad) {
+    set_smem(k_leaf_far<true>, sm);
+    k_leaf_far<true><<<nbk, 32 * kFastWarps, sm, st>>>(pd, ws.geom, nleaf, lcL, ws.tstart,
                                                        ws.txr, ws.tperm, phi, grad);
-  *nl += 2;
+  } else {
+    set_smem(k_leaf_far<false>, sm);
+    k_leaf_far<false><<<nbk, 32 * kFastWarps, sm, st>>>(pd, ws.geom, nleaf, lcL, ws.tstart,
+                                                        ws.txr, ws.tperm, phi, grad);
+  }
+  ++*nl;
   return cudaGetLastError();
 }
