@@ -218,7 +218,6 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
   if (d == 3 && prec != FMM_PREC_FP64) {
     w.sxr = carve<float4>(cur, std::max<int64_t>(n_src, 1));
     w.txr = carve<float4>(cur, std::max<int64_t>(n_tgt, 1));
-    w.lcoef = carve<float>(cur, (size_t)nleaf * P->pd.nfull);
   }
   if (d == 3 && (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3)) {
     const int esz = prec == FMM_PREC_BF16X3 ? 2 : 4;  // bytes per operand element

@@ -154,7 +154,6 @@ struct Workspace {
   // decompressed far-field coefficients M Lt / m! of every leaf
   float4* sxr;
   float4* txr;
-  float* lcoef;
   // adaptive tree (plans with levels < 0): box arrays of capacity anb_cap and
   // the points' Morton codes in sorted order
   int64_t anb_cap;

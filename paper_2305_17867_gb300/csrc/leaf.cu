@@ -246,44 +246,10 @@ void leaf_launch_g(const fmm_plan_s* P, const Workspace& ws, double* phi, double
 //
 // The gather of the tree build gives every sorted point float (x - c_own)/s
 // and its weight, c_own the centre of its own leaf.
-// k_leaf_coef: one warp per leaf decompresses Lt (FP64) and stores Dt/m! as
-// float, so the evaluation kernel reads ready coefficients.
-// k_leaf_fast: one block of four warps per target leaf; lane = target, warp w
-// takes every fourth source and every fourth polynomial row, so a source is a
-// single broadcast float4 read per warp; partial sums meet in shared memory.
+// k_leaf_fast: the near field, one warp per target leaf (P2P in packed f32x2
+// pairs).  k_leaf_far: the far field, two target leaves per warp (leaf
+// decompression in shared memory, then L2P in packed f32x2).
 // ---------------------------------------------------------------------------
-constexpr int kCoefWarps = 4;
-
-__global__ void __launch_bounds__(32 * kCoefWarps) k_leaf_coef(PlanDev pd, const Geom* __restrict__ g,
-                                                               int L, int64_t nleaf,
-                                                               const double* __restrict__ lc,
-                                                               float* __restrict__ coef) {
-  // the coefficients feed float arithmetic, so the (short, O(1)-coefficient)
-  // decompression recurrence runs in float as well
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * kCoefWarps + warp;
-  if (b >= nleaf) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float* Dt = reinterpret_cast<float*>(smraw) + (size_t)warp * pd.nfull;
-  const double s = g->s_leaf;
-  const int nt = pd.nterms > 0 ? pd.nterms : 1;
-  float cf[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) cf[t] = (float)scaled_coef(pd, t, s);
-  for (int q = lane; q < pd.nj; q += 32) Dt[q] = (float)lc[(size_t)b * pd.nj + q];
-  __syncwarp();
-  for (int ms = pd.c; ms <= pd.p; ++ms) {
-    const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
-    for (int i = b0 + lane; i < b1; i += 32) {
-      float v = 0.f;
-      for (int t = 0; t < pd.nterms; ++t) v += cf[t] * Dt[pd.rec_src[i * nt + t]];
-      Dt[i] = v;
-    }
-    __syncwarp();
-  }
-  for (int q = lane; q < pd.nfull; q += 32)
-    coef[(size_t)b * pd.nfull + q] = Dt[q] * (float)pd.inv_fact[q];
-}
-
 constexpr int kFastWarps = 4;   // target leaves per block (one warp each)
 constexpr int kStageSrc = 256;  // staged sources per warp and chunk
 
@@ -436,13 +402,13 @@ __device__ __forceinline__ float far_field(const PlanDev& pd, const float* __res
   return far;
 }
 
-// FAR = false: the near field only (P2P); phi (and grad) are overwritten with
-// it, and k_leaf_far adds the far field later (the two run on separate
-// streams, the near field concurrently with the upward and M2L passes).
-template <int K, bool GRAD, bool FAR = true>
+// The near field (P2P) alone: phi (and grad) are overwritten with it, and
+// k_leaf_far adds the far field afterwards (on the FP32 3D uniform path the
+// two run on separate streams, the near field beside the upward and M2L
+// passes).
+template <int K, bool GRAD>
 __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
-    PlanDev pd, const Geom* __restrict__ g, int L, int64_t nleaf, const float* __restrict__ coef,
-    const int* __restrict__ tstart, const float4* __restrict__ txr, const int* __restrict__ tperm,
+    PlanDev pd, const Geom* __restrict__ g, int L, int64_t nleaf, const int* __restrict__ tstart, const float4* __restrict__ txr, const int* __restrict__ tperm,
     const int* __restrict__ sstart, const float4* __restrict__ sxr, double* __restrict__ phi,
     double* __restrict__ grad) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -465,7 +431,6 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
   // leaf side and its reciprocal from the geometry record (no FP64 division)
   const double s = g->s_leaf, inv_s = g->inv_s_leaf;
   const float lam = (float)(pd.lam * s);
-  const float* cb = coef + (size_t)b * pd.nfull;
   double phi_scale, grad_scale;
   if (K == FMM_KERNEL_LAPLACE) {
     phi_scale = inv_s * (1.0 / (4.0 * 3.14159265358979323846));
@@ -565,54 +530,28 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
           for (int k = 0; k < 3; ++k) gc[k] += __shfl_xor_sync(0xffffffffu, gc[k], off);
       }
     }
-    // far field for the slots in use, each lane on its own targets
+    // write the slots in use, each lane its own targets
     const int nslot = nfull + (r ? 1 : 0);
     for (int slot = 0; slot < nslot; ++slot) {
       const bool split = slot == nfull;  // the remainder slot
       const bool valid = split ? (vc && sub == 0) : (slot == 0 ? va : vb);
-      // select values, not pointers, so the per-slot arrays stay in registers
-      const float u0 = split ? uc[0] : (slot == 0 ? ua[0] : ub[0]);
-      const float u1 = split ? uc[1] : (slot == 0 ? ua[1] : ub[1]);
-      const float u2 = split ? uc[2] : (slot == 0 ? ua[2] : ub[2]);
-      float gf[3] = {0.f, 0.f, 0.f};
-      const float far = FAR ? far_field<GRAD>(pd, cb, u0, u1, u2, gf) : 0.f;
       if (valid) {
+        // select values, not pointers, so the per-slot arrays stay in registers
         const int t = split ? tc : (slot == 0 ? ta : tb2);
         const int orig = tperm[t];
         const float nv = split ? nc : (slot == 0 ? na : nb);
-        if (phi) phi[orig] = (double)far + phi_scale * (double)nv;
+        if (phi) phi[orig] = phi_scale * (double)nv;
         if (GRAD && grad) {
           const float g0 = split ? gc[0] : (slot == 0 ? ga[0] : gb[0]);
           const float g1 = split ? gc[1] : (slot == 0 ? ga[1] : gb[1]);
           const float g2 = split ? gc[2] : (slot == 0 ? ga[2] : gb[2]);
-          grad[(size_t)orig * 3 + 0] = (double)gf[0] * inv_s + grad_scale * (double)g0;
-          grad[(size_t)orig * 3 + 1] = (double)gf[1] * inv_s + grad_scale * (double)g1;
-          grad[(size_t)orig * 3 + 2] = (double)gf[2] * inv_s + grad_scale * (double)g2;
+          grad[(size_t)orig * 3 + 0] = grad_scale * (double)g0;
+          grad[(size_t)orig * 3 + 1] = grad_scale * (double)g1;
+          grad[(size_t)orig * 3 + 2] = grad_scale * (double)g2;
         }
       }
     }
   }
-}
-
-template <int K>
-void leaf_fast_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
-                      cudaStream_t st) {
-  const PlanDev& pd = P->pd;
-  const int L = P->desc.levels;
-  const int64_t nleaf = nbox_at(3, L);
-  const size_t sm = sizeof(float) * pd.nfull * kCoefWarps;
-  set_smem(k_leaf_coef, sm);
-  k_leaf_coef<<<(unsigned)((nleaf + kCoefWarps - 1) / kCoefWarps), 32 * kCoefWarps, sm, st>>>(
-      pd, ws.geom, L, nleaf, ws.lc + ws.lev_off[L] * pd.nj, ws.lcoef);
-  const unsigned nbk = (unsigned)((nleaf + kFastWarps - 1) / kFastWarps);
-  if (grad)
-    k_leaf_fast<K, true><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, L, nleaf, ws.lcoef,
-                                                         ws.tstart, ws.txr, ws.tperm, ws.sstart,
-                                                         ws.sxr, phi, grad);
-  else
-    k_leaf_fast<K, false><<<nbk, 32 * kFastWarps, 0, st>>>(pd, ws.geom, L, nleaf, ws.lcoef,
-                                                          ws.tstart, ws.txr, ws.tperm, ws.sstart,
-                                                          ws.sxr, phi, grad);
 }
 
 // far_field for two targets at once in packed f32x2 arithmetic (both halves
@@ -653,14 +592,14 @@ __device__ __forceinline__ f2_t far_field2(const PlanDev& pd, const float* __res
   return far;
 }
 
-// Far field (L2P) added to the near field already in phi/grad, coefficients
-// from k_leaf_coef.  A warp takes two target leaves, one per half; lane l of
-// a half evaluates targets l and l + 16 of a 32-target block as the two
-// halves of packed f32x2 operations, which halves the instructions a target
-// costs (the evaluation is bound by instruction issue, not memory).
-// Each half-warp first decompresses its leaf's local expansion into N(p)
-// float coefficients with 1/m! in shared memory (the work k_leaf_coef does,
-// without the round trip through global memory), then evaluates.
+// Far field (L2P) added to the near field already in phi/grad.  A warp takes
+// two target leaves, one per half; lane l of a half evaluates targets l and
+// l + 16 of a 32-target block as the two halves of packed f32x2 operations,
+// which halves the instructions a target costs (the evaluation is bound by
+// instruction issue, not memory).  Each half-warp first decompresses its leaf's local expansion (FP64) into
+// N(p) float coefficients with 1/m! in shared memory -- the coefficients feed
+// float arithmetic, so the short, O(1)-coefficient recurrence runs in float
+// as well -- then evaluates.
 template <bool GRAD>
 __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_far(
     PlanDev pd, const Geom* __restrict__ g, int64_t nleaf, const double* __restrict__ lc,
@@ -731,11 +670,11 @@ void near_fast_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, dou
   const int64_t nleaf = nbox_at(3, L);
   const unsigned nbk = (unsigned)((nleaf + kFastWarps - 1) / kFastWarps);
   if (grad)
-    k_leaf_fast<K, true, false><<<nbk, 32 * kFastWarps, 0, st>>>(
-        pd, ws.geom, L, nleaf, ws.lcoef, ws.tstart, ws.txr, ws.tperm, ws.sstart, ws.sxr, phi, grad);
+    k_leaf_fast<K, true><<<nbk, 32 * kFastWarps, 0, st>>>(
+        pd, ws.geom, L, nleaf, ws.tstart, ws.txr, ws.tperm, ws.sstart, ws.sxr, phi, grad);
   else
-    k_leaf_fast<K, false, false><<<nbk, 32 * kFastWarps, 0, st>>>(
-        pd, ws.geom, L, nleaf, ws.lcoef, ws.tstart, ws.txr, ws.tperm, ws.sstart, ws.sxr, phi, grad);
+    k_leaf_fast<K, false><<<nbk, 32 * kFastWarps, 0, st>>>(
+        pd, ws.geom, L, nleaf, ws.tstart, ws.txr, ws.tperm, ws.sstart, ws.sxr, phi, grad);
 }
 
 template <int K, int D, typename T>
@@ -1034,25 +973,20 @@ cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* p
                              cudaStream_t st, int* nl) {
   const bool f64 = P->desc.precision == FMM_PREC_FP64;
   const int k = P->pd.kernel, d = P->pd.d;
-  if (!f64 && d == 3) {
-    if (k == FMM_KERNEL_LAPLACE) leaf_fast_launch<FMM_KERNEL_LAPLACE>(P, ws, phi, grad, st);
-    else if (k == FMM_KERNEL_YUKAWA) leaf_fast_launch<FMM_KERNEL_YUKAWA>(P, ws, phi, grad, st);
-    else leaf_fast_launch<FMM_KERNEL_BIHARMONIC>(P, ws, phi, grad, st);
-    *nl += 2;
-    return cudaGetLastError();
+  if (!f64 && d == 3) {  // near field, then far field, on one stream
+    cudaError_t e = launch_near_field(P, ws, phi, grad, st, nl);
+    if (e != cudaSuccess) return e;
+    return launch_far_field(P, ws, phi, grad, st, nl);
   }
   if (d == 2) {
     if (f64) leaf_launch<FMM_KERNEL_LAPLACE, 2, double>(P, ws, phi, grad, st);
     else leaf_launch<FMM_KERNEL_LAPLACE, 2, float>(P, ws, phi, grad, st);
   } else if (k == FMM_KERNEL_LAPLACE) {
-    if (f64) leaf_launch<FMM_KERNEL_LAPLACE, 3, double>(P, ws, phi, grad, st);
-    else leaf_launch<FMM_KERNEL_LAPLACE, 3, float>(P, ws, phi, grad, st);
+    leaf_launch<FMM_KERNEL_LAPLACE, 3, double>(P, ws, phi, grad, st);
   } else if (k == FMM_KERNEL_YUKAWA) {
-    if (f64) leaf_launch<FMM_KERNEL_YUKAWA, 3, double>(P, ws, phi, grad, st);
-    else leaf_launch<FMM_KERNEL_YUKAWA, 3, float>(P, ws, phi, grad, st);
+    leaf_launch<FMM_KERNEL_YUKAWA, 3, double>(P, ws, phi, grad, st);
   } else {
-    if (f64) leaf_launch<FMM_KERNEL_BIHARMONIC, 3, double>(P, ws, phi, grad, st);
-    else leaf_launch<FMM_KERNEL_BIHARMONIC, 3, float>(P, ws, phi, grad, st);
+    leaf_launch<FMM_KERNEL_BIHARMONIC, 3, double>(P, ws, phi, grad, st);
   }
   ++*nl;
   return cudaGetLastError();
