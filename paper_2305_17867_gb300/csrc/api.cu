@@ -431,18 +431,23 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
     cudaFree(dt);
     return FMM_ERR_NOMEM;
   }
-  int prio_low = 0, prio_high = 0;
-  if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&P->hi, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
-      cudaStreamCreateWithPriority(&P->aux, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->ev_tab, cudaEventDisableTiming) != cudaSuccess) {
-    cudaFree(dt);
-    delete P;
-    return FMM_ERR_CUDA;
+  {  // the plan's two streams and their events; on failure release what was made
+    int prio_low = 0, prio_high = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&P->hi, cudaStreamNonBlocking, prio_high) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&P->aux, cudaStreamNonBlocking, prio_low) == cudaSuccess;
+    cudaEvent_t* evs[5] = {&P->ev_in, &P->ev_fork, &P->ev_join, &P->ev_out, &P->ev_tab};
+    for (cudaEvent_t* e : evs)
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      for (cudaEvent_t* e : evs)
+        if (*e) cudaEventDestroy(*e);
+      if (P->aux) cudaStreamDestroy(P->aux);
+      if (P->hi) cudaStreamDestroy(P->hi);
+      cudaFree(dt);
+      delete P;
+      return FMM_ERR_CUDA;
+    }
   }
   P->desc = *desc;
   P->desc.pde = nullptr;
