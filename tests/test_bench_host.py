@@ -1,0 +1,76 @@
+"""Host logic of bench.py that the reported numbers rest on, checked on CPU.
+
+* The M2L translation count of a uniform tree (the unit of the roofline's
+  algorithmic FLOP figure) against a brute-force enumeration of the
+  interaction lists: target t and source s of the same level interact when
+  their parents are adjacent and they are not (Sec. 4.1, List 2).
+* The parser of the committed ncu summary that supplies the roofline's
+  traffic figure, and its refusal to report a figure for changed sources.
+* The leaf key (boxes lexicographic, x fastest).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def brute_force_m2l(d, L):
+    """(count, largest list) by enumerating every (target, source) pair per level."""
+    total, longest = 0, 0
+    for l in range(2, L + 1):
+        n = 1 << l
+        boxes = list(itertools.product(range(n), repeat=d))
+        for t in boxes:
+            k = 0
+            for s in boxes:
+                par_adj = all(abs((a >> 1) - (b >> 1)) <= 1 for a, b in zip(t, s))
+                adj = all(abs(a - b) <= 1 for a, b in zip(t, s))
+                if par_adj and not adj:
+                    k += 1
+            total += k
+            longest = max(longest, k)
+    return total, longest
+
+
+@pytest.mark.parametrize("d,L", [(2, 3), (2, 5), (3, 3)])
+def test_m2l_count_matches_enumeration(d, L):
+    total, longest = brute_force_m2l(d, L)
+    assert bench.m2l_count(d, L) == total
+    # an interior box's list: 6^d children of the parent's neighbours minus 3^d
+    assert longest == 6 ** d - 3 ** d
+
+
+def test_m2l_count_level_two_closed_form():
+    # at level 2 every pair of parents is adjacent: all n^2 pairs per axis minus
+    # the 3n - 2 adjacent ones, n = 4, raised to the dimension
+    for d in (2, 3):
+        assert bench.m2l_count(d, 2) == 16 ** d - 10 ** d
+    per_level = [bench.m2l_count(3, L) - bench.m2l_count(3, L - 1) for L in range(3, 6)]
+    assert per_level == sorted(per_level)
+
+
+def test_traffic_figure_only_for_the_captured_sources(monkeypatch):
+    path_hash = None
+    with open(bench.os.path.join(bench.ROOT, "profiles", "m2l_tc_laplace3d_p10_L5.md")) as fh:
+        for line in fh:
+            f = line.strip().strip("`").split()
+            if len(f) == 5 and f[0] == "traffic:" and f[1] == "tf32x3":
+                path_hash, want = f[4], int(f[2])
+    assert path_hash is not None
+    monkeypatch.setattr(bench, "m2l_source_hash", lambda: path_hash)
+    got, src = bench.profiled_traffic("tf32x3")
+    assert got == want and "ncu" in src
+    monkeypatch.setattr(bench, "m2l_source_hash", lambda: "0" * 16)
+    got, src = bench.profiled_traffic("tf32x3")
+    assert got is None and "changed" in src
+    got, src = bench.profiled_traffic("no-such-precision")
+    assert got is None
+
+
+def test_leaf_key_is_lexicographic_x_fastest():
+    L = 2
+    x = np.array([[0.1, 0.1, 0.1], [0.3, 0.1, 0.1], [0.1, 0.3, 0.1], [0.1, 0.1, 0.3],
+                  [0.99, 0.99, 0.99]])
+    assert bench.leaf_of(x, L).tolist() == [0, 1, 4, 16, 63]
