@@ -489,14 +489,15 @@ def run_reference(args, wl, rank):
     times, n_t, cores, what = [], 0, 1, ""
     args.cpu_leaves = max(4, args.cpu_leaves // 4)
     args.cpu_targets = max(2, args.cpu_targets // 4)
-    # every oracle step repeats the whole upward pass (seconds), so the run
-    # stops after the time budget even if fewer than --steps steps were timed
+    # every oracle step repeats the whole upward pass (seconds): the --warmup
+    # steps run as asked, and the timed steps stop after the time budget even
+    # if fewer than --steps were timed
     budget_s, spent = 150.0, 0.0
-    warm = min(max(args.warmup, 0), 1)
+    warm = max(args.warmup, 0)
     for k in range(warm + args.steps):
         idx, ref, dt, cores, what = run_cpu_oracle(wl, p, src, w, tgt, args, seed=777 + k)
-        spent += dt
         if k >= warm:
+            spent += dt
             times.append(dt)
             n_t += len(idx)
             if spent > budget_s:
