@@ -150,14 +150,26 @@ M2L_SOURCES = ["paper_2305_17867_gb300/csrc/m2l_tc.cu", "paper_2305_17867_gb300/
                "paper_2305_17867_gb300/csrc/m2l_simt.cu"]
 
 
-def m2l_source_hash() -> str:
+def code_digest(texts) -> str:
+    """Hash of source texts with // comments, trailing blanks and empty lines
+    removed, so that editing a comment does not void a capture of the code."""
     import hashlib
 
     h = hashlib.sha256()
-    for f in M2L_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+    for text in texts:
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
+
+
+def m2l_source_hash() -> str:
+    texts = []
+    for f in M2L_SOURCES:
+        with open(os.path.join(ROOT, f)) as fh:
+            texts.append(fh.read())
+    return code_digest(texts)
 
 
 def profiled_traffic(prec: str):

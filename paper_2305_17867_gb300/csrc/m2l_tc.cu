@@ -1,4 +1,4 @@
-// Tensor-core M2L (tcgen05, kind::tf32) -- eq. (m2l_toeplitz) grouped by
+// Tensor-core M2L (tcgen05, kind::tf32 / kind::f16) -- eq. (m2l_toeplitz) grouped by
 // translation offset into dense contractions on the fifth-generation tensor
 // cores, with the accumulator in TMEM.
 //
@@ -171,11 +171,12 @@ __global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const double* __
 // Warp roles: warps 0-15 drain TMEM (warp w reads TMEM lanes 32(w%4).. = rows
 // i, columns 64(w/4)..+63 = targets), warp 16 lane 0 issues TMA, warp 17 lane
 // 0 issues MMA.  Sixteen draining warps keep the running sums at 64 floats a
-// thread: 18 warps leave at most 5 per SM sub-partition, ~100 registers each.  The tensor cores truncate when they accumulate, so a long K
-// loop in one accumulator drifts; each offset's partial product therefore
-// goes to one of two 256-column TMEM buffers (the whole 512 columns), and the
-// draining warps add it into float registers (round-to-nearest) while the
-// MMA warp fills the other buffer.
+// thread: 18 warps leave at most 5 per SM sub-partition, ~100 registers each.
+// The tensor cores truncate when they accumulate, so a long K loop in one
+// accumulator drifts; each offset's partial product therefore goes to one of
+// two 256-column TMEM buffers (the whole 512 columns), and the draining warps
+// add it into float registers (round-to-nearest) while the MMA warp fills the
+// other buffer.
 constexpr int kEpiWarps = 16;
 constexpr int kNBuf = 2;
 constexpr int kBufCols = kMaxN;  // TMEM columns per accumulator buffer

@@ -74,3 +74,11 @@ def test_leaf_key_is_lexicographic_x_fastest():
     x = np.array([[0.1, 0.1, 0.1], [0.3, 0.1, 0.1], [0.1, 0.3, 0.1], [0.1, 0.1, 0.3],
                   [0.99, 0.99, 0.99]])
     assert bench.leaf_of(x, L).tolist() == [0, 1, 4, 16, 63]
+
+
+def test_code_digest_ignores_comments_only():
+    a = "int f() {  // returns one\n  return 1;\n}\n"
+    b = "// a new note\nint f() {  // returns 1\n\n  return 1;   \n}\n"
+    c = "int f() {\n  return 2;\n}\n"
+    assert bench.code_digest([a]) == bench.code_digest([b])
+    assert bench.code_digest([a]) != bench.code_digest([c])
