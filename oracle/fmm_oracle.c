@@ -13,7 +13,7 @@
  * below the 1e-12 parity bar at derivative orders up to 2p = 32.
  * Compile without -ffast-math: the sums below are meant to run as written.
  *
- * Readings of the paper used here (each is also listed in the design doc):
+ * Readings of the paper used here:
  *  R1  N(p) = C(p+d, d): the number of multi-indices of total order <= p
  *      (the binomial printed in eq. (np-count) drops the "+d").
  *  R2  Multipole basis: derivatives of G in its argument evaluated at x - c,

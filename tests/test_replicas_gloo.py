@@ -1,4 +1,4 @@
-"""The multi-rank bench path (replicas, SURVEY-style weak scaling) on CPU:
+"""The multi-rank bench path (independent replicas, weak scaling) on CPU:
 two gloo ranks, the step time is the slowest rank's and the throughput counts
 every rank's targets.  No GPU and no data-path collective is involved."""
 import os
