@@ -600,11 +600,8 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
         return cudaErrorInvalidValue;
     }
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-    attr = true;
-  }
+  // per call: the attribute belongs to the current device's context
+  cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   mark_contraction(P, 0, st);
   k_m2l_tc<F, NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
   mark_contraction(P, 1, st);
@@ -762,11 +759,7 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
     if (prm.nlev == kTcMaxLevels) break;
   }
   if (prm.nlev == 0) return cudaGetLastError();
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-    attr = true;
-  }
+  cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
   k_m2l_tc<F, NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
   ++*nl;
   return cudaGetLastError();
