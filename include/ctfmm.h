@@ -108,15 +108,17 @@ typedef struct {
   double lambda;       /* Yukawa screening; ignored otherwise */
   int d;               /* 2 or 3 */
   int p;               /* expansion order, 1..24 */
-  int levels;          /* > 0: leaf depth L of the uniform tree, 2..7 (root = 0);
-                          < 0: adaptive tree (3D; precision FP64 or FP32)
+  int levels;          /* > 0: leaf depth L of the uniform tree (root = 0), 2..7
+                          in 3D, 2..8 in 2D;
+                          < 0: adaptive tree (3D, any precision, dense M2L)
                           refined down to at most level -levels (1..10) */
   const fmm_pde* pde;  /* NULL: the kernel's own PDE */
   double root_lo[3];   /* lower corner of the root box */
   double root_size;    /* side of the root box; <= 0: bounding cube of the
                           sources and targets, found on the device per call */
   int precision;       /* FMM_PREC_* */
-  int m2l;             /* FMM_M2L_*; FFT requires precision FP64 or FP32 */
+  int m2l;             /* FMM_M2L_*; FFT requires precision FP64 or FP32 and a
+                          uniform tree; AUTO resolves to DENSE on adaptive trees */
   int max_leaf;        /* adaptive tree: a box holding more than max_leaf points
                           (sources plus targets) is split; ignored when levels > 0 */
 } fmm_plan_desc;
