@@ -64,7 +64,9 @@ enum { FMM_KERNEL_LAPLACE = 0, FMM_KERNEL_YUKAWA = 1, FMM_KERNEL_BIHARMONIC = 2 
 /* Arithmetic of the evaluation.
  *  FP64     every stage in float64 (the parity configuration).
  *  FP32     M2L as float32 SIMT products; P2M, L2P, P2P in float32; derivative
- *           tables, M2M and L2L in float64.
+ *           tables and the upper tree's M2M and L2L in float64 (the shifts
+ *           between the leaves and their parents in float32, since their input
+ *           or consumer is float32).
  *  TF32     as FP32 but M2L on the tensor cores (tcgen05 kind::tf32), one pass.
  *  TF32X3   M2L with split operands a = hi + lo in tf32, three tensor passes
  *           (hi*hi + hi*lo + lo*hi), float32 accumulation.
