@@ -1004,6 +1004,7 @@ typedef struct {
   int level, leaf;
   int64_t c[OR_MAXD];
   int64_t parent;
+  int64_t child0, nchild; /* children: boxes child0 .. child0+nchild-1, Morton order */
   int64_t s0, s1, t0, t1; /* ranges in the Morton-sorted source / target orders */
 } or_abox;
 
@@ -1110,6 +1111,7 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
     }
     const int shift = d * (D - bx[b].level - 1);
     int64_t si = bx[b].s0, ti = bx[b].t0;
+    bx[b].child0 = nbox;
     for (int ci = 0; ci < nch; ++ci) {
       int64_t s0 = si, t0 = ti;
       while (si < bx[b].s1 && (int)((ss[si].key >> shift) & (uint64_t)(nch - 1)) == ci) ++si;
@@ -1130,6 +1132,7 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
       ch->t1 = ti;
       if (ch->level > maxlev) maxlev = ch->level;
     }
+    bx[b].nchild = nbox - bx[b].child0;
   }
   /* leaf of every sorted target position */
   int64_t* tleaf = (int64_t*)malloc(sizeof(int64_t) * (ntgt > 0 ? ntgt : 1));
@@ -1172,20 +1175,22 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
     free(ys);
     free(ws);
   }
-  /* M2M, deepest level first (Sec. 4.3); a parent sums its children */
+  /* M2M, deepest level first (Sec. 4.3): every parent of level l-1 adds the
+   * translated multipoles of its children in Morton order, so the sum runs in
+   * the same order whatever the number of threads */
   for (int l = maxlev; l >= 3; --l) {
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t b = 0; b < nbox; ++b) {
-      if (bx[b].level != l) continue;
-      int64_t pb = bx[b].parent;
+    for (int64_t pb = 0; pb < nbox; ++pb) {
+      if (bx[pb].level != l - 1 || bx[pb].leaf) continue;
       double cp[OR_MAXD], cb[OR_MAXD], h[OR_MAXD];
       or_abox_center(d, lo, size, &bx[pb], cp);
-      or_abox_center(d, lo, size, &bx[b], cb);
-      for (int k = 0; k < d; ++k) h[k] = cp[k] - cb[k];
       double* psi = (double*)malloc(sizeof(double) * nj);
-      or_m2m(e, h, mp + (size_t)b * nj, psi);
-#pragma omp critical
-      for (int t = 0; t < nj; ++t) mp[(size_t)pb * nj + t] += psi[t];
+      for (int64_t b = bx[pb].child0; b < bx[pb].child0 + bx[pb].nchild; ++b) {
+        or_abox_center(d, lo, size, &bx[b], cb);
+        for (int k = 0; k < d; ++k) h[k] = cp[k] - cb[k];
+        or_m2m(e, h, mp + (size_t)b * nj, psi);
+        for (int t = 0; t < nj; ++t) mp[(size_t)pb * nj + t] += psi[t];
+      }
       free(psi);
     }
   }

@@ -100,3 +100,21 @@ def test_point_outside_root_is_rejected(oracle):
     src = np.array([[0.5, 0.5, 0.5], [1.5, 0.2, 0.2]])
     with pytest.raises(ValueError):
         oracle.fmm_adaptive("laplace", 3, 2, src, np.ones(2), src, max_leaf=1)
+
+
+def test_repeatable_across_thread_counts(oracle):
+    """The oracle gives the same bits for the same input: the adaptive M2M adds
+    the children of a parent in Morton order whatever the thread count (Sec.
+    4.3; an order that followed thread timing once made two calls differ)."""
+    src, w, tgt = plummer_case(3000, 500)
+    old = oracle.num_threads()
+    try:
+        oracle.set_num_threads(8)
+        a = oracle.fmm_adaptive("laplace", 3, 6, src, w, tgt, max_leaf=12)
+        b = oracle.fmm_adaptive("laplace", 3, 6, src, w, tgt, max_leaf=12)
+        oracle.set_num_threads(1)
+        c = oracle.fmm_adaptive("laplace", 3, 6, src, w, tgt, max_leaf=12)
+    finally:
+        oracle.set_num_threads(old)
+    assert np.array_equal(a, b)
+    assert np.array_equal(a, c)
