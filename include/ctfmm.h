@@ -5,8 +5,9 @@
  * Translation Operators for the Fast Multipole Method" (arXiv 2305.17867).
  * The library evaluates the many-body potential of eq. (1),
  *     phi(x) = sum_{y in S, y != x} G(x - y) w(y),   x in T,
- * with a uniform-tree Taylor FMM whose expansions are stored compressed by
- * the PDE that G satisfies (Sec. 3): only the multi-indices j = {m in M(p):
+ * with a Taylor FMM on a uniform or an adaptive tree whose expansions are
+ * stored compressed by the PDE that G satisfies (Sec. 3): only the
+ * multi-indices j = {m in M(p):
  * m_d < c} are kept (Lemma 5, last axis slowest), derivatives of G come from
  * r^2-led recurrences (Sec. 4.4), and every stage -- tree build, P2M, M2M,
  * M2L, L2L, L2P, P2P -- runs as CUDA kernels on the caller's stream.
@@ -52,7 +53,9 @@ typedef enum {
   FMM_ERR_NOMEM = -4,        /* plan tables could not be allocated */
   FMM_ERR_TIMEOUT = -5,      /* a bounded device wait gave up */
   FMM_ERR_DOMAIN = -6,       /* a point lay outside the root box (it was clamped) */
-  FMM_ERR_WORKSPACE = -7     /* workspace too small */
+  FMM_ERR_WORKSPACE = -7,    /* workspace too small */
+  FMM_ERR_INCOMPLETE = -8    /* a fixed-size device structure overflowed: the result
+                                is incomplete (reported by fmm_last_status) */
 } fmm_status;
 
 /* Kernels G (reading of the paper's normalisations):
@@ -145,7 +148,9 @@ int fmm_workspace_size(fmm_plan_t plan, int64_t n_src, int64_t n_tgt, size_t* by
 /* Evaluate phi (and, if grad_dev != NULL, grad phi) at the targets.
  * Adaptive plans (levels < 0) build the tree on the device level by level
  * and synchronise `stream` once per level to size the next one (so the call
- * returns after the tree is built); they compute phi only (grad_dev must be
+ * returns after the tree is built, and it cannot be captured into a CUDA
+ * graph: made while `stream` is capturing, it returns FMM_ERR_UNSUPPORTED
+ * before any work is enqueued); they compute phi only (grad_dev must be
  * NULL, else FMM_ERR_UNSUPPORTED) and return FMM_ERR_WORKSPACE if the tree
  * outgrows the workspace (it cannot when the workspace has the size
  * fmm_workspace_size reports, which bounds the number of boxes).
@@ -193,6 +198,10 @@ int fmm_eval_backward(fmm_plan_t plan, int64_t n_src, const double* src_dev,
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
  *    before any stream capture begins.
+ *  - Adaptive plans read level sizes back to the host while they build the
+ *    tree (see fmm_eval), so they cannot run under stream capture: such a call
+ *    returns FMM_ERR_UNSUPPORTED.
+ *  - phi_dev must not be NULL when n_tgt > 0 (FMM_ERR_ARG, as for fmm_eval).
  *  - Every call on a device shares the one array and it keeps the previous
  *    call's contents (the evaluation clears what must start at zero itself).
  *    Calls whose GPU work overlaps -- different streams, or different plans
@@ -202,7 +211,9 @@ int fmm_eval_noalloc(fmm_plan_t plan, int64_t n_src, const double* src_dev, cons
                      void* stream);
 
 /* Synchronise the stream of the last evaluation and return its device-side
- * status (FMM_OK, FMM_ERR_DOMAIN, FMM_ERR_TIMEOUT) or a CUDA error. */
+ * status or a CUDA error.  Precedence: FMM_ERR_TIMEOUT (a bounded device wait
+ * gave up), FMM_ERR_INCOMPLETE (an adaptive traversal stack overflowed, or any
+ * status bit this version does not know), FMM_ERR_DOMAIN, FMM_OK. */
 int fmm_last_status(fmm_plan_t plan);
 
 /* Per-phase timings (milliseconds, CUDA events) of the last evaluation when

@@ -14,6 +14,7 @@ FMM_OK = 0
 STATUS = {
     0: "ok", -1: "invalid argument", -2: "unsupported", -3: "CUDA error", -4: "out of memory",
     -5: "device wait timeout", -6: "point outside the root box", -7: "workspace too small",
+    -8: "device structure overflowed (incomplete result)",
 }
 KERNELS = {"laplace": 0, "yukawa": 1, "biharmonic": 2}
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4}

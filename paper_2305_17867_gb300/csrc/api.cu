@@ -612,6 +612,11 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
   };
   if (P->desc.levels < 0) {
     if (grad) return FMM_ERR_UNSUPPORTED;
+    {  // the adaptive build reads level sizes back to the host: not capturable
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FMM_ERR_CUDA;
+      if (cs != cudaStreamCaptureStatusNone) return FMM_ERR_UNSUPPORTED;
+    }
     mark(0);
     if ((e = launch_set_geom(P, ws, n_src, src, n_tgt, tgt, st, &nl)) != cudaSuccess) return FMM_ERR_CUDA;
     ATree tree;
@@ -768,6 +773,7 @@ extern "C" int fmm_last_status(fmm_plan_t P) {
   if (cudaMemcpy(&g, P->last_geom, sizeof(Geom), cudaMemcpyDeviceToHost) != cudaSuccess)
     return FMM_ERR_CUDA;
   if (g.flag & 2) return FMM_ERR_TIMEOUT;
+  if (g.flag & ~3) return FMM_ERR_INCOMPLETE;  // bit 4 (traversal stack) or any unknown bit
   if (g.flag & 1) return FMM_ERR_DOMAIN;
   return FMM_OK;
 }
@@ -782,6 +788,7 @@ extern "C" const char* fmm_status_string(int s) {
     case FMM_ERR_TIMEOUT: return "bounded device wait gave up";
     case FMM_ERR_DOMAIN: return "point outside the root box (clamped)";
     case FMM_ERR_WORKSPACE: return "workspace too small";
+    case FMM_ERR_INCOMPLETE: return "a fixed-size device structure overflowed (result incomplete)";
     default: return "unknown status";
   }
 }

@@ -30,7 +30,7 @@ struct Geom {
   double size;
   double s_leaf;      // size / 2^L
   double inv_s_leaf;  // 1 / s_leaf
-  int flag;  // device-side status bits (1: domain, 2: timeout)
+  int flag;  // device-side status bits (1: domain, 2: timeout, 4: traversal stack full)
   int pad;
   unsigned long long m2l_count;  // adaptive trees: M2L translations performed
 };

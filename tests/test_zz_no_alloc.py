@@ -62,3 +62,20 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     assert plan.workspace_bytes(n, n) > 32 << 20
     rc = L.fmm_eval_noalloc(plan._h, n, None, None, n, None, None, None, None)
     assert rc == -7  # FMM_ERR_WORKSPACE
+
+
+def test_noalloc_rejects_missing_output():
+    # the same argument check as fmm_eval: no launch is made, nothing is written
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_17867_gb300 import _lib
+    from paper_2305_17867_gb300.fmm import FMM
+
+    L = _lib.load()
+    for levels in (3, -4):  # uniform and adaptive plans
+        plan = FMM("laplace", d=3, p=4, levels=levels, precision="fp64")
+        s = torch.rand(100, 3, dtype=torch.float64, device="cuda")
+        w = torch.ones(100, dtype=torch.float64, device="cuda")
+        rc = L.fmm_eval_noalloc(plan._h, 100, _ptr(s), _ptr(w), 100, _ptr(s), None, None, None)
+        assert rc == -1  # FMM_ERR_ARG
