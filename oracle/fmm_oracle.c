@@ -49,7 +49,12 @@
 
 #define OR_MAXD 3
 
-enum { OR_LAPLACE = 0, OR_YUKAWA = 1, OR_BIHARMONIC = 2 };
+/* Helmholtz G = e^{i kappa r}/r (PDE Laplacian + kappa^2) is carried as its
+ * real and imaginary parts, cos(kappa r)/r and sin(kappa r)/r: both satisfy
+ * the same real PDE, so with real weights the multipoles, their compression
+ * and M2M are real and shared, and every later stage is linear in G.  The
+ * parameter lam is kappa for these two kernels. */
+enum { OR_LAPLACE = 0, OR_YUKAWA = 1, OR_BIHARMONIC = 2, OR_HELM_RE = 3, OR_HELM_IM = 4 };
 
 enum {
   OR_OK = 0,
@@ -125,7 +130,8 @@ static double or_mi_factorial(int d, const int* m) {
 /* Returns the PDE order c and fills acoef[N(c)] (caller gives >= N(4)). */
 int or_pde_for_kernel(int kernel, int d, double lam, double* acoef) {
   int m[OR_MAXD];
-  if (kernel == OR_LAPLACE || kernel == OR_YUKAWA) {
+  if (kernel == OR_LAPLACE || kernel == OR_YUKAWA || kernel == OR_HELM_RE ||
+      kernel == OR_HELM_IM) {
     int c = 2;
     int nc = or_num_terms(d, c);
     for (int i = 0; i < nc; ++i) acoef[i] = 0.0;
@@ -133,9 +139,10 @@ int or_pde_for_kernel(int kernel, int d, double lam, double* acoef) {
       for (int i = 0; i < d; ++i) m[i] = (i == k) ? 2 : 0;
       acoef[or_mi_index(d, m)] = 1.0;
     }
-    if (kernel == OR_YUKAWA) {
+    if (kernel != OR_LAPLACE) {
+      /* Yukawa: Laplacian - lambda^2; Helmholtz: Laplacian + kappa^2 */
       for (int i = 0; i < d; ++i) m[i] = 0;
-      acoef[or_mi_index(d, m)] = -lam * lam;
+      acoef[or_mi_index(d, m)] = kernel == OR_YUKAWA ? -lam * lam : lam * lam;
     }
     return c;
   }
@@ -310,12 +317,16 @@ typedef __float128 ld;
 #define LD_LOG logq
 #define LD_EXP expq
 #define LD_SQRT sqrtq
+#define LD_COS cosq
+#define LD_SIN sinq
 #define LDC(x) x##Q
 #else
 typedef long double ld;
 #define LD_LOG logl
 #define LD_EXP expl
 #define LD_SQRT sqrtl
+#define LD_COS cosl
+#define LD_SIN sinl
 #define LDC(x) x##L
 #endif
 
@@ -363,6 +374,43 @@ static void or_radial(int kernel, int d, double lam, ld r, int nmax, ld* F) {
     }
     free(cc);
     free(cn);
+  } else if ((kernel == OR_HELM_RE || kernel == OR_HELM_IM) && d == 3) {
+    /* G = e^{i kappa r}/r, F^(n) = e^{i kappa r} sum_k c[n][k] r^-k with
+       complex c: (1/r)d/dr [e^{i kappa r} r^-k] = e^{i kappa r} (i kappa r^-(k+1)
+       - k r^-(k+2)); the real or the imaginary part is kept. */
+    int kmax = 2 * nmax + 2;
+    ld* cr = (ld*)calloc((size_t)(kmax + 1), sizeof(ld));
+    ld* ci = (ld*)calloc((size_t)(kmax + 1), sizeof(ld));
+    ld* nr = (ld*)calloc((size_t)(kmax + 1), sizeof(ld));
+    ld* ni = (ld*)calloc((size_t)(kmax + 1), sizeof(ld));
+    cr[1] = LDC(1.0);
+    const ld kap = (ld)lam, rinv = LDC(1.0) / r;
+    const ld er = LD_COS(kap * r), ei = LD_SIN(kap * r);
+    for (int n = 0; n <= nmax; ++n) {
+      ld ar = LDC(0.0), ai = LDC(0.0), rp = LDC(1.0);
+      for (int k = 0; k <= kmax; ++k) {
+        ar += cr[k] * rp;
+        ai += ci[k] * rp;
+        rp *= rinv;
+      }
+      F[n] = kernel == OR_HELM_RE ? er * ar - ei * ai : er * ai + ei * ar;
+      for (int k = 0; k <= kmax; ++k) nr[k] = ni[k] = LDC(0.0);
+      for (int k = 0; k + 2 <= kmax; ++k) {
+        /* (i kappa) (cr + i ci) = -kappa ci + i kappa cr */
+        nr[k + 1] += -kap * ci[k];
+        ni[k + 1] += kap * cr[k];
+        nr[k + 2] += -(ld)k * cr[k];
+        ni[k + 2] += -(ld)k * ci[k];
+      }
+      for (int k = 0; k <= kmax; ++k) {
+        cr[k] = nr[k];
+        ci[k] = ni[k];
+      }
+    }
+    free(cr);
+    free(ci);
+    free(nr);
+    free(ni);
   } else if (kernel == OR_BIHARMONIC && d == 3) {
     /* G = r: F = r, then ((1/r)d/dr)^(n-1) r^-1 = (-1)^(n-1) (2n-3)!! r^-(2n-1) */
     ld rinv = LDC(1.0) / r, rinv2 = rinv * rinv;
@@ -454,6 +502,8 @@ static double or_green(int kernel, int d, double lam, const double* x) {
   double r = sqrt(r2);
   if (kernel == OR_LAPLACE) return d == 3 ? 1.0 / (4.0 * M_PI * r) : log(r);
   if (kernel == OR_YUKAWA) return exp(-lam * r) / r;
+  if (kernel == OR_HELM_RE) return cos(lam * r) / r;
+  if (kernel == OR_HELM_IM) return sin(lam * r) / r;
   if (kernel == OR_BIHARMONIC) return d == 3 ? r : r2 * log(r);
   return NAN;
 }
@@ -465,6 +515,8 @@ static void or_green_grad(int kernel, int d, double lam, const double* x,
   double r = sqrt(r2), f1 = NAN; /* F'(s) = (1/r) dG/dr */
   if (kernel == OR_LAPLACE) f1 = d == 3 ? -1.0 / (4.0 * M_PI * r * r2) : 1.0 / r2;
   if (kernel == OR_YUKAWA) f1 = exp(-lam * r) * (-lam / r2 - 1.0 / (r * r2));
+  if (kernel == OR_HELM_RE) f1 = -lam * sin(lam * r) / r2 - cos(lam * r) / (r * r2);
+  if (kernel == OR_HELM_IM) f1 = lam * cos(lam * r) / r2 - sin(lam * r) / (r * r2);
   if (kernel == OR_BIHARMONIC) f1 = d == 3 ? 1.0 / r : 2.0 * log(r) + 1.0;
   for (int k = 0; k < d; ++k) g[k] = x[k] * f1;
 }

@@ -23,8 +23,12 @@ _SO = os.path.join(_HERE, "_build", "libfmm_oracle.so")
 _LOCK = threading.Lock()
 _LIB = None
 
-LAPLACE, YUKAWA, BIHARMONIC = 0, 1, 2
-KERNELS = {"laplace": LAPLACE, "yukawa": YUKAWA, "biharmonic": BIHARMONIC}
+LAPLACE, YUKAWA, BIHARMONIC, HELM_RE, HELM_IM = 0, 1, 2, 3, 4
+# "helmholtz_re" / "helmholtz_im": cos(kappa r)/r and sin(kappa r)/r (lam = kappa),
+# the real and imaginary parts of the Helmholtz kernel e^{i kappa r}/r; the
+# complex "helmholtz" results below are composed from the two real FMMs.
+KERNELS = {"laplace": LAPLACE, "yukawa": YUKAWA, "biharmonic": BIHARMONIC,
+           "helmholtz_re": HELM_RE, "helmholtz_im": HELM_IM}
 
 
 def _quadlib():
@@ -222,7 +226,18 @@ def m2l_naive(d: int, p: int, D2, alpha):
     return out
 
 
+def _complex(fn, kernel, *args, **kw):
+    """Helmholtz as the real FMM of each part of G, composed re + i im."""
+    re = fn("helmholtz_re", *args, **kw)
+    im = fn("helmholtz_im", *args, **kw)
+    if isinstance(re, tuple):
+        return tuple(None if a is None else a + 1j * b for a, b in zip(re, im))
+    return re + 1j * im
+
+
 def derivatives(kernel: str, d: int, pmax: int, x, lam: float = 0.0) -> np.ndarray:
+    if kernel == "helmholtz":
+        return _complex(derivatives, kernel, d, pmax, x, lam)
     out = np.zeros(num_terms(d, pmax))
     rc = lib().or_derivatives(KERNELS[kernel], d, lam, pmax, _p(_f64(x)), _p(out))
     if rc != 0:
@@ -231,6 +246,8 @@ def derivatives(kernel: str, d: int, pmax: int, x, lam: float = 0.0) -> np.ndarr
 
 
 def derivatives_batch(kernel: str, d: int, pmax: int, x, lam: float = 0.0) -> np.ndarray:
+    if kernel == "helmholtz":
+        return _complex(derivatives_batch, kernel, d, pmax, x, lam)
     x = _f64(x).reshape(-1, d)
     out = np.zeros((x.shape[0], num_terms(d, pmax)))
     rc = lib().or_derivatives_batch(KERNELS[kernel], d, lam, pmax, x.shape[0], _p(x), _p(out))
@@ -240,6 +257,8 @@ def derivatives_batch(kernel: str, d: int, pmax: int, x, lam: float = 0.0) -> np
 
 
 def direct(kernel: str, d: int, src, w, tgt, lam: float = 0.0, grad: bool = False):
+    if kernel == "helmholtz":
+        return _complex(direct, kernel, d, src, w, tgt, lam=lam, grad=grad)
     src, w, tgt = _f64(src), _f64(w), _f64(tgt)
     nt = tgt.shape[0]
     phi = np.zeros(nt)
@@ -253,6 +272,8 @@ def fmm_uniform(kernel: str, d: int, p: int, L: int, src, w, tgt, lo=None,
                 size: float = 1.0, lam: float = 0.0, compressed: bool = True,
                 sample=None, grad: bool = False):
     """Uniform-tree FMM; with ``sample`` only those target indices are evaluated."""
+    if kernel == "helmholtz":
+        return _complex(fmm_uniform, kernel, d, p, L, src, w, tgt, lo=lo, size=size, lam=lam, compressed=compressed, sample=sample, grad=grad)
     src, w, tgt = _f64(src), _f64(w), _f64(tgt)
     lo = _f64(np.zeros(d) if lo is None else lo)
     ns = 0 if sample is None else len(sample)
