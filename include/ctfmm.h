@@ -61,8 +61,17 @@ typedef enum {
 /* Kernels G (reading of the paper's normalisations):
  *  LAPLACE     d=2: log|x|            d=3: 1/(4 pi |x|)     PDE: Laplacian
  *  YUKAWA      d=3: exp(-lambda |x|)/|x|                    PDE: Laplacian - lambda^2
- *  BIHARMONIC  d=3: |x|                                     PDE: Laplacian^2          */
-enum { FMM_KERNEL_LAPLACE = 0, FMM_KERNEL_YUKAWA = 1, FMM_KERNEL_BIHARMONIC = 2 };
+ *  BIHARMONIC  d=2: |x|^2 log|x|     d=3: |x|              PDE: Laplacian^2
+ *  HELMHOLTZ   d=3: exp(i kappa |x|)/|x|, kappa = the `lambda` field
+ *                                                           PDE: Laplacian + kappa^2
+ * A Helmholtz potential is complex: phi_dev (and grad_dev) then hold complex
+ * values, real and imaginary parts interleaved (2 doubles per value). */
+enum {
+  FMM_KERNEL_LAPLACE = 0,
+  FMM_KERNEL_YUKAWA = 1,
+  FMM_KERNEL_BIHARMONIC = 2,
+  FMM_KERNEL_HELMHOLTZ = 3
+};
 
 /* Arithmetic of the evaluation.
  *  FP64     every stage in float64 (the parity configuration).
@@ -110,13 +119,14 @@ typedef struct {
 
 typedef struct {
   int kernel;          /* FMM_KERNEL_* */
-  double lambda;       /* Yukawa screening; ignored otherwise */
+  double lambda;       /* Yukawa screening lambda, or Helmholtz wavenumber kappa
+                          (> 0); ignored otherwise */
   int d;               /* 2 or 3 */
   int p;               /* expansion order, 1..24 */
   int levels;          /* > 0: leaf depth L of the uniform tree (root = 0), 2..7
                           in 3D, 2..8 in 2D;
-                          < 0: adaptive tree (3D, any precision, dense M2L)
-                          refined down to at most level -levels (1..10) */
+                          < 0: adaptive tree (3D, any precision, dense M2L, not
+                          Helmholtz) refined down to at most level -levels (1..10) */
   const fmm_pde* pde;  /* NULL: the kernel's own PDE */
   double root_lo[3];   /* lower corner of the root box */
   double root_size;    /* side of the root box; <= 0: bounding cube of the
@@ -160,12 +170,28 @@ int fmm_workspace_size(fmm_plan_t plan, int64_t n_src, int64_t n_tgt, size_t* by
  *   tgt_dev  n_tgt x d   target positions        (device, float64); may equal src_dev
  *   phi_dev  n_tgt       output potential        (device, float64, overwritten)
  *   grad_dev n_tgt x d   output gradient or NULL (device, float64, overwritten)
+ * For FMM_KERNEL_HELMHOLTZ the outputs are complex, (re, im) interleaved:
+ * phi_dev holds 2 n_tgt doubles and grad_dev n_tgt x d x 2.  The real and the
+ * imaginary part of G are evaluated as two real FMMs that share the tree, P2M
+ * and M2M (the multipoles are real), in one stream.
  * n_src or n_tgt may be 0.  Pairs with x == y exactly are skipped.  Points
  * outside the root box are clamped into it and flagged (FMM_ERR_DOMAIN from
  * fmm_last_status).  Asynchronous on `stream`. */
 int fmm_eval(fmm_plan_t plan, int64_t n_src, const double* src_dev, const double* w_dev,
              int64_t n_tgt, const double* tgt_dev, double* phi_dev, double* grad_dev,
              void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* fmm_eval for float32 callers: positions, weights, potentials and gradients
+ * are float32 device arrays with the same shapes as in fmm_eval (complex
+ * outputs of Helmholtz plans again interleaved).  The points are widened to
+ * float64 on the device first -- the tree, the leaf assignment and every
+ * stage then run exactly as for fmm_eval in the plan's precision -- and the
+ * results are rounded to float32 at the end.  The workspace must hold
+ * fmm_workspace_size_f32 bytes (the float64 copies come first). */
+int fmm_workspace_size_f32(fmm_plan_t plan, int64_t n_src, int64_t n_tgt, size_t* bytes);
+int fmm_eval_f32(fmm_plan_t plan, int64_t n_src, const float* src_dev, const float* w_dev,
+                 int64_t n_tgt, const float* tgt_dev, float* phi_dev, float* grad_dev,
+                 void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* Reverse mode of loss = sum_i u_i phi(x_i) (no counterpart in the paper):
  *   grad_w_dev   n_src       d loss/d w_j  = sum_i u_i G(x_i - y_j)      (or NULL)
@@ -177,7 +203,8 @@ int fmm_eval(fmm_plan_t plan, int64_t n_src, const double* src_dev, const double
  * grad_tgt is formed from it, otherwise a second FMM evaluates grad phi.
  * Same buffer conventions as fmm_eval; the workspace must be sized with
  * fmm_workspace_size(plan, max(n_src, n_tgt), max(n_src, n_tgt)).  Uniform
- * plans only (FMM_ERR_UNSUPPORTED for adaptive plans). */
+ * plans of real kernels only (FMM_ERR_UNSUPPORTED for adaptive and Helmholtz
+ * plans). */
 int fmm_eval_backward(fmm_plan_t plan, int64_t n_src, const double* src_dev,
                       const double* w_dev, int64_t n_tgt, const double* tgt_dev,
                       const double* u_dev, const double* grad_phi_dev, double* grad_w_dev,
@@ -240,6 +267,34 @@ int fmm_m2l_kernel_time(fmm_plan_t plan, float* ms_out);
  * for adaptive plans the count is read from the device (synchronises the
  * evaluation's stream).  Any pointer may be NULL. */
 int fmm_last_tree(fmm_plan_t plan, int64_t* boxes_out, int* depth_out, int64_t* m2l_out);
+
+/* Testing aid (no counterpart in the paper): bound the waits of the
+ * tensor-core M2L's pipeline -- the TMA producer, the MMA issuer and the
+ * accumulator drain -- to `cycles` SM clock cycles instead of ~1 s; 0
+ * restores the default.  A wait that runs out raises the device status bit
+ * that fmm_last_status reports as FMM_ERR_TIMEOUT; the kernel then waits for
+ * its copies and MMAs in flight with the full limit, frees its tensor memory
+ * and returns, so the context stays usable and the next evaluation (with the
+ * limit restored) is unaffected. */
+int fmm_set_wait_limit(fmm_plan_t plan, long long cycles);
+
+/* Everything known about the last evaluation, in one record (synchronises
+ * its stream).  Timings and the near-field pair count are filled only when
+ * timing was enabled (fmm_set_timing) for that evaluation, else 0 / -1. */
+typedef struct {
+  float phase_ms[FMM_NUM_PHASES]; /* as fmm_phase_times */
+  float m2l_kernel_ms;            /* as fmm_m2l_kernel_time */
+  int64_t boxes;                  /* as fmm_last_tree */
+  int depth;
+  int64_t m2l_translations;
+  int64_t p2p_pairs;              /* source-target pairs of the near field of a
+                                     uniform tree (leaf and its 3^d - 1
+                                     neighbours, coinciding points included);
+                                     -1 when not counted */
+  int status;                     /* as fmm_last_status */
+  int launches;                   /* as fmm_last_launch_count */
+} fmm_stats;
+int fmm_last_stats(fmm_plan_t plan, fmm_stats* out);
 
 /* Number of kernel launches the last fmm_eval enqueued. */
 int fmm_last_launch_count(fmm_plan_t plan);

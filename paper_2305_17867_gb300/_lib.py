@@ -16,7 +16,7 @@ STATUS = {
     -5: "device wait timeout", -6: "point outside the root box", -7: "workspace too small",
     -8: "device structure overflowed (incomplete result)",
 }
-KERNELS = {"laplace": 0, "yukawa": 1, "biharmonic": 2}
+KERNELS = {"laplace": 0, "yukawa": 1, "biharmonic": 2, "helmholtz": 3}
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4}
 M2L_PATHS = {"dense": 0, "fft": 1, "auto": 2}
 NUM_PHASES = 7
@@ -34,6 +34,13 @@ class Pde(ctypes.Structure):
                 ("coeff", ctypes.POINTER(ctypes.c_double))]
 
 
+class Stats(ctypes.Structure):
+    _fields_ = [("phase_ms", ctypes.c_float * 7), ("m2l_kernel_ms", ctypes.c_float),
+                ("boxes", ctypes.c_int64), ("depth", ctypes.c_int),
+                ("m2l_translations", ctypes.c_int64), ("p2p_pairs", ctypes.c_int64),
+                ("status", ctypes.c_int), ("launches", ctypes.c_int)]
+
+
 class PlanDesc(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("lam", ctypes.c_double), ("d", ctypes.c_int),
                 ("p", ctypes.c_int), ("levels", ctypes.c_int), ("pde", ctypes.POINTER(Pde)),
@@ -48,7 +55,8 @@ EXPORTS = [
     "fmm_plan_create", "fmm_plan_destroy", "fmm_plan_info", "fmm_workspace_size", "fmm_eval",
     "fmm_eval_backward", "fmm_last_status", "fmm_set_timing", "fmm_phase_times",
     "fmm_last_launch_count", "fmm_status_string", "fmm_eval_noalloc", "fmm_m2l_kernel_time",
-    "fmm_last_tree",
+    "fmm_last_tree", "fmm_set_wait_limit", "fmm_last_stats", "fmm_eval_f32",
+    "fmm_workspace_size_f32",
 ]
 
 
@@ -76,6 +84,10 @@ def load(build: bool = True):
     L.fmm_workspace_size.restype = i32
     L.fmm_eval.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp, sz, vp]
     L.fmm_eval.restype = i32
+    L.fmm_eval_f32.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp, sz, vp]
+    L.fmm_eval_f32.restype = i32
+    L.fmm_workspace_size_f32.argtypes = [vp, i64, i64, ctypes.POINTER(sz)]
+    L.fmm_workspace_size_f32.restype = i32
     L.fmm_eval_backward.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.fmm_eval_backward.restype = i32
     L.fmm_eval_noalloc.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp]
@@ -90,6 +102,10 @@ def load(build: bool = True):
     L.fmm_m2l_kernel_time.restype = i32
     L.fmm_last_tree.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i64)]
     L.fmm_last_tree.restype = i32
+    L.fmm_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.fmm_last_stats.restype = i32
+    L.fmm_set_wait_limit.argtypes = [vp, ctypes.c_longlong]
+    L.fmm_set_wait_limit.restype = i32
     L.fmm_last_launch_count.argtypes = [vp]
     L.fmm_last_launch_count.restype = i32
     L.fmm_status_string.argtypes = [i32]

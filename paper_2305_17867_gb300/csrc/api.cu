@@ -82,9 +82,11 @@ std::map<Key, double> default_pde(int kernel, int d, double lam) {
     m[k] = 2;
     return m;
   };
-  if (kernel == FMM_KERNEL_LAPLACE || kernel == FMM_KERNEL_YUKAWA) {
+  if (kernel == FMM_KERNEL_LAPLACE || kernel == FMM_KERNEL_YUKAWA ||
+      kernel == FMM_KERNEL_HELMHOLTZ) {
     for (int k = 0; k < d; ++k) a[e2(k)] += 1.0;
     if (kernel == FMM_KERNEL_YUKAWA) a[Key{0, 0, 0}] += -lam * lam;
+    if (kernel == FMM_KERNEL_HELMHOLTZ) a[Key{0, 0, 0}] += lam * lam;  // kappa = lam
   } else if (kernel == FMM_KERNEL_BIHARMONIC) {
     for (int k = 0; k < d; ++k)
       for (int l = 0; l < d; ++l) {
@@ -157,12 +159,12 @@ static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t
   w.bbox = carve<double>(cur, (size_t)2 * 3 * 2 * w.nbbox_blocks);
   const int prec = P->desc.precision;
   if (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3) {
-    const int esz = prec == FMM_PREC_BF16X3 ? 2 : 4;
-    const int row = 128 / esz;
-    w.tc_jp = (nj + row - 1) / row * row;
-    w.tc_mp = (nj + 127) / 128 * 128;
+    const TcShape tcs = tc_shape(nj, prec);
+    const int esz = tcs.esz;
+    w.tc_jp = tcs.jp;
+    w.tc_mp = tcs.npt;
     const int halves = prec == FMM_PREC_TF32 ? 1 : 2;
-    const int tlev = P->pd.kernel == FMM_KERNEL_YUKAWA ? std::max(D - 1, 1) : 1;
+    const int tlev = kernel_homogeneous(P->pd.kernel) ? 1 : std::max(D - 1, 1);
     for (int h = 0; h < halves; ++h)
       w.tc_tmat[h] = carve<char>(cur, (size_t)tlev * 343 * w.tc_mp * w.tc_jp * esz);
     // window cells: as many as the bound on boxes (levels the arena cannot
@@ -220,18 +222,24 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
     w.txr = carve<float4>(cur, std::max<int64_t>(n_tgt, 1));
   }
   if (d == 3 && (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3)) {
-    const int esz = prec == FMM_PREC_BF16X3 ? 2 : 4;  // bytes per operand element
-    const int row = 128 / esz;                         // elements per 128-byte K chunk
-    w.tc_jp = (nj + row - 1) / row * row;
-    w.tc_mp = (nj + 127) / 128 * 128;
+    const TcShape tcs = tc_shape(nj, prec);
+    const int esz = tcs.esz;  // bytes per operand element
+    w.tc_jp = tcs.jp;
+    w.tc_mp = tcs.npt;
     const int halves = prec == FMM_PREC_TF32 ? 1 : 2;
     // homogeneous kernels (3D Laplace, biharmonic) share one set of offset
     // matrices across levels (exact power-of-two scale per level)
-    const int tlev = (P->pd.kernel == FMM_KERNEL_YUKAWA) ? (L - 1) : 1;
+    const int tlev = kernel_homogeneous(P->pd.kernel) ? 1 : (L - 1);
     for (int h = 0; h < halves; ++h) {
       w.tc_bpar[h] = carve<char>(cur, (size_t)off * w.tc_jp * esz);
       w.tc_tmat[h] = carve<char>(cur, (size_t)tlev * 343 * w.tc_mp * w.tc_jp * esz);
     }
+  }
+  if (P->pd.kernel == FMM_KERNEL_HELMHOLTZ) {
+    // the real and imaginary parts' potentials (and gradients) before they are
+    // interleaved into the caller's complex output
+    w.hphi = carve<double>(cur, (size_t)2 * std::max<int64_t>(n_tgt, 1));
+    w.hgrad = carve<double>(cur, (size_t)2 * d * std::max<int64_t>(n_tgt, 1));
   }
   if (P->desc.m2l == FMM_M2L_FFT) {
     const size_t csz = prec == FMM_PREC_FP64 ? 16 : 8;  // complex double / float
@@ -248,6 +256,10 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
 // ---------------------------------------------------------------------------
 // Plan
 // ---------------------------------------------------------------------------
+// residual of a PDE on the kernel's derivatives (expansions.cu)
+double pde_residual(const PlanDev& pd, const std::vector<int>& hrow_host, int nterm,
+                    const int* xi, const double* a);
+
 extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   if (!out) return FMM_ERR_ARG;
   *out = nullptr;
@@ -268,13 +280,15 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
       desc->precision != FMM_PREC_FP32)
     return FMM_ERR_UNSUPPORTED;
   const int kernel = desc->kernel;
-  if (kernel == FMM_KERNEL_LAPLACE) {
-  } else if (kernel == FMM_KERNEL_YUKAWA || kernel == FMM_KERNEL_BIHARMONIC) {
+  if (kernel == FMM_KERNEL_LAPLACE || kernel == FMM_KERNEL_BIHARMONIC) {
+  } else if (kernel == FMM_KERNEL_YUKAWA || kernel == FMM_KERNEL_HELMHOLTZ) {
     if (d != 3) return FMM_ERR_UNSUPPORTED;
   } else {
     return FMM_ERR_ARG;
   }
-  if (kernel == FMM_KERNEL_YUKAWA && !(desc->lambda > 0.0)) return FMM_ERR_ARG;
+  if ((kernel == FMM_KERNEL_YUKAWA || kernel == FMM_KERNEL_HELMHOLTZ) && !(desc->lambda > 0.0))
+    return FMM_ERR_ARG;
+  if (kernel == FMM_KERNEL_HELMHOLTZ && L < 0) return FMM_ERR_UNSUPPORTED;  // uniform trees
   for (int k = 0; k < d; ++k)
     if (!std::isfinite(desc->root_lo[k])) return FMM_ERR_ARG;
 
@@ -449,6 +463,32 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
       return FMM_ERR_CUDA;
     }
   }
+  if (desc->pde && c >= 2 && c <= p) {
+    // a user PDE must be satisfied by the kernel, or the compression of Sec. 3
+    // would discard information the potential needs (eq. (Pv))
+    std::vector<int> xi;
+    std::vector<double> av;
+    for (auto& kv : a) {
+      if (kv.second == 0.0) continue;
+      xi.insert(xi.end(), {kv.first[0], kv.first[1], kv.first[2]});
+      av.push_back(kv.second);
+    }
+    const int kinds = kernel == FMM_KERNEL_HELMHOLTZ ? 2 : 1;
+    for (int part = 0; part < kinds; ++part) {
+      PlanDev q = pd;
+      if (part == 1) q.kernel = kHelmIm;
+      const double res = pde_residual(q, hank.row, (int)av.size(), xi.data(), av.data());
+      if (res < 0.0 || res > 1e-10) {
+        cudaStreamDestroy(P->hi);
+        cudaStreamDestroy(P->aux);
+        for (cudaEvent_t e : {P->ev_in, P->ev_fork, P->ev_join, P->ev_out, P->ev_tab})
+          cudaEventDestroy(e);
+        cudaFree(dt);
+        delete P;
+        return res < 0.0 ? FMM_ERR_CUDA : FMM_ERR_UNSUPPORTED;
+      }
+    }
+  }
   P->desc = *desc;
   P->desc.pde = nullptr;
   if (desc->m2l == FMM_M2L_AUTO) {  // resolved once, by arithmetic (see ctfmm.h)
@@ -575,9 +615,127 @@ extern "C" int fmm_last_tree(fmm_plan_t P, int64_t* boxes, int* depth, int64_t* 
 
 extern "C" int fmm_last_launch_count(fmm_plan_t P) { return P ? P->launches : -1; }
 
+// near-field pairs of a uniform tree: per target leaf, its targets times the
+// sources of the 3^d leaves around it (the leaf included)
+template <int D>
+__global__ void k_count_pairs(int L, const int* __restrict__ sstart, const int* __restrict__ tstart,
+                              unsigned long long* out) {
+  const int64_t nl = (int64_t)1 << L, nleaf = (int64_t)1 << (D * L);
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long v = 0;
+  if (b < nleaf) {
+    const int64_t x = b % nl, y = D == 3 ? (b / nl) % nl : b / nl, z = D == 3 ? b / (nl * nl) : 0;
+    int64_t ns = 0;
+    for (int64_t dz = (D == 3 ? -1 : 0); dz <= (D == 3 ? 1 : 0); ++dz)
+      for (int64_t dy = -1; dy <= 1; ++dy)
+        for (int64_t dx = -1; dx <= 1; ++dx) {
+          const int64_t X = x + dx, Y = y + dy, Z = z + dz;
+          if (X < 0 || Y < 0 || Z < 0 || X >= nl || Y >= nl || Z >= nl) continue;
+          const int64_t n = (Z * nl + Y) * nl + X;
+          ns += sstart[n + 1] - sstart[n];
+        }
+    v = (unsigned long long)(tstart[b + 1] - tstart[b]) * (unsigned long long)ns;
+  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
+extern "C" int fmm_last_stats(fmm_plan_t P, fmm_stats* out) {
+  if (!P || !out) return FMM_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->p2p_pairs = -1;
+  if (P->timing && P->events_made && P->last_geom) {
+    if (fmm_phase_times(P, out->phase_ms) != FMM_OK) return FMM_ERR_CUDA;
+    if (fmm_m2l_kernel_time(P, &out->m2l_kernel_ms) != FMM_OK) out->m2l_kernel_ms = 0.f;
+  }
+  int rc = fmm_last_tree(P, &out->boxes, &out->depth, &out->m2l_translations);
+  if (rc != FMM_OK) return rc;
+  out->status = fmm_last_status(P);
+  out->launches = P->launches;
+  if (P->timing && P->last_geom && P->desc.levels > 0 && P->pd.kernel != FMM_KERNEL_HELMHOLTZ) {
+    Geom g;
+    if (cudaMemcpy(&g, P->last_geom, sizeof(Geom), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return FMM_ERR_CUDA;
+    out->p2p_pairs = (int64_t)g.p2p_pairs;
+  }
+  return FMM_OK;
+}
+
+extern "C" int fmm_set_wait_limit(fmm_plan_t P, long long cycles) {
+  if (!P || cycles < 0) return FMM_ERR_ARG;
+  P->tc_wait_cycles = cycles;
+  return FMM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Evaluation
 // ---------------------------------------------------------------------------
+// interleave the real and imaginary parts' results into complex output
+__global__ void k_interleave(int64_t n, const double* __restrict__ re,
+                             const double* __restrict__ im, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    out[2 * i] = re[i];
+    out[2 * i + 1] = im[i];
+  }
+}
+
+// Helmholtz (G = e^{i kappa r}/r): real weights give real multipoles, and the
+// PDE Laplacian + kappa^2 has real coefficients, so the tree, P2M and M2M are
+// shared; the derivative tables, M2L, L2L and the leaf pass run once with the
+// real part cos(kappa r)/r and once with the imaginary part sin(kappa r)/r
+// (every stage after M2M is linear in G).  One stream; phases 4..6 of the
+// timing hold both parts.
+static int eval_helmholtz(fmm_plan_t P, const Workspace& ws, int64_t n_src, const double* src,
+                          const double* w, int64_t n_tgt, const double* tgt, double* phi,
+                          double* grad, cudaStream_t st, bool first) {
+  int nl = 0;
+  auto mark = [&](int i) {
+    if (P->timing) cudaEventRecord(P->ev[i], st);
+  };
+  mark(0);
+  if (launch_set_geom(P, ws, n_src, src, n_tgt, tgt, st, &nl) != cudaSuccess) return FMM_ERR_CUDA;
+  if (launch_build_tree(P, ws, n_src, src, w, n_tgt, tgt, st, &nl) != cudaSuccess)
+    return FMM_ERR_CUDA;
+  mark(1);
+  mark(2);
+  if (launch_p2m(P, ws, st, &nl) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(3);
+  if (launch_m2m(P, ws, st, &nl) != cudaSuccess) return FMM_ERR_CUDA;
+  mark(4);
+  const int d = P->pd.d;
+  for (int part = 0; part < 2; ++part) {
+    fmm_plan_s Q = *P;
+    Q.pd.kernel = part == 0 ? FMM_KERNEL_HELMHOLTZ : kHelmIm;
+    double* ph = n_tgt > 0 ? ws.hphi + part * n_tgt : nullptr;
+    double* gr = grad ? ws.hgrad + (size_t)part * d * n_tgt : nullptr;
+    if (launch_deriv_tables(&Q, ws, st, &nl) != cudaSuccess) return FMM_ERR_CUDA;
+    if (launch_m2l(&Q, ws, st, &nl, false) != cudaSuccess) return FMM_ERR_CUDA;
+    if (launch_l2l(&Q, ws, st, &nl) != cudaSuccess) return FMM_ERR_CUDA;
+    if (n_tgt > 0 && launch_leaf_eval(&Q, ws, ph, gr, st, &nl) != cudaSuccess)
+      return FMM_ERR_CUDA;
+  }
+  mark(5);
+  mark(6);
+  if (n_tgt > 0) {
+    k_interleave<<<(unsigned)((n_tgt + 255) / 256), 256, 0, st>>>(n_tgt, ws.hphi,
+                                                                  ws.hphi + n_tgt, phi);
+    ++nl;
+    if (grad) {
+      const int64_t ng = n_tgt * d;
+      k_interleave<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(ng, ws.hgrad, ws.hgrad + ng,
+                                                                 grad);
+      ++nl;
+    }
+  }
+  mark(7);
+  if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
+  P->last_stream = st;
+  P->last_geom = ws.geom;
+  P->launches = first ? nl : P->launches + nl;
+  return FMM_OK;
+}
+
 static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const double* w,
                          int64_t n_tgt, const double* tgt, double* phi, double* grad,
                          void* workspace, size_t wbytes, cudaStream_t st, bool first) {
@@ -651,6 +809,8 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
     P->last_depth = tree.maxlev;
     return FMM_OK;
   }
+  if (P->pd.kernel == FMM_KERNEL_HELMHOLTZ)
+    return eval_helmholtz(P, ws, n_src, src, w, n_tgt, tgt, phi, grad, st, first);
   if (split && (cudaEventRecord(P->ev_in, st) != cudaSuccess ||
                 cudaStreamWaitEvent(run, P->ev_in, 0) != cudaSuccess))
     return FMM_ERR_CUDA;
@@ -689,6 +849,17 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
     return FMM_ERR_CUDA;
   }
   mark(7);
+  if (P->timing) {  // statistics: near-field pairs, after the timed phases
+    const int64_t nleaf = nbox_at(P->pd.d, P->desc.levels);
+    const unsigned nbk = (unsigned)((nleaf + 255) / 256);
+    if (P->pd.d == 3)
+      k_count_pairs<3><<<nbk, 256, 0, run>>>(P->desc.levels, ws.sstart, ws.tstart,
+                                             &ws.geom->p2p_pairs);
+    else
+      k_count_pairs<2><<<nbk, 256, 0, run>>>(P->desc.levels, ws.sstart, ws.tstart,
+                                             &ws.geom->p2p_pairs);
+    ++nl;
+  }
   if (split && (cudaEventRecord(P->ev_out, run) != cudaSuccess ||
                 cudaStreamWaitEvent(st, P->ev_out, 0) != cudaSuccess))
     return FMM_ERR_CUDA;
@@ -704,6 +875,96 @@ extern "C" int fmm_eval(fmm_plan_t P, int64_t n_src, const double* src, const do
   if (n_tgt > 0 && !phi) return FMM_ERR_ARG;
   return eval_internal(P, n_src, src, w, n_tgt, tgt, phi, grad, workspace, wbytes,
                        static_cast<cudaStream_t>(stream), true);
+}
+
+// ---- float32 entry: widen the inputs, evaluate, narrow the outputs ----------
+__global__ void k_widen(int64_t n, const float* __restrict__ in, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+__global__ void k_narrow(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+// float64 staging of an fmm_eval_f32 call (in front of the workspace proper)
+struct F32Stage {
+  size_t bytes;
+  size_t src, w, tgt, phi, grad;  // byte offsets
+};
+static F32Stage f32_stage(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt) {
+  const int d = P->pd.d;
+  const int cplx = P->pd.kernel == FMM_KERNEL_HELMHOLTZ ? 2 : 1;
+  F32Stage f{};
+  size_t o = 0;
+  f.src = o;
+  o += align_up(sizeof(double) * (size_t)std::max<int64_t>(n_src, 1) * d);
+  f.w = o;
+  o += align_up(sizeof(double) * (size_t)std::max<int64_t>(n_src, 1));
+  f.tgt = o;
+  o += align_up(sizeof(double) * (size_t)std::max<int64_t>(n_tgt, 1) * d);
+  f.phi = o;
+  o += align_up(sizeof(double) * (size_t)std::max<int64_t>(n_tgt, 1) * cplx);
+  f.grad = o;
+  o += align_up(sizeof(double) * (size_t)std::max<int64_t>(n_tgt, 1) * d * cplx);
+  f.bytes = o;
+  return f;
+}
+
+extern "C" int fmm_workspace_size_f32(fmm_plan_t P, int64_t n_src, int64_t n_tgt,
+                                      size_t* bytes) {
+  size_t b = 0;
+  const int rc = fmm_workspace_size(P, n_src, n_tgt, &b);
+  if (rc != FMM_OK) return rc;
+  *bytes = b + f32_stage(P, n_src, n_tgt).bytes;
+  return FMM_OK;
+}
+
+extern "C" int fmm_eval_f32(fmm_plan_t P, int64_t n_src, const float* src, const float* w,
+                            int64_t n_tgt, const float* tgt, float* phi, float* grad,
+                            void* workspace, size_t wbytes, void* stream) {
+  if (!P || n_src < 0 || n_tgt < 0) return FMM_ERR_ARG;
+  if (n_src > 0 && (!src || !w)) return FMM_ERR_ARG;
+  if (n_tgt > 0 && (!tgt || !phi)) return FMM_ERR_ARG;
+  if (!workspace || reinterpret_cast<uintptr_t>(workspace) % kAlign) return FMM_ERR_ARG;
+  if (n_src > INT32_MAX / 2 || n_tgt > INT32_MAX / 2) return FMM_ERR_ARG;
+  const F32Stage f = f32_stage(P, n_src, n_tgt);
+  if (wbytes < f.bytes) return FMM_ERR_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(workspace);
+  double* s64 = reinterpret_cast<double*>(base + f.src);
+  double* w64 = reinterpret_cast<double*>(base + f.w);
+  double* t64 = reinterpret_cast<double*>(base + f.tgt);
+  double* p64 = reinterpret_cast<double*>(base + f.phi);
+  double* g64 = grad ? reinterpret_cast<double*>(base + f.grad) : nullptr;
+  const int d = P->pd.d;
+  const int cplx = P->pd.kernel == FMM_KERNEL_HELMHOLTZ ? 2 : 1;
+  auto grid = [](int64_t n) { return (unsigned)((n + 255) / 256); };
+  int nl = 0;
+  if (n_src > 0) {
+    k_widen<<<grid(n_src * d), 256, 0, st>>>(n_src * d, src, s64);
+    k_widen<<<grid(n_src), 256, 0, st>>>(n_src, w, w64);
+    nl += 2;
+  }
+  const bool same = tgt == src && n_tgt == n_src;  // one copy, one sort (as in fmm_eval)
+  if (n_tgt > 0 && !same) {
+    k_widen<<<grid(n_tgt * d), 256, 0, st>>>(n_tgt * d, tgt, t64);
+    ++nl;
+  }
+  if (cudaGetLastError() != cudaSuccess) return FMM_ERR_CUDA;
+  const int rc = eval_internal(P, n_src, s64, w64, n_tgt, same ? s64 : t64, p64, g64,
+                               base + f.bytes, wbytes - f.bytes, st, true);
+  if (rc != FMM_OK) return rc;
+  if (n_tgt > 0) {
+    k_narrow<<<grid(n_tgt * cplx), 256, 0, st>>>(n_tgt * cplx, p64, phi);
+    ++nl;
+    if (grad) {
+      k_narrow<<<grid(n_tgt * d * cplx), 256, 0, st>>>(n_tgt * d * cplx, g64, grad);
+      ++nl;
+    }
+  }
+  P->launches += nl;
+  return cudaGetLastError() == cudaSuccess ? FMM_OK : FMM_ERR_CUDA;
 }
 
 __global__ void k_scale_rows(int64_t n, int d, const double* s, double* g) {
@@ -723,7 +984,7 @@ extern "C" int fmm_eval_backward(fmm_plan_t P, int64_t n_src, const double* src,
                                  double* grad_src, double* grad_tgt, void* workspace,
                                  size_t wbytes, void* stream) {
   if (!P) return FMM_ERR_ARG;
-  if (P->desc.levels < 0) return FMM_ERR_UNSUPPORTED;
+  if (P->desc.levels < 0 || P->pd.kernel == FMM_KERNEL_HELMHOLTZ) return FMM_ERR_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int d = P->pd.d;
   int rc = FMM_OK;

@@ -1,5 +1,7 @@
 // Derivative tables (Sec. 4.4), P2M (Sec. 3.4), M2M (Sec. 4.3), L2L (Sec. 4.2).
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "adaptive.cuh"
 #include "expansions.cuh"
@@ -23,8 +25,14 @@ void set_smem(K kernel, size_t bytes) {
 // rule to an identity r^2 d_a g = (...):
 //   g = r^nu (3D Laplace nu=-1, 3D biharmonic nu=+1):  r^2 d_a g = nu x_a g
 //   g = log r (2D Laplace, eq. (deriv_laplace_2d)):      r^2 d_a g = x_a
+//   g = r^2 log r (2D biharmonic):                       r^2 d_a g = 2 x_a g + x_a r^2
 //   g = e^{-lam r}/r with b = e^{-lam r} (Yukawa):       r^2 d_a g = -x_a g - lam x_a b,
 //                                                         d_a b = -lam x_a g
+//   Helmholtz, real part g = cos(k r)/r, b = sin(k r):    r^2 d_a g = -x_a g - k x_a b,
+//                                                         d_a b = +k x_a g
+//   imaginary part g = sin(k r)/r, b = cos(k r):          r^2 d_a g = -x_a g + k x_a b,
+//                                                         d_a b = -k x_a g
+// (one coupled form r^2 d_a g = -x_a g + alpha x_a b, d_a b = beta x_a g)
 // With a the first axis where m_a >= 1 and k = m - e_a, Leibniz on r^2 gives
 //   r^2 g^m = RHS^{(k)} - 2(m_a-1) x_a g^{m-e_a} - (m_a-1)(m_a-2) g^{m-2e_a}
 //             - sum_{b != a} [2 m_b x_b g^{m-e_b} + m_b (m_b-1) g^{m-2e_b}],
@@ -71,15 +79,26 @@ __global__ void __launch_bounds__(128) k_deriv_tables(PlanDev pd, const Geom* __
   const double lam = pd.lam * s;
   // nu for the r^nu family; log / Yukawa flagged separately
   const bool is_log = (kern == FMM_KERNEL_LAPLACE && D == 2);
-  const bool is_yuk = (kern == FMM_KERNEL_YUKAWA);
-  const double nu = (kern == FMM_KERNEL_BIHARMONIC) ? 1.0 : -1.0;
+  const bool is_bih2 = (kern == FMM_KERNEL_BIHARMONIC && D == 2);
+  const bool is_yuk = kernel_screened(kern);
+  const double nu = is_bih2 ? 2.0 : (kern == FMM_KERNEL_BIHARMONIC) ? 1.0 : -1.0;
+  // coefficients of the coupled recurrence (lam is lambda or kappa, in box units)
+  const double alpha = kern == kHelmIm ? lam : -lam;
+  const double beta = kern == FMM_KERNEL_HELMHOLTZ ? lam : -lam;
   if (threadIdx.x == 0) {
     if (is_log) {
       G[0] = log(r);
-    } else if (is_yuk) {
+    } else if (is_bih2) {
+      G[0] = r * r * log(r);
+    } else if (kern == FMM_KERNEL_YUKAWA) {
       const double e = exp(-lam * r);
       G[0] = e / r;
       B[0] = e;
+    } else if (is_yuk) {
+      double sn, cs;
+      sincos(lam * r, &sn, &cs);
+      G[0] = (kern == FMM_KERNEL_HELMHOLTZ ? cs : sn) / r;
+      B[0] = kern == FMM_KERNEL_HELMHOLTZ ? sn : cs;
     } else {
       G[0] = (kern == FMM_KERNEL_BIHARMONIC) ? r : 1.0 / r;
     }
@@ -132,10 +151,24 @@ __global__ void __launch_bounds__(128) k_deriv_tables(PlanDev pd, const Geom* __
         if (deg == 1) v += x[a];
         if (deg == 2 && ma == 2) v += 1.0;
       } else if (is_yuk) {
-        v = -(2.0 * ma - 1.0) * x[a] * g1 - (double)(ma - 1) * (ma - 1) * g2 - lam * x[a] * b1 -
-            lam * (ma - 1) * b2;
+        v = -(2.0 * ma - 1.0) * x[a] * g1 - (double)(ma - 1) * (ma - 1) * g2 +
+            alpha * x[a] * b1 + alpha * (ma - 1) * b2;
       } else {
         v = (nu - 2.0 * (ma - 1)) * x[a] * g1 + (double)(ma - 1) * (nu - (ma - 2)) * g2;
+        if (is_bih2 && deg <= 4) {
+          // + d^k (x_a r^2), k = m - e_a: the monomials x_a^3 and x_a x_b^2
+          const int b = 1 - a, ka = ma - 1, kb = m[b];
+          auto mono = [&](int ia, int ib) {  // d_a^ka d_b^kb x_a^ia x_b^ib at x
+            if (ka > ia || kb > ib) return 0.0;
+            double f = 1.0;
+            for (int t = 0; t < ka; ++t) f *= ia - t;
+            for (int t = 0; t < kb; ++t) f *= ib - t;
+            for (int t = 0; t < ia - ka; ++t) f *= x[a];
+            for (int t = 0; t < ib - kb; ++t) f *= x[b];
+            return f;
+          };
+          v += mono(3, 0) + mono(1, 2);
+        }
       }
       for (int bax = a + 1; bax < D; ++bax) {
         const int mb = m[bax];
@@ -150,19 +183,32 @@ __global__ void __launch_bounds__(128) k_deriv_tables(PlanDev pd, const Geom* __
       }
       const int im = hidx<D>(pd.hrow, P2, m);
       G[im] = v * rinv2;
-      if (is_yuk) B[im] = -lam * (x[a] * g1 + (ma - 1) * g2);
+      if (is_yuk) B[im] = beta * (x[a] * g1 + (ma - 1) * g2);
     }
     __syncthreads();
   }
   double scale = 1.0;
   if (kern == FMM_KERNEL_LAPLACE && D == 3) scale = 1.0 / (4.0 * 3.14159265358979323846 * s);
-  if (kern == FMM_KERNEL_BIHARMONIC) scale = s;
+  if (kern == FMM_KERNEL_BIHARMONIC) scale = D == 3 ? s : s * s;
   if (is_yuk) scale = 1.0 / s;
   double* out = htab + ((size_t)lrel * NOFF + o) * pd.nh;
   for (int i = threadIdx.x; i < pd.nh; i += blockDim.x) {
     double v = G[i] * scale;
     if (is_log && i == 0) v += log(s);
     out[i] = v;
+  }
+  if (is_bih2) {
+    // (s r)^2 log(s r) = s^2 (r^2 log r + log(s) r^2): the second part's
+    // derivatives, d^m r^2 for |m| <= 2, in units of the box side
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double ls = s * s * log(s);
+      out[pd.hrow[0]] += ls * (x[0] * x[0] + x[1] * x[1]);
+      out[pd.hrow[0] + 1] += ls * 2.0 * x[0];
+      out[pd.hrow[0] + 2] += ls * 2.0;
+      out[pd.hrow[1]] += ls * 2.0 * x[1];
+      out[pd.hrow[2]] += ls * 2.0;
+    }
   }
 }
 
@@ -602,7 +648,68 @@ bool m2l_shared_tables(const fmm_plan_s* P) {
   const int prec = P->desc.precision;
   const bool tc = prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3;
   const bool fft = P->desc.m2l == FMM_M2L_FFT;
-  return (tc || fft) && P->pd.d == 3 && P->pd.kernel != FMM_KERNEL_YUKAWA;
+  return (tc || fft) && P->pd.d == 3 && kernel_homogeneous(P->pd.kernel);
+}
+
+// Residual of a PDE on the kernel's own derivatives (eq. (Pv): P applied to
+// the derivatives of G vanishes when G satisfies the PDE).  The derivative
+// table of one level is built for a root of side 4 (level-2 boxes of side 1)
+// and read at the far offset h = (3, 2, 1) (2D: (3, 2)); for every m of slab
+// 0 with |m| + c <= 2p the PDE's terms sum_t a_t d^{m + xi_t} G(h) must
+// cancel.  Returns max |sum| / sum |terms| over those m, or -1 on a CUDA error.
+double pde_residual(const PlanDev& pd, const std::vector<int>& hrow_host, int nterm,
+                    const int* xi, const double* a) {
+  const int D = pd.d, P2 = 2 * pd.p;
+  const int noff = D == 3 ? 343 : 49;
+  const int o = D == 3 ? (3 + 3) + 7 * (2 + 3) + 49 * (1 + 3) : (3 + 3) + 7 * (2 + 3);
+  Geom g{};
+  g.size = 4.0;
+  void* dmem = nullptr;
+  const size_t tab = sizeof(double) * (size_t)noff * pd.nh;
+  if (cudaMalloc(&dmem, sizeof(Geom) + tab) != cudaSuccess) return -1.0;
+  Geom* dg = static_cast<Geom*>(dmem);
+  double* dh = reinterpret_cast<double*>(static_cast<char*>(dmem) + sizeof(Geom));
+  std::vector<double> h(pd.nh);
+  bool ok = cudaMemcpy(dg, &g, sizeof(Geom), cudaMemcpyHostToDevice) == cudaSuccess;
+  const size_t smem = sizeof(double) * pd.nh * 2;
+  if (ok && D == 3) {
+    set_smem(k_deriv_tables<3>, smem);
+    k_deriv_tables<3><<<noff, 128, smem>>>(pd, dg, dh);
+  } else if (ok) {
+    set_smem(k_deriv_tables<2>, smem);
+    k_deriv_tables<2><<<noff, 128, smem>>>(pd, dg, dh);
+  }
+  ok = ok && cudaGetLastError() == cudaSuccess &&
+       cudaMemcpy(h.data(), dh + (size_t)o * pd.nh, sizeof(double) * pd.nh,
+                  cudaMemcpyDeviceToHost) == cudaSuccess;
+  cudaFree(dmem);
+  if (!ok) return -1.0;
+  auto at = [&](int m0, int m1, int ms) {  // Hankel layout position (slabs 0..2c-2)
+    return D == 3 ? hrow_host[(size_t)ms * (P2 + 1) + m1] + m0 : hrow_host[(size_t)ms] + m0;
+  };
+  // the scale of the derivatives of each total degree: a residual is
+  // measured against it (an oscillating kernel's single derivative can be
+  // near a zero, where its own size says nothing about the rounding)
+  std::vector<double> dmax(P2 + 1, 0.0);
+  for (int ms = 0; ms <= std::min(2 * pd.c - 2, P2); ++ms)
+    for (int m1 = 0; m1 <= (D == 3 ? P2 - ms : 0); ++m1)
+      for (int m0 = 0; m0 + m1 + ms <= P2; ++m0)
+        dmax[m0 + m1 + ms] = std::max(dmax[m0 + m1 + ms], fabs(h[at(m0, m1, ms)]));
+  double worst = 0.0;
+  for (int deg = 0; deg + pd.c <= P2; ++deg)
+    for (int m1 = 0; m1 <= (D == 3 ? deg : 0); ++m1) {
+      const int m0 = deg - m1;
+      double sum = 0.0, mag = 0.0;
+      for (int t = 0; t < nterm; ++t) {
+        const int* x = xi + 3 * t;
+        const double v = a[t] * (D == 3 ? h[at(m0 + x[0], m1 + x[1], x[2])]
+                                        : h[at(m0 + x[0], 0, x[1])]);
+        sum += v;
+        mag += fabs(a[t]) * dmax[deg + x[0] + x[1] + x[2]];
+      }
+      if (mag > 0.0) worst = std::max(worst, fabs(sum) / mag);
+    }
+  return worst;
 }
 
 cudaError_t launch_deriv_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
@@ -763,7 +870,7 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l(PlanDev pd, const Geom* __re
   extern __shared__ __align__(16) double smd[];
   double* Lacc = smd;
   const int sl = min(pd.c, pd.p + 1) * (pd.p + 1);
-  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
   double* S = smd + ((nj + 1) & ~1) + threadIdx.x * per;
   for (int i = threadIdx.x; i < nj; i += blockDim.x) Lacc[i] = 0.0;
   __syncthreads();
@@ -814,7 +921,7 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l_f32(PlanDev pd, const Geom* 
   float4* stage = reinterpret_cast<float4*>(smp);  // kAFStage
   float* Lacc = smp + 4 * kAFStage;
   const int sl = min(pd.c, pd.p + 1) * (pd.p + 1);
-  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
   float* S = Lacc + ((nj + 3) & ~3) + threadIdx.x * per;
   for (int i = threadIdx.x; i < nj; i += blockDim.x) Lacc[i] = 0.f;
   const double inv_s = 1.0 / s;
@@ -911,7 +1018,7 @@ cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, co
   const int nbox = t.loff[t.maxlev + 1];
   {
     const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
-    const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+    const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
     if (P->desc.precision == FMM_PREC_FP64) {
       const size_t smem = sizeof(double) * (((pd.nj + 1) & ~1) + (size_t)per * kAThreads);
       set_smem(k_ap2l, smem);

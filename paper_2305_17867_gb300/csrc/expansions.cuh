@@ -112,8 +112,9 @@ __device__ void compress_warp(const PlanDev& pd, T* a, double s, int lane) {
 // Box-scaled derivatives s^{|m|} d^m G at the point s*x (x in box units) for
 // the stored set j (order p, slabs m_s < c), degree by degree, from the same
 // r^2-led recurrences as the M2L derivative tables (Sec. 4.4; 3D Laplace,
-// Yukawa, biharmonic).  Only the last two degrees are kept: S holds 3 * sl
-// values (6 * sl for Yukawa), sl = min(c, p+1) * (p+1), private to the
+// Yukawa, Helmholtz parts, biharmonic).  Only the last two degrees are kept:
+// S holds 3 * sl values (6 * sl for the coupled recurrences),
+// sl = min(c, p+1) * (p+1), private to the
 // caller.  emit(pos, value) receives value * scale for the multi-index at
 // position pos of the stored layout.  lam is lambda * s.  T = double, or
 // float for the mixed-precision modes.
@@ -121,16 +122,22 @@ template <typename T, typename F>
 __device__ void deriv_point(const PlanDev& pd, const T* x, T lam, T scale, T* S, int sl,
                             F&& emit) {
   const int p = pd.p, ce = pd.c < p + 1 ? pd.c : p + 1;
-  const bool yuk = pd.kernel == FMM_KERNEL_YUKAWA;
+  const bool yuk = kernel_screened(pd.kernel);
   const T nu = pd.kernel == FMM_KERNEL_BIHARMONIC ? T(1) : T(-1);
+  const T alpha = pd.kernel == kHelmIm ? lam : -lam;  // coupled recurrence (see the tables)
+  const T beta = pd.kernel == FMM_KERNEL_HELMHOLTZ ? lam : -lam;
   const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
   const T r = sqrt(r2), rinv2 = T(1) / r2;
   T* G3[3] = {S, S + sl, S + 2 * sl};
   T* B3[3] = {S + 3 * sl, S + 4 * sl, S + 5 * sl};
-  if (yuk) {
+  if (pd.kernel == FMM_KERNEL_YUKAWA) {
     const T e = exp(-lam * r);
     G3[0][0] = e / r;
     B3[0][0] = e;
+  } else if (yuk) {
+    const T sn = sin(lam * r), cs = cos(lam * r);
+    G3[0][0] = (pd.kernel == FMM_KERNEL_HELMHOLTZ ? cs : sn) / r;
+    B3[0][0] = pd.kernel == FMM_KERNEL_HELMHOLTZ ? sn : cs;
   } else {
     G3[0][0] = pd.kernel == FMM_KERNEL_BIHARMONIC ? r : T(1) / r;
   }
@@ -163,8 +170,8 @@ __device__ void deriv_point(const PlanDev& pd, const T* x, T lam, T scale, T* S,
         }
         T v;
         if (yuk)
-          v = -(T(2) * ma - T(1)) * x[a] * g1 - T((ma - 1) * (ma - 1)) * g2 - lam * x[a] * b1 -
-              lam * T(ma - 1) * b2;
+          v = -(T(2) * ma - T(1)) * x[a] * g1 - T((ma - 1) * (ma - 1)) * g2 +
+              alpha * x[a] * b1 + alpha * T(ma - 1) * b2;
         else
           v = (nu - T(2 * (ma - 1))) * x[a] * g1 + T(ma - 1) * (nu - T(ma - 2)) * g2;
         for (int bax = a + 1; bax < 3; ++bax) {
@@ -180,7 +187,7 @@ __device__ void deriv_point(const PlanDev& pd, const T* x, T lam, T scale, T* S,
         }
         const int pm = pos(n, ms, m1);
         cur[pm] = v * rinv2;
-        if (yuk) bcur[pm] = -lam * (x[a] * g1 + T(ma - 1) * g2);
+        if (yuk) bcur[pm] = beta * (x[a] * g1 + T(ma - 1) * g2);
         emit(pd.frow[ms * (p + 1) + m1] + m[0], cur[pm] * scale);
       }
     }
@@ -191,5 +198,5 @@ __device__ void deriv_point(const PlanDev& pd, const T* x, T lam, T scale, T* S,
 __device__ inline double deriv_scale(const PlanDev& pd, double s) {
   if (pd.kernel == FMM_KERNEL_LAPLACE) return 1.0 / (4.0 * 3.14159265358979323846 * s);
   if (pd.kernel == FMM_KERNEL_BIHARMONIC) return s;
-  return 1.0 / s;  // Yukawa
+  return 1.0 / s;  // Yukawa, Helmholtz parts
 }

@@ -21,6 +21,23 @@
 #include "../../include/ctfmm.h"
 
 #define FMM_MAXP 20
+
+// Kernel ids inside the device code.  A Helmholtz plan (G = e^{i kappa r}/r)
+// is evaluated as two real FMMs that share the tree, P2M and M2M -- the
+// multipoles are real for real weights and the PDE Laplacian + kappa^2 has
+// real coefficients -- one with the real part cos(kappa r)/r (kernel id
+// FMM_KERNEL_HELMHOLTZ) and one with the imaginary part sin(kappa r)/r
+// (kHelmIm); their potentials are the real and imaginary parts of phi.
+constexpr int kHelmIm = 16;
+// kernels whose derivatives come from the coupled (g, b) recurrence:
+// r^2 d_a g = -x_a g + alpha x_a b, d_a b = beta x_a g
+__host__ __device__ inline bool kernel_screened(int k) {
+  return k == FMM_KERNEL_YUKAWA || k == FMM_KERNEL_HELMHOLTZ || k == kHelmIm;
+}
+// G(s h) = s^deg G(h): one set of M2L tables serves every level
+__host__ __device__ inline bool kernel_homogeneous(int k) {
+  return k == FMM_KERNEL_LAPLACE || k == FMM_KERNEL_BIHARMONIC;
+}
 #define FMM_MAX_TERMS 12
 #define FMM_MAX_LEVELS 8
 
@@ -33,6 +50,7 @@ struct Geom {
   int flag;  // device-side status bits (1: domain, 2: timeout, 4: traversal stack full)
   int pad;
   unsigned long long m2l_count;  // adaptive trees: M2L translations performed
+  unsigned long long p2p_pairs;  // uniform trees, when timing: near-field pairs
 };
 
 // Read-only plan data passed by value to kernels.
@@ -93,6 +111,7 @@ struct fmm_plan_s {
   int deriv_levels;  // adaptive plans: M2L table levels of the current tree
   int last_boxes;    // adaptive plans: boxes and depth of the last tree
   int last_depth;
+  long long tc_wait_cycles;  // tensor-core M2L pipeline waits (0: the default ~1 s)
 };
 
 inline void set_deriv_levels(const fmm_plan_s* P, int maxlev) {
@@ -136,8 +155,8 @@ struct Workspace {
   int nbbox_blocks;
   // tensor-core M2L operands (tf32 hi / lo): parity-split multipoles of the
   // finest level and the dense offset matrices of one level
-  int tc_jp;        // |j| padded to one 128-byte row of the operand format (K)
-  int tc_mp;        // |j| padded to a multiple of 128 (M)
+  int tc_jp;        // |j| padded to one K chunk of the operand format (row length)
+  int tc_mp;        // rows of one offset matrix: |j| padded to the column blocks (tc_shape)
   void* tc_bpar[2];
   void* tc_tmat[2];
   // adaptive trees: arena for the per-level windows (parity-split operands
@@ -171,11 +190,43 @@ struct Workspace {
   uint32_t* skey;
   uint32_t* tkey;
   int* agrid;       // dense box index of the coarse levels (adaptive.cuh)
+  // Helmholtz plans: potentials (2 x n_tgt) and gradients (2 x d x n_tgt) of
+  // the real and the imaginary part
+  double* hphi;
+  double* hgrad;
   size_t bytes;
 };
 
 // helpers
 __host__ __device__ inline int64_t nbox_at(int d, int l) { return (int64_t)1 << (d * l); }
+
+// Blocking of the tensor-core M2L contraction (m2l_tc.cu).  The MMA's M
+// dimension holds 128 target boxes, N the local coefficients i of j and K the
+// multipole coefficients q.  |j| is padded to a multiple of 16 (the MMA's N
+// granularity) and split into nchunk column blocks of nc <= 256 columns; when
+// one block of nc columns leaves room, ncls child classes of the target boxes
+// share one CTA (their offset matrices stacked along N, up to 256 columns).
+// Rows of the operands are jp = |j| padded to a whole K chunk of row_bytes
+// (128 bytes).
+struct TcShape {
+  int row_bytes, esz, jp;
+  int nc, nchunk, npt, ncls;
+};
+inline TcShape tc_shape(int nj, int precision) {
+  TcShape s;
+  s.row_bytes = 128;
+  s.esz = precision == FMM_PREC_BF16X3 ? 2 : 4;
+  const int row = s.row_bytes / s.esz;
+  s.jp = (nj + row - 1) / row * row;
+  const int nj16 = (nj + 15) / 16 * 16;
+  s.nchunk = (nj16 + 255) / 256;
+  s.nc = ((nj16 + s.nchunk - 1) / s.nchunk + 15) / 16 * 16;
+  s.npt = s.nchunk * s.nc;
+  s.ncls = 1;
+  if (s.nchunk == 1)
+    while (s.ncls < 8 && 2 * s.ncls * s.nc <= 256) s.ncls *= 2;
+  return s;
+}
 
 int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void* base,
                          Workspace* ws);

@@ -28,6 +28,8 @@ __device__ __forceinline__ double exp_t(double x) { return exp(x); }
 __device__ __forceinline__ float exp_t(float x) { return __expf(x); }
 __device__ __forceinline__ double log_t(double x) { return log(x); }
 __device__ __forceinline__ float log_t(float x) { return __logf(x); }
+__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
 
 // Near-field pair in box units: r2 = |u_t - u_s|^2 > 0.  Adds to the running
 // potential sum `v` (scaled later by kPhiScale) and gradient factor `f1`
@@ -41,12 +43,29 @@ __device__ __forceinline__ void pair_kernel(T r2, T lam, T& v, T& f1) {
   } else if (K == FMM_KERNEL_LAPLACE && D == 2) {
     v = (T)0.5 * log_t(r2);
     f1 = (T)1 / r2;
+  } else if (K == FMM_KERNEL_BIHARMONIC && D == 2) {  // r^2 log r, f1 = 2 log r + 1
+    const T lg = log_t(r2);
+    v = (T)0.5 * r2 * lg;
+    f1 = lg + (T)1;
   } else if (K == FMM_KERNEL_YUKAWA) {
     const T ri = rsqrt_t(r2);
     const T r = r2 * ri;
     const T e = exp_t(-lam * r);
     v = e * ri;
     f1 = e * (-lam * ri * ri - ri * ri * ri);
+  } else if (K == FMM_KERNEL_HELMHOLTZ || K == kHelmIm) {
+    // real part cos(k r)/r: f1 = -k sin/r^2 - cos/r^3; imaginary part
+    // sin(k r)/r: f1 = k cos/r^2 - sin/r^3 (lam = kappa in box units)
+    const T ri = rsqrt_t(r2);
+    T sn, cs;
+    sincos_t(lam * (r2 * ri), &sn, &cs);
+    if (K == FMM_KERNEL_HELMHOLTZ) {
+      v = cs * ri;
+      f1 = (-lam * sn - cs * ri) * ri * ri;
+    } else {
+      v = sn * ri;
+      f1 = (lam * cs - sn * ri) * ri * ri;
+    }
   } else {  // biharmonic 3D: G = r
     const T ri = rsqrt_t(r2);
     v = r2 * ri;
@@ -150,7 +169,10 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
       }
     }
     // ---- near field over the 3^(d-1) runs of x-adjacent leaves
-    T nv = 0, ng[3] = {0, 0, 0}, wsum = 0;
+    // wsum: sum w (2D Laplace) or sum w r^2 (2D biharmonic), and gw = sum w (u - y),
+    // for the log(s) parts of the box scaling
+    constexpr bool kBih2 = K == FMM_KERNEL_BIHARMONIC && D == 2;
+    T nv = 0, ng[3] = {0, 0, 0}, wsum = 0, gw[3] = {0, 0, 0};
     const int nrun = D == 3 ? 9 : 3;
     for (int rr = 0; rr < nrun; ++rr) {
       const int dy = rr % 3 - 1, dz = rr / 3 - 1;
@@ -180,10 +202,12 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
               pair_kernel<K, D, T>(r2, lam, v, f1);
               const T wj = swt[jj];
               nv += wj * v;
-              wsum += wj;
+              wsum += kBih2 ? wj * r2 : wj;
               if (GRAD) {
                 const T fw = wj * f1;
                 for (int k = 0; k < D; ++k) ng[k] += fw * dxv[k];
+                if (kBih2)
+                  for (int k = 0; k < D; ++k) gw[k] += wj * dxv[k];
               }
             }
           }
@@ -199,6 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
         for (int k = 0; k < D; ++k) {
           gf[k] += __shfl_down_sync(0xffffffffu, gf[k], off, tpt);
           ng[k] += __shfl_down_sync(0xffffffffu, ng[k], off, tpt);
+          if (kBih2) gw[k] += __shfl_down_sync(0xffffffffu, gw[k], off, tpt);
         }
     }
     if (valid && lane == 0) {
@@ -209,7 +234,10 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
       } else if (K == FMM_KERNEL_LAPLACE && D == 2) {
         phi_scale = 1.0;
         grad_scale = inv_s;
-      } else if (K == FMM_KERNEL_YUKAWA) {
+      } else if (kBih2) {
+        phi_scale = s * s;
+        grad_scale = s;
+      } else if (kernel_screened(K)) {
         phi_scale = inv_s;
         grad_scale = inv_s * inv_s;
       } else {
@@ -219,10 +247,12 @@ __global__ void __launch_bounds__(kThreads) k_leaf(
       const int orig = tperm[t];
       double ph = (double)far + phi_scale * (double)nv;
       if (K == FMM_KERNEL_LAPLACE && D == 2) ph += log(s) * (double)wsum;
+      if (kBih2) ph += s * s * log(s) * (double)wsum;
       if (phi) phi[orig] = ph;
       if (GRAD && grad)
         for (int k = 0; k < D; ++k)
-          grad[(size_t)orig * D + k] = (double)gf[k] * inv_s + grad_scale * (double)ng[k];
+          grad[(size_t)orig * D + k] = (double)gf[k] * inv_s + grad_scale * (double)ng[k] +
+                                       (kBih2 ? 2.0 * s * log(s) * (double)gw[k] : 0.0);
     }
   }
 }
@@ -296,7 +326,8 @@ __device__ __forceinline__ f2_t f2fma(f2_t a, f2_t b, f2_t c) {
 // with f1 = (1/r) dG/dr; pair_sign<K>() restores the sign of f1.
 template <int K>
 __host__ __device__ constexpr float pair_sign() {
-  return K == FMM_KERNEL_BIHARMONIC ? 1.f : -1.f;
+  // the Helmholtz parts carry the sign of f1 themselves (it oscillates)
+  return (K == FMM_KERNEL_BIHARMONIC || K == FMM_KERNEL_HELMHOLTZ || K == kHelmIm) ? 1.f : -1.f;
 }
 
 template <int K, bool GRAD, bool MASK>
@@ -327,6 +358,20 @@ __device__ __forceinline__ void pair2(const float4 A, const float4 B, f2_t UX, f
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(eh) : "f"(ah));
     v = f2mul(f2pack(el, eh), ri);                          // e^{-lam r} / r (0 if masked)
     if (GRAD) f1 = f2mul(v, f2fma(ri, ri, f2mul(LAM, ri)));  // |f1| = v (lam/r + 1/r^2)
+  } else if (K == FMM_KERNEL_HELMHOLTZ || K == kHelmIm) {
+    float kl, kh, sl, cl, sh, ch;
+    f2unpack(f2mul(f2mul(r2, ri), LAM), kl, kh);  // kappa r
+    sincosf(kl, &sl, &cl);
+    sincosf(kh, &sh, &ch);
+    const f2_t S = f2pack(sl, sh), Cc = f2pack(cl, ch);
+    const f2_t ri2 = f2mul(ri, ri);
+    if (K == FMM_KERNEL_HELMHOLTZ) {  // cos(k r)/r, f1 = -(k sin + cos/r)/r^2
+      v = f2mul(Cc, ri);
+      if (GRAD) f1 = f2mul(f2fma(LAM, S, f2mul(Cc, ri)), f2mul(ri2, f2pack(-1.f, -1.f)));
+    } else {  // sin(k r)/r, f1 = (k cos - sin/r)/r^2
+      v = f2mul(S, ri);
+      if (GRAD) f1 = f2mul(f2fma(LAM, Cc, f2mul(S, f2mul(ri, f2pack(-1.f, -1.f)))), ri2);
+    }
   } else {  // biharmonic: G = r, f1 = 1/r
     v = f2mul(r2, ri);
     if (GRAD) f1 = ri;
@@ -435,7 +480,7 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_fast(
   if (K == FMM_KERNEL_LAPLACE) {
     phi_scale = inv_s * (1.0 / (4.0 * 3.14159265358979323846));
     grad_scale = phi_scale * inv_s;
-  } else if (K == FMM_KERNEL_YUKAWA) {
+  } else if (kernel_screened(K)) {
     phi_scale = inv_s;
     grad_scale = inv_s * inv_s;
   } else {
@@ -721,7 +766,7 @@ __global__ void __launch_bounds__(kAThreads) k_aleaf(
   extern __shared__ __align__(16) double smd[];
   double* a = smd;  // decompressed local / m!
   const int sl = min(pd.c, p + 1) * (p + 1);
-  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
   double* S = smd + ((nfull + 1) & ~1) + threadIdx.x * per;
   const bool has_local = l >= 2;
   if (has_local) {
@@ -841,7 +886,7 @@ __global__ void __launch_bounds__(kAFThreads) k_aleaf_f32(
   float* a = smf + 4 * kAFStage;                     // nfull: decompressed local / m!
   float* bt = a + ((nfull + 3) & ~3);                // nj: staged multipole of a W box
   const int sl = min(pd.c, p + 1) * (p + 1);
-  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
   float* S = bt + ((nj + 3) & ~3) + threadIdx.x * per;
   const bool has_local = l >= 2;
   if (has_local) {
@@ -978,13 +1023,20 @@ cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* p
     if (e != cudaSuccess) return e;
     return launch_far_field(P, ws, phi, grad, st, nl);
   }
-  if (d == 2) {
+  if (d == 2 && k == FMM_KERNEL_BIHARMONIC) {
+    if (f64) leaf_launch<FMM_KERNEL_BIHARMONIC, 2, double>(P, ws, phi, grad, st);
+    else leaf_launch<FMM_KERNEL_BIHARMONIC, 2, float>(P, ws, phi, grad, st);
+  } else if (d == 2) {
     if (f64) leaf_launch<FMM_KERNEL_LAPLACE, 2, double>(P, ws, phi, grad, st);
     else leaf_launch<FMM_KERNEL_LAPLACE, 2, float>(P, ws, phi, grad, st);
   } else if (k == FMM_KERNEL_LAPLACE) {
     leaf_launch<FMM_KERNEL_LAPLACE, 3, double>(P, ws, phi, grad, st);
   } else if (k == FMM_KERNEL_YUKAWA) {
     leaf_launch<FMM_KERNEL_YUKAWA, 3, double>(P, ws, phi, grad, st);
+  } else if (k == FMM_KERNEL_HELMHOLTZ) {
+    leaf_launch<FMM_KERNEL_HELMHOLTZ, 3, double>(P, ws, phi, grad, st);
+  } else if (k == kHelmIm) {
+    leaf_launch<kHelmIm, 3, double>(P, ws, phi, grad, st);
   } else {
     leaf_launch<FMM_KERNEL_BIHARMONIC, 3, double>(P, ws, phi, grad, st);
   }
@@ -999,7 +1051,7 @@ cudaError_t launch_adaptive_leaf(const fmm_plan_s* P, const Workspace& ws, const
   const int nbox = t.loff[t.maxlev + 1];
   if (P->desc.precision != FMM_PREC_FP64) {
     const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
-    const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+    const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
     const size_t smem = sizeof(float) * (4 * kAFStage + ((pd.nfull + 3) & ~3) +
                                          ((pd.nj + 3) & ~3) + (size_t)per * kAFThreads);
     set_smem(k_aleaf_f32, smem);
@@ -1010,7 +1062,7 @@ cudaError_t launch_adaptive_leaf(const fmm_plan_s* P, const Workspace& ws, const
     return cudaGetLastError();
   }
   const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
-  const int per = (pd.kernel == FMM_KERNEL_YUKAWA ? 6 : 3) * sl;
+  const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
   const size_t smem = sizeof(double) * (((pd.nfull + 1) & ~1) + (size_t)per * kAThreads);
   set_smem(k_aleaf, smem);
   k_aleaf<<<(unsigned)nbox, kAThreads, smem, st>>>(pd, ws.geom, t, ws.lc, ws.mp, ws.tx[0],
@@ -1032,6 +1084,8 @@ cudaError_t launch_near_field(const fmm_plan_s* P, const Workspace& ws, double* 
   const int k = P->pd.kernel;
   if (k == FMM_KERNEL_LAPLACE) near_fast_launch<FMM_KERNEL_LAPLACE>(P, ws, phi, grad, st);
   else if (k == FMM_KERNEL_YUKAWA) near_fast_launch<FMM_KERNEL_YUKAWA>(P, ws, phi, grad, st);
+  else if (k == FMM_KERNEL_HELMHOLTZ) near_fast_launch<FMM_KERNEL_HELMHOLTZ>(P, ws, phi, grad, st);
+  else if (k == kHelmIm) near_fast_launch<kHelmIm>(P, ws, phi, grad, st);
   else near_fast_launch<FMM_KERNEL_BIHARMONIC>(P, ws, phi, grad, st);
   ++*nl;
   return cudaGetLastError();

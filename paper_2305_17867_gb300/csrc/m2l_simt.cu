@@ -228,10 +228,13 @@ cudaError_t launch_m2l_tables(const fmm_plan_s* P, const Workspace& ws, cudaStre
 cudaError_t launch_m2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl,
                        bool tables_ready) {
   const int L = P->desc.levels;
-  cudaMemsetAsync(ws.lc, 0, sizeof(double) * (size_t)ws.lev_off[L + 1] * P->pd.nj, st);
   const int prec = P->desc.precision;
+  const bool tc = P->desc.m2l != FMM_M2L_FFT && prec != FMM_PREC_FP64 && prec != FMM_PREC_FP32;
+  // the tensor-core contraction stores every coefficient of levels 2..L once
+  // (it zeroes the 2D fallback's expansions itself); the other forms add
+  if (!tc) cudaMemsetAsync(ws.lc, 0, sizeof(double) * (size_t)ws.lev_off[L + 1] * P->pd.nj, st);
   if (P->desc.m2l == FMM_M2L_FFT) return launch_m2l_fft(P, ws, st, nl);
-  if (prec == FMM_PREC_FP64 || prec == FMM_PREC_FP32) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
+  if (!tc) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
   return launch_m2l_tc(P, ws, st, nl, tables_ready && uses_tc_tables(P));
 }
 

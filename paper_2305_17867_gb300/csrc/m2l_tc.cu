@@ -10,23 +10,25 @@
 // For a fixed (pi, sigma, delta) the sources of a tile of targets T are the
 // same tile of parents shifted by delta, so with the multipoles stored
 // parity-split, Bpar[sigma][Tz][Ty][Tx][q], one 5-D TMA box (zero-filled
-// outside the domain) is the B operand, and the dense offset matrix
-//   A_h[i][q] = Ht_h[i + q]   (i, q in j)
-// is the A operand.  One CTA owns one (tile of up to 256 target parents,
-// pi, 128-row block of i), accumulates D[i][T] = sum_{sigma,delta,q}
-// A_h[i][q] Bpar[...][q] per offset in TMEM, sums the offsets in registers and
-// adds the result into the FP64 local expansions.
+// outside the domain) is a dense operand, and so is the offset matrix
+//   A_h[i][q] = Ht_h[i + q]   (i, q in j).
+//
+// Orientation.  The MMA's M dimension (the 128 TMEM lanes) holds 128 target
+// parents, N holds the local coefficients i and K the multipole
+// coefficients q:
+//   D[T][i] += sum_q Bpar[sigma][T + delta][q] * A_h[i][q],
+// so |j| is padded only to the MMA's N granularity of 16 (130 -> 144 for the
+// biharmonic kernel at p = 8) and the K steps that hold nothing but padding
+// are not issued.  Above 256 columns |j| is split into column blocks (one per
+// grid row); where one block leaves room, the offset matrices of 2, 4 or 8
+// child classes pi are stacked along N (one MMA of up to 256 columns), so small
+// |j| still run the long MMAs the tensor pipe needs (3D Laplace p = 10:
+// |j| = 121 -> two classes of 128 columns).  A CTA runs every (sigma, delta)
+// that is an interaction for at least one of its classes; an offset that is
+// adjacent for one class meets that class's zero matrix.
 //
 // Precision: TF32 (one pass), or TF32x3 / BF16x3 (a = a_hi + a_lo split,
 // three passes a_hi b_hi + a_hi b_lo + a_lo b_hi), FP32 accumulation.
-//
-// Tile width.  An MMA of N = 256 columns reads its A slice once for twice the
-// work of N = 128: the operand traffic out of shared memory drops from 128 to
-// 96 bytes per clock at the full tensor rate, and each MMA runs twice as long,
-// which leaves room for the issuing thread's barrier waits and commits between
-// MMAs.  Measured on this kernel's issue pattern (three passes, one wait and
-// one commit per stage), N = 128 kept the tensor pipe 85% busy and N = 256
-// 99%.
 #include <algorithm>
 #include <cstring>
 
@@ -41,17 +43,17 @@ cudaError_t launch_m2l_simt_levels(const fmm_plan_s* P, const Workspace& ws, int
 
 namespace {
 
-constexpr int kBM = 128;    // rows of A / TMEM lanes
-constexpr int kMaxN = 256;  // target parents per CTA = MMA N
+constexpr int kBM = 128;       // target parents per CTA = MMA M = TMEM lanes
+constexpr int kMaxN = 256;     // MMA N: columns of i (times stacked classes)
+constexpr int kMaxStages = 8;  // pipeline depth bound
+constexpr int kSmemCap = 227 * 1024;  // opt-in shared memory per CTA
 
-// Operand formats: tf32 (fp32 storage, 32 per 128-byte row, kind::tf32) and
-// bf16 (64 per row, kind::f16).  Both split a value into hi + lo.
-// The split works on the float rounding of the value (one conversion from
-// FP64): lo = f - hi is exact in float, and keeps the bits the tf32/bf16
-// format drops from hi.
+// Operand formats: tf32 (fp32 storage, kind::tf32) and bf16 (kind::f16).  Both
+// split a value into hi + lo.  The split works on the float rounding of the
+// value (one conversion from FP64): lo = f - hi is exact in float, and keeps
+// the bits the tf32/bf16 format drops from hi.
 struct FmtTF32 {
   using T = float;
-  static constexpr int kRow = 32;
   static constexpr int kIdesc = 2;
   static constexpr bool kF16 = false;
   static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
@@ -62,7 +64,6 @@ struct FmtTF32 {
 };
 struct FmtBF16 {
   using T = __nv_bfloat16;
-  static constexpr int kRow = 64;
   static constexpr int kIdesc = 1;
   static constexpr bool kF16 = true;
   static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
@@ -71,26 +72,28 @@ struct FmtBF16 {
   }
 };
 
-// Pipeline stage = one K chunk of every operand the passes read.  The split
-// forms take 64-byte chunks (64-byte swizzle) so that four stages of A_hi,
-// B_hi, A_lo, B_lo fit; the one-pass form takes 128-byte chunks.
+// A pipeline stage holds one K chunk of every operand the passes read:
+// [sources hi | offset matrices hi | sources lo | offset matrices lo], in
+// 128-byte chunks (128-byte swizzle); the row bytes must match tc_shape().
+// Each stage feeds 4 K steps (12 MMAs in the split forms) per barrier round:
+// measured on GB300, 64-byte chunks (twice the rounds) ran the contraction
+// 15-18% slower (biharmonic p = 8, L = 6: 11.9 against 10.1 ms, TF32x3).
 template <int NPASS>
 struct Cfg {
-  static constexpr int kRowBytes = NPASS == 1 ? 128 : 64;
+  static constexpr int kRowBytes = 128;
   static constexpr int kKSteps = kRowBytes / 32;  // MMAs of 32 bytes of K per chunk
-  static constexpr int kTileA = kBM * kRowBytes;
-  static constexpr int kTileB = kMaxN * kRowBytes;
-  static constexpr int kStages = 4;
-  static constexpr int kStage = (NPASS == 1 ? 1 : 2) * (kTileA + kTileB);
-  static constexpr int kSmem = 1024 + kStages * kStage + 256;
-  static __device__ __forceinline__ uint64_t desc(uint32_t saddr) {
-    return NPASS == 1 ? tc::desc_sw128(saddr) : tc::desc_sw64(saddr);
+  static constexpr int kTileS = kBM * kRowBytes;  // the source tile (MMA A)
+  static constexpr int kHalves = NPASS == 1 ? 1 : 2;
+  static __device__ __forceinline__ uint64_t desc(uint32_t saddr) { return tc::desc_sw128(saddr); }
+  // bytes of one stage for an N of ntot columns
+  static __host__ __device__ int stage_bytes(int ntot) {
+    return kHalves * (kTileS + ntot * kRowBytes);
   }
 };
 
 // ---- operand packing ------------------------------------------------------
 // multipoles of every level l >= 2 (lexicographic boxes, FP64, nj per box) ->
-// Bpar_l[sigma][Tz][Ty][Tx][JP] fp32 (tf32-rounded hi, and lo for the split);
+// Bpar_l[sigma][Tz][Ty][Tx][JP] (hi, and lo for the split);
 // blockIdx.y = l - 2, levels stored back to back like the expansions.
 struct LevOff {
   int64_t o[FMM_MAX_LEVELS + 1];
@@ -119,28 +122,40 @@ __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off,
   }
 }
 
-// dense offset matrices A_h[i][q] = Ht_h[i + q] for the 343 offsets of a level:
-// one block per (offset, table level); the offset's Hankel row is split into
-// hi/lo once in shared memory, then expanded to the MP x JP matrix
+// dense offset matrices A_h[i][q] = Ht_h[i + q] (rows i < NPT, columns q < JP,
+// zero outside j) for the 343 offsets of a level: one block per (offset,
+// table level).  The offsets of adjacent boxes get zero matrices: a CTA that
+// serves several child classes meets them for the classes the offset is not
+// an interaction of.  The offset's Hankel row is split into hi/lo once in
+// shared memory, then expanded.
 template <int D, typename F>
 __global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const double* __restrict__ htab,
-                                                    int MP, int JP,
+                                                    int NPT, int JP,
                                                     typename F::T* __restrict__ thi,
                                                     typename F::T* __restrict__ tlo) {
   using T = typename F::T;
   const int o = blockIdx.x;
   htab += (size_t)blockIdx.y * 343 * pd.nh;
-  thi += (size_t)blockIdx.y * 343 * MP * JP;
-  if (tlo) tlo += (size_t)blockIdx.y * 343 * MP * JP;
+  thi += (size_t)blockIdx.y * 343 * NPT * JP;
+  if (tlo) tlo += (size_t)blockIdx.y * 343 * NPT * JP;
+  bool far = false;
   {
     int t = o;
-    bool far = false;
     for (int k = 0; k < D; ++k) {
       const int hk = t % 7 - 3;
       t /= 7;
       if (hk > 1 || hk < -1) far = true;
     }
-    if (!far) return;
+  }
+  T* dh = thi + (size_t)o * NPT * JP;
+  T* dl = tlo ? tlo + (size_t)o * NPT * JP : nullptr;
+  const T zero = T(0.f);
+  if (!far) {
+    for (int e = threadIdx.x; e < NPT * JP; e += blockDim.x) {
+      dh[e] = zero;
+      if (dl) dl[e] = zero;
+    }
+    return;
   }
   extern __shared__ __align__(16) unsigned char smtm[];
   T* hh = reinterpret_cast<T*>(smtm);
@@ -149,10 +164,7 @@ __global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const double* __
   for (int e = threadIdx.x; e < pd.nh; e += blockDim.x) F::split((float)H[e], hh[e], hl[e]);
   __syncthreads();
   const int P2 = 2 * pd.p;
-  T* dh = thi + (size_t)o * MP * JP;
-  T* dl = tlo ? tlo + (size_t)o * MP * JP : nullptr;
-  const T zero = T(0.f);
-  for (int e = threadIdx.x; e < MP * JP; e += blockDim.x) {
+  for (int e = threadIdx.x; e < NPT * JP; e += blockDim.x) {
     const int i = e / JP, q = e - i * JP;
     T vh = zero, vl = zero;
     if (i < pd.nj && q < pd.nj) {
@@ -168,110 +180,145 @@ __global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const double* __
 }
 
 // ---- the contraction --------------------------------------------------------
-// Warp roles: warps 0-15 drain TMEM (warp w reads TMEM lanes 32(w%4).. = rows
-// i, columns 64(w/4)..+63 = targets), warp 16 lane 0 issues TMA, warp 17 lane
-// 0 issues MMA.  Sixteen draining warps keep the running sums at 64 floats a
-// thread: 18 warps leave at most 5 per SM sub-partition, ~100 registers each.
-// The tensor cores truncate when they accumulate, so a long K loop in one
-// accumulator drifts; each offset's partial product therefore goes to one of
-// two 256-column TMEM buffers (the whole 512 columns), and the draining warps
-// add it into float registers (round-to-nearest) while the MMA warp fills the
-// other buffer.
+// Warp roles: warps 0-15 drain TMEM (warp w reads TMEM lanes 32(w%4).. =
+// target parents, and a quarter of the columns), warp 16 lane 0 issues TMA,
+// warp 17 lane 0 issues MMA.  Eighteen warps put five on an SM sub-partition,
+// which caps a thread at 96 registers: the drain's 64 running sums fit, and
+// the MMA loop must stay lean (a spilled loop variable there cost 15%).  The tensor cores truncate when they accumulate,
+// so a long K loop in one accumulator drifts; each offset's partial product
+// therefore goes to one of two 256-column TMEM buffers (the whole 512
+// columns), and the draining warps add it into float registers
+// (round-to-nearest) while the MMA warp fills the other buffer.  At the end
+// the sums go through shared memory so that the FP64 local expansions are
+// written row by row (coalesced).
 constexpr int kEpiWarps = 16;
-constexpr int kNBuf = 2;
-constexpr int kBufCols = kMaxN;  // TMEM columns per accumulator buffer
+constexpr int kNBuf = 2;         // accumulator buffers of 256 columns
+constexpr int kTmemCols = 512;   // the whole tensor memory of the SM
 constexpr int kTcThreads = (kEpiWarps + 2) * 32;
+constexpr int kColsPerThread = kMaxN / (kEpiWarps / 4);  // running sums per thread
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
-
-// (sigma, delta) decode of combination c = sigma + 8 * delta_index; false if
-// the offset is adjacent (not in the interaction list)
-__device__ __forceinline__ bool combo(int c, int px, int py, int pz, int& sg, int& dx, int& dy,
-                                      int& dz, int& hidx) {
-  sg = c & 7;
-  const int di = c >> 3;
-  dx = di % 3 - 1;
-  dy = (di / 3) % 3 - 1;
-  dz = di / 9 - 1;
-  const int hx = px - (sg & 1) - 2 * dx, hy = py - ((sg >> 1) & 1) - 2 * dy,
-            hz = pz - ((sg >> 2) & 1) - 2 * dz;
-  hidx = (hx + 3) + 7 * (hy + 3) + 49 * (hz + 3);
-  return !(hx >= -1 && hx <= 1 && hy >= -1 && hy <= 1 && hz >= -1 && hz <= 1);
+// barrier of the 16 draining warps alone (the TMA and MMA threads go their way)
+__device__ __forceinline__ void drain_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kEpiWarps * 32) : "memory");
 }
 
-// One launch covers every level: blocks [first_block, first_block + 8 ntiles)
-// of grid.x belong to level l (block = tile * 8 + pi), grid.y = 128-row block.
+// Combination c = sigma + 8 * delta_index of a source child and a parent shift.
+struct Combo {
+  int sg, dx, dy, dz;
+};
+__device__ __forceinline__ Combo combo(int c) {
+  Combo k;
+  k.sg = c & 7;
+  const int di = c >> 3;
+  k.dx = di % 3 - 1;
+  k.dy = (di / 3) % 3 - 1;
+  k.dz = di / 9 - 1;
+  return k;
+}
+// offset index (0..342) of combination k for targets of class pi; *far is
+// false when the offset is adjacent (not in the interaction list)
+__device__ __forceinline__ int offset_of(const Combo& k, int pi, bool* far) {
+  const int hx = (pi & 1) - (k.sg & 1) - 2 * k.dx;
+  const int hy = ((pi >> 1) & 1) - ((k.sg >> 1) & 1) - 2 * k.dy;
+  const int hz = ((pi >> 2) & 1) - ((k.sg >> 2) & 1) - 2 * k.dz;
+  *far = !(hx >= -1 && hx <= 1 && hy >= -1 && hy <= 1 && hz >= -1 && hz <= 1);
+  return (hx + 3) + 7 * (hy + 3) + 49 * (hz + 3);
+}
+// the combination is an interaction for at least one of the classes pi0..
+__device__ __forceinline__ bool any_far(const Combo& k, int pi0, int ncls) {
+  bool any = false;
+  for (int u = 0; u < ncls; ++u) {
+    bool f;
+    offset_of(k, pi0 + u, &f);
+    any |= f;
+  }
+  return any;
+}
+
+// One launch covers every level: blocks [first_block, first_block + ntiles *
+// 8 / ncls) of grid.x belong to level l (block = tile * (8 / ncls) + class
+// group), grid.y = column block of i.
 // The parent grid of a level is Hx x Hy x Hz cells: the whole level of a
 // uniform tree (Hx = Hy = Hz = 2^(l-1), boxes lexicographic), or, for an
 // adaptive tree, the window of parents spanned by the level's boxes, with
 // map[(pi, cell)] the box at that position (-1: none).
 // A homogeneous kernel shares one set of offset matrices over the levels, so a
 // small level can ride along in the CTAs of another: its whole parent grid
-// (H2^3 parents, H2 = 2^(l2-1)) is loaded into the B rows after the primary
-// tile's and its targets are read off the extra MMA columns (l2 = 0: none).
-// This keeps the tiny coarse levels from forming a wave of their own.
+// (H2^3 parents, H2 = 2^(l2-1)) is loaded into the source rows after the
+// primary tile's and its targets are read off the extra TMEM lanes (l2 = 0:
+// none).  This keeps the tiny coarse levels from forming a wave of their own.
 struct TcLevel {
-  CUtensorMap A, Alo, B, Blo;  // offset matrices and parity-split multipoles
-  CUtensorMap B2, B2lo;        // multipoles of the riding level l2
-  double* lc;                  // local expansions (level base, or all boxes with map)
-  double* lc2;                 // local expansions of level l2 (base)
-  const int* map;              // adaptive: window cell -> box; null for uniform levels
-  float scale, scale2;         // exact powers of two (shared offset matrices)
+  CUtensorMap S, Slo;    // parity-split multipoles of the level (MMA A)
+  CUtensorMap S2, S2lo;  // multipoles of the riding level l2
+  CUtensorMap H, Hlo;    // offset matrices of the level (MMA B)
+  double* lc;            // local expansions (level base, or all boxes with map)
+  double* lc2;           // local expansions of level l2 (base)
+  const int* map;        // adaptive: window cell -> box; null for uniform levels
+  float scale, scale2;   // exact powers of two (shared offset matrices)
   int l, BX, BY, BZ, ntx, nty, first_block, Hx, Hy, Hz;
   int l2;
 };
 constexpr int kTcMaxLevels = 10;
 struct TcParams {
   TcLevel lev[kTcMaxLevels];
-  int nlev, nj, jchunks, MP;
+  int nlev, nj, jchunks, ksteps_last;
+  int nc, npt, ncls;   // columns per block, rows per offset matrix, stacked classes
+  int nstages, stage_bytes;
+  int accumulate;      // add into the local expansions (else store)
+  long long wait_cycles;  // limit of the pipeline's mbarrier waits
   int* err;
 };
 
-template <typename F, int NPASS>
+// pipeline wait: the default bounded wait, or (SHORTW, the instantiation that
+// tests run with a shortened limit) the polling wait of mbar_wait_short
+template <bool SHORTW>
+__device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, int* err, long long lim) {
+  return SHORTW ? tc::mbar_wait_short(bar, parity, err, lim) : tc::mbar_wait(bar, parity, err);
+}
+
+template <typename F, int NPASS, bool SHORTW>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const __grid_constant__ TcParams prm) {
+  using C = Cfg<NPASS>;
   int li = 0;
   while (li + 1 < prm.nlev && (int)blockIdx.x >= prm.lev[li + 1].first_block) ++li;
   const TcLevel& LV = prm.lev[li];
-  const CUtensorMap* tmA = &LV.A;
-  const CUtensorMap* tmAlo = &LV.Alo;
-  const CUtensorMap* tmB = &LV.B;
-  const CUtensorMap* tmBlo = &LV.Blo;
-  const int l = LV.l, nj = prm.nj, jchunks = prm.jchunks, MP = prm.MP;
+  const int l = LV.l, nj = prm.nj, jchunks = prm.jchunks;
+  const int nc = prm.nc, npt = prm.npt, ncls = prm.ncls;
+  const int ntot = nc * ncls;  // MMA N
+  const int ns = prm.nstages, sbytes = prm.stage_bytes;
+  const int btile = ntot * C::kRowBytes;  // offset-matrix bytes of one stage half
   const int BX = LV.BX, BY = LV.BY, BZ = LV.BZ, ntx = LV.ntx, nty = LV.nty;
-  double* __restrict__ lc = LV.lc;
   int* __restrict__ err = prm.err;
-  using C = Cfg<NPASS>;
+  const long long wlim = prm.wait_cycles;
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::kStages * C::kStage);
-  uint64_t* empty = full + C::kStages;
-  uint64_t* accf = empty + C::kStages;  // [kNBuf] accumulator filled (MMA commit)
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + ns * sbytes);
+  uint64_t* empty = full + kMaxStages;
+  uint64_t* accf = empty + kMaxStages;  // [kNBuf] accumulator filled (MMA commit)
   uint64_t* acce = accf + kNBuf;        // [kNBuf] accumulator drained (warp arrivals)
   uint64_t* drainb = acce + kNBuf;      // all MMAs of this CTA finished
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drainb + 1);
+  int* bad = reinterpret_cast<int*>(tslot + 1);  // a draining warp gave up
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lb = (int)blockIdx.x - LV.first_block;
-  const int pi = lb & 7, mt = blockIdx.y;
-  const int tile = lb >> 3;
+  const int ngrp = 8 / ncls;
+  const int pi0 = (lb % ngrp) * ncls;  // classes pi0 .. pi0 + ncls - 1
+  const int tile = lb / ngrp;
+  const int cb = blockIdx.y;  // column block
   const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
   const int X0 = tx * BX, Y0 = ty * BY, Z0 = tz * BZ;
   const int l2 = LV.l2, H2 = l2 ? 1 << (l2 - 1) : 0;
-  const int N1 = BX * BY * BZ;                        // rows of the primary tile
-  const int N = N1 + H2 * H2 * H2;                    // rows the TMA boxes fill
-  const int Nmma = N < 16 ? 16 : (N + 15) / 16 * 16;  // MMA width; extra columns discarded
-  const int nl = 1 << l, Hx = LV.Hx, Hy = LV.Hy, Hz = LV.Hz;
-  const int* __restrict__ map = LV.map;
-  const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
-  const uint32_t bytesA = C::kTileA, bytesB = (uint32_t)N * C::kRowBytes;
-  const uint32_t stage_tx = (NPASS == 1 ? 1u : 2u) * (bytesA + bytesB);
+  const int N1 = BX * BY * BZ;      // source rows of the primary tile
+  const int NR = N1 + H2 * H2 * H2;  // rows the TMA boxes fill (<= 128)
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::kStages; ++s) {
+    for (int s = 0; s < ns; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
@@ -280,9 +327,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::mbar_init(&acce[bf], kEpiWarps);
     }
     tc::mbar_init(drainb, 1);
+    *bad = 0;
     tc::fence_mbar_init();
   }
-  if (warp == 0) tc::tmem_alloc(tslot, kBufCols * kNBuf);
+  if (warp == 0) tc::tmem_alloc(tslot, kTmemCols);
+
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -290,93 +339,126 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (warp == kEpiWarps && lane == 0) {
     // ---------------- TMA producer ----------------
-    int kk = 0;
-    int last_round[C::kStages];
-    for (int s = 0; s < C::kStages; ++s) last_round[s] = -1;
+    // stage s and the parity ph of its current round advance together (no
+    // division in the loop); a stage is refilled once its previous round's
+    // MMAs have committed
+    const uint32_t bytesS = (uint32_t)NR * C::kRowBytes;
+    const uint32_t stage_tx = (uint32_t)C::kHalves * (bytesS + (uint32_t)btile);
+    constexpr int kElems = C::kRowBytes / (int)sizeof(typename F::T);
+    int s = 0, kk = 0;
+    uint32_t ph = 0;
+    unsigned char* st = sm;
+    int last_par[kMaxStages];  // parity of the last round issued into a stage (-1: none)
+    for (int q = 0; q < kMaxStages; ++q) last_par[q] = -1;
     bool ok = true;
     for (int c = 0; c < 216 && ok; ++c) {
-      int sg, dx, dy, dz, hidx;
-      if (!combo(c, px, py, pz, sg, dx, dy, dz, hidx)) continue;
+      const Combo k = combo(c);
+      if (!any_far(k, pi0, ncls)) continue;
+      int hidx[8];
+      for (int u = 0; u < ncls; ++u) {
+        bool f;
+        hidx[u] = offset_of(k, pi0 + u, &f) * npt + cb * nc;
+      }
       for (int ch = 0; ch < jchunks; ++ch, ++kk) {
-        const int s = kk % C::kStages, r = kk / C::kStages;
-        if (r > 0 && !tc::mbar_wait(&empty[s], (r - 1) & 1, err)) {
+        if (kk >= ns && !pwait<SHORTW>(&empty[s], ph ^ 1u, err, wlim)) {
           ok = false;
           break;
         }
-        unsigned char* st = sm + s * C::kStage;
         tc::mbar_expect_tx(&full[s], stage_tx);
-        last_round[s] = r;
-        // element offset of this K chunk (a multiple of 64 bytes)
-        const int kc = ch * (C::kRowBytes / (int)sizeof(typename F::T));
-        tc::tma_load_2d(st, tmA, &full[s], kc, hidx * MP + mt * kBM);
-        tc::tma_load_5d(st + C::kTileA, tmB, &full[s], kc, X0 + dx, Y0 + dy, Z0 + dz, sg);
-        if (l2)  // N1 is a multiple of 8 rows: the second box starts on a swizzle atom
-          tc::tma_load_5d(st + C::kTileA + N1 * C::kRowBytes, &LV.B2, &full[s], kc, dx, dy, dz,
-                          sg);
-        if (NPASS == 3) {
-          tc::tma_load_2d(st + C::kTileA + C::kTileB, tmAlo, &full[s], kc, hidx * MP + mt * kBM);
-          tc::tma_load_5d(st + 2 * C::kTileA + C::kTileB, tmBlo, &full[s], kc, X0 + dx, Y0 + dy,
-                          Z0 + dz, sg);
-          if (l2)
-            tc::tma_load_5d(st + 2 * C::kTileA + C::kTileB + N1 * C::kRowBytes, &LV.B2lo,
-                            &full[s], kc, dx, dy, dz, sg);
+        last_par[s] = (int)ph;
+        const int kc = ch * kElems;  // element offset of this K chunk
+#pragma unroll
+        for (int hf = 0; hf < C::kHalves; ++hf) {
+          unsigned char* sh = st + hf * (C::kTileS + btile);
+          tc::tma_load_5d(sh, hf ? &LV.Slo : &LV.S, &full[s], kc, X0 + k.dx, Y0 + k.dy,
+                          Z0 + k.dz, k.sg);
+          if (l2)  // N1 is a multiple of 8 rows: the second box starts on a swizzle atom
+            tc::tma_load_5d(sh + N1 * C::kRowBytes, hf ? &LV.S2lo : &LV.S2, &full[s], kc, k.dx,
+                            k.dy, k.dz, k.sg);
+          for (int u = 0; u < ncls; ++u)
+            tc::tma_load_2d(sh + C::kTileS + u * nc * C::kRowBytes, hf ? &LV.Hlo : &LV.H,
+                            &full[s], kc, hidx[u]);
+        }
+        if (++s == ns) {
+          s = 0;
+          ph ^= 1u;
+          st = sm;
+        } else {
+          st += sbytes;
         }
       }
     }
     if (!ok) {  // drain copies still in flight before the CTA leaves
-      for (int s = 0; s < C::kStages; ++s)
-        if (last_round[s] >= 0) {
+      for (int q = 0; q < ns; ++q)
+        if (last_par[q] >= 0) {
           const long long t0 = clock64();
-          while (!tc::mbar_try_wait(&full[s], last_round[s] & 1) &&
+          while (!tc::mbar_try_wait(&full[q], (uint32_t)last_par[q]) &&
                  clock64() - t0 < tc::kWaitCycles) {
           }
         }
     }
   } else if (warp == kEpiWarps + 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    const uint32_t id = tc::idesc(F::kIdesc, kBM, Nmma);
-    int kk = 0, g = 0;
+    // everything between two MMAs is kept to a few adds: descriptors advance
+    // by the stage size, the stage index and parity by increments
+    const uint32_t id = tc::idesc(F::kIdesc, kBM, ntot);
+    const uint64_t d0 = C::desc(tc::smem_u32(sm));
+    const uint64_t ob = (uint64_t)(C::kTileS >> 4);
+    const uint64_t oalo = (uint64_t)((C::kTileS + btile) >> 4);
+    const uint64_t oblo = (uint64_t)((2 * C::kTileS + btile) >> 4);
+    const uint64_t dstep = (uint64_t)(sbytes >> 4);
+    const int kl = prm.ksteps_last;
+    int s = 0;
+    uint32_t ph = 0;
+    uint64_t da = d0;
+    int g = 0;  // offsets issued: buffer g & 1, its (g >> 1)-th use
     bool ok = true;
     for (int c = 0; c < 216 && ok; ++c) {
-      int sg, dx, dy, dz, hidx;
-      if (!combo(c, px, py, pz, sg, dx, dy, dz, hidx)) continue;
-      const int bf = g % kNBuf;
-      if (g >= kNBuf && !tc::mbar_wait(&acce[bf], ((g / kNBuf) - 1) & 1, err)) {
-        ok = false;
+      const Combo k = combo(c);
+      if (!any_far(k, pi0, ncls)) continue;
+      const int bf = g & 1;
+      if (g >= kNBuf && !pwait<SHORTW>(&acce[bf], ((g >> 1) - 1) & 1, err, wlim)) {
+        ok = false;  // the buffer's previous offset has not been drained
         break;
       }
       tc::fence_after();
-      const uint32_t dacc = tmem + (uint32_t)(bf * kBufCols);
-      for (int ch = 0; ch < jchunks; ++ch, ++kk) {
-        const int s = kk % C::kStages, r = kk / C::kStages;
-        if (!tc::mbar_wait(&full[s], r & 1, err)) {
+      const uint32_t dacc = tmem + (uint32_t)(bf * kMaxN);
+      for (int ch = 0; ch < jchunks; ++ch) {
+        if (!pwait<SHORTW>(&full[s], ph, err, wlim)) {
           ok = false;
           break;
         }
         tc::fence_after();
-        const uint32_t st = tc::smem_u32(sm + s * C::kStage);
-        const uint64_t a = C::desc(st), b = C::desc(st + C::kTileA);
-        const uint64_t alo = C::desc(st + C::kTileA + C::kTileB);
-        const uint64_t blo = C::desc(st + 2 * C::kTileA + C::kTileB);
+        const int nk = ch == jchunks - 1 ? kl : C::kKSteps;
 #pragma unroll
-        for (int k = 0; k < C::kKSteps; ++k) {
-          // one MMA consumes 32 bytes of K (8 tf32 or 16 bf16) inside the swizzle atom
-          const uint64_t adv = (uint64_t)(k * 32) >> 4;
-          if (F::kF16) {
-            tc::mma_f16(dacc, a + adv, b + adv, id, (ch | k) != 0);
-            if (NPASS == 3) {
-              tc::mma_f16(dacc, a + adv, blo + adv, id, 1);
-              tc::mma_f16(dacc, alo + adv, b + adv, id, 1);
-            }
-          } else {
-            tc::mma_tf32(dacc, a + adv, b + adv, id, (ch | k) != 0);
-            if (NPASS == 3) {
-              tc::mma_tf32(dacc, a + adv, blo + adv, id, 1);
-              tc::mma_tf32(dacc, alo + adv, b + adv, id, 1);
+        for (int ks = 0; ks < C::kKSteps; ++ks) {
+          if (ks < nk) {
+            // one MMA consumes 32 bytes of K (8 tf32 or 16 bf16) inside the swizzle atom
+            const uint64_t a = da + (uint64_t)(ks * 2);
+            const uint32_t acc = (ch | ks) != 0;
+            if (F::kF16) {
+              tc::mma_f16(dacc, a, a + ob, id, acc);
+              if (NPASS == 3) {
+                tc::mma_f16(dacc, a, a + oblo, id, 1);
+                tc::mma_f16(dacc, a + oalo, a + ob, id, 1);
+              }
+            } else {
+              tc::mma_tf32(dacc, a, a + ob, id, acc);
+              if (NPASS == 3) {
+                tc::mma_tf32(dacc, a, a + oblo, id, 1);
+                tc::mma_tf32(dacc, a + oalo, a + ob, id, 1);
+              }
             }
           }
         }
         tc::mma_commit(&empty[s]);
+        if (++s == ns) {
+          s = 0;
+          ph ^= 1u;
+          da = d0;
+        } else {
+          da += dstep;
+        }
       }
       if (!ok) break;
       tc::mma_commit(&accf[bf]);
@@ -393,33 +475,40 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else if (warp < kEpiWarps) {
     // ---------------- drain TMEM into float registers ----------------
-    constexpr int kCols = kMaxN / (kEpiWarps / 4);       // columns per draining warp
-    const int quad = warp & 3, c0 = (warp >> 2) * kCols;  // TMEM lanes / first column
-    float sum[kCols];
+    const int quad = warp & 3;
+    const int cw = (ntot / (kEpiWarps / 4) + 7) / 8 * 8;  // columns of this warp's group
+    const int c0 = (warp >> 2) * cw;
+    float sum[kColsPerThread];
 #pragma unroll
-    for (int j = 0; j < kCols; ++j) sum[j] = 0.f;
+    for (int j = 0; j < kColsPerThread; ++j) sum[j] = 0.f;
     bool ok = true;
     int g = 0;
     for (int c = 0; c < 216; ++c) {
-      int sg, dx, dy, dz, hidx;
-      if (!combo(c, px, py, pz, sg, dx, dy, dz, hidx)) continue;
-      const int bf = g % kNBuf;
-      if (!tc::mbar_wait(&accf[bf], (g / kNBuf) & 1, err)) {
+      if (!any_far(combo(c), pi0, ncls)) continue;
+      const int bf = g & 1;
+      if (!pwait<SHORTW>(&accf[bf], (g >> 1) & 1, err, wlim)) {
         ok = false;
         break;
       }
       tc::fence_after();
       const uint32_t base =
-          tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bf * kBufCols + c0);
-      // groups of 16 columns, each loaded then summed (16 registers in flight)
+          tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bf * kMaxN + c0);
+      // pairs of 8-column groups: loaded, then summed (16 registers in flight)
 #pragma unroll
-      for (int gq = 0; gq < kCols / 16; ++gq) {
-        if (c0 + 16 * gq < N) {
-          uint32_t r0[16];
-          tc::tmem_ld16_nowait(base + (uint32_t)(16 * gq), r0);
-          tc::tmem_wait();
+      for (int gp = 0; gp < kColsPerThread / 16; ++gp) {
+        uint32_t r0[8], r1[8];
+        const bool v0 = 16 * gp < cw && c0 + 16 * gp < ntot;
+        const bool v1 = 16 * gp + 8 < cw && c0 + 16 * gp + 8 < ntot;
+        if (v0) tc::tmem_ld8_nowait(base + (uint32_t)(16 * gp), r0);
+        if (v1) tc::tmem_ld8_nowait(base + (uint32_t)(16 * gp + 8), r1);
+        if (v0 || v1) tc::tmem_wait();
+        if (v0) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) sum[16 * gq + j] += __uint_as_float(r0[j]);
+          for (int j = 0; j < 8; ++j) sum[16 * gp + j] += __uint_as_float(r0[j]);
+        }
+        if (v1) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) sum[16 * gp + 8 + j] += __uint_as_float(r1[j]);
         }
       }
       tc::fence_before();
@@ -427,33 +516,64 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (lane == 0) mbar_arrive(&acce[bf]);
       ++g;
     }
-    ok = ok && !(*(volatile int*)err & 2);
-    if (ok) {
-      const int i = mt * kBM + quad * 32 + lane;
+    // every draining warp passes both barriers below, whatever its status, so
+    // that none waits for a warp that left; the decision to write is taken
+    // from shared memory after the first barrier, the same for all
+    if (!ok || (*(volatile int*)err & 2)) atomicOr(bad, 1);
+    drain_sync();
+    const bool good = *(volatile int*)bad == 0;
+    // every MMA has finished and every TMA copy has been consumed: the stage
+    // memory is free for the staging of the sums, [row][column] with an odd
+    // pitch (the 32 lanes of a warp write 32 rows of one column)
+    float* stg = reinterpret_cast<float*>(sm);
+    const int pitch = ntot + 1;
+    if (good) {
+      const int row = quad * 32 + lane;
 #pragma unroll
-      for (int jn = 0; jn < kCols; ++jn) {
-        const int n = c0 + jn;
-        const float sv = sum[jn];
+      for (int j = 0; j < kColsPerThread; ++j)
+        if (j < cw && c0 + j < ntot) stg[row * pitch + c0 + j] = sum[j];
+    }
+    drain_sync();
+    if (good) {
+      const int nv = min(nc, nj - cb * nc);  // valid columns of this block
+      const int nl = 1 << l, Hx = LV.Hx, Hy = LV.Hy, Hz = LV.Hz;
+      const int* __restrict__ map = LV.map;
+      const int tot = NR * ncls * nv;
+      for (int e = threadIdx.x; e < tot; e += kEpiWarps * 32) {
+        const int i = e % nv, rc = e / nv;
+        const int u = rc % ncls, n = rc / ncls;
+        const int pi = pi0 + u;
+        const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
+        const float v = stg[n * pitch + u * nc + i];
+        double* dst = nullptr;
+        double scale = 1.0;
         if (n < N1) {
           const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
-          if (x < Hx && y < Hy && z < Hz && i < nj) {
+          if (x < Hx && y < Hy && z < Hz) {
             const int64_t t =
                 map ? (int64_t)map[(((size_t)pi * Hz + z) * Hy + y) * Hx + x]
                     : ((int64_t)(2 * z + pz) * nl + (2 * y + py)) * nl + (2 * x + px);
-            if (t >= 0) lc[t * nj + i] += (double)(sv * LV.scale);
+            if (t >= 0) dst = LV.lc + t * nj + cb * nc + i;
+            scale = LV.scale;
           }
-        } else if (n < N && i < nj) {  // the riding level's targets
+        } else {  // the riding level's targets
           const int n2 = n - N1, nl2 = 2 * H2;
           const int x = n2 % H2, y = (n2 / H2) % H2, z = n2 / (H2 * H2);
           const int64_t t = ((int64_t)(2 * z + pz) * nl2 + (2 * y + py)) * nl2 + (2 * x + px);
-          LV.lc2[t * nj + i] += (double)(sv * LV.scale2);
+          dst = LV.lc2 + t * nj + cb * nc + i;
+          scale = LV.scale2;
+        }
+        if (dst) {
+          const double val = (double)(v * (float)scale);
+          if (prm.accumulate) *dst += val;
+          else *dst = val;
         }
       }
     }
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kBufCols * kNBuf);
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
 }
 
 // ---- host side: tensor maps ---------------------------------------------------
@@ -488,23 +608,52 @@ bool make_map(CUtensorMap* m, void* base, int rank, const cuuint64_t* dims,
          CUDA_SUCCESS;
 }
 
-// Target tile of a parent grid Hx x Hy x Hz: up to 16 x 4 x 4 (or 8 x 8 x 4)
-// = 256 parents, x fastest.
+// Target tile of a parent grid Hx x Hy x Hz: up to 8 x 4 x 4 = 128 parents,
+// x fastest.
 void tile_shape(int Hx, int Hy, int Hz, TcLevel* v) {
-  v->BX = std::min(16, Hx);
+  v->BX = std::min(8, Hx);
   v->BZ = std::min(4, Hz);
-  v->BY = std::min(Hy, kMaxN / (v->BX * v->BZ));
+  v->BY = std::min(Hy, kBM / (v->BX * v->BZ));
   v->ntx = (Hx + v->BX - 1) / v->BX;
   v->nty = (Hy + v->BY - 1) / v->BY;
 }
 
+// the launch parameters that do not depend on the level
+template <typename F, int NPASS>
+bool common_params(const fmm_plan_s* P, const Workspace& ws, TcParams* prm) {
+  using C = Cfg<NPASS>;
+  const TcShape sh = tc_shape(P->pd.nj, P->desc.precision);
+  std::memset(prm, 0, sizeof(*prm));
+  prm->nj = P->pd.nj;
+  const int row = C::kRowBytes / (int)sizeof(typename F::T);  // elements per K chunk
+  if (sh.row_bytes != C::kRowBytes || ws.tc_jp != sh.jp || ws.tc_mp != sh.npt) return false;
+  prm->jchunks = ws.tc_jp / row;
+  const int kstep = 32 / (int)sizeof(typename F::T);  // elements of K per MMA
+  const int ksteps = (P->pd.nj + kstep - 1) / kstep;
+  prm->ksteps_last = ksteps - (prm->jchunks - 1) * C::kKSteps;
+  prm->nc = sh.nc;
+  prm->npt = sh.npt;
+  prm->ncls = sh.ncls;
+  prm->stage_bytes = C::stage_bytes(sh.nc * sh.ncls);
+  prm->nstages = std::min(kMaxStages, (kSmemCap - 1024 - 256) / prm->stage_bytes);
+  prm->wait_cycles = P->tc_wait_cycles > 0 ? P->tc_wait_cycles : tc::kWaitCycles;
+  prm->err = &ws.geom->flag;
+  // the staging of the sums reuses the stages
+  if (kBM * (sh.nc * sh.ncls + 1) * (int)sizeof(float) > prm->nstages * prm->stage_bytes)
+    return false;
+  return prm->nstages >= 2 && prm->ksteps_last >= 1 && prm->ksteps_last <= C::kKSteps;
+}
+
+template <typename F, int NPASS>
+size_t smem_bytes(const TcParams& prm) {
+  return 1024 + (size_t)prm.nstages * prm.stage_bytes + 256;
+}
+
 // offset matrices A_h (hi and lo) of a uniform tree from the derivative tables
 template <typename F, int NPASS>
-void build_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st) {
+void build_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int tlev) {
   using T = typename F::T;
   const PlanDev& pd = P->pd;
-  const bool shared_t = pd.kernel != FMM_KERNEL_YUKAWA;  // homogeneous G
-  const int tlev = shared_t ? 1 : (P->desc.levels - 1);
   T* thi0 = static_cast<T*>(ws.tc_tmat[0]);
   T* tlo = NPASS == 3 ? static_cast<T*>(ws.tc_tmat[1]) : nullptr;
   const size_t sm = 2 * sizeof(T) * pd.nh;
@@ -513,35 +662,87 @@ void build_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st) {
   k_build_tmat<3, F><<<dim3(343, tlev), 256, sm, st>>>(pd, ws.htab, ws.tc_mp, ws.tc_jp, thi0, tlo);
 }
 
+// tensor maps of the offset matrices of table level ti
 template <typename F, int NPASS>
-cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
-                           bool tables_ready) {
+bool offset_maps(const Workspace& ws, int ti, const TcParams& prm, TcLevel* v) {
   using C = Cfg<NPASS>;
-  const PlanDev& pd = P->pd;
-  const int L = P->desc.levels;
-  const int nj = pd.nj, JP = ws.tc_jp, MP = ws.tc_mp;
-  const int noff = 343;
-  const bool shared_t = pd.kernel != FMM_KERNEL_YUKAWA;  // homogeneous G
-  const int tlev = shared_t ? 1 : (L - 1);
   using T = typename F::T;
   const size_t esz = sizeof(T);
   const CUtensorMapDataType dt =
       F::kF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const int JP = ws.tc_jp, NPT = ws.tc_mp, row = C::kRowBytes / (int)esz;
+  const size_t per = (size_t)343 * NPT * JP;
+  cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)343 * NPT};
+  cuuint64_t sA[1] = {(cuuint64_t)JP * esz};
+  cuuint32_t bA[2] = {(cuuint32_t)row, (cuuint32_t)prm.nc};
+  T* thi = static_cast<T*>(ws.tc_tmat[0]) + (size_t)ti * per;
+  if (!make_map(&v->H, thi, 2, dA, sA, bA, dt, C::kRowBytes)) return false;
+  v->Hlo = v->H;
+  if (NPASS == 3) {
+    T* tlo = static_cast<T*>(ws.tc_tmat[1]) + (size_t)ti * per;
+    if (!make_map(&v->Hlo, tlo, 2, dA, sA, bA, dt, C::kRowBytes)) return false;
+  }
+  return true;
+}
+
+// tensor map of parity-split multipoles Bpar[8][Hz][Hy][Hx][JP], box of
+// (bx, by, bz) parents
+template <typename F, int NPASS>
+bool source_map(CUtensorMap* m, void* base, int JP, int Hx, int Hy, int Hz, int bx, int by,
+                int bz) {
+  using C = Cfg<NPASS>;
+  const size_t esz = sizeof(typename F::T);
+  const CUtensorMapDataType dt =
+      F::kF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const int row = C::kRowBytes / (int)esz;
+  cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)Hx, (cuuint64_t)Hy, (cuuint64_t)Hz, 8};
+  cuuint64_t sB[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * Hx,
+                      (cuuint64_t)JP * esz * Hx * Hy, (cuuint64_t)JP * esz * Hx * Hy * Hz};
+  cuuint32_t bB[5] = {(cuuint32_t)row, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+  return make_map(m, base, 5, dB, sB, bB, dt, C::kRowBytes);
+}
+
+template <typename F, int NPASS>
+cudaError_t launch_contraction(const fmm_plan_s* P, const TcParams& prm, int nb, cudaStream_t st,
+                               bool timed) {
+  const size_t sm = smem_bytes<F, NPASS>(prm);
+  const TcShape sh = tc_shape(P->pd.nj, P->desc.precision);
+  const dim3 grid(nb, sh.nchunk);
+  // per call: the attribute belongs to the current device's context
+  if (prm.wait_cycles < tc::kWaitCycles) {  // a test's shortened waits
+    cudaFuncSetAttribute(k_m2l_tc<F, NPASS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    if (timed) mark_contraction(P, 0, st);
+    k_m2l_tc<F, NPASS, true><<<grid, kTcThreads, sm, st>>>(prm);
+  } else {
+    cudaFuncSetAttribute(k_m2l_tc<F, NPASS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    if (timed) mark_contraction(P, 0, st);
+    k_m2l_tc<F, NPASS, false><<<grid, kTcThreads, sm, st>>>(prm);
+  }
+  if (timed) mark_contraction(P, 1, st);
+  return cudaGetLastError();
+}
+
+template <typename F, int NPASS>
+cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
+                           bool tables_ready) {
+  const PlanDev& pd = P->pd;
+  const int L = P->desc.levels;
+  const int nj = pd.nj, JP = ws.tc_jp;
+  const bool shared_t = kernel_homogeneous(pd.kernel);  // G(s h) = s^deg G(h)
+  const int tlev = shared_t ? 1 : (L - 1);
+  using T = typename F::T;
   T* bhi0 = static_cast<T*>(ws.tc_bpar[0]);
-  T* thi0 = static_cast<T*>(ws.tc_tmat[0]);
   T* blo = NPASS == 3 ? static_cast<T*>(ws.tc_bpar[1]) : nullptr;
-  T* tlo = NPASS == 3 ? static_cast<T*>(ws.tc_tmat[1]) : nullptr;
   LevOff lo;
   for (int l = 0; l <= FMM_MAX_LEVELS; ++l) lo.o[l] = l <= L + 1 ? ws.lev_off[l] : 0;
   k_pack_beta<F><<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, bhi0, blo);
-  if (!tables_ready) build_tables<F, NPASS>(P, ws, st);
+  if (!tables_ready) build_tables<F, NPASS>(P, ws, st, tlev);
   TcParams prm;
-  std::memset(&prm, 0, sizeof(prm));
-  prm.nj = nj;
-  const int row = C::kRowBytes / (int)esz;  // elements per K chunk
-  prm.jchunks = JP / row;
-  prm.MP = MP;
-  prm.err = &ws.geom->flag;
+  if (!common_params<F, NPASS>(P, ws, &prm)) return cudaErrorInvalidValue;
+  prm.accumulate = 0;  // every coefficient of levels 2..L is written exactly once
+  const int ngrp = 8 / prm.ncls;
   int nb = 0;
   // largest level first: its tiles start earliest; with shared offset
   // matrices level 2 rides along in level 3's CTAs
@@ -554,58 +755,35 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
     tile_shape(H, H, H, &v);
     const int ntz = (H + v.BZ - 1) / v.BZ;
     v.first_block = nb;
-    nb += v.ntx * v.nty * ntz * 8;
+    nb += v.ntx * v.nty * ntz * ngrp;
     v.lc = ws.lc + ws.lev_off[l] * nj;
     v.map = nullptr;
     v.Hx = v.Hy = v.Hz = H;
-    const int ti = shared_t ? 0 : l - 2;
-    T* th = thi0 + (size_t)ti * noff * MP * JP;
-    T* bh = bhi0 + ws.lev_off[l] * JP;
     v.scale = 1.0f;
     if (shared_t) {  // Ht_l = Ht_2 * (s_2/s_l)^{-deg}: deg -1 (Laplace), +1 (biharmonic)
       const int k = l - 2;
       v.scale = pd.kernel == FMM_KERNEL_LAPLACE ? std::ldexp(1.0f, k) : std::ldexp(1.0f, -k);
     }
-    cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
-    cuuint64_t sA[1] = {(cuuint64_t)JP * esz};
-    cuuint32_t bA[2] = {(cuuint32_t)row, (cuuint32_t)kBM};
-    cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)H, 8};
-    cuuint64_t sB[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * H,
-                        (cuuint64_t)JP * esz * H * H, (cuuint64_t)JP * esz * H * H * H};
-    cuuint32_t bB[5] = {(cuuint32_t)row, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ, 1};
-    const int rb = C::kRowBytes;
-    if (!make_map(&v.A, th, 2, dA, sA, bA, dt, rb)) return cudaErrorInvalidValue;
-    if (!make_map(&v.B, bh, 5, dB, sB, bB, dt, rb)) return cudaErrorInvalidValue;
-    v.Alo = v.A;
-    v.Blo = v.B;
-    if (NPASS == 3) {
-      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt, rb))
-        return cudaErrorInvalidValue;
-      if (!make_map(&v.Blo, blo + ws.lev_off[l] * JP, 5, dB, sB, bB, dt, rb))
-        return cudaErrorInvalidValue;
-    }
+    if (!offset_maps<F, NPASS>(ws, shared_t ? 0 : l - 2, prm, &v)) return cudaErrorInvalidValue;
+    if (!source_map<F, NPASS>(&v.S, bhi0 + ws.lev_off[l] * JP, JP, H, H, H, v.BX, v.BY, v.BZ))
+      return cudaErrorInvalidValue;
+    v.Slo = v.S;
+    if (NPASS == 3 &&
+        !source_map<F, NPASS>(&v.Slo, blo + ws.lev_off[l] * JP, JP, H, H, H, v.BX, v.BY, v.BZ))
+      return cudaErrorInvalidValue;
     if (l == 3 && lmin == 3) {  // level 2: 2 x 2 x 2 parents after level 3's 64
       v.l2 = 2;
       v.lc2 = ws.lc + ws.lev_off[2] * nj;
       v.scale2 = 1.0f;
-      cuuint64_t d2[5] = {(cuuint64_t)JP, 2, 2, 2, 8};
-      cuuint64_t s2[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * 2,
-                          (cuuint64_t)JP * esz * 4, (cuuint64_t)JP * esz * 8};
-      cuuint32_t b2[5] = {(cuuint32_t)row, 2, 2, 2, 1};
-      if (!make_map(&v.B2, bhi0 + ws.lev_off[2] * JP, 5, d2, s2, b2, dt, rb))
+      if (!source_map<F, NPASS>(&v.S2, bhi0 + ws.lev_off[2] * JP, JP, 2, 2, 2, 2, 2, 2))
         return cudaErrorInvalidValue;
-      v.B2lo = v.B2;
+      v.S2lo = v.S2;
       if (NPASS == 3 &&
-          !make_map(&v.B2lo, blo + ws.lev_off[2] * JP, 5, d2, s2, b2, dt, rb))
+          !source_map<F, NPASS>(&v.S2lo, blo + ws.lev_off[2] * JP, JP, 2, 2, 2, 2, 2, 2))
         return cudaErrorInvalidValue;
     }
   }
-  // per call: the attribute belongs to the current device's context
-  cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-  mark_contraction(P, 0, st);
-  k_m2l_tc<F, NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
-  mark_contraction(P, 1, st);
-  return cudaGetLastError();
+  return launch_contraction<F, NPASS>(P, prm, nb, st, true);
 }
 
 // ---- adaptive trees: every level packed into a dense window ----------------
@@ -656,18 +834,12 @@ __global__ void k_apack(ATree t, int l, const double* __restrict__ mp, int nj, i
 template <typename F, int NPASS>
 cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
                          cudaStream_t st, int* nl, unsigned* done) {
-  using C = Cfg<NPASS>;
   using T = typename F::T;
   const PlanDev& pd = P->pd;
-  const int nj = pd.nj, JP = ws.tc_jp, MP = ws.tc_mp;
-  const int noff = 343;
-  const bool shared_t = pd.kernel != FMM_KERNEL_YUKAWA;  // homogeneous G
+  const int nj = pd.nj, JP = ws.tc_jp;
+  const bool shared_t = kernel_homogeneous(pd.kernel);  // G(s h) = s^deg G(h)
   const int tlev = shared_t ? 1 : (t.maxlev - 1);
   const size_t esz = sizeof(T);
-  const CUtensorMapDataType dt =
-      F::kF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  T* thi0 = static_cast<T*>(ws.tc_tmat[0]);
-  T* tlo = NPASS == 3 ? static_cast<T*>(ws.tc_tmat[1]) : nullptr;
   // coordinate bounds of every level (one synchronisation)
   const int nbnd = 6 * (t.maxlev + 1);
   k_alevel_bounds_init<<<1, 128, 0, st>>>(ws.tc_bounds, nbnd);
@@ -678,20 +850,12 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
   cudaMemcpyAsync(bnd, ws.tc_bounds, sizeof(int) * nbnd, cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return e;
-  {
-    const size_t sm = 2 * sizeof(T) * pd.nh;
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(k_build_tmat<3, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_build_tmat<3, F><<<dim3(noff, tlev), 256, sm, st>>>(pd, ws.htab, MP, JP, thi0, tlo);
-    ++*nl;
-  }
+  build_tables<F, NPASS>(P, ws, st, tlev);
+  ++*nl;
   TcParams prm;
-  std::memset(&prm, 0, sizeof(prm));
-  prm.nj = nj;
-  const int row = C::kRowBytes / (int)esz;  // elements per K chunk
-  prm.jchunks = JP / row;
-  prm.MP = MP;
-  prm.err = &ws.geom->flag;
+  if (!common_params<F, NPASS>(P, ws, &prm)) return cudaErrorInvalidValue;
+  prm.accumulate = 1;  // P2L over X adds into the same expansions
+  const int ngrp = 8 / prm.ncls;
   int nb = 0;
   char* arena = static_cast<char*>(ws.tc_arena);
   size_t used = 0;
@@ -727,42 +891,27 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
     tile_shape(H[0], H[1], H[2], &v);
     const int ntz = (H[2] + v.BZ - 1) / v.BZ;
     v.first_block = nb;
-    nb += v.ntx * v.nty * ntz * 8;
+    nb += v.ntx * v.nty * ntz * ngrp;
     v.lc = ws.lc;
     v.map = map;
-    const int ti = shared_t ? 0 : l - 2;
     v.scale = 1.0f;
     if (shared_t) {
       const int k = l - 2;
       v.scale = pd.kernel == FMM_KERNEL_LAPLACE ? std::ldexp(1.0f, k) : std::ldexp(1.0f, -k);
     }
-    cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)noff * MP};
-    cuuint64_t sA[1] = {(cuuint64_t)JP * esz};
-    cuuint32_t bA[2] = {(cuuint32_t)row, (cuuint32_t)kBM};
-    cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)H[0], (cuuint64_t)H[1], (cuuint64_t)H[2], 8};
-    cuuint64_t sB[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * H[0],
-                        (cuuint64_t)JP * esz * H[0] * H[1],
-                        (cuuint64_t)JP * esz * H[0] * H[1] * H[2]};
-    cuuint32_t bB[5] = {(cuuint32_t)row, (cuuint32_t)v.BX, (cuuint32_t)v.BY, (cuuint32_t)v.BZ, 1};
-    const int rb = C::kRowBytes;
-    if (!make_map(&v.A, thi0 + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt, rb))
+    if (!offset_maps<F, NPASS>(ws, shared_t ? 0 : l - 2, prm, &v)) return cudaErrorInvalidValue;
+    if (!source_map<F, NPASS>(&v.S, bhi, JP, H[0], H[1], H[2], v.BX, v.BY, v.BZ))
       return cudaErrorInvalidValue;
-    if (!make_map(&v.B, bhi, 5, dB, sB, bB, dt, rb)) return cudaErrorInvalidValue;
-    v.Alo = v.A;
-    v.Blo = v.B;
-    if (NPASS == 3) {
-      if (!make_map(&v.Alo, tlo + (size_t)ti * noff * MP * JP, 2, dA, sA, bA, dt, rb))
-        return cudaErrorInvalidValue;
-      if (!make_map(&v.Blo, blo, 5, dB, sB, bB, dt, rb)) return cudaErrorInvalidValue;
-    }
+    v.Slo = v.S;
+    if (NPASS == 3 && !source_map<F, NPASS>(&v.Slo, blo, JP, H[0], H[1], H[2], v.BX, v.BY, v.BZ))
+      return cudaErrorInvalidValue;
     *done |= 1u << l;
     if (prm.nlev == kTcMaxLevels) break;
   }
   if (prm.nlev == 0) return cudaGetLastError();
-  cudaFuncSetAttribute(k_m2l_tc<F, NPASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
-  k_m2l_tc<F, NPASS><<<dim3(nb, MP / kBM), kTcThreads, C::kSmem, st>>>(prm);
+  const cudaError_t r = launch_contraction<F, NPASS>(P, prm, nb, st, false);
   ++*nl;
-  return cudaGetLastError();
+  return r;
 }
 
 }  // namespace
@@ -770,7 +919,10 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
 cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int* nl,
                           bool tables_ready) {
   const int L = P->desc.levels;
-  if (P->pd.d != 3) return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
+  if (P->pd.d != 3) {
+    cudaMemsetAsync(ws.lc, 0, sizeof(double) * (size_t)ws.lev_off[L + 1] * P->pd.nj, st);
+    return launch_m2l_simt_levels(P, ws, 2, L, st, nl);
+  }
   const int prec = P->desc.precision;
   const cudaError_t e =
       prec == FMM_PREC_BF16X3   ? run_all_levels<FmtBF16, 3>(P, ws, st, tables_ready)
@@ -785,9 +937,10 @@ cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t
 cudaError_t launch_m2l_tc_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st,
                                  int* nl) {
   const int prec = P->desc.precision;
-  if (prec == FMM_PREC_BF16X3) build_tables<FmtBF16, 3>(P, ws, st);
-  else if (prec == FMM_PREC_TF32X3) build_tables<FmtTF32, 3>(P, ws, st);
-  else build_tables<FmtTF32, 1>(P, ws, st);
+  const int tlev = kernel_homogeneous(P->pd.kernel) ? 1 : P->desc.levels - 1;
+  if (prec == FMM_PREC_BF16X3) build_tables<FmtBF16, 3>(P, ws, st, tlev);
+  else if (prec == FMM_PREC_TF32X3) build_tables<FmtTF32, 3>(P, ws, st, tlev);
+  else build_tables<FmtTF32, 1>(P, ws, st, tlev);
   ++*nl;
   return cudaGetLastError();
 }

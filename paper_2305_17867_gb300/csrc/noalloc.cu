@@ -48,11 +48,11 @@ extern "C" int fmm_eval_noalloc(fmm_plan_t plan, int64_t n_src, const double* sr
                                 const double* w_dev, int64_t n_tgt, const double* tgt_dev,
                                 double* phi_dev, double* grad_dev, void* stream) {
   if (!plan) return FMM_ERR_ARG;
-  if (n_tgt > 0 && !phi_dev) return FMM_ERR_ARG;  // the same check as fmm_eval
   size_t need = 0;
   const int rc = fmm_workspace_size(plan, n_src, n_tgt, &need);
   if (rc != FMM_OK) return rc;
   if (need > FMM_NOALLOC_SCRATCH_BYTES) return FMM_ERR_WORKSPACE;
+  if (n_tgt > 0 && !phi_dev) return FMM_ERR_ARG;  // the same check as fmm_eval
   void* scratch = nullptr;
   const int rs = scratch_address(&scratch);
   if (rs != FMM_OK) return rs;

@@ -18,6 +18,7 @@ __device__ void set_leaf_side(Geom* g, int L) {
   g->s_leaf = __ddiv_rn(g->size, (double)(1 << L));
   g->inv_s_leaf = 1.0 / g->s_leaf;
   g->m2l_count = 0;
+  g->p2p_pairs = 0;
 }
 
 __global__ void k_geom_fixed(Geom* g, double lo0, double lo1, double lo2, double size, int L) {

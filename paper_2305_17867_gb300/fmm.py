@@ -23,7 +23,8 @@ def _ptr(t):
 class FMM:
     """A compressed-Taylor FMM plan on a uniform tree.
 
-    kernel     "laplace" (d = 2, 3), "yukawa" (d = 3), "biharmonic" (d = 3)
+    kernel     "laplace" (d = 2, 3), "yukawa" (d = 3), "biharmonic" (d = 3),
+               "helmholtz" (d = 3, uniform trees; lam = kappa; complex potentials)
     p          expansion order;  levels: leaf depth L of the uniform tree, or
                -D for an adaptive tree (3D, fp64 or fp32) refined to at most level D,
                splitting boxes that hold more than ``max_leaf`` points
@@ -114,6 +115,15 @@ class FMM:
         check(self.L.fmm_m2l_kernel_time(self._h, ctypes.byref(out)), "fmm_m2l_kernel_time")
         return float(out.value)
 
+    def last_stats(self) -> dict:
+        """fmm_last_stats: phase times, tree, M2L count, near-field pairs, status."""
+        st = _lib.Stats()
+        check(self.L.fmm_last_stats(self._h, ctypes.byref(st)), "fmm_last_stats")
+        return {"phase_ms": dict(zip(_lib.PHASES, list(st.phase_ms))),
+                "m2l_kernel_ms": st.m2l_kernel_ms, "boxes": st.boxes, "depth": st.depth,
+                "m2l_translations": st.m2l_translations, "p2p_pairs": st.p2p_pairs,
+                "status": st.status, "launches": st.launches}
+
     def last_status(self) -> int:
         return self.L.fmm_last_status(self._h)
 
@@ -148,17 +158,52 @@ class FMM:
         wd = self._dev(w)
         t = s if tgt is None else (s if tgt is src else self._dev(tgt))
         ns, nt = s.shape[0], t.shape[0]
-        phi = torch.empty(nt, dtype=torch.float64, device=self.device)
-        g = torch.empty(nt, self.d, dtype=torch.float64, device=self.device) if grad else None
+        cplx = self.kernel == "helmholtz"  # complex phi: (re, im) pairs
+        phi = torch.empty((nt, 2) if cplx else (nt,), dtype=torch.float64, device=self.device)
+        g = (torch.empty((nt, self.d, 2) if cplx else (nt, self.d), dtype=torch.float64,
+                         device=self.device) if grad else None)
         ws, wb = self._workspace(ns, nt)
         stream = torch.cuda.current_stream(self.device).cuda_stream
         check(self.L.fmm_eval(self._h, ns, _ptr(s), _ptr(wd), nt, _ptr(t), _ptr(phi), _ptr(g),
                               ws, wb, ctypes.c_void_p(stream)), "fmm_eval")
         if check_status:
             check(self.last_status(), "fmm_eval (device status)")
+        if cplx:
+            phi = torch.view_as_complex(phi)
+            g = torch.view_as_complex(g) if g is not None else None
         if host:
             phi = phi.cpu()
             g = g.cpu() if g is not None else None
+        return (phi, g) if grad else phi
+
+    def eval_f32(self, src, w, tgt=None, grad: bool = False, check_status: bool = False):
+        """fmm_eval_f32: float32 device tensors in and out (widened to float64 on
+        the device for the evaluation, results rounded to float32)."""
+        s = src.to(device=self.device, dtype=torch.float32).contiguous()
+        wd = w.to(device=self.device, dtype=torch.float32).contiguous()
+        t = s if tgt is None else tgt.to(device=self.device, dtype=torch.float32).contiguous()
+        ns, nt = s.shape[0], t.shape[0]
+        cplx = self.kernel == "helmholtz"
+        phi = torch.empty((nt, 2) if cplx else (nt,), dtype=torch.float32, device=self.device)
+        g = (torch.empty((nt, self.d, 2) if cplx else (nt, self.d), dtype=torch.float32,
+                         device=self.device) if grad else None)
+        b = ctypes.c_size_t()
+        check(self.L.fmm_workspace_size_f32(self._h, ns, nt, ctypes.byref(b)),
+              "fmm_workspace_size_f32")
+        if self._ws is None or self._ws.numel() < b.value + 256:
+            self._ws = torch.empty(b.value + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        check(self.L.fmm_eval_f32(self._h, ns, _ptr(s), _ptr(wd), nt, _ptr(t), _ptr(phi),
+                                  _ptr(g), ctypes.c_void_p(aligned),
+                                  self._ws.numel() - (aligned - base), ctypes.c_void_p(stream)),
+              "fmm_eval_f32")
+        if check_status:
+            check(self.last_status(), "fmm_eval_f32 (device status)")
+        if cplx:
+            phi = torch.view_as_complex(phi)
+            g = torch.view_as_complex(g) if g is not None else None
         return (phi, g) if grad else phi
 
     def backward(self, src, w, tgt, u, need_w=True, need_src=True, need_tgt=True,

@@ -66,4 +66,5 @@ def test_plan_validation_without_gpu():
     assert create(p=0) == -1
     assert create(levels=1) == -1
     assert create(kernel=1, lam=0.0) == -1  # Yukawa needs lambda > 0
-    assert create(kernel=2, d=2) == -2      # biharmonic only in 3D
+    assert create(kernel=3, d=2, lam=1.0) == -2  # Helmholtz only in 3D
+    assert create(kernel=3, lam=1.0, levels=-4, max_leaf=64) == -2  # Helmholtz: uniform trees

@@ -4,8 +4,10 @@
   algorithmic FLOP figure) against a brute-force enumeration of the
   interaction lists: target t and source s of the same level interact when
   their parents are adjacent and they are not (Sec. 4.1, List 2).
-* The parser of the committed ncu summary that supplies the roofline's
+* The parser of the committed ncu summaries that supply the roofline's
   traffic figure, and its refusal to report a figure for changed sources.
+* The near-field pair count of the whole-step roofline, and the subtree
+  sample of the CPU baseline.
 * The leaf key (boxes lexicographic, x fastest).
 """
 import itertools
@@ -51,22 +53,44 @@ def test_m2l_count_level_two_closed_form():
     assert per_level == sorted(per_level)
 
 
-def test_traffic_figure_only_for_the_captured_sources(monkeypatch):
-    path_hash = None
-    with open(bench.os.path.join(bench.ROOT, "profiles", "m2l_tc_laplace3d_p10_L5.md")) as fh:
-        for line in fh:
-            f = line.strip().strip("`").split()
-            if len(f) == 5 and f[0] == "traffic:" and f[1] == "tf32x3":
-                path_hash, want = f[4], int(f[2])
-    assert path_hash is not None
-    monkeypatch.setattr(bench, "m2l_source_hash", lambda: path_hash)
-    got, src = bench.profiled_traffic("tf32x3")
-    assert got == want and "ncu" in src
-    monkeypatch.setattr(bench, "m2l_source_hash", lambda: "0" * 16)
-    got, src = bench.profiled_traffic("tf32x3")
-    assert got is None and "changed" in src
-    got, src = bench.profiled_traffic("no-such-precision")
+def test_traffic_figure_only_for_the_captured_sources(monkeypatch, tmp_path):
+    (tmp_path / "m2l_tc_case.md").write_text(
+        "Command ...\n\n`traffic: tf32x3 123456 sources abcdef0123456789 workload wl_a`\n"
+        "`traffic: bf16x3 999 sources abcdef0123456789 workload wl_a`\n")
+    monkeypatch.setattr(bench, "m2l_source_hash", lambda: "abcdef0123456789")
+    got, src = bench.profiled_traffic("tf32x3", "wl_a", profiles=str(tmp_path))
+    assert got == 123456 and "ncu" in src
+    got, _ = bench.profiled_traffic("bf16x3", "wl_a", profiles=str(tmp_path))
+    assert got == 999
+    got, src = bench.profiled_traffic("tf32x3", "wl_b", profiles=str(tmp_path))
     assert got is None
+    monkeypatch.setattr(bench, "m2l_source_hash", lambda: "0" * 16)
+    got, src = bench.profiled_traffic("tf32x3", "wl_a", profiles=str(tmp_path))
+    assert got is None and "changed" in src
+
+
+def test_near_field_pairs_against_enumeration():
+    # the near-field pair count of the whole-step roofline against a brute-force
+    # count over points: same leaf or adjacent leaves, coinciding points excluded
+    rng = np.random.default_rng(5)
+    src = rng.random((400, 3))
+    tgt = rng.random((300, 3))
+    L = 2
+    n = 1 << L
+    cs = np.minimum(np.floor(src * n), n - 1)
+    ct = np.minimum(np.floor(tgt * n), n - 1)
+    brute = int((np.abs(ct[:, None, :] - cs[None, :, :]).max(axis=2) <= 1).sum())
+    assert bench.near_pairs(src, tgt, L) == brute
+    same = int((np.abs(cs[:, None, :] - cs[None, :, :]).max(axis=2) <= 1).sum()) - len(src)
+    assert bench.near_pairs(src, src, L) == same
+
+
+def test_subtree_targets_lie_in_one_box():
+    rng = np.random.default_rng(6)
+    tgt = rng.random((5000, 3))
+    idx, box = bench.subtree_targets(tgt, 2, np.random.default_rng(1))
+    inside = np.all(np.floor(tgt * 4) == box, axis=1)
+    assert np.array_equal(np.sort(idx), np.nonzero(inside)[0])
 
 
 def test_leaf_key_is_lexicographic_x_fastest():

@@ -21,19 +21,20 @@ L = 4
 N_SAMPLE = 64
 
 # Tolerances (relative L2 against the FP64 oracle, same tree and p):
-#  fp64 dense   the FP64 parity bar
-#  fp64 fft     transform sums of (2p+1)^2 (2c-1) terms: a few hundred unit
-#               roundoffs of the largest scaled term
-#  fp32 fft     the same sums in float
+#  fp64 dense   the FP64 parity bar (measured 1.7e-15 .. 2.9e-15)
+#  fp64 fft     transform sums of (2p+1)^2 (2c-1) terms: up to a few hundred
+#               unit roundoffs of the largest scaled term (measured 4.9e-15 ..
+#               5.3e-14), held to the same FP64 bar
+#  fp32 fft     the same sums in float (measured 9.8e-7 .. 1.8e-5)
 #  tf32x3       hi/lo split products (~2^-22 per product) summed over K = |j|
-#               terms with cancellation
-#  bf16x3       hi/lo bf16 (~2^-17 per operand)
+#               terms with cancellation (measured 1.1e-6 .. 1.7e-6)
+#  bf16x3       hi/lo bf16 (~2^-17 per operand; measured 4.6e-6 .. 9.3e-6)
 TOL = {
     ("fp64", "dense"): 1e-12,
     ("fp64", "fft"): 1e-12,
-    ("fp32", "fft"): 2e-4,
-    ("tf32x3", "dense"): 2e-5,
-    ("bf16x3", "dense"): 2e-4,
+    ("fp32", "fft"): 1e-4,
+    ("tf32x3", "dense"): 5e-6,
+    ("bf16x3", "dense"): 3e-5,
 }
 
 CASES = {
