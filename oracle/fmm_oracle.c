@@ -1049,6 +1049,12 @@ int or_fmm_uniform(int kernel, int d, double lam, int p, int L, int compressed,
 /*                   adjacent to B (exactly the A with B in W(A)) -> P2L      */
 /* Local expansions live at levels >= 2: L2L from the parent, plus M2L over V */
 /* and P2L over X.  Every leaf evaluates L2P, P2P over U and M2P over W.      */
+/* A W or X interaction is summed directly (P2P) when the box on the far side */
+/* holds no more points than an expansion has coefficients (|j|): a W box C  */
+/* with at most |j| sources is summed at the leaf's targets in place of M2P;  */
+/* an X pair (A, B) whose box B holds at most |j| targets (its whole subtree) */
+/* sends A's sources straight to those targets in place of P2L.  The choice   */
+/* depends on one box's count only, so every target gets each pair once.     */
 /* The lists are found by testing their definitions against every box.       */
 /* ------------------------------------------------------------------------ */
 
@@ -1123,7 +1129,8 @@ static int or_sort_points(int d, int D, const double* lo, double size, int64_t n
 /* Adaptive FMM (3D and 2D).  If nsample > 0 only the listed targets are
  * evaluated (outputs in sample order).  stats (optional, 8 entries): boxes,
  * leaves, deepest level, then |U|, |V|, |W|, |X| summed over the boxes that
- * the evaluated targets use.  cover (optional, one per evaluated target):
+ * the evaluated targets use, and how many of the W and X pairs among them were
+ * summed directly.  cover (optional, one per evaluated target):
  * the number of sources the lists of that target's leaf and ancestors reach,
  * with multiplicity (exactly n_src when every pair is covered once and no
  * source coincides with the target). */
@@ -1201,7 +1208,7 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
   double* lc = (double*)calloc(nbx * nj, sizeof(double));
   char* need = (char*)calloc(nbx, 1);
   double* vxcov = (double*)calloc(nbx, sizeof(double));
-  int64_t cnt[4] = {0, 0, 0, 0};
+  int64_t cnt[5] = {0, 0, 0, 0, 0};
 
   const int64_t neval = nsample > 0 ? nsample : ntgt;
   for (int64_t t = 0; t < neval; ++t) {
@@ -1283,7 +1290,7 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
         for (int k = 0; k < d; ++k) h[k] = cb[k] - cp[k];
         or_l2l(e, h, lc + (size_t)pb * nj, Lb);
       }
-      int64_t nv = 0, nx = 0;
+      int64_t nv = 0, nx = 0, nxd = 0;
       double cov = 0.0;
       for (int64_t a = 0; a < nbox; ++a) {
         const or_abox* A = &bx[a];
@@ -1297,8 +1304,14 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
           ++nv;
         } else if (A->leaf && A->level < l && or_abox_adjacent(d, A, &bx[pb]) &&
                    !or_abox_adjacent(d, A, &bx[b])) {
-          /* X: P2L (eq. (stored_local_coeffs)) */
+          /* X: P2L (eq. (stored_local_coeffs)); with at most |j| targets
+           * under B the leaves sum A's sources directly instead */
           int64_t n = A->s1 - A->s0;
+          ++nx;
+          if (bx[b].t1 - bx[b].t0 <= nj) {
+            ++nxd;
+            continue;
+          }
           if (n > 0) {
             double* ys = (double*)malloc(sizeof(double) * n * d);
             double* ws = (double*)malloc(sizeof(double) * n);
@@ -1312,7 +1325,6 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
             free(ws);
           }
           cov += (double)n;
-          ++nx;
         }
       }
       vxcov[b] = cov + vxcov[pb];
@@ -1320,6 +1332,8 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
       cnt[1] += nv;
 #pragma omp atomic
       cnt[3] += nx;
+#pragma omp atomic
+      cnt[4] += nxd;
     }
   }
 
@@ -1335,32 +1349,55 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
     or_abox_center(d, lo, size, B, cb);
     double acc = B->level >= 2 ? or_l2p(e, cb, lc + (size_t)b * nj, x, NULL) : 0.0;
     double cov = B->level >= 2 ? vxcov[b] : 0.0;
-    int64_t nu = 0, nw = 0;
+    int64_t nu = 0, nw = 0, nwd = 0;
+    /* direct sum (eq. (1)) of the sources of box A at x, skipping x itself */
+    #define OR_DIRECT(A)                                                     \
+      for (int64_t q = (A)->s0; q < (A)->s1; ++q) {                          \
+        int64_t is = ss[q].idx;                                              \
+        double r[OR_MAXD];                                                   \
+        int same = 1;                                                        \
+        for (int k = 0; k < d; ++k) {                                        \
+          r[k] = x[k] - src[is * d + k];                                     \
+          same &= (r[k] == 0.0);                                             \
+        }                                                                    \
+        if (same) continue;                                                  \
+        acc += or_green(kernel, d, lam, r) * w[is];                          \
+        cov += 1.0;                                                          \
+      }
     for (int64_t a = 0; a < nbox; ++a) {
       const or_abox* A = &bx[a];
       if (A->leaf && or_abox_adjacent(d, A, B)) {
-        for (int64_t q = A->s0; q < A->s1; ++q) {
-          int64_t is = ss[q].idx;
-          double r[OR_MAXD];
-          int same = 1;
-          for (int k = 0; k < d; ++k) {
-            r[k] = x[k] - src[is * d + k];
-            same &= (r[k] == 0.0);
-          }
-          if (same) continue;
-          acc += or_green(kernel, d, lam, r) * w[is];
-          cov += 1.0;
-        }
+        OR_DIRECT(A)
         ++nu;
       } else if (A->level > B->level && A->parent >= 0 &&
                  or_abox_adjacent(d, &bx[A->parent], B) && !or_abox_adjacent(d, A, B)) {
-        double ca[OR_MAXD];
-        or_abox_center(d, lo, size, A, ca);
-        acc += or_m2p(e, kernel, lam, ca, mp + (size_t)a * nj, x);
-        cov += (double)(A->s1 - A->s0);
+        if (A->s1 - A->s0 <= nj) {
+          OR_DIRECT(A)  /* W box with at most |j| sources */
+          ++nwd;
+        } else {
+          double ca[OR_MAXD];
+          or_abox_center(d, lo, size, A, ca);
+          acc += or_m2p(e, kernel, lam, ca, mp + (size_t)a * nj, x);
+          cov += (double)(A->s1 - A->s0);
+        }
         ++nw;
       }
     }
+    /* X pairs (A, C) of the leaf's ancestors C (and the leaf) of level >= 2
+     * holding at most |j| targets: A's sources directly */
+    for (int64_t cbx = b; cbx >= 0 && bx[cbx].level >= 2 && bx[cbx].t1 - bx[cbx].t0 <= nj;
+         cbx = bx[cbx].parent) {
+      const or_abox* C = &bx[cbx];
+      const or_abox* PC = &bx[C->parent];
+      for (int64_t a = 0; a < nbox; ++a) {
+        const or_abox* A = &bx[a];
+        if (A->leaf && A->level < C->level && or_abox_adjacent(d, A, PC) &&
+            !or_abox_adjacent(d, A, C)) {
+          OR_DIRECT(A)
+        }
+      }
+    }
+    #undef OR_DIRECT
     phi[t] = acc;
     if (cover) cover[t] = cov;
     int first = 0;
@@ -1376,6 +1413,8 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
       cnt[0] += nu;
 #pragma omp atomic
       cnt[2] += nw;
+#pragma omp atomic
+      cnt[4] += nwd;
     }
   }
   if (stats) {
@@ -1388,7 +1427,7 @@ int or_fmm_adaptive(int kernel, int d, double lam, int p, int max_leaf, int max_
     stats[4] = cnt[1];
     stats[5] = cnt[2];
     stats[6] = cnt[3];
-    stats[7] = 0;
+    stats[7] = cnt[4];
   }
   free(leafdone);
   free(D2);

@@ -293,8 +293,9 @@ def fmm_adaptive(kernel: str, d: int, p: int, src, w, tgt, max_leaf: int = 64,
                  max_depth: int = 10, lo=None, size: float = 1.0, lam: float = 0.0,
                  sample=None, want_stats: bool = False):
     """Adaptive-tree FMM (U/V/W/X lists).  Returns phi, or (phi, stats, cover)
-    with stats = dict(boxes, leaves, depth, U, V, W, X) and cover = sources
-    reached per evaluated target (with multiplicity)."""
+    with stats = dict(boxes, leaves, depth, U, V, W, X, WX_direct) and cover =
+    sources reached per evaluated target (with multiplicity); WX_direct counts
+    the W and X pairs summed directly (boxes of at most |j| points)."""
     src, w, tgt = _f64(src), _f64(w), _f64(tgt)
     lo = _f64(np.zeros(d) if lo is None else lo)
     ns = 0 if sample is None else len(sample)
@@ -310,8 +311,8 @@ def fmm_adaptive(kernel: str, d: int, p: int, src, w, tgt, max_leaf: int = 64,
         raise ValueError(f"oracle adaptive FMM failed with status {rc}")
     if not want_stats:
         return phi
-    keys = ["boxes", "leaves", "depth", "U", "V", "W", "X"]
-    return phi, dict(zip(keys, [int(v) for v in st[:7]])), cov
+    keys = ["boxes", "leaves", "depth", "U", "V", "W", "X", "WX_direct"]
+    return phi, dict(zip(keys, [int(v) for v in st[:8]])), cov
 
 
 def num_threads() -> int:

@@ -4,7 +4,9 @@ not come from the oracle itself:
 * a tree that refines every box to the same depth is the uniform tree, so the
   adaptive driver must reproduce the uniform driver (W = X = empty);
 * the lists of a target's leaf and of its ancestors must reach every source
-  exactly once (counted with multiplicity through U, V, W and X);
+  exactly once (counted with multiplicity through U, V, W and X, whether a W
+  or X pair goes through an expansion or, for a box of at most |j| points,
+  is summed directly);
 * the result converges to the direct sum of eq. (1) as p grows.
 """
 import numpy as np
@@ -47,6 +49,9 @@ def test_lists_reach_every_source_once(oracle, same):
     _, st, cov = oracle.fmm_adaptive("laplace", 3, 2, src, w, tgt, max_leaf=24,
                                      want_stats=True)
     assert st["W"] > 0 and st["X"] > 0 and st["depth"] >= 5
+    # |j| = 9 at p = 2 against leaves of up to 24 points: some W and X pairs
+    # are summed directly, the others through M2P and P2L
+    assert 0 < st["WX_direct"] < st["W"] + st["X"]
     expect = len(w) - (1 if same else 0)  # the coinciding source is skipped
     assert np.all(cov == expect)
 
