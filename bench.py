@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--p", type=int, default=0, help="override the expansion order")
     ap.add_argument("--precision", default=os.environ.get("FMM_BENCH_PRECISION", "auto"),
-                    help="fp64|fp32|tf32|tf32x3|bf16x3; auto = tf32x3 on uniform 3D trees, "
+                    help="fp64|fp32|tf32|tf32x3|bf16x3|f16x3; auto = tf32x3 on uniform 3D trees, "
                          "else fp64")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m2l", default="dense", choices=["dense", "fft"],
@@ -320,7 +320,7 @@ def peak_of(prec, m2l, d, peaks, peak_src):
     """(peak TFLOP/s, bound, text) of the M2L contraction in this arithmetic."""
     tf32_dense = peaks["bf16_tflops"] * 1.1 / 2.25
     clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    tensor = m2l == "dense" and d == 3 and prec in ("tf32", "tf32x3", "bf16x3")
+    tensor = m2l == "dense" and d == 3 and prec in ("tf32", "tf32x3", "bf16x3", "f16x3")
     if tensor and prec == "tf32":
         return tf32_dense, "tensor", f"tf32 dense = bf16 {peak_src} x 1.1/2.25"
     if tensor and prec == "tf32x3":
@@ -328,6 +328,8 @@ def peak_of(prec, m2l, d, peaks, peak_src):
         return tf32_dense / 3.0, "tensor", f"tf32x3 = (bf16 {peak_src} x 1.1/2.25) / 3 passes"
     if tensor and prec == "bf16x3":
         return peaks["bf16_tflops"] / 3.0, "tensor", f"bf16x3 = bf16 dense {peak_src} / 3 passes"
+    if tensor and prec == "f16x3":  # fp16 and bf16 share the 16-bit tensor rate
+        return peaks["bf16_tflops"] / 3.0, "tensor", f"f16x3 = bf16 dense {peak_src} / 3 passes"
     if prec == "fp64":
         return (152 * 2 * 2 * clock / 1e12, "alu",
                 "fp64 FMA: 152 SMs x 2 lanes x 2 x max clock (nominal 1.25 TFLOP/s)")

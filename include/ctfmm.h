@@ -82,18 +82,28 @@ enum {
  *  TF32     as FP32 but M2L on the tensor cores (tcgen05 kind::tf32), one pass.
  *  TF32X3   M2L with split operands a = hi + lo in tf32, three tensor passes
  *           (hi*hi + hi*lo + lo*hi), float32 accumulation.
- *  BF16X3   the same split in bf16 (kind::f16), float32 accumulation.        */
+ *  BF16X3   the same split in bf16 (kind::f16), float32 accumulation.
+ *  F16X3    the same split in fp16 (kind::f16): fp16 keeps tf32's 11-bit
+ *           significand, so the products are as exact as TF32X3's, at the
+ *           rate of the 16-bit tensor cores.  Its 5-bit exponent is made to
+ *           suffice by exact power-of-two scalings: each box's multipole
+ *           (times q!) is scaled into [1/2, 1), the offset matrices are taken
+ *           as Ht_{i+q} / (i! q!) over a power of two of the level's
+ *           derivative scale, and the scalings are undone in float as each
+ *           offset's product leaves the accumulator.  3D uniform trees only
+ *           (an adaptive plan returns FMM_ERR_UNSUPPORTED).                */
 enum {
   FMM_PREC_FP64 = 0,
   FMM_PREC_FP32 = 1,
   FMM_PREC_TF32 = 2,
   FMM_PREC_TF32X3 = 3,
-  FMM_PREC_BF16X3 = 4
+  FMM_PREC_BF16X3 = 4,
+  FMM_PREC_F16X3 = 5
 };
 
 /* How M2L applies the translation of eq. (m2l_toeplitz).
  *  DENSE  as a dense |j| x |j| product per (target, source) pair: the CUDA
- *         cores for FP64/FP32, the tensor cores for TF32/TF32X3/BF16X3.
+ *         cores for FP64/FP32, the tensor cores for TF32/TF32X3/BF16X3/F16X3.
  *  FFT    in its convolution form (eq. (convolution_m2l)): every box's
  *         multipole is transformed once to a (2p+1)^{d-1} (2c-1) spectrum,
  *         each target accumulates sum_h Hhat_h * Bhat_{t-h} over its
@@ -105,8 +115,8 @@ enum { FMM_M2L_DENSE = 0, FMM_M2L_FFT = 1, FMM_M2L_AUTO = 2 };
 /* AUTO picks by arithmetic, following measurements on GB300 (3D biharmonic,
  * L = 6, p = 4..16): FFT for FP64 (its stencil runs at ~95% of the FP64 FMA
  * rate, 5-6x fewer operations than dense) and for FP32 (CUDA-core dense
- * products are slower still); DENSE on the tensor cores for TF32, TF32X3 and
- * BF16X3.  Adaptive plans use DENSE. */
+ * products are slower still); DENSE on the tensor cores for TF32, TF32X3,
+ * BF16X3 and F16X3.  Adaptive plans use DENSE. */
 
 /* A constant-coefficient PDE L = sum_t coeff[t] d^{multi_idx[t]}  (eq.
  * (define_pde_op)).  multi_idx is n_terms x d exponents.  The PDE must have

@@ -17,7 +17,7 @@ STATUS = {
     -8: "device structure overflowed (incomplete result)",
 }
 KERNELS = {"laplace": 0, "yukawa": 1, "biharmonic": 2, "helmholtz": 3}
-PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4, "f16x3": 5}
 M2L_PATHS = {"dense": 0, "fft": 1, "auto": 2}
 NUM_PHASES = 7
 PHASES = ["tree", "derivatives", "p2m", "m2m", "m2l", "l2l", "leaf"]

@@ -158,7 +158,7 @@ static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t
   w.nbbox_blocks = (int)std::min<int64_t>(1024, (std::max(n_src, n_tgt) + 255) / 256 + 1);
   w.bbox = carve<double>(cur, (size_t)2 * 3 * 2 * w.nbbox_blocks);
   const int prec = P->desc.precision;
-  if (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3) {
+  if (prec_tensor(prec)) {
     const TcShape tcs = tc_shape(nj, prec);
     const int esz = tcs.esz;
     w.tc_jp = tcs.jp;
@@ -221,7 +221,7 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
     w.sxr = carve<float4>(cur, std::max<int64_t>(n_src, 1));
     w.txr = carve<float4>(cur, std::max<int64_t>(n_tgt, 1));
   }
-  if (d == 3 && (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3)) {
+  if (d == 3 && prec_tensor(prec)) {
     const TcShape tcs = tc_shape(nj, prec);
     const int esz = tcs.esz;  // bytes per operand element
     w.tc_jp = tcs.jp;
@@ -234,6 +234,7 @@ int fmm_workspace_layout(const fmm_plan_s* P, int64_t n_src, int64_t n_tgt, void
       w.tc_bpar[h] = carve<char>(cur, (size_t)off * w.tc_jp * esz);
       w.tc_tmat[h] = carve<char>(cur, (size_t)tlev * 343 * w.tc_mp * w.tc_jp * esz);
     }
+    if (prec == FMM_PREC_F16X3) w.tc_bscale = carve<float>(cur, (size_t)off);
   }
   if (P->pd.kernel == FMM_KERNEL_HELMHOLTZ) {
     // the real and imaginary parts' potentials (and gradients) before they are
@@ -273,7 +274,9 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   } else if (L < 2 || L > (d == 3 ? 7 : 8)) {
     return FMM_ERR_ARG;
   }
-  if (desc->precision < FMM_PREC_FP64 || desc->precision > FMM_PREC_BF16X3) return FMM_ERR_ARG;
+  if (desc->precision < FMM_PREC_FP64 || desc->precision > FMM_PREC_F16X3) return FMM_ERR_ARG;
+  // the F16X3 scalings are laid out for the uniform trees' parent grids
+  if (desc->precision == FMM_PREC_F16X3 && desc->levels < 0) return FMM_ERR_UNSUPPORTED;
   if (desc->m2l != FMM_M2L_DENSE && desc->m2l != FMM_M2L_FFT && desc->m2l != FMM_M2L_AUTO)
     return FMM_ERR_ARG;
   if (desc->m2l == FMM_M2L_FFT && desc->precision != FMM_PREC_FP64 &&
@@ -332,6 +335,7 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
       deg += kv.first[k];
     }
     pd.tcoef[t] = -kv.second / alead;
+    pd.tcoef_f[t] = (float)pd.tcoef[t];
     pd.tpow[t] = c - deg;
   }
 
@@ -383,6 +387,7 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   // upload
   const size_t n_mi = align_up(sizeof(char4) * pd.nfull);
   const size_t n_if = align_up(sizeof(double) * pd.nfull);
+  const size_t n_iff = align_up(sizeof(float) * pd.nfull);
   const size_t n_rc = align_up(sizeof(int16_t) * pd.nfull * nt);
   const size_t n_fr = align_up(sizeof(int) * full.row.size());
   const size_t n_hr = align_up(sizeof(int) * hank.row.size());
@@ -410,9 +415,33 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   for (int n = 0; n <= 2 * p; ++n) ftab.push_back(std::pow(g, n));
   for (int n = 0; n <= 2 * p; ++n) ftab.push_back(std::pow(g, -n));
   const size_t n_ft = align_up(sizeof(double) * ftab.size());
-  const size_t total = n_mi + n_if + 2 * n_rc + n_fr + n_hr + n_ft;
+  // P2M monomial segments (d = 3): each row (m_1, m_s) of the full layout cut
+  // into runs of at most 4 consecutive m_0
+  std::vector<int> seg;
+  if (d == 3)
+    for (int ms = 0; ms <= p; ++ms)
+      for (int m1 = 0; m1 <= p - ms; ++m1) {
+        const int len = p - ms - m1 + 1;
+        for (int a = 0; a < len; a += 4) {
+          const int pos = full.row[(size_t)ms * (p + 1) + m1] + a;
+          seg.push_back(a | (m1 << 5) | (ms << 10) | (std::min(4, len - a) << 15) | (pos << 18));
+        }
+      }
+  pd.p2m_nseg = (int)seg.size();
+  const size_t n_sg = align_up(sizeof(int) * std::max<size_t>(seg.size(), 1));
+  const size_t total = n_mi + n_if + 2 * n_rc + n_fr + n_hr + n_ft + 2 * n_iff + n_sg;
   std::vector<char> host(total, 0);
   char* h = host.data();
+  {
+    std::vector<float> iff(pd.nfull), ff(pd.nfull);
+    for (int i = 0; i < pd.nfull; ++i) {
+      iff[i] = (float)inv_fact[i];
+      ff[i] = (float)(1.0 / inv_fact[i]);  // m! < 2^53: exact in double
+    }
+    std::memcpy(h + total - n_sg - 2 * n_iff, iff.data(), sizeof(float) * pd.nfull);
+    std::memcpy(h + total - n_sg - n_iff, ff.data(), sizeof(float) * pd.nfull);
+  }
+  if (!seg.empty()) std::memcpy(h + total - n_sg, seg.data(), sizeof(int) * seg.size());
   std::memcpy(h, mi.data(), sizeof(char4) * pd.nfull);
   std::memcpy(h + n_mi, inv_fact.data(), sizeof(double) * pd.nfull);
   std::memcpy(h + n_mi + n_if, rec.data(), sizeof(int16_t) * rec.size());
@@ -429,6 +458,9 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
   char* db = static_cast<char*>(dt);
   pd.mi = reinterpret_cast<const char4*>(db);
   pd.inv_fact = reinterpret_cast<const double*>(db + n_mi);
+  pd.inv_fact_f = reinterpret_cast<const float*>(db + total - n_sg - 2 * n_iff);
+  pd.fact_f = reinterpret_cast<const float*>(db + total - n_sg - n_iff);
+  pd.p2m_seg = reinterpret_cast<const int*>(db + total - n_sg);
   pd.rec_src = reinterpret_cast<const int16_t*>(db + n_mi + n_if);
   pd.cmp_src = reinterpret_cast<const int16_t*>(db + n_mi + n_if + n_rc);
   pd.frow = reinterpret_cast<const int*>(db + n_mi + n_if + 2 * n_rc);

@@ -5,6 +5,7 @@
 
 #include "adaptive.cuh"
 #include "expansions.cuh"
+#include "passes_f32.cuh"
 
 namespace {
 
@@ -237,8 +238,8 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
   T* pw = reinterpret_cast<T*>(smraw);
   T* alpha = reinterpret_cast<T*>(smraw + align_bytes<T>(sizeof(T) * CH * D * (p + 1)));
   int bc[3];
-  double c[3], s;
-  box_center<D>(g, L, b, bc, c, &s);
+  double c[3] = {0.0, 0.0, 0.0}, s = g->s_leaf;
+  if (!rel) box_center<D>(g, L, b, bc, c, &s);
   const double inv_s = rel ? 0.0 : 1.0 / s;  // only the FP64-input path divides
   T acc[kMaxT];
   char4 mt[kMaxT];
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kThreads) k_p2m(PlanDev pd, const Geom* __rest
 #pragma unroll
   for (int k = 0; k < kMaxT; ++k) {
     const int q = threadIdx.x + k * blockDim.x;
-    if (q < nfull) alpha[q] = acc[k] * (T)pd.inv_fact[q];
+    if (q < nfull) alpha[q] = acc[k] * inv_fact_t<T>(pd, q);
   }
   __syncthreads();
   compress_smem<T>(pd, alpha, s);
@@ -373,7 +374,7 @@ __device__ void p2m_warp_body(const PlanDev& pd, const double* c, double s, int 
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
     const int q = lane + 32 * t;
-    if (t < nt && q < nfull) alpha[q] = acc[t] * (T)pd.inv_fact[q];
+    if (t < nt && q < nfull) alpha[q] = acc[t] * inv_fact_t<T>(pd, q);
   }
   __syncwarp();
   compress_warp<T>(pd, alpha, s, lane);
@@ -398,9 +399,10 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_p2m_warp(
     for (int q = lane; q < nj; q += 32) mp[(size_t)b * nj + q] = 0.0;
     return;
   }
+  // the box-relative copy (float path) needs only the side: no FP64 centre
   int bc[3];
-  double c[3], s;
-  box_center<D>(g, L, b, bc, c, &s);
+  double c[3] = {0.0, 0.0, 0.0}, s = g->s_leaf;
+  if (!rel) box_center<D>(g, L, b, bc, c, &s);
   p2m_warp_body<D, T, NT>(pd, c, s, i0, i1, x0, x1, x2, w, rel, pw, alpha, lane,
                           mp + (size_t)b * nj);
 }
@@ -451,10 +453,11 @@ __device__ void m2m_body(const PlanDev& pd, double s, const int64_t* crow,
   T* sig = Y + NC * nj;                   // nfull
   T* tab = sig + nfull;                   // 2 (sign) x (p+1): (+-1/2)^e / e!
   if (threadIdx.x <= p) {
-    // (1/2)^e / e!: inv_fact[e] is 1/e! (multi-index (e,0,0) sits at position e)
-    const double v = pow2_neg<double>((int)threadIdx.x) * pd.inv_fact[threadIdx.x];
-    tab[threadIdx.x] = (T)v;                                      // h = +1/2 (child bit 0)
-    tab[(p + 1) + threadIdx.x] = (T)((threadIdx.x & 1) ? -v : v);  // h = -1/2 (child bit 1)
+    // (1/2)^e / e!: inv_fact[e] is 1/e! (multi-index (e,0,0) sits at position e);
+    // the power of two is exact, so the product is rounded once in either type
+    const T v = pow2_neg<T>((int)threadIdx.x) * inv_fact_t<T>(pd, threadIdx.x);
+    tab[threadIdx.x] = v;                                    // h = +1/2 (child bit 0)
+    tab[(p + 1) + threadIdx.x] = (threadIdx.x & 1) ? -v : v;  // h = -1/2 (child bit 1)
   }
   for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
     const int ci = e / nj, q = e % nj;
@@ -512,10 +515,11 @@ __global__ void __launch_bounds__(kThreads) k_m2m(PlanDev pd, const Geom* __rest
                                                   double* __restrict__ mpp) {
   constexpr int NC = 1 << D;
   const int b = blockIdx.x;
-  int bc[3];
-  double cp[3], s;
-  box_center<D>(g, l, b, bc, cp, &s);
-  const int nlc = 1 << (l + 1);
+  // box coordinates by integer arithmetic and the side alone (the centre is
+  // not needed, and FP64 runs at 1/64 of the FP32 rate)
+  const int nl = 1 << l, nlc = nl << 1;
+  int bc[3] = {b & (nl - 1), (b >> l) & (nl - 1), D == 3 ? b >> (2 * l) : 0};
+  const double s = __dmul_rn(g->size, pow2_neg<double>(l));
   int64_t crow[NC];
   for (int ci = 0; ci < NC; ++ci) {
     int64_t cb = 0;
@@ -558,9 +562,9 @@ __device__ void l2l_body(const PlanDev& pd, double s, const double* __restrict__
   for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = (T)par[q];
   if (threadIdx.x <= p) {
     // (1/4)^e / e!
-    const double v = pow2_neg<double>(2 * (int)threadIdx.x) * pd.inv_fact[threadIdx.x];
-    tab[threadIdx.x] = (T)((threadIdx.x & 1) ? -v : v);  // child bit 0: h/S = -1/4
-    tab[(p + 1) + threadIdx.x] = (T)v;                    // child bit 1: h/S = +1/4
+    const T v = pow2_neg<T>(2 * (int)threadIdx.x) * inv_fact_t<T>(pd, threadIdx.x);
+    tab[threadIdx.x] = (threadIdx.x & 1) ? -v : v;  // child bit 0: h/S = -1/4
+    tab[(p + 1) + threadIdx.x] = v;                  // child bit 1: h/S = +1/4
   }
   __syncthreads();
   decompress_smem<T>(pd, Dt, s);
@@ -614,10 +618,9 @@ __global__ void __launch_bounds__(kThreads) k_l2l(PlanDev pd, const Geom* __rest
                                                   double* __restrict__ lcc) {
   constexpr int NC = 1 << D;
   const int b = blockIdx.x;
-  int bc[3];
-  double cp[3], s;
-  box_center<D>(g, l, b, bc, cp, &s);
-  const int nlc = 1 << (l + 1);
+  const int nl = 1 << l, nlc = nl << 1;  // integer box coordinates, the side alone
+  int bc[3] = {b & (nl - 1), (b >> l) & (nl - 1), D == 3 ? b >> (2 * l) : 0};
+  const double s = __dmul_rn(g->size, pow2_neg<double>(l));
   int64_t crow[NC];
   for (int ci = 0; ci < NC; ++ci) {
     int64_t cb = 0;
@@ -646,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_al2l(PlanDev pd, const Geom* __res
 
 bool m2l_shared_tables(const fmm_plan_s* P) {
   const int prec = P->desc.precision;
-  const bool tc = prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3;
+  const bool tc = prec_tensor(prec);
   const bool fft = P->desc.m2l == FMM_M2L_FFT;
   return (tc || fft) && P->pd.d == 3 && kernel_homogeneous(P->pd.kernel);
 }
@@ -737,6 +740,10 @@ cudaError_t launch_p2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   const int L = P->desc.levels, d = pd.d;
   const int64_t nleaf = nbox_at(d, L);
   const bool f64 = P->desc.precision == FMM_PREC_FP64;
+  if (!f64 && launch_p2m_f32(P, ws, st)) {  // 3D, box-relative float points
+    ++*nl;
+    return cudaGetLastError();
+  }
   const size_t tsz = f64 ? 8 : 4;
   const size_t smem = align_bytes<double>(tsz * 32 * d * (pd.p + 1)) + tsz * pd.nfull;
   double* mpL = ws.mp + ws.lev_off[L] * pd.nj;
@@ -792,6 +799,13 @@ cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   // In the mixed modes the leaf multipoles come from the float P2M, so their
   // first shift runs in float too; shifts higher in the tree stay FP64.
   const bool mixed = P->desc.precision != FMM_PREC_FP64;
+  if (d == 3 && passes_f32_order(pd.p)) {  // warp-per-box kernels
+    for (int l = L - 1; l >= 2; --l) {
+      launch_m2m_warp(P, ws, l, !(mixed && l == L - 1), st);
+      ++*nl;
+    }
+    return cudaGetLastError();
+  }
   for (int l = L - 1; l >= 2; --l) {
     const double* mpc = ws.mp + ws.lev_off[l + 1] * pd.nj;
     double* mpp = ws.mp + ws.lev_off[l] * pd.nj;
@@ -820,6 +834,13 @@ cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   // In the mixed modes the leaf locals feed the float L2P, so the last shift
   // (to the leaves) runs in float; shifts higher in the tree stay FP64.
   const bool mixed = P->desc.precision != FMM_PREC_FP64;
+  if (d == 3 && passes_f32_order(pd.p)) {  // warp-per-box kernels
+    for (int l = 2; l < L; ++l) {
+      launch_l2l_warp(P, ws, l, !(mixed && l == L - 1), st);
+      ++*nl;
+    }
+    return cudaGetLastError();
+  }
   for (int l = 2; l < L; ++l) {
     const double* lcp = ws.lc + ws.lev_off[l] * pd.nj;
     double* lcc = ws.lc + ws.lev_off[l + 1] * pd.nj;
@@ -844,7 +865,8 @@ cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
 
 // ---------------------------------------------------------------------------
 // Adaptive tree: P2L over X (eq. (stored_local_coeffs)) into every box of
-// level >= 2 that holds targets.  X(B) = the leaves coarser than B that are
+// level >= 2 that holds more than |j| targets (below that the leaves sum the
+// X leaves' sources directly, which costs less).  X(B) = the leaves coarser than B that are
 // adjacent to P(B) but not to B; each is a neighbour of B's ancestor at its
 // own level, so the block walks the 27 neighbours of every ancestor.  Threads
 // share the sources of each X leaf; every source adds w * Ht((c_B - y)/s)
@@ -861,7 +883,8 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l(PlanDev pd, const Geom* __re
                                                     const double* __restrict__ sw,
                                                     double* __restrict__ lc) {
   const int b = t.loff[2] + blockIdx.x;
-  if (b >= t.loff[t.maxlev + 1] || t.t1[b] == t.t0[b]) return;
+  // a box of at most |j| targets has its X pairs summed directly by the leaves
+  if (b >= t.loff[t.maxlev + 1] || t.t1[b] - t.t0[b] <= pd.nj) return;
   const int nj = pd.nj;
   int l, bc[3];
   abox(t, b, &l, bc);
@@ -911,7 +934,8 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l_f32(PlanDev pd, const Geom* 
                                                         const double* __restrict__ sw,
                                                         double* __restrict__ lc) {
   const int b = t.loff[2] + blockIdx.x;
-  if (b >= t.loff[t.maxlev + 1] || t.t1[b] == t.t0[b]) return;
+  // a box of at most |j| targets has its X pairs summed directly by the leaves
+  if (b >= t.loff[t.maxlev + 1] || t.t1[b] - t.t0[b] <= pd.nj) return;
   const int nj = pd.nj;
   int l, bc[3];
   abox(t, b, &l, bc);

@@ -46,12 +46,37 @@ __device__ __forceinline__ double scaled_coef(const PlanDev& pd, int t, double s
   return v;
 }
 
+// the scaled coefficient in the kernel's arithmetic: float kernels take the
+// float copy when no power of s enters (every term of the PDE's order c, as
+// for the Laplace and biharmonic operators), so that no FP64 work is done
+template <typename T>
+__device__ __forceinline__ T scaled_coef_t(const PlanDev& pd, int t, double s);
+template <>
+__device__ __forceinline__ double scaled_coef_t<double>(const PlanDev& pd, int t, double s) {
+  return scaled_coef(pd, t, s);
+}
+template <>
+__device__ __forceinline__ float scaled_coef_t<float>(const PlanDev& pd, int t, double s) {
+  return pd.tpow[t] == 0 ? pd.tcoef_f[t] : (float)scaled_coef(pd, t, s);
+}
+// 1/m! in the kernel's arithmetic
+template <typename T>
+__device__ __forceinline__ T inv_fact_t(const PlanDev& pd, int q);
+template <>
+__device__ __forceinline__ double inv_fact_t<double>(const PlanDev& pd, int q) {
+  return pd.inv_fact[q];
+}
+template <>
+__device__ __forceinline__ float inv_fact_t<float>(const PlanDev& pd, int q) {
+  return pd.inv_fact_f[q];
+}
+
 // D[j] given in a[0..nj); fill slabs c..p (decompression, eq. (decompression)).
 template <typename T>
 __device__ void decompress_smem(const PlanDev& pd, T* a, double s) {
   const int nt = pd.nterms > 0 ? pd.nterms : 1;
   T coef[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) coef[t] = (T)scaled_coef(pd, t, s);
+  for (int t = 0; t < pd.nterms; ++t) coef[t] = scaled_coef_t<T>(pd, t, s);
   for (int ms = pd.c; ms <= pd.p; ++ms) {
     const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
     for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
@@ -69,7 +94,7 @@ template <typename T>
 __device__ void compress_smem(const PlanDev& pd, T* a, double s) {
   const int nt = pd.nterms > 0 ? pd.nterms : 1;
   T coef[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) coef[t] = (T)scaled_coef(pd, t, s);
+  for (int t = 0; t < pd.nterms; ++t) coef[t] = scaled_coef_t<T>(pd, t, s);
   for (int ms = pd.p - 1; ms >= 0; --ms) {
     const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
     for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
@@ -94,7 +119,7 @@ template <typename T>
 __device__ void compress_warp(const PlanDev& pd, T* a, double s, int lane) {
   const int nt = pd.nterms > 0 ? pd.nterms : 1;
   T coef[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) coef[t] = (T)scaled_coef(pd, t, s);
+  for (int t = 0; t < pd.nterms; ++t) coef[t] = scaled_coef_t<T>(pd, t, s);
   for (int ms = pd.p - 1; ms >= 0; --ms) {
     const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
     for (int i = b0 + lane; i < b1; i += 32) {
@@ -103,6 +128,23 @@ __device__ void compress_warp(const PlanDev& pd, T* a, double s, int lane) {
         const int src = pd.cmp_src[i * nt + t];
         if (src >= 0) v += coef[t] * a[src];
       }
+      a[i] = v;
+    }
+    __syncwarp();
+  }
+}
+
+// Warp-synchronous version of decompress_smem: one warp owns `a`.
+template <typename T>
+__device__ void decompress_warp(const PlanDev& pd, T* a, double s, int lane) {
+  const int nt = pd.nterms > 0 ? pd.nterms : 1;
+  T coef[FMM_MAX_TERMS];
+  for (int t = 0; t < pd.nterms; ++t) coef[t] = scaled_coef_t<T>(pd, t, s);
+  for (int ms = pd.c; ms <= pd.p; ++ms) {
+    const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
+    for (int i = b0 + lane; i < b1; i += 32) {
+      T v = 0;
+      for (int t = 0; t < pd.nterms; ++t) v += coef[t] * a[pd.rec_src[i * nt + t]];
       a[i] = v;
     }
     __syncwarp();

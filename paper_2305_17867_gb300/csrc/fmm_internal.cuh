@@ -34,6 +34,11 @@ constexpr int kHelmIm = 16;
 __host__ __device__ inline bool kernel_screened(int k) {
   return k == FMM_KERNEL_YUKAWA || k == FMM_KERNEL_HELMHOLTZ || k == kHelmIm;
 }
+// the precisions whose dense M2L runs on the tensor cores (3D)
+__host__ __device__ inline bool prec_tensor(int prec) {
+  return prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3 ||
+         prec == FMM_PREC_F16X3;
+}
 // G(s h) = s^deg G(h): one set of M2L tables serves every level
 __host__ __device__ inline bool kernel_homogeneous(int k) {
   return k == FMM_KERNEL_LAPLACE || k == FMM_KERNEL_BIHARMONIC;
@@ -64,14 +69,21 @@ struct PlanDev {
   int nterms;                      // decompression recurrence terms
   int tsh[FMM_MAX_TERMS][3];       // shift xi - c e_s  (d=2 uses [0],[1])
   double tcoef[FMM_MAX_TERMS];     // -a_xi / a_{c e_s}
+  float tcoef_f[FMM_MAX_TERMS];    // the same rounded to float (float kernels, tpow = 0)
   int tpow[FMM_MAX_TERMS];         // c - |xi|: power of s_l in the scaled coefficient
   // device tables
   const char4* mi;         // nfull: (m0, m1, m2, |m|); d=2 uses (m0, m_s, 0, |m|)
   const double* inv_fact;  // nfull: 1/m!
+  const float* inv_fact_f; // nfull: 1/m! rounded to float (float kernels: no FP64 work)
+  const float* fact_f;     // nfull: m! = m_0! m_1! m_2! rounded to float
   const int16_t* rec_src;  // nfull x nterms: decompression sources (rows with m_s >= c)
   const int16_t* cmp_src;  // nfull x nterms: compression gather sources (-1 = none)
   const int* frow;         // full layout row bases:   [m_s*(p+1) + m_1]   (d=2: [m_s])
   const int* hrow;         // Hankel layout row bases: [m_s*(2p+1) + m_1]  (d=2: [m_s])
+  // P2M monomial segments (d = 3): runs of up to 4 consecutive m_0 of one row
+  // of the full layout, packed m_0 | m_1 << 5 | m_s << 10 | len << 15 | pos << 18
+  const int* p2m_seg;
+  int p2m_nseg;
 };
 
 // Transform sizes and tables of the FFT form of M2L (eq. (convolution_m2l)).
@@ -159,6 +171,7 @@ struct Workspace {
   int tc_mp;        // rows of one offset matrix: |j| padded to the column blocks (tc_shape)
   void* tc_bpar[2];
   void* tc_tmat[2];
+  float* tc_bscale;  // F16X3: the power of two each box's packed multipole was divided by
   // adaptive trees: arena for the per-level windows (parity-split operands
   // and cell -> box maps) and the per-level coordinate bounds
   void* tc_arena;
@@ -215,7 +228,7 @@ struct TcShape {
 inline TcShape tc_shape(int nj, int precision) {
   TcShape s;
   s.row_bytes = 128;
-  s.esz = precision == FMM_PREC_BF16X3 ? 2 : 4;
+  s.esz = (precision == FMM_PREC_BF16X3 || precision == FMM_PREC_F16X3) ? 2 : 4;
   const int row = s.row_bytes / s.esz;
   s.jp = (nj + row - 1) / row * row;
   const int nj16 = (nj + 15) / 16 * 16;

@@ -11,6 +11,8 @@
 
 #include "adaptive.cuh"
 #include "expansions.cuh"
+#include "f32x2.cuh"
+#include "passes_f32.cuh"
 
 namespace {
 
@@ -296,30 +298,6 @@ __device__ __forceinline__ float rsqrt_fast(float x) {  // hardware approximatio
 // Staged sources come in pairs: A = (x0, x1, y0, y1), B = (z0, z1, w0, w1)
 // in box units relative to the target leaf; an odd count is padded with a
 // far, weightless source.
-typedef unsigned long long f2_t;
-__device__ __forceinline__ f2_t f2pack(float lo, float hi) {
-  f2_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(f2_t a, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
-}
-__device__ __forceinline__ f2_t f2sub(f2_t a, f2_t b) {
-  f2_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t f2mul(f2_t a, f2_t b) {
-  f2_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2_t f2fma(f2_t a, f2_t b, f2_t c) {
-  f2_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
 
 // Accumulates one source pair into (acc, g) for the target u = (UX, UY, UZ)
 // (each coordinate broadcast into both halves).  g collects sum w |f1| (u - y)
@@ -662,7 +640,7 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_far(
   {
     const int nt = pd.nterms > 0 ? pd.nterms : 1;
     float cf[FMM_MAX_TERMS];
-    for (int t = 0; t < pd.nterms; ++t) cf[t] = (float)scaled_coef(pd, t, g->s_leaf);
+    for (int t = 0; t < pd.nterms; ++t) cf[t] = scaled_coef_t<float>(pd, t, g->s_leaf);
     for (int q = l16; q < pd.nj; q += 16) Dt[q] = (float)lc[(size_t)bl * pd.nj + q];
     __syncwarp();
     for (int ms = pd.c; ms <= pd.p; ++ms) {  // the same sweep in both halves
@@ -674,7 +652,7 @@ __global__ void __launch_bounds__(32 * kFastWarps) k_leaf_far(
       }
       __syncwarp();
     }
-    for (int q = l16; q < pd.nfull; q += 16) Dt[q] *= (float)pd.inv_fact[q];
+    for (int q = l16; q < pd.nfull; q += 16) Dt[q] *= pd.inv_fact_f[q];
     __syncwarp();
   }
   const float* cb = Dt;
@@ -738,10 +716,36 @@ void leaf_launch(const fmm_plan_s* P, const Workspace& ws, double* phi, double* 
 //      the leaf's colleagues that are leaves, and the finer adjacent leaves
 //      found by descending the non-leaf colleagues -> P2P (eq. (1));
 //   W: the boxes met in that descent that are not adjacent to the leaf
-//      (their parent is) -> M2P, sum_q Ht_q((x - c_C)/s_C) bt_C[q].
+//      (their parent is) -> M2P, sum_q Ht_q((x - c_C)/s_C) bt_C[q], or P2P
+//      when the box holds at most |j| sources;
+//   X pairs of the leaf and its ancestors holding at most |j| targets -> P2P
+//      (the P2L pass leaves those boxes out).
 // ---------------------------------------------------------------------------
 constexpr int kAThreads = 64;
 constexpr int kAStack = 8 * (FMM_MAX_ADEPTH + 1);
+
+// X pairs summed directly: for the leaf b (level l, coordinates bc) and each
+// ancestor C of level >= 2 holding at most nj targets in its subtree, the
+// leaves A of X(C) -- coarser than C, adjacent to C's parent, not adjacent to
+// C; each is a neighbour of C's ancestor at A's own level -- send their
+// sources to b's targets through p2p(A) (the P2L pass skips such C).
+template <typename F>
+__device__ void x_direct(const ATree& t, int b, int l, const int* bc, int nj, F&& p2p) {
+  int lc = l;
+  for (int C = b; C >= 0 && lc >= 2 && t.t1[C] - t.t0[C] <= nj; C = t.par[C], --lc) {
+    const int cc[3] = {bc[0] >> (l - lc), bc[1] >> (l - lc), bc[2] >> (l - lc)};
+    const int pc[3] = {cc[0] >> 1, cc[1] >> 1, cc[2] >> 1};
+    for (int lp = lc - 1; lp >= 0; --lp) {
+      const int an[3] = {cc[0] >> (lc - lp), cc[1] >> (lc - lp), cc[2] >> (lc - lp)};
+      for (int nb = 0; nb < 27; ++nb) {
+        const int nc[3] = {an[0] + nb % 3 - 1, an[1] + (nb / 3) % 3 - 1, an[2] + nb / 9 - 1};
+        const int A = alookup(t, lp, nc);
+        if (A < 0 || !t.leaf[A]) continue;
+        if (aadjacent(lp, nc, lc - 1, pc) && !aadjacent(lp, nc, lc, cc)) p2p(A);
+      }
+    }
+  }
+}
 
 __device__ __forceinline__ double green3(int kern, double lam, double r2) {
   const double ri = rsqrt(r2);
@@ -838,7 +842,8 @@ __global__ void __launch_bounds__(kAThreads) k_aleaf(
         int le, ce[3];
         abox(t, E, &le, ce);
         if (!aadjacent(le, ce, l, bc)) {
-          m2p(E, le, ce);
+          if (t.s1[E] - t.s0[E] <= pd.nj) p2p(E);  // W box of at most |j| sources
+          else m2p(E, le, ce);
         } else if (t.leaf[E]) {
           p2p(E);
         } else {
@@ -851,6 +856,7 @@ __global__ void __launch_bounds__(kAThreads) k_aleaf(
         }
       }
     }
+    x_direct(t, b, l, bc, pd.nj, p2p);
     phi[tperm[ti]] = acc;
   }
 }
@@ -893,7 +899,7 @@ __global__ void __launch_bounds__(kAFThreads) k_aleaf_f32(
     for (int q = threadIdx.x; q < nj; q += blockDim.x) a[q] = (float)lc[(size_t)b * nj + q];
     __syncthreads();
     decompress_smem<float>(pd, a, s);
-    for (int q = threadIdx.x; q < nfull; q += blockDim.x) a[q] *= (float)pd.inv_fact[q];
+    for (int q = threadIdx.x; q < nfull; q += blockDim.x) a[q] *= pd.inv_fact_f[q];
     __syncthreads();
   }
   const int kern = pd.kernel;
@@ -995,7 +1001,8 @@ __global__ void __launch_bounds__(kAFThreads) k_aleaf_f32(
         int le, ce[3];
         abox(t, E, &le, ce);
         if (!aadjacent(le, ce, l, bc)) {
-          m2pf(E, le, ce);
+          if (t.s1[E] - t.s0[E] <= nj) p2p(E);  // W box of at most |j| sources
+          else m2pf(E, le, ce);
         } else if (t.leaf[E]) {
           p2p(E);
         } else {
@@ -1008,6 +1015,7 @@ __global__ void __launch_bounds__(kAFThreads) k_aleaf_f32(
         }
       }
     }
+    x_direct(t, b, l, bc, nj, p2p);  // block-uniform walk (p2p stages block-wide)
     if (valid) phi[tperm[ti]] = (double)far + near_scale * (double)near + (double)m2p;
   }
 }
@@ -1095,6 +1103,10 @@ cudaError_t launch_near_field(const fmm_plan_s* P, const Workspace& ws, double* 
 cudaError_t launch_far_field(const fmm_plan_s* P, const Workspace& ws, double* phi,
                              double* grad, cudaStream_t st, int* nl) {
   const PlanDev& pd = P->pd;
+  if (launch_l2p_f32(P, ws, phi, grad, st)) {  // orders with the warp-per-leaf kernel
+    ++*nl;
+    return cudaGetLastError();
+  }
   const int L = P->desc.levels;
   const int64_t nleaf = nbox_at(3, L);
   const double* lcL = ws.lc + ws.lev_off[L] * pd.nj;

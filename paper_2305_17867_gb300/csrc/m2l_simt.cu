@@ -246,7 +246,7 @@ cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const 
   const int prec = P->desc.precision;
   unsigned done = 0;
   mark_contraction(P, 0, st);
-  if (prec == FMM_PREC_TF32 || prec == FMM_PREC_TF32X3 || prec == FMM_PREC_BF16X3) {
+  if (prec_tensor(prec)) {
     const cudaError_t e = launch_adaptive_m2l_tc(P, ws, t, st, nl, &done);
     if (e != cudaSuccess) return e;
   }

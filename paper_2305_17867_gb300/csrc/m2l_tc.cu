@@ -33,6 +33,7 @@
 #include <cstring>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "adaptive.cuh"
 #include "expansions.cuh"
@@ -56,6 +57,8 @@ struct FmtTF32 {
   using T = float;
   static constexpr int kIdesc = 2;
   static constexpr bool kF16 = false;
+  static constexpr bool kScaled = false;
+  static constexpr CUtensorMapDataType kMapType = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
     const float h = tc::tf32_rna(f);
     hi = h;
@@ -66,11 +69,43 @@ struct FmtBF16 {
   using T = __nv_bfloat16;
   static constexpr int kIdesc = 1;
   static constexpr bool kF16 = true;
+  static constexpr bool kScaled = false;
+  static constexpr CUtensorMapDataType kMapType = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
     hi = __float2bfloat16_rn(f);
     lo = __float2bfloat16_rn(f - __bfloat162float(hi));
   }
 };
+// fp16 (kind::f16, type 0): tf32's 11-bit significand, a 5-bit exponent.
+// The operands are scaled into its range by powers of two (kScaled): a box's
+// multipole bt_q q! by 2^-e_box (its largest entry into [1/2, 1)), the offset
+// matrix Ht_{i+q} / (i! q!) by the power of two of the level's derivative
+// scale; the draining warps multiply each offset's product by 2^e_box of the
+// row's source box and the epilogue by i! and the table scale.  Entries far
+// below a matrix's largest fall into fp16's subnormal range, where hi + lo
+// still holds them to 2^-25 absolute (relative to that largest entry).
+struct FmtF16 {
+  using T = __half;
+  static constexpr int kIdesc = 0;
+  static constexpr bool kF16 = true;
+  static constexpr bool kScaled = true;
+  static constexpr CUtensorMapDataType kMapType = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  static __device__ __forceinline__ void split(float f, T& hi, T& lo) {
+    hi = __float2half_rn(f);
+    lo = __float2half_rn(f - __half2float(hi));
+  }
+};
+
+// the power of two of the derivative tables' scale at level l (Laplace
+// 1/(4 pi s), biharmonic s, the screened and oscillatory kernels 1/s): the
+// F16X3 offset matrices are divided by it
+__host__ __device__ inline double tc_norm(int kernel, double size, int l) {
+  const double s = size / (double)(1 << l);
+  const double ds = kernel == FMM_KERNEL_LAPLACE ? 1.0 / (4.0 * 3.14159265358979323846 * s)
+                    : kernel == FMM_KERNEL_BIHARMONIC ? s
+                                                      : 1.0 / s;
+  return std::ldexp(1.0, std::ilogb(ds));
+}
 
 // A pipeline stage holds one K chunk of every operand the passes read:
 // [sources hi | offset matrices hi | sources lo | offset matrices lo], in
@@ -122,6 +157,46 @@ __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off,
   }
 }
 
+// The F16X3 packing: one warp per box, bt_q q! scaled by 2^-e so that its
+// largest entry lies in [1/2, 1); 2^e goes to bscale in the same parity-split
+// cell order (one value per box).
+template <typename F>
+__global__ void __launch_bounds__(256) k_pack_beta_scaled(const double* __restrict__ mp,
+                                                          const LevOff lev_off, int nj, int JP,
+                                                          const float* __restrict__ fact_f,
+                                                          typename F::T* __restrict__ bhi,
+                                                          typename F::T* __restrict__ blo,
+                                                          float* __restrict__ bscale) {
+  const int l = blockIdx.y + 2;
+  const int nl = 1 << l, H = nl >> 1;
+  const int64_t nbox = (int64_t)1 << (3 * l);
+  const double* mpl = mp + lev_off.o[l] * nj;
+  typename F::T* bh = bhi + lev_off.o[l] * JP;
+  typename F::T* bl = blo + lev_off.o[l] * JP;
+  float* bs = bscale + lev_off.o[l];
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nbox; b += nw) {
+    const int x = (int)(b & (nl - 1)), y = (int)((b >> l) & (nl - 1)), z = (int)(b >> (2 * l));
+    const int sg = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
+    const size_t cell = (((size_t)sg * H + (z >> 1)) * H + (y >> 1)) * H + (x >> 1);
+    const double* src = mpl + b * nj;
+    float m = 0.f;
+    for (int q = lane; q < nj; q += 32) m = fmaxf(m, fabsf((float)src[q] * fact_f[q]));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    const int e = m > 0.f ? ilogbf(m) + 1 : 0;
+    const float down = ldexpf(1.f, -e);  // exact
+    for (int q = lane; q < JP; q += 32) {
+      const float v = q < nj ? (float)src[q] * fact_f[q] * down : 0.f;
+      typename F::T hi, lo;
+      F::split(v, hi, lo);
+      bh[cell * JP + q] = hi;
+      bl[cell * JP + q] = lo;
+    }
+    if (lane == 0) bs[cell] = ldexpf(1.f, e);
+  }
+}
+
 // dense offset matrices A_h[i][q] = Ht_h[i + q] (rows i < NPT, columns q < JP,
 // zero outside j) for the 343 offsets of a level: one block per (offset,
 // table level).  The offsets of adjacent boxes get zero matrices: a CTA that
@@ -129,7 +204,8 @@ __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off,
 // an interaction of.  The offset's Hankel row is split into hi/lo once in
 // shared memory, then expanded.
 template <int D, typename F>
-__global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const double* __restrict__ htab,
+__global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const Geom* __restrict__ g,
+                                                    const double* __restrict__ htab,
                                                     int NPT, int JP,
                                                     typename F::T* __restrict__ thi,
                                                     typename F::T* __restrict__ tlo) {
@@ -158,12 +234,31 @@ __global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const double* __
     return;
   }
   extern __shared__ __align__(16) unsigned char smtm[];
+  const double* H = htab + (size_t)o * pd.nh;
+  const int P2 = 2 * pd.p;
+  if (F::kScaled) {  // Ht_{i+q} / (i! q! norm), with the very float m! the packing uses
+    double* rf = reinterpret_cast<double*>(smtm);  // 1 / m! of the stored set
+    for (int e = threadIdx.x; e < pd.nj; e += blockDim.x) rf[e] = 1.0 / (double)pd.fact_f[e];
+    __syncthreads();
+    const double rn = 1.0 / tc_norm(pd.kernel, g->size, blockIdx.y + 2);  // a power of two
+    for (int e = threadIdx.x; e < NPT * JP; e += blockDim.x) {
+      const int i = e / JP, q = e - i * JP;
+      T vh = zero, vl = zero;
+      if (i < pd.nj && q < pd.nj) {
+        const char4 a = pd.mi[i], b = pd.mi[q];
+        const int m0 = a.x + b.x, m1 = a.y + b.y, m2 = a.z + b.z;
+        const int idx = D == 3 ? pd.hrow[m2 * (P2 + 1) + m1] + m0 : pd.hrow[m1] + m0;
+        F::split((float)(H[idx] * rn * rf[i] * rf[q]), vh, vl);
+      }
+      dh[e] = vh;
+      if (dl) dl[e] = vl;
+    }
+    return;
+  }
   T* hh = reinterpret_cast<T*>(smtm);
   T* hl = hh + pd.nh;
-  const double* H = htab + (size_t)o * pd.nh;
   for (int e = threadIdx.x; e < pd.nh; e += blockDim.x) F::split((float)H[e], hh[e], hl[e]);
   __syncthreads();
-  const int P2 = 2 * pd.p;
   for (int e = threadIdx.x; e < NPT * JP; e += blockDim.x) {
     const int i = e / JP, q = e - i * JP;
     T vh = zero, vl = zero;
@@ -195,7 +290,11 @@ constexpr int kEpiWarps = 16;
 constexpr int kNBuf = 2;         // accumulator buffers of 256 columns
 constexpr int kTmemCols = 512;   // the whole tensor memory of the SM
 constexpr int kTcThreads = (kEpiWarps + 2) * 32;
-constexpr int kColsPerThread = kMaxN / (kEpiWarps / 4);  // running sums per thread
+// running sums per thread: a quarter of the MMA's columns; instantiated for
+// N <= 192 (48) and N <= 256 (64) -- the smaller count leaves the registers
+// that the F16X3 drain's row scales need under the 96-register cap
+constexpr int kColsSmall = 48;
+constexpr int kColsLarge = kMaxN / (kEpiWarps / 4);
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
@@ -257,6 +356,8 @@ struct TcLevel {
   double* lc;            // local expansions (level base, or all boxes with map)
   double* lc2;           // local expansions of level l2 (base)
   const int* map;        // adaptive: window cell -> box; null for uniform levels
+  const float* bscale;   // F16X3: 2^e_box of the level's packed multipoles (cell order)
+  const float* bscale2;  // the same for the riding level l2
   float scale, scale2;   // exact powers of two (shared offset matrices)
   int l, BX, BY, BZ, ntx, nty, first_block, Hx, Hy, Hz;
   int l2;
@@ -270,7 +371,59 @@ struct TcParams {
   int accumulate;      // add into the local expansions (else store)
   long long wait_cycles;  // limit of the pipeline's mbarrier waits
   int* err;
+  // F16X3: the table norm (tc_norm at table level tlev_fixed, or at the CTA's
+  // level when 0) and m! of the local coefficients
+  const Geom* geom;
+  int kernel, tlev_fixed;
+  const float* fact_f;
 };
+
+// F16X3: where the scale 2^e_box of the source box feeding TMEM lane `row`
+// is found, packed in one register (the drain has none to spare): the row's
+// parent (x, y, z) in its level's cell grid (hx, hy, hz) gives
+// base = (z hy + y) hx + x (< 2^21 for levels <= 8), bits 21..26 flag the
+// neighbours that exist (x-1, x+1, y-1, y+1, z-1, z+1), bit 27 the riding
+// level's rows and bit 28 a loaded row inside its grid (0: no source).
+__device__ __forceinline__ int row_scale_setup(const TcLevel& LV, int row, int N1, int NR, int X0,
+                                               int Y0, int Z0, int BX, int BY, int H2) {
+  if (row >= NR) return 0;
+  int x, y, z, hx, hy, hz, ride = 0;
+  if (row < N1) {
+    x = X0 + row % BX;
+    y = Y0 + (row / BX) % BY;
+    z = Z0 + row / (BX * BY);
+    hx = LV.Hx;
+    hy = LV.Hy;
+    hz = LV.Hz;
+  } else {
+    const int n2 = row - N1;
+    x = n2 % H2;
+    y = (n2 / H2) % H2;
+    z = n2 / (H2 * H2);
+    hx = hy = hz = H2;
+    ride = 1;
+  }
+  if (x >= hx || y >= hy || z >= hz) return 0;  // a target outside the grid: not stored
+  const int mask = (x > 0) | ((x + 1 < hx) << 1) | ((y > 0) << 2) | ((y + 1 < hy) << 3) |
+                   ((z > 0) << 4) | ((z + 1 < hz) << 5) | (ride << 6) | (1 << 7);
+  return ((z * hy + y) * hx + x) | (mask << 21);
+}
+
+// 2^e_box of the source (child sg of the parent shifted by (dx, dy, dz)); 0
+// for a source outside the grid, whose TMA rows are zero
+__device__ __forceinline__ float row_scale(const TcLevel& LV, int H2, int rb, int sg, int dx,
+                                           int dy, int dz) {
+  const int mask = rb >> 21;
+  if (!(mask & 128)) return 0.f;
+  const bool ok = (dx >= 0 || (mask & 1)) && (dx <= 0 || (mask & 2)) &&
+                  (dy >= 0 || (mask & 4)) && (dy <= 0 || (mask & 8)) &&
+                  (dz >= 0 || (mask & 16)) && (dz <= 0 || (mask & 32));
+  if (!ok) return 0.f;
+  const bool ride = mask & 64;
+  const int hx = ride ? H2 : LV.Hx, hy = ride ? H2 : LV.Hy, hz = ride ? H2 : LV.Hz;
+  const float* bs = ride ? LV.bscale2 : LV.bscale;
+  return bs[(rb & 0x1fffff) + ((sg * hz + dz) * hy + dy) * hx + dx];
+}
 
 // pipeline wait: the default bounded wait, or (SHORTW, the instantiation that
 // tests run with a shortened limit) the polling wait of mbar_wait_short
@@ -279,7 +432,7 @@ __device__ __forceinline__ bool pwait(uint64_t* bar, uint32_t parity, int* err, 
   return SHORTW ? tc::mbar_wait_short(bar, parity, err, lim) : tc::mbar_wait(bar, parity, err);
 }
 
-template <typename F, int NPASS, bool SHORTW>
+template <typename F, int NPASS, bool SHORTW, int NCOL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const __grid_constant__ TcParams prm) {
   using C = Cfg<NPASS>;
@@ -478,14 +631,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int quad = warp & 3;
     const int cw = (ntot / (kEpiWarps / 4) + 7) / 8 * 8;  // columns of this warp's group
     const int c0 = (warp >> 2) * cw;
-    float sum[kColsPerThread];
+    float sum[NCOL];
 #pragma unroll
-    for (int j = 0; j < kColsPerThread; ++j) sum[j] = 0.f;
+    for (int j = 0; j < NCOL; ++j) sum[j] = 0.f;
     bool ok = true;
     int g = 0;
+    const int row = quad * 32 + lane;  // this thread's TMEM lane
+    const int rb = F::kScaled ? row_scale_setup(LV, row, N1, NR, X0, Y0, Z0, BX, BY, H2) : 0;
     for (int c = 0; c < 216; ++c) {
-      if (!any_far(combo(c), pi0, ncls)) continue;
+      const Combo kc = combo(c);
+      if (!any_far(kc, pi0, ncls)) continue;
       const int bf = g & 1;
+      // F16X3: the power of two the row's source multipole was divided by
+      // (read before the wait, off the critical path)
+      const float rs =
+          F::kScaled ? row_scale(LV, H2, rb, kc.sg, kc.dx, kc.dy, kc.dz) : 1.f;
       if (!pwait<SHORTW>(&accf[bf], (g >> 1) & 1, err, wlim)) {
         ok = false;
         break;
@@ -495,7 +655,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(bf * kMaxN + c0);
       // pairs of 8-column groups: loaded, then summed (16 registers in flight)
 #pragma unroll
-      for (int gp = 0; gp < kColsPerThread / 16; ++gp) {
+      for (int gp = 0; gp < NCOL / 16; ++gp) {
         uint32_t r0[8], r1[8];
         const bool v0 = 16 * gp < cw && c0 + 16 * gp < ntot;
         const bool v1 = 16 * gp + 8 < cw && c0 + 16 * gp + 8 < ntot;
@@ -504,11 +664,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (v0 || v1) tc::tmem_wait();
         if (v0) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) sum[16 * gp + j] += __uint_as_float(r0[j]);
+          for (int j = 0; j < 8; ++j)
+            sum[16 * gp + j] = F::kScaled ? fmaf(__uint_as_float(r0[j]), rs, sum[16 * gp + j])
+                                          : sum[16 * gp + j] + __uint_as_float(r0[j]);
         }
         if (v1) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) sum[16 * gp + 8 + j] += __uint_as_float(r1[j]);
+          for (int j = 0; j < 8; ++j)
+            sum[16 * gp + 8 + j] =
+                F::kScaled ? fmaf(__uint_as_float(r1[j]), rs, sum[16 * gp + 8 + j])
+                           : sum[16 * gp + 8 + j] + __uint_as_float(r1[j]);
         }
       }
       tc::fence_before();
@@ -528,14 +693,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     float* stg = reinterpret_cast<float*>(sm);
     const int pitch = ntot + 1;
     if (good) {
-      const int row = quad * 32 + lane;
 #pragma unroll
-      for (int j = 0; j < kColsPerThread; ++j)
+      for (int j = 0; j < NCOL; ++j)
         if (j < cw && c0 + j < ntot) stg[row * pitch + c0 + j] = sum[j];
     }
     drain_sync();
     if (good) {
       const int nv = min(nc, nj - cb * nc);  // valid columns of this block
+      // F16X3: the table norm of the offset matrices this level used
+      const float tn = F::kScaled ? (float)tc_norm(prm.kernel, prm.geom->size,
+                                                   prm.tlev_fixed ? prm.tlev_fixed : l)
+                                  : 1.f;
       const int nl = 1 << l, Hx = LV.Hx, Hy = LV.Hy, Hz = LV.Hz;
       const int* __restrict__ map = LV.map;
       const int tot = NR * ncls * nv;
@@ -544,7 +712,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int u = rc % ncls, n = rc / ncls;
         const int pi = pi0 + u;
         const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
-        const float v = stg[n * pitch + u * nc + i];
+        float v = stg[n * pitch + u * nc + i];
+        if (F::kScaled) v *= prm.fact_f[cb * nc + i] * tn;  // i! and the table norm
         double* dst = nullptr;
         double scale = 1.0;
         if (n < N1) {
@@ -656,10 +825,11 @@ void build_tables(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st, int
   const PlanDev& pd = P->pd;
   T* thi0 = static_cast<T*>(ws.tc_tmat[0]);
   T* tlo = NPASS == 3 ? static_cast<T*>(ws.tc_tmat[1]) : nullptr;
-  const size_t sm = 2 * sizeof(T) * pd.nh;
+  const size_t sm = std::max(2 * sizeof(T) * pd.nh, sizeof(double) * pd.nj);
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(k_build_tmat<3, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_build_tmat<3, F><<<dim3(343, tlev), 256, sm, st>>>(pd, ws.htab, ws.tc_mp, ws.tc_jp, thi0, tlo);
+  k_build_tmat<3, F><<<dim3(343, tlev), 256, sm, st>>>(pd, ws.geom, ws.htab, ws.tc_mp, ws.tc_jp,
+                                                       thi0, tlo);
 }
 
 // tensor maps of the offset matrices of table level ti
@@ -668,8 +838,7 @@ bool offset_maps(const Workspace& ws, int ti, const TcParams& prm, TcLevel* v) {
   using C = Cfg<NPASS>;
   using T = typename F::T;
   const size_t esz = sizeof(T);
-  const CUtensorMapDataType dt =
-      F::kF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = F::kMapType;
   const int JP = ws.tc_jp, NPT = ws.tc_mp, row = C::kRowBytes / (int)esz;
   const size_t per = (size_t)343 * NPT * JP;
   cuuint64_t dA[2] = {(cuuint64_t)JP, (cuuint64_t)343 * NPT};
@@ -692,8 +861,7 @@ bool source_map(CUtensorMap* m, void* base, int JP, int Hx, int Hy, int Hz, int 
                 int bz) {
   using C = Cfg<NPASS>;
   const size_t esz = sizeof(typename F::T);
-  const CUtensorMapDataType dt =
-      F::kF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapDataType dt = F::kMapType;
   const int row = C::kRowBytes / (int)esz;
   cuuint64_t dB[5] = {(cuuint64_t)JP, (cuuint64_t)Hx, (cuuint64_t)Hy, (cuuint64_t)Hz, 8};
   cuuint64_t sB[4] = {(cuuint64_t)JP * esz, (cuuint64_t)JP * esz * Hx,
@@ -702,23 +870,29 @@ bool source_map(CUtensorMap* m, void* base, int JP, int Hx, int Hy, int Hz, int 
   return make_map(m, base, 5, dB, sB, bB, dt, C::kRowBytes);
 }
 
+template <typename F, int NPASS, bool SHORTW, int NCOL>
+void launch_variant(const TcParams& prm, dim3 grid, size_t sm, cudaStream_t st) {
+  cudaFuncSetAttribute(k_m2l_tc<F, NPASS, SHORTW, NCOL>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_m2l_tc<F, NPASS, SHORTW, NCOL><<<grid, kTcThreads, sm, st>>>(prm);
+}
+
 template <typename F, int NPASS>
 cudaError_t launch_contraction(const fmm_plan_s* P, const TcParams& prm, int nb, cudaStream_t st,
                                bool timed) {
   const size_t sm = smem_bytes<F, NPASS>(prm);
   const TcShape sh = tc_shape(P->pd.nj, P->desc.precision);
   const dim3 grid(nb, sh.nchunk);
+  // a drain warp's columns: cw = N / 4 rounded up to 8
+  const bool small = ((prm.nc * prm.ncls) / (kEpiWarps / 4) + 7) / 8 * 8 <= kColsSmall;
   // per call: the attribute belongs to the current device's context
+  if (timed) mark_contraction(P, 0, st);
   if (prm.wait_cycles < tc::kWaitCycles) {  // a test's shortened waits
-    cudaFuncSetAttribute(k_m2l_tc<F, NPASS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
-    if (timed) mark_contraction(P, 0, st);
-    k_m2l_tc<F, NPASS, true><<<grid, kTcThreads, sm, st>>>(prm);
+    if (small) launch_variant<F, NPASS, true, kColsSmall>(prm, grid, sm, st);
+    else launch_variant<F, NPASS, true, kColsLarge>(prm, grid, sm, st);
   } else {
-    cudaFuncSetAttribute(k_m2l_tc<F, NPASS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
-    if (timed) mark_contraction(P, 0, st);
-    k_m2l_tc<F, NPASS, false><<<grid, kTcThreads, sm, st>>>(prm);
+    if (small) launch_variant<F, NPASS, false, kColsSmall>(prm, grid, sm, st);
+    else launch_variant<F, NPASS, false, kColsLarge>(prm, grid, sm, st);
   }
   if (timed) mark_contraction(P, 1, st);
   return cudaGetLastError();
@@ -737,11 +911,19 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
   T* blo = NPASS == 3 ? static_cast<T*>(ws.tc_bpar[1]) : nullptr;
   LevOff lo;
   for (int l = 0; l <= FMM_MAX_LEVELS; ++l) lo.o[l] = l <= L + 1 ? ws.lev_off[l] : 0;
-  k_pack_beta<F><<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, bhi0, blo);
+  if (F::kScaled)
+    k_pack_beta_scaled<F><<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, pd.fact_f,
+                                                                bhi0, blo, ws.tc_bscale);
+  else
+    k_pack_beta<F><<<dim3(152 * 4, L - 1), 256, 0, st>>>(ws.mp, lo, nj, JP, bhi0, blo);
   if (!tables_ready) build_tables<F, NPASS>(P, ws, st, tlev);
   TcParams prm;
   if (!common_params<F, NPASS>(P, ws, &prm)) return cudaErrorInvalidValue;
   prm.accumulate = 0;  // every coefficient of levels 2..L is written exactly once
+  prm.geom = ws.geom;
+  prm.kernel = pd.kernel;
+  prm.tlev_fixed = shared_t ? 2 : 0;  // shared tables are level 2's
+  prm.fact_f = pd.fact_f;
   const int ngrp = 8 / prm.ncls;
   int nb = 0;
   // largest level first: its tiles start earliest; with shared offset
@@ -758,6 +940,8 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
     nb += v.ntx * v.nty * ntz * ngrp;
     v.lc = ws.lc + ws.lev_off[l] * nj;
     v.map = nullptr;
+    v.bscale = F::kScaled ? ws.tc_bscale + ws.lev_off[l] : nullptr;
+    v.bscale2 = nullptr;
     v.Hx = v.Hy = v.Hz = H;
     v.scale = 1.0f;
     if (shared_t) {  // Ht_l = Ht_2 * (s_2/s_l)^{-deg}: deg -1 (Laplace), +1 (biharmonic)
@@ -774,6 +958,7 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
     if (l == 3 && lmin == 3) {  // level 2: 2 x 2 x 2 parents after level 3's 64
       v.l2 = 2;
       v.lc2 = ws.lc + ws.lev_off[2] * nj;
+      v.bscale2 = F::kScaled ? ws.tc_bscale + ws.lev_off[2] : nullptr;
       v.scale2 = 1.0f;
       if (!source_map<F, NPASS>(&v.S2, bhi0 + ws.lev_off[2] * JP, JP, 2, 2, 2, 2, 2, 2))
         return cudaErrorInvalidValue;
@@ -925,7 +1110,8 @@ cudaError_t launch_m2l_tc(const fmm_plan_s* P, const Workspace& ws, cudaStream_t
   }
   const int prec = P->desc.precision;
   const cudaError_t e =
-      prec == FMM_PREC_BF16X3   ? run_all_levels<FmtBF16, 3>(P, ws, st, tables_ready)
+      prec == FMM_PREC_F16X3    ? run_all_levels<FmtF16, 3>(P, ws, st, tables_ready)
+      : prec == FMM_PREC_BF16X3 ? run_all_levels<FmtBF16, 3>(P, ws, st, tables_ready)
       : prec == FMM_PREC_TF32X3 ? run_all_levels<FmtTF32, 3>(P, ws, st, tables_ready)
                                 : run_all_levels<FmtTF32, 1>(P, ws, st, tables_ready);
   *nl += tables_ready ? 2 : 3;
@@ -938,7 +1124,8 @@ cudaError_t launch_m2l_tc_tables(const fmm_plan_s* P, const Workspace& ws, cudaS
                                  int* nl) {
   const int prec = P->desc.precision;
   const int tlev = kernel_homogeneous(P->pd.kernel) ? 1 : P->desc.levels - 1;
-  if (prec == FMM_PREC_BF16X3) build_tables<FmtBF16, 3>(P, ws, st, tlev);
+  if (prec == FMM_PREC_F16X3) build_tables<FmtF16, 3>(P, ws, st, tlev);
+  else if (prec == FMM_PREC_BF16X3) build_tables<FmtBF16, 3>(P, ws, st, tlev);
   else if (prec == FMM_PREC_TF32X3) build_tables<FmtTF32, 3>(P, ws, st, tlev);
   else build_tables<FmtTF32, 1>(P, ws, st, tlev);
   ++*nl;

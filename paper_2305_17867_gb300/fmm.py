@@ -29,7 +29,7 @@ class FMM:
                -D for an adaptive tree (3D, fp64 or fp32) refined to at most level D,
                splitting boxes that hold more than ``max_leaf`` points
     root_lo, root_size  root box; root_size <= 0 picks the bounding cube per call
-    precision  "fp64" | "fp32" | "tf32" | "tf32x3" | "bf16x3"
+    precision  "fp64" | "fp32" | "tf32" | "tf32x3" | "bf16x3" | "f16x3"
     m2l        "dense" (eq. (m2l_toeplitz) as dense products) | "fft" (its
                convolution form, eq. (convolution_m2l); fp64 and fp32 only) |
                "auto" (fft for fp64/fp32, dense tensor cores otherwise)

@@ -59,8 +59,9 @@ def test_plan_validation_without_gpu():
         assert not h.value
         return rc
 
-    for prec in (2, 3, 4):  # tensor-core formats have no FFT form
+    for prec in (2, 3, 4, 5):  # tensor-core formats have no FFT form
         assert create(precision=prec, m2l=1) == -2
+    assert create(precision=5, levels=-4, max_leaf=64) == -2  # F16X3: uniform trees
     assert create(m2l=3) == -1
     assert create(precision=7) == -1
     assert create(p=0) == -1

@@ -67,6 +67,9 @@ def test_plummer_matches_oracle(torch_cuda, oracle, kernel, p, lam, n):
     ref, st, _ = oracle.fmm_adaptive(kernel, 3, p, src, w, tgt, max_leaf=32, lam=lam,
                                      want_stats=True)
     assert st["W"] > 0 and st["X"] > 0
+    # W and X pairs of both kinds: summed directly (boxes of at most |j|
+    # points) and through M2P / P2L (the few larger boxes)
+    assert 0 < st["WX_direct"] < st["W"] + st["X"]
     got, (nb, depth), nv = gpu_adaptive(torch_cuda, kernel, p, src, w, tgt, lam=lam,
                                         max_leaf=32, counts=True)
     assert (nb, depth) == (st["boxes"], st["depth"])
@@ -88,6 +91,7 @@ def test_depth_cap(torch_cuda, oracle):
     tgt = rng.random((2000, 3))
     ref, st, _ = oracle.fmm_adaptive("laplace", 3, 6, src, w, tgt, max_leaf=8, max_depth=5,
                                      want_stats=True)
+    assert 0 < st["WX_direct"] < st["W"] + st["X"]  # the capped cluster: M2P and P2L
     got, (nb, depth) = gpu_adaptive(torch_cuda, "laplace", 6, src, w, tgt, max_leaf=8, depth=5)
     assert depth == 5 and nb == st["boxes"]
     assert rel_l2(got, ref) < FP64_TOL
