@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--p", type=int, default=0, help="override the expansion order")
     ap.add_argument("--precision", default=os.environ.get("FMM_BENCH_PRECISION", "auto"),
-                    help="fp64|fp32|tf32|tf32x3|bf16x3|f16x3; auto = tf32x3 on uniform 3D trees, "
+                    help="fp64|fp32|tf32|tf32x3|bf16x3|f16x3; auto = f16x3 on uniform 3D trees, "
                          "else fp64")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m2l", default="dense", choices=["dense", "fft"],
@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--alt-precision", default="auto",
                     help="second tensor-core form reported in the same line (none to skip); "
-                         "auto = bf16x3 beside tf32x3 and tf32x3 beside bf16x3")
+                         "auto = tf32x3 beside f16x3 and bf16x3, f16x3 beside tf32x3")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--cpu-level", type=int, default=3,
@@ -247,7 +247,7 @@ def job_throughput(n_per_rank: int, world: int, ms: float) -> float:
 def precision_of(args, wl):
     if args.precision != "auto":
         return args.precision
-    return "tf32x3" if (wl.d == 3 and wl.levels > 0) else "fp64"
+    return "f16x3" if (wl.d == 3 and wl.levels > 0) else "fp64"
 
 
 def make_plan(wl, p, prec, m2l, dev):
@@ -625,7 +625,7 @@ def main():
     if not backward and wl.levels > 0:
         alt = args.alt_precision
         if alt == "auto":
-            alt = {"tf32x3": "bf16x3", "bf16x3": "tf32x3"}.get(prec, "none")
+            alt = {"f16x3": "tf32x3", "tf32x3": "f16x3", "bf16x3": "tf32x3"}.get(prec, "none")
         if alt != "none" and alt != prec:
             arms["alt"] = side_arm(wl, p, alt, "dense", dev, s, wt, t, flush, stream, nm2l,
                                    max(2, min(args.steps, 10)))

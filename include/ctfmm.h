@@ -86,12 +86,13 @@ enum {
  *  F16X3    the same split in fp16 (kind::f16): fp16 keeps tf32's 11-bit
  *           significand, so the products are as exact as TF32X3's, at the
  *           rate of the 16-bit tensor cores.  Its 5-bit exponent is made to
- *           suffice by exact power-of-two scalings: each box's multipole
- *           (times q!) is scaled into [1/2, 1), the offset matrices are taken
- *           as Ht_{i+q} / (i! q!) over a power of two of the level's
- *           derivative scale, and the scalings are undone in float as each
- *           offset's product leaves the accumulator.  3D uniform trees only
- *           (an adaptive plan returns FMM_ERR_UNSUPPORTED).                */
+ *           suffice by scalings: with S_m = m! (sqrt 2)^|m|, each box's
+ *           multipole times S_q is scaled by a power of two into [1/2, 1), the
+ *           offset matrices are taken as Ht_{i+q} / (S_i S_q) over a power of
+ *           two of the level's derivative scale, and the scalings are undone
+ *           in float as each offset's product leaves the accumulator.  3D
+ *           uniform trees only (an adaptive plan returns
+ *           FMM_ERR_UNSUPPORTED).                                          */
 enum {
   FMM_PREC_FP64 = 0,
   FMM_PREC_FP32 = 1,

@@ -436,7 +436,8 @@ extern "C" int fmm_plan_create(fmm_plan_t* out, const fmm_plan_desc* desc) {
     std::vector<float> iff(pd.nfull), ff(pd.nfull);
     for (int i = 0; i < pd.nfull; ++i) {
       iff[i] = (float)inv_fact[i];
-      ff[i] = (float)(1.0 / inv_fact[i]);  // m! < 2^53: exact in double
+      // m! (sqrt 2)^|m| (m! < 2^53: exact in double): the F16X3 operand scale
+      ff[i] = (float)(1.0 / inv_fact[i] * std::pow(std::sqrt(2.0), (double)mi[i].w));
     }
     std::memcpy(h + total - n_sg - 2 * n_iff, iff.data(), sizeof(float) * pd.nfull);
     std::memcpy(h + total - n_sg - n_iff, ff.data(), sizeof(float) * pd.nfull);

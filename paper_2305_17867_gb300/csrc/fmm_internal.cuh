@@ -75,7 +75,8 @@ struct PlanDev {
   const char4* mi;         // nfull: (m0, m1, m2, |m|); d=2 uses (m0, m_s, 0, |m|)
   const double* inv_fact;  // nfull: 1/m!
   const float* inv_fact_f; // nfull: 1/m! rounded to float (float kernels: no FP64 work)
-  const float* fact_f;     // nfull: m! = m_0! m_1! m_2! rounded to float
+  const float* fact_f;     // nfull: m! (sqrt 2)^|m| rounded to float (m! = m_0! m_1! m_2!),
+                           // the F16X3 operand scale (its offset matrices divide by it)
   const int16_t* rec_src;  // nfull x nterms: decompression sources (rows with m_s >= c)
   const int16_t* cmp_src;  // nfull x nterms: compression gather sources (-1 = none)
   const int* frow;         // full layout row bases:   [m_s*(p+1) + m_1]   (d=2: [m_s])

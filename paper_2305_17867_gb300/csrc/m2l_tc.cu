@@ -77,13 +77,17 @@ struct FmtBF16 {
   }
 };
 // fp16 (kind::f16, type 0): tf32's 11-bit significand, a 5-bit exponent.
-// The operands are scaled into its range by powers of two (kScaled): a box's
-// multipole bt_q q! by 2^-e_box (its largest entry into [1/2, 1)), the offset
-// matrix Ht_{i+q} / (i! q!) by the power of two of the level's derivative
-// scale; the draining warps multiply each offset's product by 2^e_box of the
-// row's source box and the epilogue by i! and the table scale.  Entries far
-// below a matrix's largest fall into fp16's subnormal range, where hi + lo
-// still holds them to 2^-25 absolute (relative to that largest entry).
+// The operands are scaled into its range (kScaled).  With S_m = m! (sqrt 2)^|m|
+// (the float table fact_f): a box's multipole bt_q S_q, times 2^-e_box so that
+// its largest entry lies in [1/2, 1); the offset matrix Ht_{i+q} / (S_i S_q)
+// over the power of two of the level's derivative scale.  Dividing by i! q!
+// turns the Hankel entries into binomially weighted Taylor coefficients of G,
+// which grow like (sqrt 2)^{|i+q|} at the nearest offsets (their singularity
+// lies sqrt 2 box sides away in complex directions); (sqrt 2)^{|i+q|} takes
+// that growth out, so the entries stay below ~10 up to p = 16 (65504 is
+// fp16's largest) while the rows of high |i| stay out of the subnormal range.
+// The draining warps multiply each offset's product by 2^e_box of the row's
+// source box and the epilogue by S_i and the table scale.
 struct FmtF16 {
   using T = __half;
   static constexpr int kIdesc = 0;
@@ -157,7 +161,7 @@ __global__ void k_pack_beta(const double* __restrict__ mp, const LevOff lev_off,
   }
 }
 
-// The F16X3 packing: one warp per box, bt_q q! scaled by 2^-e so that its
+// The F16X3 packing: one warp per box, bt_q S_q scaled by 2^-e so that its
 // largest entry lies in [1/2, 1); 2^e goes to bscale in the same parity-split
 // cell order (one value per box).
 template <typename F>
@@ -236,8 +240,8 @@ __global__ void __launch_bounds__(256) k_build_tmat(PlanDev pd, const Geom* __re
   extern __shared__ __align__(16) unsigned char smtm[];
   const double* H = htab + (size_t)o * pd.nh;
   const int P2 = 2 * pd.p;
-  if (F::kScaled) {  // Ht_{i+q} / (i! q! norm), with the very float m! the packing uses
-    double* rf = reinterpret_cast<double*>(smtm);  // 1 / m! of the stored set
+  if (F::kScaled) {  // Ht_{i+q} / (S_i S_q norm), with the very float S_m the packing uses
+    double* rf = reinterpret_cast<double*>(smtm);  // 1 / S_m of the stored set
     for (int e = threadIdx.x; e < pd.nj; e += blockDim.x) rf[e] = 1.0 / (double)pd.fact_f[e];
     __syncthreads();
     const double rn = 1.0 / tc_norm(pd.kernel, g->size, blockIdx.y + 2);  // a power of two
@@ -713,7 +717,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int pi = pi0 + u;
         const int px = pi & 1, py = (pi >> 1) & 1, pz = (pi >> 2) & 1;
         float v = stg[n * pitch + u * nc + i];
-        if (F::kScaled) v *= prm.fact_f[cb * nc + i] * tn;  // i! and the table norm
+        if (F::kScaled) v *= prm.fact_f[cb * nc + i] * tn;  // S_i and the table norm
         double* dst = nullptr;
         double scale = 1.0;
         if (n < N1) {
