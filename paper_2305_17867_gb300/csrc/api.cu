@@ -149,6 +149,7 @@ static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t
   w.at0 = carve<int>(cur, nb);
   w.at1 = carve<int>(cur, nb);
   w.aleaf = carve<int>(cur, nb);
+  w.am2p = carve<unsigned char>(cur, nb);
   w.anch = carve<int>(cur, nb);
   w.ascan = carve<int>(cur, nb + 1);
   w.mp = carve<double>(cur, (size_t)nb * nj);

@@ -199,6 +199,7 @@ struct Workspace {
   int* at0;
   int* at1;
   int* aleaf;
+  unsigned char* am2p;  // per box: a leaf with W boxes of more than |j| sources (float pass)
   int* anch;
   int* ascan;
   uint32_t* skey;
@@ -293,5 +294,7 @@ cudaError_t launch_adaptive_m2l_tc(const fmm_plan_s* P, const Workspace& ws, con
                                    cudaStream_t st, int* nlaunch, unsigned* done_mask);
 cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
                                     cudaStream_t st, int* nlaunch);
+cudaError_t launch_adaptive_leaf_warp(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
+                                      double* phi, cudaStream_t st, int* nlaunch);
 cudaError_t launch_adaptive_leaf(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
                                  double* phi, cudaStream_t st, int* nlaunch);

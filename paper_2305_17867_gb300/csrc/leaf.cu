@@ -861,165 +861,6 @@ __global__ void __launch_bounds__(kAThreads) k_aleaf(
   }
 }
 
-// ---------------------------------------------------------------------------
-// Adaptive tree, float (the mixed-precision modes): one block per leaf B
-// holding targets, the same list walk as k_aleaf (identical in every thread,
-// so the block stays in step).  Coordinates are taken relative to B's centre
-// in units of its side once (FP64 subtraction, then float): targets per
-// block, the sources of every U leaf by the block while staging them in
-// shared memory.  M2P over W runs the float derivative recurrence at
-// (x - c_C)/s_C = u s_B/s_C + (c_B - c_C)/s_C against the staged multipole.
-// ---------------------------------------------------------------------------
-constexpr int kAFThreads = 64;
-constexpr int kAFStage = 256;
-
-__global__ void __launch_bounds__(kAFThreads) k_aleaf_f32(
-    PlanDev pd, const Geom* __restrict__ g, ATree t, const double* __restrict__ lc,
-    const double* __restrict__ mp, const double* __restrict__ tx0, const double* __restrict__ tx1,
-    const double* __restrict__ tx2, const int* __restrict__ tperm, const double* __restrict__ sx0,
-    const double* __restrict__ sx1, const double* __restrict__ sx2, const double* __restrict__ sw,
-    double* __restrict__ phi, int* __restrict__ err) {
-  const int b = blockIdx.x;
-  if (b >= t.loff[t.maxlev + 1] || !t.leaf[b] || t.t1[b] == t.t0[b]) return;
-  const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
-  int l, bc[3];
-  abox(t, b, &l, bc);
-  double cb[3], s;
-  abox_center(g, l, bc, cb, &s);
-  const double inv_s = 1.0 / s;
-  extern __shared__ __align__(16) float smf[];
-  float4* stage = reinterpret_cast<float4*>(smf);  // kAFStage
-  float* a = smf + 4 * kAFStage;                     // nfull: decompressed local / m!
-  float* bt = a + ((nfull + 3) & ~3);                // nj: staged multipole of a W box
-  const int sl = min(pd.c, p + 1) * (p + 1);
-  const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
-  float* S = bt + ((nj + 3) & ~3) + threadIdx.x * per;
-  const bool has_local = l >= 2;
-  if (has_local) {
-    for (int q = threadIdx.x; q < nj; q += blockDim.x) a[q] = (float)lc[(size_t)b * nj + q];
-    __syncthreads();
-    decompress_smem<float>(pd, a, s);
-    for (int q = threadIdx.x; q < nfull; q += blockDim.x) a[q] *= pd.inv_fact_f[q];
-    __syncthreads();
-  }
-  const int kern = pd.kernel;
-  const float lam_s = (float)(pd.lam * s);
-  const float nl2e = -lam_s * 1.4426950408889634f;
-  double near_scale;  // box units -> physical
-  if (kern == FMM_KERNEL_LAPLACE) near_scale = inv_s * (1.0 / (4.0 * 3.14159265358979323846));
-  else if (kern == FMM_KERNEL_YUKAWA) near_scale = inv_s;
-  else near_scale = s;
-  for (int tb = t.t0[b]; tb < t.t1[b]; tb += blockDim.x) {
-    const int ti = tb + threadIdx.x;
-    const bool valid = ti < t.t1[b];
-    float u[3] = {0.f, 0.f, 0.f};
-    if (valid) {
-      u[0] = (float)((tx0[ti] - cb[0]) * inv_s);
-      u[1] = (float)((tx1[ti] - cb[1]) * inv_s);
-      u[2] = (float)((tx2[ti] - cb[2]) * inv_s);
-    }
-    float far = 0.f, near = 0.f, m2p = 0.f;
-    if (has_local) {
-      float gf[3];
-      far = far_field<false>(pd, a, u[0], u[1], u[2], gf);
-    }
-    // P2P against leaf A (block-wide; own leaf: x == y skipped)
-    auto p2p = [&](int A) {
-      const bool own = A == b;
-      for (int jb = t.s0[A]; jb < t.s1[A]; jb += kAFStage) {
-        const int n = min(kAFStage, t.s1[A] - jb);
-        __syncthreads();
-        for (int q = threadIdx.x; q < n; q += blockDim.x) {
-          const int j = jb + q;
-          stage[q] = make_float4((float)((sx0[j] - cb[0]) * inv_s), (float)((sx1[j] - cb[1]) * inv_s),
-                                 (float)((sx2[j] - cb[2]) * inv_s), (float)sw[j]);
-        }
-        __syncthreads();
-        if (valid) {
-          for (int q = 0; q < n; ++q) {
-            const float4 v = stage[q];
-            const float dx = u[0] - v.x, dy = u[1] - v.y, dz = u[2] - v.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, own ? 0.f : 1e-30f)));
-            if (own && r2 == 0.f) continue;
-            const float ri = rsqrt_fast(r2);
-            float gv;
-            if (kern == FMM_KERNEL_LAPLACE) {
-              gv = ri;
-            } else if (kern == FMM_KERNEL_YUKAWA) {
-              float e;
-              asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(nl2e * r2 * ri));
-              gv = e * ri;
-            } else {
-              gv = r2 * ri;
-            }
-            near = fmaf(v.w, gv, near);
-          }
-        }
-      }
-    };
-    // M2P from box C (level lc_, coordinates cc)
-    auto m2pf = [&](int C, int lc_, const int* cc) {
-      double c2[3], s2;
-      abox_center(g, lc_, cc, c2, &s2);
-      __syncthreads();
-      for (int q = threadIdx.x; q < nj; q += blockDim.x) bt[q] = (float)mp[(size_t)C * nj + q];
-      __syncthreads();
-      if (valid) {
-        const double is2 = 1.0 / s2;
-        const float ratio = (float)(s * is2);  // a power of two
-        const float y[3] = {fmaf(u[0], ratio, (float)((cb[0] - c2[0]) * is2)),
-                            fmaf(u[1], ratio, (float)((cb[1] - c2[1]) * is2)),
-                            fmaf(u[2], ratio, (float)((cb[2] - c2[2]) * is2))};
-        float v = 0.f;
-        deriv_point<float>(pd, y, (float)(pd.lam * s2), (float)deriv_scale(pd, s2), S, sl,
-                           [&](int pos, float h) { v = fmaf(h, bt[pos], v); });
-        m2p += v;
-      }
-    };
-    for (int lp = l - 1; lp >= 0; --lp) {  // U: coarser adjacent leaves
-      const int an[3] = {bc[0] >> (l - lp), bc[1] >> (l - lp), bc[2] >> (l - lp)};
-      for (int nb = 0; nb < 27; ++nb) {
-        const int nc[3] = {an[0] + nb % 3 - 1, an[1] + (nb / 3) % 3 - 1, an[2] + nb / 9 - 1};
-        const int A = alookup(t, lp, nc);
-        if (A >= 0 && t.leaf[A] && aadjacent(lp, nc, l, bc)) p2p(A);
-      }
-    }
-    for (int nb = 0; nb < 27; ++nb) {  // colleagues, then their descendants
-      const int nc[3] = {bc[0] + nb % 3 - 1, bc[1] + (nb / 3) % 3 - 1, bc[2] + nb / 9 - 1};
-      const int C = alookup(t, l, nc);
-      if (C < 0) continue;
-      if (t.leaf[C]) {
-        p2p(C);
-        continue;
-      }
-      int stack[kAStack];
-      int sp = 0;
-      for (int ci = 0; ci < 8; ++ci)
-        if (t.child[8 * C + ci] >= 0) stack[sp++] = t.child[8 * C + ci];
-      while (sp > 0) {
-        const int E = stack[--sp];
-        int le, ce[3];
-        abox(t, E, &le, ce);
-        if (!aadjacent(le, ce, l, bc)) {
-          if (t.s1[E] - t.s0[E] <= nj) p2p(E);  // W box of at most |j| sources
-          else m2pf(E, le, ce);
-        } else if (t.leaf[E]) {
-          p2p(E);
-        } else {
-          for (int ci = 0; ci < 8; ++ci) {
-            const int F = t.child[8 * E + ci];
-            if (F < 0) continue;
-            if (sp < kAStack) stack[sp++] = F;
-            else atomicOr(err, 4);
-          }
-        }
-      }
-    }
-    x_direct(t, b, l, bc, nj, p2p);  // block-uniform walk (p2p stages block-wide)
-    if (valid) phi[tperm[ti]] = (double)far + near_scale * (double)near + (double)m2p;
-  }
-}
-
 }  // namespace
 
 cudaError_t launch_leaf_eval(const fmm_plan_s* P, const Workspace& ws, double* phi, double* grad,
@@ -1057,18 +898,7 @@ cudaError_t launch_adaptive_leaf(const fmm_plan_s* P, const Workspace& ws, const
                                  double* phi, cudaStream_t st, int* nl) {
   const PlanDev& pd = P->pd;
   const int nbox = t.loff[t.maxlev + 1];
-  if (P->desc.precision != FMM_PREC_FP64) {
-    const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
-    const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
-    const size_t smem = sizeof(float) * (4 * kAFStage + ((pd.nfull + 3) & ~3) +
-                                         ((pd.nj + 3) & ~3) + (size_t)per * kAFThreads);
-    set_smem(k_aleaf_f32, smem);
-    k_aleaf_f32<<<(unsigned)nbox, kAFThreads, smem, st>>>(
-        pd, ws.geom, t, ws.lc, ws.mp, ws.tx[0], ws.tx[1], ws.tx[2], ws.tperm, ws.sx[0], ws.sx[1],
-        ws.sx[2], ws.sw, phi, &ws.geom->flag);
-    ++*nl;
-    return cudaGetLastError();
-  }
+  if (P->desc.precision != FMM_PREC_FP64) return launch_adaptive_leaf_warp(P, ws, t, phi, st, nl);
   const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
   const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
   const size_t smem = sizeof(double) * (((pd.nfull + 1) & ~1) + (size_t)per * kAThreads);

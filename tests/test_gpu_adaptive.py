@@ -150,6 +150,23 @@ def test_adaptive_fp32_sources_are_targets(torch_cuda, oracle):
     assert rel_l2(got, ref) < FP32_TOL
 
 
+def test_adaptive_fp32_leaf_shapes(torch_cuda, oracle):
+    # the float leaf pass spreads a leaf's targets over the lanes of a warp:
+    # leaves of up to 64 targets (sources are targets, 64 per leaf), a cluster
+    # below the depth cap whose leaves hold hundreds of targets (taken 64 at a
+    # time), and W boxes above |j| sources next to it (M2P, the second kernel)
+    rng = np.random.default_rng(46)
+    src = np.concatenate([0.3 + 1e-3 * rng.random((3000, 3)), rng.random((9000, 3))])
+    w = rng.normal(size=len(src))
+    ref, st, _ = oracle.fmm_adaptive("laplace", 3, 6, src, w, src, max_leaf=64, max_depth=6,
+                                     want_stats=True)
+    assert 0 < st["WX_direct"] < st["W"] + st["X"]
+    got, (nb, depth) = gpu_adaptive(torch_cuda, "laplace", 6, src, w, max_leaf=64, depth=6,
+                                    precision="fp32")
+    assert depth == 6 and nb == st["boxes"]
+    assert rel_l2(got, ref) < FP32_TOL
+
+
 # Tensor-core M2L on the adaptive tree (each level packed into a dense window);
 # tolerances as for the uniform tree's mixed-precision forms.
 TC_TOL = {"tf32x3": 2e-5, "bf16x3": 1e-4, "tf32": 3e-3}
