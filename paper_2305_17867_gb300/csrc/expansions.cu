@@ -1019,7 +1019,7 @@ cudaError_t launch_adaptive_upward(const fmm_plan_s* P, const Workspace& ws, con
     else AP2M(TT, 32);                                                                     \
   } while (0)
     if (P->desc.precision == FMM_PREC_FP64) AP2MN(double);
-    else AP2MN(float);  // float sums from FP64 inputs in the mixed modes
+    else if (!launch_ap2m_f32(P, ws, t, st)) AP2MN(float);  // float sums from FP64 inputs
 #undef AP2MN
 #undef AP2M
     ++*nl;

@@ -474,6 +474,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int N1 = BX * BY * BZ;      // source rows of the primary tile
   const int NR = N1 + H2 * H2 * H2;  // rows the TMA boxes fill (<= 128)
 
+  if (LV.map) {  // an adaptive window's tile whose target cells hold no box: nothing to do
+    int any = 0;
+    for (int e = threadIdx.x; e < N1 * ncls; e += blockDim.x) {
+      const int n = e % N1, u = e / N1;
+      const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
+      if (x < LV.Hx && y < LV.Hy && z < LV.Hz)
+        any |= LV.map[(((size_t)(pi0 + u) * LV.Hz + z) * LV.Hy + y) * LV.Hx + x] >= 0;
+    }
+    if (!__syncthreads_or(any)) return;  // block-uniform, before any barrier or TMEM
+  }
+
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
       tc::mbar_init(&full[s], 1);
@@ -1016,7 +1027,7 @@ __global__ void k_apack(ATree t, int l, const double* __restrict__ mp, int nj, i
     F::split(v, hi, lo);
     bhi[cell * JP + q] = hi;
     if (blo) blo[cell * JP + q] = lo;
-    if (q == 0) map[cell] = b;
+    if (q == 0) map[cell] = t.t1[b] > t.t0[b] ? b : -1;  // only boxes with targets get locals
   }
 }
 

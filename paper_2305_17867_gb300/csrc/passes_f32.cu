@@ -24,6 +24,7 @@
 //
 // Orders p in {4, 6, 8, 10, 12, 16} are compiled (the register rows are
 // sized by p); other orders keep the block-per-box kernels.
+#include "adaptive.cuh"
 #include "expansions.cuh"
 #include "f32x2.cuh"
 #include "passes_f32.cuh"
@@ -334,24 +335,18 @@ __device__ __forceinline__ f2_t lds2(const float2* p) {
   return *reinterpret_cast<const f2_t*>(p);
 }
 
-__global__ void __launch_bounds__(32 * kWarps) k_p2m_seg(PlanDev pd, const Geom* __restrict__ g,
-                                                         int64_t nleaf,
-                                                         const int* __restrict__ start,
-                                                         const float4* __restrict__ rel,
-                                                         double* __restrict__ mp) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (b >= nleaf) return;
+// the segment P2M of one box of side `side` with sources i0..i1: load(j)
+// gives source j's (c - y)/s (x, y, z) and weight (w); the compressed
+// box-scaled multipole goes to out
+template <typename Load>
+__device__ void p2m_seg_body(const PlanDev& pd, double side, int i0, int i1, Load load,
+                             float* base, int lane, double* __restrict__ out) {
   const int p = pd.p, nfull = pd.nfull, nj = pd.nj, nseg = pd.p2m_nseg;
   const int ps = (p + 1) | 1;
-  extern __shared__ __align__(16) float smf[];
-  float* base = smf + (size_t)warp * p2m_floats(p, nfull);
   float2* TX = reinterpret_cast<float2*>(base);  // [16 source pairs][ps]: x^e
   float2* TY = TX + 16 * ps;                     // w y^e
   float2* TZ = TY + 16 * ps;                     // z^e
   float* alpha = base + 3 * 16 * ps * 2;
-  const int i0 = start[b], i1 = start[b + 1];
-  double* out = mp + b * nj;
   if (i0 == i1) {
     for (int q = lane; q < nj; q += 32) out[q] = 0.0;
     return;
@@ -360,9 +355,9 @@ __global__ void __launch_bounds__(32 * kWarps) k_p2m_seg(PlanDev pd, const Geom*
   for (int j0 = i0; j0 < i1; j0 += 32) {
     const int n = min(32, i1 - j0);
     __syncwarp();
-    {  // lane j: powers of source j0 + j, (c - y)/s = -(y - c)/s; past the end, weight 0
-      const float4 r = lane < n ? rel[j0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float ux = -r.x, uy = -r.y, uz = -r.z;
+    {  // lane j: powers of source j0 + j; past the end, weight 0
+      const float4 r = lane < n ? load(j0 + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float ux = r.x, uy = r.y, uz = r.z;
       float vx = 1.f, vy = r.w, vz = 1.f;
       float* px = reinterpret_cast<float*>(TX + (lane >> 1) * ps) + (lane & 1);
       float* py = reinterpret_cast<float*>(TY + (lane >> 1) * ps) + (lane & 1);
@@ -422,8 +417,53 @@ __global__ void __launch_bounds__(32 * kWarps) k_p2m_seg(PlanDev pd, const Geom*
   __syncwarp();
   for (int q = lane; q < nfull; q += 32) alpha[q] *= pd.inv_fact_f[q];
   __syncwarp();
-  compress_warp<float>(pd, alpha, g->s_leaf, lane);
+  compress_warp<float>(pd, alpha, side, lane);
   for (int q = lane; q < nj; q += 32) out[q] = (double)alpha[q];
+}
+
+// uniform tree: the leaves' box-relative float copies (y - c)/s
+__global__ void __launch_bounds__(32 * kWarps) k_p2m_seg(PlanDev pd, const Geom* __restrict__ g,
+                                                         int64_t nleaf,
+                                                         const int* __restrict__ start,
+                                                         const float4* __restrict__ rel,
+                                                         double* __restrict__ mp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (b >= nleaf) return;
+  extern __shared__ __align__(16) float smf[];
+  p2m_seg_body(
+      pd, g->s_leaf, start[b], start[b + 1],
+      [&](int j) {
+        const float4 r = rel[j];
+        return make_float4(-r.x, -r.y, -r.z, r.w);
+      },
+      smf + (size_t)warp * p2m_floats(pd.p, pd.nfull), lane, mp + b * pd.nj);
+}
+
+// adaptive tree: every leaf of level >= 2, (c - y)/s from the FP64 sorted
+// sources (one FP64 subtraction and product per coordinate)
+__global__ void __launch_bounds__(32 * kWarps) k_ap2m_seg(PlanDev pd, const Geom* __restrict__ g,
+                                                          ATree t, const double* __restrict__ x0,
+                                                          const double* __restrict__ x1,
+                                                          const double* __restrict__ x2,
+                                                          const double* __restrict__ w,
+                                                          double* __restrict__ mp) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = t.loff[2] + blockIdx.x * (blockDim.x >> 5) + warp;
+  if (b >= t.loff[t.maxlev + 1] || !t.leaf[b] || t.s1[b] == t.s0[b]) return;
+  int l, bc[3];
+  abox(t, b, &l, bc);
+  double c[3], s;
+  abox_center(g, l, bc, c, &s);
+  const double inv_s = 1.0 / s;
+  extern __shared__ __align__(16) float smf[];
+  p2m_seg_body(
+      pd, s, t.s0[b], t.s1[b],
+      [&](int j) {
+        return make_float4((float)((c[0] - x0[j]) * inv_s), (float)((c[1] - x1[j]) * inv_s),
+                           (float)((c[2] - x2[j]) * inv_s), (float)w[j]);
+      },
+      smf + (size_t)warp * p2m_floats(pd.p, pd.nfull), lane, mp + (size_t)b * pd.nj);
 }
 
 // ---------------------------------------------------------------------------
@@ -599,6 +639,18 @@ bool launch_p2m_f32(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st) {
   const int nw = warps_for(k_p2m_seg, sizeof(float) * p2m_floats(pd.p, pd.nfull), &smem);
   k_p2m_seg<<<(unsigned)((nleaf + nw - 1) / nw), 32 * nw, smem, st>>>(
       pd, ws.geom, nleaf, ws.sstart, ws.sxr, ws.mp + ws.lev_off[L] * pd.nj);
+  return true;
+}
+
+bool launch_ap2m_f32(const fmm_plan_s* P, const Workspace& ws, const ATree& t, cudaStream_t st) {
+  const PlanDev& pd = P->pd;
+  if (pd.d != 3 || pd.p2m_nseg <= 0 || t.maxlev < 2) return false;
+  const int n = t.loff[t.maxlev + 1] - t.loff[2];
+  size_t smem;
+  const int nw = warps_for(k_ap2m_seg, sizeof(float) * p2m_floats(pd.p, pd.nfull), &smem);
+  k_ap2m_seg<<<(unsigned)((n + nw - 1) / nw), 32 * nw, smem, st>>>(pd, ws.geom, t, ws.sx[0],
+                                                                    ws.sx[1], ws.sx[2], ws.sw,
+                                                                    ws.mp);
   return true;
 }
 

@@ -8,6 +8,9 @@
 
 bool passes_f32_order(int p);
 bool launch_p2m_f32(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st);
+// the same for the leaves (level >= 2) of an adaptive tree, from its FP64 points
+struct ATree;
+bool launch_ap2m_f32(const fmm_plan_s* P, const Workspace& ws, const ATree& t, cudaStream_t st);
 // M2M from level l + 1 into level l, L2L from level l into level l + 1, in
 // FP64 (f64) or float arithmetic
 bool launch_m2m_warp(const fmm_plan_s* P, const Workspace& ws, int l, bool f64,
