@@ -150,6 +150,7 @@ static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t
   w.at1 = carve<int>(cur, nb);
   w.aleaf = carve<int>(cur, nb);
   w.am2p = carve<unsigned char>(cur, nb);
+  w.aloff = carve<int>(cur, FMM_MAX_ADEPTH + 4 + 6 * (FMM_MAX_ADEPTH + 2));
   w.anch = carve<int>(cur, nb);
   w.ascan = carve<int>(cur, nb + 1);
   w.mp = carve<double>(cur, (size_t)nb * nj);
@@ -172,7 +173,6 @@ static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t
     // hold fall back to the float CUDA-core M2L)
     w.tc_arena_bytes = (size_t)nb * ((size_t)w.tc_jp * esz * halves + sizeof(int));
     w.tc_arena = carve<char>(cur, w.tc_arena_bytes);
-    w.tc_bounds = carve<int>(cur, 6 * (FMM_MAX_ADEPTH + 2));
   }
   w.bytes = (size_t)(cur - static_cast<char*>(base));
   if (ws) *ws = w;

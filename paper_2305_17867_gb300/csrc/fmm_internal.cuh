@@ -124,6 +124,9 @@ struct fmm_plan_s {
   int deriv_levels;  // adaptive plans: M2L table levels of the current tree
   int last_boxes;    // adaptive plans: boxes and depth of the last tree
   int last_depth;
+  // adaptive plans: per level l, the smallest (6l + k) and largest (6l + 3 + k)
+  // coordinate k of the last tree's boxes, read with its level offsets
+  int abnd[6 * (16 + 2)];
   long long tc_wait_cycles;  // tensor-core M2L pipeline waits (0: the default ~1 s)
 };
 
@@ -177,7 +180,6 @@ struct Workspace {
   // and cell -> box maps) and the per-level coordinate bounds
   void* tc_arena;
   size_t tc_arena_bytes;
-  int* tc_bounds;
   // FFT form of M2L: spectra of the multipoles and of the local sums of every
   // box of levels 2..L (kfp complex each) and of the offset tables
   void* fft_b;
@@ -200,6 +202,8 @@ struct Workspace {
   int* at1;
   int* aleaf;
   unsigned char* am2p;  // per box: a leaf with W boxes of more than |j| sources (float pass)
+  int* aloff;           // tree build: level offsets on the device, the overflow flag, the
+                        // per-level coordinate bounds
   int* anch;
   int* ascan;
   uint32_t* skey;

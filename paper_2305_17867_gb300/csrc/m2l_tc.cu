@@ -987,23 +987,8 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
 }
 
 // ---- adaptive trees: every level packed into a dense window ----------------
-// bounds[6 l + k] / [6 l + 3 + k]: smallest / largest coordinate k of the
-// boxes of level l
-__global__ void k_alevel_bounds_init(int* bounds, int n) {
-  const int i = threadIdx.x;
-  if (i < n) bounds[i] = (i % 6) < 3 ? 0x7fffffff : -1;
-}
-
-__global__ void k_alevel_bounds(ATree t, int* __restrict__ bounds) {
-  const int b = t.loff[2] + blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= t.loff[t.maxlev + 1]) return;
-  int l, c[3];
-  abox(t, b, &l, c);
-  for (int k = 0; k < 3; ++k) {
-    atomicMin(&bounds[6 * l + k], c[k]);
-    atomicMax(&bounds[6 * l + 3 + k], c[k]);
-  }
-}
+// (the windows come from the tree's per-level coordinate bounds, read with its
+// level offsets)
 
 // the level's boxes into Bpar[sigma][Tz][Ty][Tx][JP] (hi and lo) of a window
 // with parent origin W and size H, and map[sigma][Tz][Ty][Tx] = box
@@ -1040,16 +1025,8 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
   const bool shared_t = kernel_homogeneous(pd.kernel);  // G(s h) = s^deg G(h)
   const int tlev = shared_t ? 1 : (t.maxlev - 1);
   const size_t esz = sizeof(T);
-  // coordinate bounds of every level (one synchronisation)
-  const int nbnd = 6 * (t.maxlev + 1);
-  k_alevel_bounds_init<<<1, 128, 0, st>>>(ws.tc_bounds, nbnd);
-  const int nbox2 = t.loff[t.maxlev + 1] - t.loff[2];
-  k_alevel_bounds<<<(nbox2 + 255) / 256, 256, 0, st>>>(t, ws.tc_bounds);
-  *nl += 2;
-  int bnd[6 * (FMM_MAX_ADEPTH + 2)];
-  cudaMemcpyAsync(bnd, ws.tc_bounds, sizeof(int) * nbnd, cudaMemcpyDeviceToHost, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return e;
+  // coordinate bounds of every level, read with the tree's level offsets
+  const int* bnd = P->abnd;
   build_tables<F, NPASS>(P, ws, st, tlev);
   ++*nl;
   TcParams prm;

@@ -305,7 +305,9 @@ __global__ void k_amorton(int64_t n, const double* __restrict__ x, const Geom* _
 }
 
 __global__ void k_atree_root(int* lev, int* par, uint32_t* key, int* s0, int* s1, int* t0,
-                             int* t1, int ns, int nt) {
+                             int* t1, int ns, int nt, int* dlo, int nlo) {
+  for (int l = 0; l < nlo; ++l) dlo[l] = l == 0 ? 0 : 1;  // level offsets: the root alone
+  dlo[nlo] = 0;                                          // overflow flag
   lev[0] = 0;
   par[0] = -1;
   key[0] = 0;
@@ -313,6 +315,33 @@ __global__ void k_atree_root(int* lev, int* par, uint32_t* key, int* s0, int* s1
   s1[0] = ns;
   t0[0] = 0;
   t1[0] = nt;
+}
+
+// per-level coordinate bounds of the boxes of levels >= 2 (the windows of the
+// adaptive tensor-core M2L): bnd[6 l + k] = min, bnd[6 l + 3 + k] = max
+__global__ void k_abounds_init(int* bnd, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) bnd[i] = (i % 6) < 3 ? 0x7fffffff : -1;
+}
+__global__ void k_abounds(const int* __restrict__ dlo, int D, const int* __restrict__ lev,
+                          const uint32_t* __restrict__ key, int* __restrict__ bnd) {
+  // boxes are stored level by level, so a warp mostly holds one level: reduce
+  // over the lanes of each level first, one atomic per level and warp
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;  // the grid covers whole warps
+  int l = -1, c[3] = {0, 0, 0};
+  if (b < dlo[D + 1] && lev[b] >= 2) {
+    l = lev[b];
+    demorton3(key[b], l, c);
+  }
+  const unsigned grp = __match_any_sync(0xffffffffu, l);
+  if (l < 0) return;
+  const bool lead = (threadIdx.x & 31) == __ffs(grp) - 1;
+  for (int k = 0; k < 3; ++k) {
+    const int mn = __reduce_min_sync(grp, c[k]), mx = __reduce_max_sync(grp, c[k]);
+    if (lead) {
+      atomicMin(&bnd[6 * l + k], mn);
+      atomicMax(&bnd[6 * l + 3 + k], mx);
+    }
+  }
 }
 
 // dense index of the coarse levels: grid[(8^l - 1)/7 + code] = box
@@ -349,13 +378,15 @@ __device__ inline void child_bounds(const uint32_t* skey, const uint32_t* tkey, 
   tb[8] = t1;
 }
 
-// split decision and number of non-empty children of every box of one level
-__global__ void k_atree_split(int b0, int b1, int l, int D, int max_leaf,
+// split decision and number of non-empty children of every box of level l,
+// boxes dlo[l] .. dlo[l+1] (level offsets kept on the device)
+__global__ void k_atree_split(const int* __restrict__ dlo, int l, int D, int max_leaf,
                               const uint32_t* __restrict__ key, const int* __restrict__ s0,
                               const int* __restrict__ s1, const int* __restrict__ t0,
                               const int* __restrict__ t1, const uint32_t* __restrict__ skey,
                               const uint32_t* __restrict__ tkey, int* __restrict__ leaf,
                               int* __restrict__ child, int* __restrict__ nch) {
+  const int b0 = dlo[l], b1 = dlo[l + 1];
   const int b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= b1) return;
   for (int ci = 0; ci < 8; ++ci) child[8 * b + ci] = -1;
@@ -373,18 +404,27 @@ __global__ void k_atree_split(int b0, int b1, int l, int D, int max_leaf,
   nch[b - b0] = n;
 }
 
-// create the children of the level's split boxes at next + scan[b - b0]
-__global__ void k_atree_emit(int b0, int b1, int l, int D, int next, const int* __restrict__ scan,
+// create the children of level l's split boxes at dlo[l+1] + scan[b - b0]
+// (scan[cap] = the children of the level, the counts past the level being
+// zero) and set dlo[l+2]; past the capacity, raise dlo[nlo] and add none
+__global__ void k_atree_emit(int* __restrict__ dlo, int nlo, int cap, int l, int D,
+                             const int* __restrict__ scan,
                              uint32_t* __restrict__ key, int* __restrict__ lev,
                              int* __restrict__ par, int* __restrict__ s0, int* __restrict__ s1,
                              int* __restrict__ t0, int* __restrict__ t1,
                              const uint32_t* __restrict__ skey, const uint32_t* __restrict__ tkey,
                              const int* __restrict__ leaf, int* __restrict__ child) {
+  const int b0 = dlo[l], b1 = dlo[l + 1], total = scan[cap];
+  const bool over = (int64_t)b1 + total > cap;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // read by the next level's kernels only
+    dlo[l + 2] = over ? b1 : b1 + total;
+    if (over) dlo[nlo] = 1;
+  }
   const int b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= b1 || leaf[b]) return;
+  if (over || b >= b1 || leaf[b]) return;
   int sb[9], tb[9];
   child_bounds(skey, tkey, key[b], l, D, s0[b], s1[b], t0[b], t1[b], sb, tb);
-  int pos = next + scan[b - b0];
+  int pos = b1 + scan[b - b0];
   for (int ci = 0; ci < 8; ++ci) {
     if (sb[ci + 1] == sb[ci] && tb[ci + 1] == tb[ci]) continue;
     key[pos] = (key[b] << 3) | (uint32_t)ci;
@@ -551,37 +591,52 @@ cudaError_t launch_build_adaptive(const fmm_plan_s* P, const Workspace& ws, int6
     e = asort_points(ws, n_tgt, tgt, nullptr, ws.tx, nullptr, ws.tperm, ws.tkey, D, st, nl);
     if (e != cudaSuccess) return e;
   }
+  // Level by level without the host: the level offsets live on the device
+  // (dlo[0..D+2], overflow flag at dlo[D+3]); every level's kernels cover the
+  // capacity and read their box range there.  One read at the end.
+  const int nlo = D + 3;
+  int* dlo = ws.aloff;
+  const int cap = (int)ws.anb_cap;
   k_atree_root<<<1, 1, 0, st>>>(ws.alev, ws.apar, ws.akey, ws.as0, ws.as1, ws.at0, ws.at1,
-                                (int)n_src, (int)n_tgt);
+                                (int)n_src, (int)n_tgt, dlo, nlo);
   ++*nl;
-  int loff[FMM_MAX_ADEPTH + 2];
-  loff[0] = 0;
-  loff[1] = 1;
-  int maxlev = 0;
   for (int l = 0; l <= D; ++l) {
-    const int b0 = loff[l], b1 = loff[l + 1], n = b1 - b0;
-    k_atree_split<<<nblocks(n, 128), 128, 0, st>>>(b0, b1, l, D, P->desc.max_leaf, ws.akey,
-                                                   ws.as0, ws.as1, ws.at0, ws.at1, ws.skey,
-                                                   ws.tkey, ws.aleaf, ws.achild, ws.anch);
+    // counts past the level's boxes stay zero, so the scan of the whole
+    // capacity ends in the level's total
+    cudaMemsetAsync(ws.anch, 0, sizeof(int) * (size_t)cap, st);
+    k_atree_split<<<nblocks(cap, 128), 128, 0, st>>>(dlo, l, D, P->desc.max_leaf, ws.akey,
+                                                     ws.as0, ws.as1, ws.at0, ws.at1, ws.skey,
+                                                     ws.tkey, ws.aleaf, ws.achild, ws.anch);
     ++*nl;
     if (l == D) break;
-    e = scan_ints(ws.anch, ws.ascan, n, ws.hist_sums, st, nl);
+    e = scan_ints(ws.anch, ws.ascan, cap, ws.hist_sums, st, nl);
     if (e != cudaSuccess) return e;
-    int total = 0;
-    cudaMemcpyAsync(&total, ws.ascan + n, sizeof(int), cudaMemcpyDeviceToHost, st);
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    if (total == 0) break;
-    if ((int64_t)b1 + total > ws.anb_cap) {
-      *overflow = 1;
-      return cudaSuccess;
-    }
-    k_atree_emit<<<nblocks(n, 128), 128, 0, st>>>(b0, b1, l, D, b1, ws.ascan, ws.akey, ws.alev,
-                                                  ws.apar, ws.as0, ws.as1, ws.at0, ws.at1,
-                                                  ws.skey, ws.tkey, ws.aleaf, ws.achild);
+    k_atree_emit<<<nblocks(cap, 128), 128, 0, st>>>(dlo, nlo, cap, l, D, ws.ascan, ws.akey,
+                                                    ws.alev, ws.apar, ws.as0, ws.as1, ws.at0,
+                                                    ws.at1, ws.skey, ws.tkey, ws.aleaf,
+                                                    ws.achild);
     ++*nl;
-    loff[l + 2] = b1 + total;
-    maxlev = l + 1;
   }
+  // the levels' coordinate bounds (for the adaptive M2L's windows), read in the same copy
+  int* dbnd = dlo + nlo + 1;
+  const int nbnd = 6 * (D + 2);
+  k_abounds_init<<<1, 128, 0, st>>>(dbnd, nbnd);
+  k_abounds<<<nblocks(cap, 256), 256, 0, st>>>(dlo, D, ws.alev, ws.akey, dbnd);
+  *nl += 2;
+  static_assert(sizeof(P->abnd) >= sizeof(int) * 6 * (FMM_MAX_ADEPTH + 2), "level bounds");
+  int hlo[FMM_MAX_ADEPTH + 4 + 6 * (FMM_MAX_ADEPTH + 2)];
+  cudaMemcpyAsync(hlo, dlo, sizeof(int) * (nlo + 1 + nbnd), cudaMemcpyDeviceToHost, st);
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  std::copy(hlo + nlo + 1, hlo + nlo + 1 + nbnd, const_cast<fmm_plan_s*>(P)->abnd);
+  if (hlo[nlo]) {
+    *overflow = 1;
+    return cudaSuccess;
+  }
+  int loff[FMM_MAX_ADEPTH + 2];
+  int maxlev = 0;
+  for (int l = 0; l <= D + 1; ++l) loff[l] = hlo[l];
+  for (int l = 1; l <= D; ++l)
+    if (hlo[l + 1] > hlo[l]) maxlev = l;
   t->key = ws.akey;
   t->lev = ws.alev;
   t->par = ws.apar;
