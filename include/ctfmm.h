@@ -289,6 +289,17 @@ int fmm_last_tree(fmm_plan_t plan, int64_t* boxes_out, int* depth_out, int64_t* 
  * limit restored) is unaffected. */
 int fmm_set_wait_limit(fmm_plan_t plan, long long cycles);
 
+/* Testing aid (no counterpart in the paper): the double-word float
+ * arithmetic (a value held as the unevaluated sum of two floats, ~48 bits)
+ * that the mixed-precision modes use for the M2M and L2L shifts above the
+ * leaf level, applied elementwise on the GPU.  x, y and out are HOST arrays
+ * of n doubles; each input is first rounded to a double-word float, the
+ * result is converted back to double:
+ *   op 0: out = x + y     op 1: out = x * y     op 2: out = x * y + x
+ * Synchronous (default stream).  Returns FMM_ERR_ARG for an unknown op,
+ * n < 0, or a null pointer with n > 0; FMM_ERR_CUDA on a CUDA error. */
+int fmm_selftest_dw(int op, int64_t n, const double* x, const double* y, double* out);
+
 /* Everything known about the last evaluation, in one record (synchronises
  * its stream).  Timings and the near-field pair count are filled only when
  * timing was enabled (fmm_set_timing) for that evaluation, else 0 / -1. */

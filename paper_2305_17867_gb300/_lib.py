@@ -56,7 +56,7 @@ EXPORTS = [
     "fmm_eval_backward", "fmm_last_status", "fmm_set_timing", "fmm_phase_times",
     "fmm_last_launch_count", "fmm_status_string", "fmm_eval_noalloc", "fmm_m2l_kernel_time",
     "fmm_last_tree", "fmm_set_wait_limit", "fmm_last_stats", "fmm_eval_f32",
-    "fmm_workspace_size_f32",
+    "fmm_workspace_size_f32", "fmm_selftest_dw",
 ]
 
 
@@ -108,6 +108,8 @@ def load(build: bool = True):
     L.fmm_set_wait_limit.restype = i32
     L.fmm_last_launch_count.argtypes = [vp]
     L.fmm_last_launch_count.restype = i32
+    L.fmm_selftest_dw.argtypes = [i32, i64, vp, vp, vp]
+    L.fmm_selftest_dw.restype = i32
     L.fmm_status_string.argtypes = [i32]
     L.fmm_status_string.restype = ctypes.c_char_p
     _LIB = L

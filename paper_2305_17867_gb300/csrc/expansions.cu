@@ -797,11 +797,12 @@ cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels, d = pd.d;
   // In the mixed modes the leaf multipoles come from the float P2M, so their
-  // first shift runs in float too; shifts higher in the tree stay FP64.
+  // first shift runs in float too; shifts higher in the tree keep FP64-class
+  // precision in double-word floats (FP64 in the FP64 mode).
   const bool mixed = P->desc.precision != FMM_PREC_FP64;
   if (d == 3 && passes_f32_order(pd.p)) {  // warp-per-box kernels
     for (int l = L - 1; l >= 2; --l) {
-      launch_m2m_warp(P, ws, l, !(mixed && l == L - 1), st);
+      launch_m2m_warp(P, ws, l, !mixed ? kShiftF64 : l == L - 1 ? kShiftF32 : kShiftDW, st);
       ++*nl;
     }
     return cudaGetLastError();
@@ -810,7 +811,7 @@ cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
     const double* mpc = ws.mp + ws.lev_off[l + 1] * pd.nj;
     double* mpp = ws.mp + ws.lev_off[l] * pd.nj;
     const bool f32 = mixed && l == L - 1;
-    const size_t tsz = f32 ? 4 : 8;
+    const size_t tsz = f32 ? 4 : 8;  // sizeof(dwf) == sizeof(double)
     const size_t smem = tsz * (3 * (1 << d) * pd.nj + pd.nfull + 2 * (pd.p + 1));
 #define M2M_GO(DD, TT)                                                                     \
   do {                                                                                     \
@@ -818,9 +819,9 @@ cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
     k_m2m<DD, TT><<<(unsigned)nbox_at(DD, l), kThreads, smem, st>>>(pd, ws.geom, l, mpc, mpp); \
   } while (0)
     if (d == 3) {
-      if (f32) M2M_GO(3, float); else M2M_GO(3, double);
+      if (f32) M2M_GO(3, float); else if (mixed) M2M_GO(3, dwf); else M2M_GO(3, double);
     } else {
-      if (f32) M2M_GO(2, float); else M2M_GO(2, double);
+      if (f32) M2M_GO(2, float); else if (mixed) M2M_GO(2, dwf); else M2M_GO(2, double);
     }
 #undef M2M_GO
     ++*nl;
@@ -832,11 +833,12 @@ cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
   const PlanDev& pd = P->pd;
   const int L = P->desc.levels, d = pd.d;
   // In the mixed modes the leaf locals feed the float L2P, so the last shift
-  // (to the leaves) runs in float; shifts higher in the tree stay FP64.
+  // (to the leaves) runs in float; shifts higher in the tree keep FP64-class
+  // precision in double-word floats (FP64 in the FP64 mode).
   const bool mixed = P->desc.precision != FMM_PREC_FP64;
   if (d == 3 && passes_f32_order(pd.p)) {  // warp-per-box kernels
     for (int l = 2; l < L; ++l) {
-      launch_l2l_warp(P, ws, l, !(mixed && l == L - 1), st);
+      launch_l2l_warp(P, ws, l, !mixed ? kShiftF64 : l == L - 1 ? kShiftF32 : kShiftDW, st);
       ++*nl;
     }
     return cudaGetLastError();
@@ -845,7 +847,7 @@ cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
     const double* lcp = ws.lc + ws.lev_off[l] * pd.nj;
     double* lcc = ws.lc + ws.lev_off[l + 1] * pd.nj;
     const bool f32 = mixed && l == L - 1;
-    const size_t tsz = f32 ? 4 : 8;
+    const size_t tsz = f32 ? 4 : 8;  // sizeof(dwf) == sizeof(double)
     const size_t smem = tsz * (7 * pd.nfull + 2 * (pd.p + 1));
 #define L2L_GO(DD, TT)                                                                     \
   do {                                                                                     \
@@ -853,9 +855,9 @@ cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
     k_l2l<DD, TT><<<(unsigned)nbox_at(DD, l), kThreads, smem, st>>>(pd, ws.geom, l, lcp, lcc); \
   } while (0)
     if (d == 3) {
-      if (f32) L2L_GO(3, float); else L2L_GO(3, double);
+      if (f32) L2L_GO(3, float); else if (mixed) L2L_GO(3, dwf); else L2L_GO(3, double);
     } else {
-      if (f32) L2L_GO(2, float); else L2L_GO(2, double);
+      if (f32) L2L_GO(2, float); else if (mixed) L2L_GO(2, dwf); else L2L_GO(2, double);
     }
 #undef L2L_GO
     ++*nl;
@@ -1024,12 +1026,15 @@ cudaError_t launch_adaptive_upward(const fmm_plan_s* P, const Workspace& ws, con
 #undef AP2M
     ++*nl;
   }
-  // M2M, deepest parents first
+  // M2M, deepest parents first: FP64, or double-word floats in the mixed modes
+  const bool f64 = P->desc.precision == FMM_PREC_FP64;
   const size_t smem = sizeof(double) * (3 * 8 * pd.nj + pd.nfull + 2 * (pd.p + 1));
-  set_smem(k_am2m<double>, smem);
+  if (f64) set_smem(k_am2m<double>, smem);
+  else set_smem(k_am2m<dwf>, smem);
   for (int l = t.maxlev - 1; l >= 2; --l) {
     const int n = t.loff[l + 1] - t.loff[l];
-    k_am2m<double><<<(unsigned)n, kThreads, smem, st>>>(pd, ws.geom, t, l, ws.mp);
+    if (f64) k_am2m<double><<<(unsigned)n, kThreads, smem, st>>>(pd, ws.geom, t, l, ws.mp);
+    else k_am2m<dwf><<<(unsigned)n, kThreads, smem, st>>>(pd, ws.geom, t, l, ws.mp);
     ++*nl;
   }
   return cudaGetLastError();
@@ -1057,11 +1062,15 @@ cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, co
     }
     ++*nl;
   }
+  // L2L: FP64, or double-word floats in the mixed modes
+  const bool f64 = P->desc.precision == FMM_PREC_FP64;
   const size_t smem = sizeof(double) * (7 * pd.nfull + 2 * (pd.p + 1));
-  set_smem(k_al2l<double>, smem);
+  if (f64) set_smem(k_al2l<double>, smem);
+  else set_smem(k_al2l<dwf>, smem);
   for (int l = 2; l < t.maxlev; ++l) {
     const int n = t.loff[l + 1] - t.loff[l];
-    k_al2l<double><<<(unsigned)n, kThreads, smem, st>>>(pd, ws.geom, t, l, ws.lc);
+    if (f64) k_al2l<double><<<(unsigned)n, kThreads, smem, st>>>(pd, ws.geom, t, l, ws.lc);
+    else k_al2l<dwf><<<(unsigned)n, kThreads, smem, st>>>(pd, ws.geom, t, l, ws.lc);
     ++*nl;
   }
   return cudaGetLastError();

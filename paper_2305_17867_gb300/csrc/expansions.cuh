@@ -2,6 +2,7 @@
 // and the sparse decompression / compression sweeps of Thm 4.
 #pragma once
 
+#include "dwf.cuh"
 #include "fmm_internal.cuh"
 
 // number of rows of the full layout and the start of slab ms
@@ -21,6 +22,10 @@ __device__ __forceinline__ float pow2_neg<float>(int e) {
 template <>
 __device__ __forceinline__ double pow2_neg<double>(int e) {
   return __longlong_as_double((long long)(1023 - e) << 52);
+}
+template <>
+__device__ __forceinline__ dwf pow2_neg<dwf>(int e) {
+  return dwf(pow2_neg<float>(e), 0.f);
 }
 
 // Box centre at level l (lexicographic index b, x fastest), round-to-nearest
@@ -59,6 +64,10 @@ template <>
 __device__ __forceinline__ float scaled_coef_t<float>(const PlanDev& pd, int t, double s) {
   return pd.tpow[t] == 0 ? pd.tcoef_f[t] : (float)scaled_coef(pd, t, s);
 }
+template <>
+__device__ __forceinline__ dwf scaled_coef_t<dwf>(const PlanDev& pd, int t, double s) {
+  return dwf(scaled_coef(pd, t, s));
+}
 // 1/m! in the kernel's arithmetic
 template <typename T>
 __device__ __forceinline__ T inv_fact_t(const PlanDev& pd, int q);
@@ -69,6 +78,10 @@ __device__ __forceinline__ double inv_fact_t<double>(const PlanDev& pd, int q) {
 template <>
 __device__ __forceinline__ float inv_fact_t<float>(const PlanDev& pd, int q) {
   return pd.inv_fact_f[q];
+}
+template <>
+__device__ __forceinline__ dwf inv_fact_t<dwf>(const PlanDev& pd, int q) {
+  return dwf(pd.inv_fact[q]);
 }
 
 // D[j] given in a[0..nj); fill slabs c..p (decompression, eq. (decompression)).

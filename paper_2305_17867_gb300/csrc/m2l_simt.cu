@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_m2l_simt(PlanDev pd, int l,
 // Adaptive tree: one block per box of level >= 2 holding targets.  V(B) =
 // children of the boxes adjacent to P(B) that are not adjacent to B, found by
 // looking up the 27 neighbours of the parent; their offsets lie in [-3,3]^3.
-template <typename T, bool COUNT_ONLY = false>
+template <typename T>
 __global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
                                                    const double* __restrict__ mp,
                                                    double* __restrict__ lc,
@@ -133,9 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
                                                    unsigned skip_mask) {
   const int b = t.loff[2] + blockIdx.x;
   if (b >= t.loff[t.maxlev + 1] || t.t1[b] == t.t0[b]) return;
-  // COUNT_ONLY: count the interaction lists of the levels in skip_mask (done
-  // on the tensor cores); otherwise translate the other levels
-  if ((((skip_mask >> t.lev[b]) & 1u) != 0) != COUNT_ONLY) return;
+  if ((skip_mask >> t.lev[b]) & 1u) return;  // done on the tensor cores
   const int nj = pd.nj, nh = pd.nh;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* H = reinterpret_cast<T*>(smraw);
@@ -160,19 +158,51 @@ __global__ void __launch_bounds__(kThreads) k_am2l(PlanDev pd, ATree t,
       const int d0 = bc[0] - cc[0], d1 = bc[1] - cc[1], d2 = bc[2] - cc[2];
       if (d0 >= -1 && d0 <= 1 && d1 >= -1 && d1 <= 1 && d2 >= -1 && d2 <= 1) continue;
       const int o = (d0 + 3) + 7 * (d1 + 3) + 49 * (d2 + 3);
-      if (!COUNT_ONLY)
-        m2l_one_source<3, T>(pd, ht + (size_t)o * nh, mp + (size_t)C * nj, H, bs, acc, ii0, ii1,
-                             iis);
+      m2l_one_source<3, T>(pd, ht + (size_t)o * nh, mp + (size_t)C * nj, H, bs, acc, ii0, ii1,
+                           iis);
       ++nv;
     }
   }
   if (threadIdx.x == 0 && nv) atomicAdd(count, nv);
-  if (COUNT_ONLY) return;
 #pragma unroll
   for (int k = 0; k < kMaxI; ++k) {
     const int i = threadIdx.x + k * blockDim.x;
     if (i < nj) lc[(size_t)b * nj + i] += (double)acc[k];
   }
+}
+
+// The interaction-list sizes of the levels in `mask` (translated on the
+// tensor cores, which run over whole windows and count nothing): one warp per
+// box holding targets, lane n < 27 takes the n-th neighbour of the parent and
+// counts its children that are not adjacent to the box.
+constexpr int kCountWarps = 8;
+__global__ void __launch_bounds__(32 * kCountWarps) k_am2l_count(ATree t, unsigned mask,
+                                                                unsigned long long* count) {
+  __shared__ unsigned long long blk;
+  if (threadIdx.x == 0) blk = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int b = t.loff[2] + (int)(blockIdx.x * kCountWarps + (threadIdx.x >> 5));
+  const bool live = b < t.loff[t.maxlev + 1] && t.t1[b] > t.t0[b] && ((mask >> t.lev[b]) & 1u);
+  unsigned nv = 0;
+  if (live && lane < 27) {
+    int l, bc[3];
+    abox(t, b, &l, bc);
+    const int nc[3] = {(bc[0] >> 1) + lane % 3 - 1, (bc[1] >> 1) + (lane / 3) % 3 - 1,
+                       (bc[2] >> 1) + lane / 9 - 1};
+    const int Pn = alookup(t, l - 1, nc);
+    if (Pn >= 0 && !t.leaf[Pn])
+      for (int ci = 0; ci < 8; ++ci) {
+        if (t.child[8 * Pn + ci] < 0) continue;
+        const int d0 = bc[0] - (2 * nc[0] + (ci & 1)), d1 = bc[1] - (2 * nc[1] + ((ci >> 1) & 1)),
+                  d2 = bc[2] - (2 * nc[2] + ((ci >> 2) & 1));
+        nv += !(d0 >= -1 && d0 <= 1 && d1 >= -1 && d1 <= 1 && d2 >= -1 && d2 <= 1);
+      }
+  }
+  nv = __reduce_add_sync(0xffffffffu, nv);
+  if (lane == 0 && nv) atomicAdd(&blk, (unsigned long long)nv);
+  __syncthreads();
+  if (threadIdx.x == 0 && blk) atomicAdd(count, blk);
 }
 
 }  // namespace
@@ -253,8 +283,8 @@ cudaError_t launch_adaptive_m2l(const fmm_plan_s* P, const Workspace& ws, const 
   unsigned all = 0;
   for (int l = 2; l <= t.maxlev; ++l) all |= 1u << l;
   if (done) {  // interaction-list counts of the tensor-core levels
-    k_am2l<float, true><<<nb, 32, 0, st>>>(pd, t, ws.mp, ws.lc, ws.htab, &ws.geom->m2l_count,
-                                          done);
+    k_am2l_count<<<(nb + kCountWarps - 1) / kCountWarps, 32 * kCountWarps, 0, st>>>(
+        t, done, &ws.geom->m2l_count);
     ++*nl;
   }
   if ((done & all) != all) {

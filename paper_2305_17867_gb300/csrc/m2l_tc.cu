@@ -1047,7 +1047,17 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
     const size_t cells = (size_t)8 * H[0] * H[1] * H[2];
     auto a256 = [](size_t x) { return (x + 255) / 256 * 256; };
     const size_t need = a256(cells * cell_bytes) * (NPASS == 3 ? 2 : 1) + a256(cells * sizeof(int));
-    if (used + need > ws.tc_arena_bytes) continue;  // left to the CUDA cores
+    if (need > ws.tc_arena_bytes) continue;  // a window larger than the arena: CUDA cores
+    if (used + need > ws.tc_arena_bytes || prm.nlev == kTcMaxLevels) {
+      // contract the levels packed so far, then pack the next ones into the
+      // same arena (the stream orders the packing after that launch)
+      const cudaError_t e = launch_contraction<F, NPASS>(P, prm, nb, st, false);
+      ++*nl;
+      if (e != cudaSuccess) return e;
+      prm.nlev = 0;
+      nb = 0;
+      used = 0;
+    }
     T* bhi = reinterpret_cast<T*>(arena + used);
     T* blo = NPASS == 3 ? reinterpret_cast<T*>(arena + used + a256(cells * cell_bytes)) : nullptr;
     int* map = reinterpret_cast<int*>(arena + used + a256(cells * cell_bytes) * (NPASS == 3 ? 2 : 1));
@@ -1083,7 +1093,6 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
     if (NPASS == 3 && !source_map<F, NPASS>(&v.Slo, blo, JP, H[0], H[1], H[2], v.BX, v.BY, v.BZ))
       return cudaErrorInvalidValue;
     *done |= 1u << l;
-    if (prm.nlev == kTcMaxLevels) break;
   }
   if (prm.nlev == 0) return cudaGetLastError();
   const cudaError_t r = launch_contraction<F, NPASS>(P, prm, nb, st, false);

@@ -62,6 +62,21 @@ __constant__ float c_quarter[FMM_MAXP + 1] = TC21(0.25);
 __constant__ double c_half_d[FMM_MAXP + 1] = TD21(0.5);
 __constant__ double c_quarter_d[FMM_MAXP + 1] = TD21(0.25);
 #undef TD21
+// the same as double-word floats: (float) v and (float) (v - (float) v)
+constexpr float2 dw_split(double v) {
+  return float2{(float)v, (float)(v - (double)(float)v)};
+}
+#define TW21(h)                                                                           \
+  {dw_split(taylor_coef(0, h)),  dw_split(taylor_coef(1, h)),  dw_split(taylor_coef(2, h)),  \
+   dw_split(taylor_coef(3, h)),  dw_split(taylor_coef(4, h)),  dw_split(taylor_coef(5, h)),  \
+   dw_split(taylor_coef(6, h)),  dw_split(taylor_coef(7, h)),  dw_split(taylor_coef(8, h)),  \
+   dw_split(taylor_coef(9, h)),  dw_split(taylor_coef(10, h)), dw_split(taylor_coef(11, h)), \
+   dw_split(taylor_coef(12, h)), dw_split(taylor_coef(13, h)), dw_split(taylor_coef(14, h)), \
+   dw_split(taylor_coef(15, h)), dw_split(taylor_coef(16, h)), dw_split(taylor_coef(17, h)), \
+   dw_split(taylor_coef(18, h)), dw_split(taylor_coef(19, h)), dw_split(taylor_coef(20, h))}
+__constant__ float2 c_half_w[FMM_MAXP + 1] = TW21(0.5);
+__constant__ float2 c_quarter_w[FMM_MAXP + 1] = TW21(0.25);
+#undef TW21
 
 // h^t / t! in the kernel's arithmetic (H = 0: h = 1/2, H = 1: h = 1/4)
 template <typename T, int H>
@@ -74,6 +89,12 @@ template <>
 __device__ __forceinline__ double shift_coef<double, 0>(int t) { return c_half_d[t]; }
 template <>
 __device__ __forceinline__ double shift_coef<double, 1>(int t) { return c_quarter_d[t]; }
+template <>
+__device__ __forceinline__ dwf shift_coef<dwf, 0>(int t) { return dwf(c_half_w[t].x, c_half_w[t].y); }
+template <>
+__device__ __forceinline__ dwf shift_coef<dwf, 1>(int t) {
+  return dwf(c_quarter_w[t].x, c_quarter_w[t].y);
+}
 
 constexpr int kWarps = 8;  // boxes (warps) per block, fewer when shared memory is short
 
@@ -654,11 +675,15 @@ bool launch_ap2m_f32(const fmm_plan_s* P, const Workspace& ws, const ATree& t, c
   return true;
 }
 
-bool launch_m2m_warp(const fmm_plan_s* P, const Workspace& ws, int l, bool f64,
+bool launch_m2m_warp(const fmm_plan_s* P, const Workspace& ws, int l, ShiftArith a,
                      cudaStream_t st) {
   if (P->pd.d != 3) return false;
-  if (f64) {
+  if (a == kShiftF64) {
 #define GO(PP) m2m_go<double, PP>(P, ws, l, st)
+    PASSES_DISPATCH(P->pd.p, GO)
+#undef GO
+  } else if (a == kShiftDW) {
+#define GO(PP) m2m_go<dwf, PP>(P, ws, l, st)
     PASSES_DISPATCH(P->pd.p, GO)
 #undef GO
   } else {
@@ -669,11 +694,15 @@ bool launch_m2m_warp(const fmm_plan_s* P, const Workspace& ws, int l, bool f64,
   return true;
 }
 
-bool launch_l2l_warp(const fmm_plan_s* P, const Workspace& ws, int l, bool f64,
+bool launch_l2l_warp(const fmm_plan_s* P, const Workspace& ws, int l, ShiftArith a,
                      cudaStream_t st) {
   if (P->pd.d != 3) return false;
-  if (f64) {
+  if (a == kShiftF64) {
 #define GO(PP) l2l_go<double, PP>(P, ws, l, st)
+    PASSES_DISPATCH(P->pd.p, GO)
+#undef GO
+  } else if (a == kShiftDW) {
+#define GO(PP) l2l_go<dwf, PP>(P, ws, l, st)
     PASSES_DISPATCH(P->pd.p, GO)
 #undef GO
   } else {

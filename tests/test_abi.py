@@ -69,3 +69,16 @@ def test_plan_validation_without_gpu():
     assert create(kernel=1, lam=0.0) == -1  # Yukawa needs lambda > 0
     assert create(kernel=3, d=2, lam=1.0) == -2  # Helmholtz only in 3D
     assert create(kernel=3, lam=1.0, levels=-4, max_leaf=64) == -2  # Helmholtz: uniform trees
+
+
+def test_dw_selftest_validation_without_gpu():
+    # argument checks come before any CUDA call
+    from paper_2305_17867_gb300 import _lib
+
+    L = _lib.load()
+    x = (ctypes.c_double * 2)(1.0, 2.0)
+    assert L.fmm_selftest_dw(3, 2, x, x, x) == -1  # FMM_ERR_ARG
+    assert L.fmm_selftest_dw(-1, 2, x, x, x) == -1  # FMM_ERR_ARG
+    assert L.fmm_selftest_dw(0, -1, x, x, x) == -1  # FMM_ERR_ARG
+    assert L.fmm_selftest_dw(0, 2, None, x, x) == -1  # FMM_ERR_ARG
+    assert L.fmm_selftest_dw(1, 0, None, None, None) == _lib.FMM_OK
