@@ -436,9 +436,28 @@ __global__ void __launch_bounds__(32 * kP2mWarps) k_ap2m_warp(
 // a product of 1D Taylor shifts, applied one axis at a time (x, then y on the
 // embedded slabs m_s < c, then the slow axis into every slab); the children's
 // sigmas are summed, rescaled to the parent's side (2^{-|q|}) and compressed
-// once with the parent's recurrence (M^T is linear).  One block per parent;
-// the 2^d children are shifted concurrently.
+// once with the parent's recurrence (M^T is linear).  One block per parent.
+// The children on either side of the centre along an axis have h = +1/2 and
+// -1/2 (child units), so the shifts of a pair sum to
+//   sum_t f_t (b0 + (-1)^t b1)[q - t],  f_t = (1/2)^t / t!:
+// the pair's sum E and difference O are formed first and one shift reads E at
+// even and O at odd t.  Summing right after each axis (linearity) leaves 4
+// pairs for x, 2 for y and 1 for the slow axis.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline size_t m2m_block_elems(int D, int nj, int nfull, int p) {
+  return (size_t)((1 << D) + (1 << D) / 2 + (D == 3 ? 2 : 0)) * nj + nfull + p + 1;
+}
+
+// in place: (a, b) -> (a + b, a - b) for the n-element arrays a and b
+template <typename T>
+__device__ __forceinline__ void pair_eo(T* a, T* b, int n) {
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const T x = a[q], y = b[q];
+    a[q] = x + y;
+    b[q] = x - y;
+  }
+}
+
 // body of M2M for a parent of side s: child ci's multipole is the row
 // crow[ci] of mpc (-1: no child, taken as zero); the result goes to out
 template <int D, typename T>
@@ -447,62 +466,78 @@ __device__ void m2m_body(const PlanDev& pd, double s, const int64_t* crow,
   constexpr int NC = 1 << D;
   const int p = pd.p, c = pd.c, nfull = pd.nfull, nj = pd.nj;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* bet = reinterpret_cast<T*>(smraw);  // NC * nj
-  T* X = bet + NC * nj;                   // NC * nj
-  T* Y = X + NC * nj;                     // NC * nj  (D == 3)
-  T* sig = Y + NC * nj;                   // nfull
-  T* tab = sig + nfull;                   // 2 (sign) x (p+1): (+-1/2)^e / e!
-  if (threadIdx.x <= p) {
-    // (1/2)^e / e!: inv_fact[e] is 1/e! (multi-index (e,0,0) sits at position e);
-    // the power of two is exact, so the product is rounded once in either type
-    const T v = pow2_neg<T>((int)threadIdx.x) * inv_fact_t<T>(pd, threadIdx.x);
-    tab[threadIdx.x] = v;                                    // h = +1/2 (child bit 0)
-    tab[(p + 1) + threadIdx.x] = (threadIdx.x & 1) ? -v : v;  // h = -1/2 (child bit 1)
-  }
-  for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
-    const int ci = e / nj, q = e % nj;
-    bet[e] = crow[ci] >= 0 ? (T)mpc[(size_t)crow[ci] * nj + q] : (T)0;
+  T* bet = reinterpret_cast<T*>(smraw);         // NC * nj: x pairs (E, O) of the children
+  T* X = bet + NC * nj;                          // NC/2 * nj: x-shifted pairs, then y (E, O)
+  T* Y = X + (NC / 2) * nj;                      // 2 * nj (D == 3): y-shifted, then slow (E, O)
+  T* sig = Y + (D == 3 ? 2 * nj : 0);            // nfull
+  T* f = sig + nfull;                            // p + 1: (1/2)^t / t!
+  if (threadIdx.x <= p)  // the power of two is exact: one rounding in either type
+    f[threadIdx.x] = pow2_neg<T>((int)threadIdx.x) * inv_fact_t<T>(pd, threadIdx.x);
+  // children 2k and 2k+1 differ in the x bit: their sum and difference
+  for (int e = threadIdx.x; e < (NC / 2) * nj; e += blockDim.x) {
+    const int k = e / nj, q = e % nj;
+    const T b0 = crow[2 * k] >= 0 ? (T)mpc[(size_t)crow[2 * k] * nj + q] : (T)0;
+    const T b1 = crow[2 * k + 1] >= 0 ? (T)mpc[(size_t)crow[2 * k + 1] * nj + q] : (T)0;
+    bet[2 * k * nj + q] = b0 + b1;
+    bet[(2 * k + 1) * nj + q] = b0 - b1;
   }
   __syncthreads();
-  // x shift on the stored slabs: X[q] = sum_{t <= q0} f[t] bet[q - t]
-  for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
-    const int ci = e / nj, q = e % nj;
-    const T* f = tab + (ci & 1) * (p + 1);
+  // x shift of each pair on the stored slabs: X[k][q] = sum_{t <= q0} f_t (E|O)[q - t]
+  for (int e = threadIdx.x; e < (NC / 2) * nj; e += blockDim.x) {
+    const int k = e / nj, q = e % nj;
+    const T* E = bet + 2 * k * nj;
+    const T* O = E + nj;
     const int q0 = pd.mi[q].x;
-    T acc = 0;
-    for (int t = 0; t <= q0; ++t) acc += f[t] * bet[e - t];
-    X[e] = acc;
+    T ae = 0, ao = 0;
+    int t = 0;
+    for (; t + 1 <= q0; t += 2) {
+      ae += f[t] * E[q - t];
+      ao += f[t + 1] * O[q - t - 1];
+    }
+    if (t <= q0) ae += f[t] * E[q - t];
+    X[e] = ae + ao;
   }
   __syncthreads();
-  const T* Zin = X;
+  const T* Z = X;  // the slow axis' pair: E at 0, O at nj
   if (D == 3) {
-    // y shift: Y[q0, q1, is] = sum_{t <= q1} f[t] X[q0, q1 - t, is]
-    for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
-      const int ci = e / nj, q = e % nj;
-      const T* f = tab + ((ci >> 1) & 1) * (p + 1);
-      const char4 m = pd.mi[q];
-      const T* Xc = X + ci * nj;
-      T acc = 0;
-      for (int t = 0; t <= m.y; ++t) acc += f[t] * Xc[pd.frow[m.z * (p + 1) + m.y - t] + m.x];
-      Y[e] = acc;
+    // X[2m], X[2m+1] differ in the y bit (slow bit m)
+    pair_eo<T>(X, X + nj, nj);
+    pair_eo<T>(X + 2 * nj, X + 3 * nj, nj);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * nj; e += blockDim.x) {
+      const int m = e / nj, q = e % nj;
+      const char4 mi = pd.mi[q];
+      const T* E = X + 2 * m * nj;
+      const T* O = E + nj;
+      const int* fr = pd.frow + mi.z * (p + 1) + mi.y;  // row m_1 - t at fr[-t]
+      T ae = 0, ao = 0;
+      int t = 0;
+      for (; t + 1 <= mi.y; t += 2) {
+        ae += f[t] * E[fr[-t] + mi.x];
+        ao += f[t + 1] * O[fr[-t - 1] + mi.x];
+      }
+      if (t <= mi.y) ae += f[t] * E[fr[-t] + mi.x];
+      Y[e] = ae + ao;
     }
     __syncthreads();
-    Zin = Y;
+    pair_eo<T>(Y, Y + nj, nj);
+    Z = Y;
+  } else {
+    pair_eo<T>(X, X + nj, nj);  // X[0], X[1] differ in the slow bit
   }
-  // slow-axis shift into every slab, summed over the children, rescaled
+  __syncthreads();
+  // slow-axis shift into every slab, rescaled
   for (int q = threadIdx.x; q < nfull; q += blockDim.x) {
     const char4 m = pd.mi[q];
     const int q0 = m.x, q1 = D == 3 ? m.y : 0, qs = D == 3 ? m.z : m.y;
-    T acc = 0;
-    for (int ci = 0; ci < NC; ++ci) {
-      const T* f = tab + ((ci >> (D - 1)) & 1) * (p + 1);
-      const T* Zc = Zin + ci * nj;
-      for (int is = 0; is <= min(qs, c - 1); ++is) {
-        const int src = D == 3 ? pd.frow[is * (p + 1) + q1] + q0 : pd.frow[is] + q0;
-        acc += f[qs - is] * Zc[src];
-      }
+    T ae = 0, ao = 0;
+    for (int is = 0; is <= min(qs, c - 1); ++is) {
+      const int src = D == 3 ? pd.frow[is * (p + 1) + q1] + q0 : pd.frow[is] + q0;
+      const int t = qs - is;
+      if (t & 1) ao += f[t] * Z[nj + src];
+      else ae += f[t] * Z[src];
     }
-    sig[q] = acc * pow2_neg<T>((int)m.w);
+    sig[q] = (ae + ao) * pow2_neg<T>((int)m.w);
   }
   __syncthreads();
   compress_smem<T>(pd, sig, s);
@@ -544,71 +579,89 @@ __global__ void __launch_bounds__(kThreads) k_am2m(PlanDev pd, const Geom* __res
 // ---------------------------------------------------------------------------
 // L2L (Sec. 4.2, eq. (l2l-expr), un-normalised): with Dt = M Lt_parent,
 //   Lt_child_i += 2^{-|i|} sum_{q >= i} Dt_q (h/S)^{q-i} / (q-i)!,  i in j,
-// h = c_child - c_parent = +-S/4 per axis.  Applied as 1D shifts along x
-// (two sign variants), y (four variants) and the slow axis (eight children,
-// stored slabs only); the x and y partial shifts are shared by the children.
+// h = c_child - c_parent = +-S/4 per axis.  Applied as 1D shifts along x, y
+// and the slow axis (into the children's stored slabs).  The children on
+// either side along an axis have h/S = -1/4 (bit 0) and +1/4 (bit 1): with
+// g_t = (1/4)^t / t!, the even-t and odd-t partial sums se, so of one shift
+// give se - so for bit 0 and se + so for bit 1, so each axis costs one shift
+// per incoming array: 1 along x, 2 along y, 4 along the slow axis.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline size_t l2l_block_elems(int D, int nfull, int p) {
+  return (size_t)(D == 3 ? 7 : 3) * nfull + p + 1;
+}
+
 // body of L2L for a parent of side s with local row `par`: child ci receives
 // into row crow[ci] of lcc (-1: no child)
 template <int D, typename T>
 __device__ void l2l_body(const PlanDev& pd, double s, const double* __restrict__ par,
                          const int64_t* crow, double* __restrict__ lcc) {
+  constexpr int NC = 1 << D;
   const int p = pd.p, nfull = pd.nfull, nj = pd.nj;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Dt = reinterpret_cast<T*>(smraw);       // nfull
-  T* X = Dt + nfull;                          // 2 * nfull
-  T* Y = X + 2 * nfull;                       // 4 * nfull (D == 3)
-  T* tab = Y + (D == 3 ? 4 * nfull : 0);      // 2 x (p+1): (-+1/4)^e / e!
+  T* X = Dt + nfull;                          // 2 * nfull: x bit 0, 1
+  T* Y = X + 2 * nfull;                       // 4 * nfull (D == 3): sx + 2 sy
+  T* g = Y + (D == 3 ? 4 * nfull : 0);        // p + 1: (1/4)^t / t!
   for (int q = threadIdx.x; q < nj; q += blockDim.x) Dt[q] = (T)par[q];
-  if (threadIdx.x <= p) {
-    // (1/4)^e / e!
-    const T v = pow2_neg<T>(2 * (int)threadIdx.x) * inv_fact_t<T>(pd, threadIdx.x);
-    tab[threadIdx.x] = (threadIdx.x & 1) ? -v : v;  // child bit 0: h/S = -1/4
-    tab[(p + 1) + threadIdx.x] = v;                  // child bit 1: h/S = +1/4
-  }
+  if (threadIdx.x <= p)
+    g[threadIdx.x] = pow2_neg<T>(2 * (int)threadIdx.x) * inv_fact_t<T>(pd, threadIdx.x);
   __syncthreads();
   decompress_smem<T>(pd, Dt, s);
-  // x shift: X[v][q] = sum_{t >= 0} g_v[t] Dt[q + t] along the row of q
-  for (int e = threadIdx.x; e < 2 * nfull; e += blockDim.x) {
-    const int v = e / nfull, q = e % nfull;
+  // x shift along the row of q: u[t] = Dt[q + t]
+  for (int q = threadIdx.x; q < nfull; q += blockDim.x) {
     const char4 m = pd.mi[q];
     const int qs = D == 3 ? m.z : m.y, q1 = D == 3 ? m.y : 0;
     const int len = p - qs - q1 - m.x + 1;
-    const T* gv = tab + v * (p + 1);
-    T acc = 0;
-    for (int t = 0; t < len; ++t) acc += gv[t] * Dt[q + t];
-    X[e] = acc;
+    T se = 0, so = 0;
+    int t = 0;
+    for (; t + 1 < len; t += 2) {
+      se += g[t] * Dt[q + t];
+      so += g[t + 1] * Dt[q + t + 1];
+    }
+    if (t < len) se += g[t] * Dt[q + t];
+    X[q] = se - so;
+    X[nfull + q] = se + so;
   }
   __syncthreads();
-  const T* Zin = X;
+  const T* Z = X;  // the slow axis' inputs: NC/2 arrays of nfull
   if (D == 3) {
-    for (int e = threadIdx.x; e < 4 * nfull; e += blockDim.x) {
-      const int v = e / nfull, q = e % nfull;  // v = sx + 2 sy
+    // y shift of each x variant: u[t] = X_sx[row m_1 + t]
+    for (int e = threadIdx.x; e < 2 * nfull; e += blockDim.x) {
+      const int sx = e / nfull, q = e % nfull;
       const char4 m = pd.mi[q];
-      const T* gv = tab + (v >> 1) * (p + 1);
-      const T* Xv = X + (v & 1) * nfull;
-      T acc = 0;
-      for (int t = 0; t <= p - m.z - m.x - m.y; ++t)
-        acc += gv[t] * Xv[pd.frow[m.z * (p + 1) + m.y + t] + m.x];
-      Y[e] = acc;
+      const T* Xv = X + sx * nfull;
+      const int* fr = pd.frow + m.z * (p + 1) + m.y;
+      const int len = p - m.z - m.x - m.y + 1;
+      T se = 0, so = 0;
+      int t = 0;
+      for (; t + 1 < len; t += 2) {
+        se += g[t] * Xv[fr[t] + m.x];
+        so += g[t + 1] * Xv[fr[t + 1] + m.x];
+      }
+      if (t < len) se += g[t] * Xv[fr[t] + m.x];
+      Y[sx * nfull + q] = se - so;        // sy = 0
+      Y[(sx + 2) * nfull + q] = se + so;  // sy = 1
     }
     __syncthreads();
-    Zin = Y;
+    Z = Y;
   }
-  constexpr int NC = 1 << D;
-  for (int e = threadIdx.x; e < NC * nj; e += blockDim.x) {
-    const int ci = e / nj, i = e % nj;
-    if (crow[ci] < 0) continue;
+  // slow axis into the stored slabs of the children (v, bit 0) and (v, bit 1)
+  for (int e = threadIdx.x; e < (NC / 2) * nj; e += blockDim.x) {
+    const int v = e / nj, i = e % nj;
+    const int64_t r0 = crow[v], r1 = crow[v + NC / 2];
+    if (r0 < 0 && r1 < 0) continue;
     const char4 m = pd.mi[i];
     const int i0 = m.x, i1 = D == 3 ? m.y : 0, is = D == 3 ? m.z : m.y;
-    const T* gv = tab + ((ci >> (D - 1)) & 1) * (p + 1);
-    const T* Zv = Zin + (ci & (NC / 2 - 1)) * nfull;
-    T acc = 0;
+    const T* Zv = Z + v * nfull;
+    T se = 0, so = 0;
     for (int qs = is; qs <= p - i0 - i1; ++qs) {
       const int src = D == 3 ? pd.frow[qs * (p + 1) + i1] + i0 : pd.frow[qs] + i0;
-      acc += gv[qs - is] * Zv[src];
+      if ((qs - is) & 1) so += g[qs - is] * Zv[src];
+      else se += g[qs - is] * Zv[src];
     }
-    lcc[(size_t)crow[ci] * nj + i] += (double)(acc * pow2_neg<T>((int)m.w));
+    const T sc = pow2_neg<T>((int)m.w);
+    if (r0 >= 0) lcc[(size_t)r0 * nj + i] += (double)((se - so) * sc);
+    if (r1 >= 0) lcc[(size_t)r1 * nj + i] += (double)((se + so) * sc);
   }
 }
 
@@ -812,7 +865,7 @@ cudaError_t launch_m2m(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
     double* mpp = ws.mp + ws.lev_off[l] * pd.nj;
     const bool f32 = mixed && l == L - 1;
     const size_t tsz = f32 ? 4 : 8;  // sizeof(dwf) == sizeof(double)
-    const size_t smem = tsz * (3 * (1 << d) * pd.nj + pd.nfull + 2 * (pd.p + 1));
+    const size_t smem = tsz * m2m_block_elems(d, pd.nj, pd.nfull, pd.p);
 #define M2M_GO(DD, TT)                                                                     \
   do {                                                                                     \
     set_smem(k_m2m<DD, TT>, smem);                                                         \
@@ -848,7 +901,7 @@ cudaError_t launch_l2l(const fmm_plan_s* P, const Workspace& ws, cudaStream_t st
     double* lcc = ws.lc + ws.lev_off[l + 1] * pd.nj;
     const bool f32 = mixed && l == L - 1;
     const size_t tsz = f32 ? 4 : 8;  // sizeof(dwf) == sizeof(double)
-    const size_t smem = tsz * (7 * pd.nfull + 2 * (pd.p + 1));
+    const size_t smem = tsz * l2l_block_elems(d, pd.nfull, pd.p);
 #define L2L_GO(DD, TT)                                                                     \
   do {                                                                                     \
     set_smem(k_l2l<DD, TT>, smem);                                                         \
@@ -1028,7 +1081,7 @@ cudaError_t launch_adaptive_upward(const fmm_plan_s* P, const Workspace& ws, con
   }
   // M2M, deepest parents first: FP64, or double-word floats in the mixed modes
   const bool f64 = P->desc.precision == FMM_PREC_FP64;
-  const size_t smem = sizeof(double) * (3 * 8 * pd.nj + pd.nfull + 2 * (pd.p + 1));
+  const size_t smem = sizeof(double) * m2m_block_elems(3, pd.nj, pd.nfull, pd.p);
   if (f64) set_smem(k_am2m<double>, smem);
   else set_smem(k_am2m<dwf>, smem);
   for (int l = t.maxlev - 1; l >= 2; --l) {
@@ -1064,7 +1117,7 @@ cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, co
   }
   // L2L: FP64, or double-word floats in the mixed modes
   const bool f64 = P->desc.precision == FMM_PREC_FP64;
-  const size_t smem = sizeof(double) * (7 * pd.nfull + 2 * (pd.p + 1));
+  const size_t smem = sizeof(double) * l2l_block_elems(3, pd.nfull, pd.p);
   if (f64) set_smem(k_al2l<double>, smem);
   else set_smem(k_al2l<dwf>, smem);
   for (int l = 2; l < t.maxlev; ++l) {

@@ -405,16 +405,16 @@ __global__ void k_atree_split(const int* __restrict__ dlo, int l, int D, int max
 }
 
 // create the children of level l's split boxes at dlo[l+1] + scan[b - b0]
-// (scan[cap] = the children of the level, the counts past the level being
+// (scan[nscan] = the children of the level, the counts past the level being
 // zero) and set dlo[l+2]; past the capacity, raise dlo[nlo] and add none
-__global__ void k_atree_emit(int* __restrict__ dlo, int nlo, int cap, int l, int D,
+__global__ void k_atree_emit(int* __restrict__ dlo, int nlo, int cap, int nscan, int l, int D,
                              const int* __restrict__ scan,
                              uint32_t* __restrict__ key, int* __restrict__ lev,
                              int* __restrict__ par, int* __restrict__ s0, int* __restrict__ s1,
                              int* __restrict__ t0, int* __restrict__ t1,
                              const uint32_t* __restrict__ skey, const uint32_t* __restrict__ tkey,
                              const int* __restrict__ leaf, int* __restrict__ child) {
-  const int b0 = dlo[l], b1 = dlo[l + 1], total = scan[cap];
+  const int b0 = dlo[l], b1 = dlo[l + 1], total = scan[nscan];
   const bool over = (int64_t)b1 + total > cap;
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // read by the next level's kernels only
     dlo[l + 2] = over ? b1 : b1 + total;
@@ -592,30 +592,40 @@ cudaError_t launch_build_adaptive(const fmm_plan_s* P, const Workspace& ws, int6
     if (e != cudaSuccess) return e;
   }
   // Level by level without the host: the level offsets live on the device
-  // (dlo[0..D+2], overflow flag at dlo[D+3]); every level's kernels cover the
-  // capacity and read their box range there.  One read at the end.
+  // (dlo[0..D+2], overflow flag at dlo[D+3]) and every level's kernels read
+  // their box range there.  One read at the end.  The host sizes each
+  // level's launches by a bound on its box count: level l+1 holds at most 8
+  // children of each split box of level l, there are at most n / (max_leaf + 1)
+  // split boxes (their point sets are disjoint), and no box is empty.
   const int nlo = D + 3;
   int* dlo = ws.aloff;
   const int cap = (int)ws.anb_cap;
+  const int64_t npts = n_src + (ws.tkey != ws.skey ? n_tgt : 0);
+  const int64_t splits_cap = (n_src + n_tgt) / ((int64_t)P->desc.max_leaf + 1);
   k_atree_root<<<1, 1, 0, st>>>(ws.alev, ws.apar, ws.akey, ws.as0, ws.as1, ws.at0, ws.at1,
                                 (int)n_src, (int)n_tgt, dlo, nlo);
   ++*nl;
+  int64_t bound = 1;  // boxes of level l at most
   for (int l = 0; l <= D; ++l) {
-    // counts past the level's boxes stay zero, so the scan of the whole
-    // capacity ends in the level's total
-    cudaMemsetAsync(ws.anch, 0, sizeof(int) * (size_t)cap, st);
-    k_atree_split<<<nblocks(cap, 128), 128, 0, st>>>(dlo, l, D, P->desc.max_leaf, ws.akey,
-                                                     ws.as0, ws.as1, ws.at0, ws.at1, ws.skey,
-                                                     ws.tkey, ws.aleaf, ws.achild, ws.anch);
+    // (at least one thread and count: a level past the last split holds no
+    // box, and its emit still has to carry the offset down)
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(bound, cap));
+    // counts past the level's boxes stay zero, so the scan of nb counts ends
+    // in the level's total
+    cudaMemsetAsync(ws.anch, 0, sizeof(int) * (size_t)nb, st);
+    k_atree_split<<<nblocks(nb, 128), 128, 0, st>>>(dlo, l, D, P->desc.max_leaf, ws.akey,
+                                                    ws.as0, ws.as1, ws.at0, ws.at1, ws.skey,
+                                                    ws.tkey, ws.aleaf, ws.achild, ws.anch);
     ++*nl;
     if (l == D) break;
-    e = scan_ints(ws.anch, ws.ascan, cap, ws.hist_sums, st, nl);
+    e = scan_ints(ws.anch, ws.ascan, nb, ws.hist_sums, st, nl);
     if (e != cudaSuccess) return e;
-    k_atree_emit<<<nblocks(cap, 128), 128, 0, st>>>(dlo, nlo, cap, l, D, ws.ascan, ws.akey,
-                                                    ws.alev, ws.apar, ws.as0, ws.as1, ws.at0,
-                                                    ws.at1, ws.skey, ws.tkey, ws.aleaf,
-                                                    ws.achild);
+    k_atree_emit<<<nblocks(nb, 128), 128, 0, st>>>(dlo, nlo, cap, nb, l, D, ws.ascan, ws.akey,
+                                                   ws.alev, ws.apar, ws.as0, ws.as1, ws.at0,
+                                                   ws.at1, ws.skey, ws.tkey, ws.aleaf,
+                                                   ws.achild);
     ++*nl;
+    bound = std::min<int64_t>(8 * std::min<int64_t>(bound, splits_cap), std::max<int64_t>(npts, 1));
   }
   // the levels' coordinate bounds (for the adaptive M2L's windows), read in the same copy
   int* dbnd = dlo + nlo + 1;
