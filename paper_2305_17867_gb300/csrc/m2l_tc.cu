@@ -353,6 +353,17 @@ __device__ __forceinline__ bool any_far(const Combo& k, int pi0, int ncls) {
 // (H2^3 parents, H2 = 2^(l2-1)) is loaded into the source rows after the
 // primary tile's and its targets are read off the extra TMEM lanes (l2 = 0:
 // none).  This keeps the tiny coarse levels from forming a wave of their own.
+// Gathered levels (adaptive trees, gather != 0): the MMA's 128 rows are 128
+// target cells of one class taken from a list (tlist: the cells holding a box
+// with targets, grouped by class at offsets toff[0..8], Morton order inside a
+// class), and each offset's source rows are gathered from the parity-split
+// window (rows ghi, glo; row zero_row is all zeros and stands for a source
+// outside the window) by the producer warp's cp.async copies into the layout
+// the TMA would have written.  CTA 8k + u of the level takes entries
+// 128k .. 128k + 127 of class u's list: the k-th chunks of the eight classes
+// cover about the same region and run together, so the window rows they share
+// are read from L2 (class-major order measured 2.7x slower per CTA, the
+// window exceeding L2); CTAs past a class's list leave at once.
 struct TcLevel {
   CUtensorMap S, Slo;    // parity-split multipoles of the level (MMA A)
   CUtensorMap S2, S2lo;  // multipoles of the riding level l2
@@ -362,9 +373,14 @@ struct TcLevel {
   const int* map;        // adaptive: window cell -> box; null for uniform levels
   const float* bscale;   // F16X3: 2^e_box of the level's packed multipoles (cell order)
   const float* bscale2;  // the same for the riding level l2
+  const int* tlist;      // gathered levels: target cells grouped by class
+  const int* toff;       // gathered levels: offsets of the classes in tlist [9]
+  const char* ghi;       // gathered levels: the window's rows (hi, lo), JP per row
+  const char* glo;
   float scale, scale2;   // exact powers of two (shared offset matrices)
   int l, BX, BY, BZ, ntx, nty, first_block, Hx, Hy, Hz;
   int l2;
+  int gather, zero_row;
 };
 constexpr int kTcMaxLevels = 10;
 struct TcParams {
@@ -465,8 +481,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int lb = (int)blockIdx.x - LV.first_block;
   const int ngrp = 8 / ncls;
-  const int pi0 = (lb % ngrp) * ncls;  // classes pi0 .. pi0 + ncls - 1
-  const int tile = lb / ngrp;
+  int pi0 = (lb % ngrp) * ncls;  // classes pi0 .. pi0 + ncls - 1
+  const int tile = LV.gather ? 0 : lb / ngrp;
+  int gstart = 0, grows = 0;  // gathered levels: this CTA's entries of tlist
+  if (LV.gather) {  // (ncls == 1) block lb: entries 128 (lb / 8).. of class lb % 8
+    pi0 = lb & 7;
+    const int n = LV.toff[pi0 + 1] - LV.toff[pi0], k0 = (lb >> 3) * kBM;
+    if (k0 >= n) return;  // a surplus CTA: block-uniform, before any barrier or TMEM
+    gstart = LV.toff[pi0] + k0;
+    grows = min(kBM, n - k0);
+  }
   const int cb = blockIdx.y;  // column block
   const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
   const int X0 = tx * BX, Y0 = ty * BY, Z0 = tz * BZ;
@@ -474,7 +498,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int N1 = BX * BY * BZ;      // source rows of the primary tile
   const int NR = N1 + H2 * H2 * H2;  // rows the TMA boxes fill (<= 128)
 
-  if (LV.map) {  // an adaptive window's tile whose target cells hold no box: nothing to do
+  if (LV.map && !LV.gather) {  // a window's tile whose target cells hold no box: nothing to do
     int any = 0;
     for (int e = threadIdx.x; e < N1 * ncls; e += blockDim.x) {
       const int n = e % N1, u = e / N1;
@@ -487,7 +511,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
-      tc::mbar_init(&full[s], 1);
+      // gathered levels: lane 0's arm plus the 32 lanes' copy arrivals
+      tc::mbar_init(&full[s], LV.gather ? 33 : 1);
       tc::mbar_init(&empty[s], 1);
     }
     for (int bf = 0; bf < kNBuf; ++bf) {
@@ -505,7 +530,99 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc::fence_after();
   const uint32_t tmem = *tslot;
 
-  if (warp == kEpiWarps && lane == 0) {
+  if (warp == kEpiWarps && LV.gather) {
+    // ---------------- producer, gathered rows ----------------
+    // The 32 lanes copy the 128 source rows of each stage with cp.async, 16
+    // bytes at a time, into the 128-byte-swizzled layout (lane i: 16-byte
+    // column i % 8 of rows i / 8 + 4k) and arrive on the stage barrier when
+    // their copies land; lane 0 also waits for free stages and loads the
+    // offset matrices by TMA.
+    const uint32_t stage_tx = (uint32_t)C::kHalves * (uint32_t)btile;  // the TMA part
+    const size_t pitch = (size_t)jchunks * C::kRowBytes;              // bytes per window row
+    int* rowix = reinterpret_cast<int*>(sm + ns * sbytes + 256);      // [kBM] source rows
+    const int Hx = LV.Hx, Hy = LV.Hy, Hz = LV.Hz;
+    const int q16 = lane & 7, r0 = lane >> 3;
+    int cx[4], cy[4], cz[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = 4 * lane + j;
+      cx[j] = cy[j] = cz[j] = -4;  // no target: every source outside the window
+      if (n < grows) {
+        const int cell = LV.tlist[gstart + n];
+        cx[j] = cell % Hx;
+        cy[j] = (cell / Hx) % Hy;
+        cz[j] = cell / (Hx * Hy);
+      }
+    }
+    int s = 0, kk = 0;
+    uint32_t ph = 0;
+    unsigned char* st = sm;
+    int last_par[kMaxStages];  // (lane 0) parity of the last round armed in a stage
+    for (int q = 0; q < kMaxStages; ++q) last_par[q] = -1;
+    bool ok = true;
+    for (int c = 0; c < 216 && ok; ++c) {
+      const Combo k = combo(c);
+      if (!any_far(k, pi0, 1)) continue;
+      __syncwarp();  // the previous combination's rows have been read
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int x = cx[j] + k.dx, y = cy[j] + k.dy, z = cz[j] + k.dz;
+        rowix[4 * lane + j] = (x >= 0 && x < Hx && y >= 0 && y < Hy && z >= 0 && z < Hz)
+                                  ? ((k.sg * Hz + z) * Hy + y) * Hx + x
+                                  : LV.zero_row;
+      }
+      __syncwarp();
+      bool f;
+      const int hidx = offset_of(k, pi0, &f) * npt + cb * nc;
+      for (int ch = 0; ch < jchunks; ++ch, ++kk) {
+        int go = 1;
+        if (lane == 0) {
+          if (kk >= ns && !pwait<SHORTW>(&empty[s], ph ^ 1u, err, wlim)) {
+            go = 0;
+          } else {
+            tc::mbar_expect_tx(&full[s], stage_tx);
+            last_par[s] = (int)ph;
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, go, 0)) {  // the stage is free before any copy
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int hf = 0; hf < C::kHalves; ++hf) {
+          unsigned char* sh = st + hf * (C::kTileS + btile);
+          const char* g = (hf ? LV.glo : LV.ghi) + (size_t)ch * C::kRowBytes + q16 * 16;
+#pragma unroll 8
+          for (int i = 0; i < kBM / 4; ++i) {
+            const int rr = r0 + 4 * i;
+            tc::cp_async16(sh + rr * C::kRowBytes + ((q16 ^ (rr & 7)) << 4),
+                           g + (size_t)rowix[rr] * pitch);
+          }
+          if (lane == 0)
+            tc::tma_load_2d(sh + C::kTileS, hf ? &LV.Hlo : &LV.H, &full[s], ch * (C::kRowBytes /
+                            (int)sizeof(typename F::T)), hidx);
+        }
+        tc::cp_async_arrive(&full[s]);
+        if (++s == ns) {
+          s = 0;
+          ph ^= 1u;
+          st = sm;
+        } else {
+          st += sbytes;
+        }
+      }
+    }
+    tc::cp_async_wait_all();  // every copy of this warp has landed before it leaves
+    if (!ok && lane == 0) {  // TMA copies still in flight before the CTA leaves
+      for (int q = 0; q < ns; ++q)
+        if (last_par[q] >= 0) {
+          const long long t0 = clock64();
+          while (!tc::mbar_try_wait(&full[q], (uint32_t)last_par[q]) &&
+                 clock64() - t0 < tc::kWaitCycles) {
+          }
+        }
+    }
+  } else if (warp == kEpiWarps && lane == 0) {
     // ---------------- TMA producer ----------------
     // stage s and the parity ph of its current round advance together (no
     // division in the loop); a stage is refilled once its previous round's
@@ -576,6 +693,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint64_t oblo = (uint64_t)((2 * C::kTileS + btile) >> 4);
     const uint64_t dstep = (uint64_t)(sbytes >> 4);
     const int kl = prm.ksteps_last;
+    const bool gath = LV.gather != 0;
     int s = 0;
     uint32_t ph = 0;
     uint64_t da = d0;
@@ -597,6 +715,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           break;
         }
         tc::fence_after();
+        if (gath) tc::fence_proxy_async();  // the copies went through the generic proxy
         const int nk = ch == jchunks - 1 ? kl : C::kKSteps;
 #pragma unroll
         for (int ks = 0; ks < C::kKSteps; ++ks) {
@@ -731,7 +850,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (F::kScaled) v *= prm.fact_f[cb * nc + i] * tn;  // S_i and the table norm
         double* dst = nullptr;
         double scale = 1.0;
-        if (n < N1) {
+        if (LV.gather) {  // row n: entry gstart + n of the class list
+          if (n < grows) {
+            const int64_t t = (int64_t)map[(size_t)pi * Hz * Hy * Hx + LV.tlist[gstart + n]];
+            if (t >= 0) dst = LV.lc + t * nj + cb * nc + i;
+            scale = LV.scale;
+          }
+        } else if (n < N1) {
           const int x = X0 + n % BX, y = Y0 + (n / BX) % BY, z = Z0 + n / (BX * BY);
           if (x < Hx && y < Hy && z < Hz) {
             const int64_t t =
@@ -819,7 +944,7 @@ bool common_params(const fmm_plan_s* P, const Workspace& ws, TcParams* prm) {
   prm->npt = sh.npt;
   prm->ncls = sh.ncls;
   prm->stage_bytes = C::stage_bytes(sh.nc * sh.ncls);
-  prm->nstages = std::min(kMaxStages, (kSmemCap - 1024 - 256) / prm->stage_bytes);
+  prm->nstages = std::min(kMaxStages, (kSmemCap - 1024 - 256 - kBM * (int)sizeof(int)) / prm->stage_bytes);
   prm->wait_cycles = P->tc_wait_cycles > 0 ? P->tc_wait_cycles : tc::kWaitCycles;
   prm->err = &ws.geom->flag;
   // the staging of the sums reuses the stages
@@ -830,7 +955,7 @@ bool common_params(const fmm_plan_s* P, const Workspace& ws, TcParams* prm) {
 
 template <typename F, int NPASS>
 size_t smem_bytes(const TcParams& prm) {
-  return 1024 + (size_t)prm.nstages * prm.stage_bytes + 256;
+  return 1024 + (size_t)prm.nstages * prm.stage_bytes + 256 + kBM * sizeof(int);
 }
 
 // offset matrices A_h (hi and lo) of a uniform tree from the derivative tables
@@ -1016,6 +1141,72 @@ __global__ void k_apack(ATree t, int l, const double* __restrict__ mp, int nj, i
   }
 }
 
+// The target cells of level l (boxes holding targets, parent cell in the
+// window with parent origin W and size H) grouped by class: toff[u] is where
+// class u starts in tlist, toff[8] the total; inside a class the cells keep
+// the boxes' Morton order (one block of 1024 threads per level: class counts,
+// then positions by warp ballots and a prefix over the warps of each chunk).
+__global__ void __launch_bounds__(1024) k_alist(ATree t, int l, int W0x, int W0y, int W0z,
+                                                int Hx, int Hy, int* __restrict__ tlist,
+                                                int* __restrict__ toff) {
+  __shared__ int wcnt[32][8];
+  __shared__ int base[8];
+  const int b0 = t.loff[l], n = t.loff[l + 1] - b0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x < 8) base[threadIdx.x] = 0;
+  __syncthreads();
+  auto classify = [&](int i, int* cell) {
+    if (i >= n || t.t1[b0 + i] == t.t0[b0 + i]) return -1;
+    int c[3];
+    demorton3(t.key[b0 + i], l, c);
+    *cell = (((c[2] >> 1) - W0z) * Hy + ((c[1] >> 1) - W0y)) * Hx + ((c[0] >> 1) - W0x);
+    return (c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2);
+  };
+  for (int i0 = 0; i0 < n; i0 += 1024) {  // class counts
+    int cell;
+    const int cls = classify(i0 + (int)threadIdx.x, &cell);
+    for (int u = 0; u < 8; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, cls == u);
+      if (lane == 0 && m) atomicAdd(&base[u], __popc(m));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int u = 0; u < 8; ++u) {
+      const int c = base[u];
+      base[u] = acc;
+      toff[u] = acc;
+      acc += c;
+    }
+    toff[8] = acc;
+  }
+  __syncthreads();
+  for (int i0 = 0; i0 < n; i0 += 1024) {  // positions
+    int cell = 0;
+    const int cls = classify(i0 + (int)threadIdx.x, &cell);
+    unsigned mine = 0;
+    for (int u = 0; u < 8; ++u) {
+      const unsigned m = __ballot_sync(0xffffffffu, cls == u);
+      if (lane == 0) wcnt[warp][u] = __popc(m);
+      if (cls == u) mine = m;
+    }
+    __syncthreads();
+    if (cls >= 0) {
+      int pos = base[cls] + __popc(mine & ((1u << lane) - 1u));
+      for (int w = 0; w < warp; ++w) pos += wcnt[w][cls];
+      tlist[pos] = cell;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+      int add = 0;
+      for (int w = 0; w < 32; ++w) add += wcnt[w][threadIdx.x];
+      base[threadIdx.x] += add;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename F, int NPASS>
 cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& t,
                          cudaStream_t st, int* nl, unsigned* done) {
@@ -1032,7 +1223,13 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
   TcParams prm;
   if (!common_params<F, NPASS>(P, ws, &prm)) return cudaErrorInvalidValue;
   prm.accumulate = 1;  // P2L over X adds into the same expansions
-  const int ngrp = 8 / prm.ncls;
+  if (prm.ncls != 1) {  // gathered rows belong to one class: no stacked classes
+    using C = Cfg<NPASS>;
+    prm.ncls = 1;
+    prm.stage_bytes = C::stage_bytes(prm.nc);
+    prm.nstages = std::min(kMaxStages, (kSmemCap - 1024 - 256 - kBM * (int)sizeof(int)) / prm.stage_bytes);
+  }
+  const int ngrp = 8;
   int nb = 0;
   char* arena = static_cast<char*>(ws.tc_arena);
   size_t used = 0;
@@ -1045,8 +1242,18 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
       H[k] = (bnd[6 * l + 3 + k] >> 1) - W0[k] + 1;
     }
     const size_t cells = (size_t)8 * H[0] * H[1] * H[2];
+    const unsigned nbl = (unsigned)(t.loff[l + 1] - t.loff[l]);
+    // a window less than half full is contracted over its target cells alone
+    // (the source rows gathered); a fuller one in tiles of the window.  On the
+    // 2M-point Plummer tree, gathering levels 7 and 8 (43% and 39% full) saved
+    // 1.5 ms; level 6 (64% full, a 201 MB window beyond L2) ran 3x slower
+    // per CTA gathered than in tiles.
+    const bool gather = 2.0 * (double)nbl < (double)cells;
     auto a256 = [](size_t x) { return (x + 255) / 256 * 256; };
-    const size_t need = a256(cells * cell_bytes) * (NPASS == 3 ? 2 : 1) + a256(cells * sizeof(int));
+    const size_t rows = cells + (gather ? 1 : 0);  // gathered: a zero row at the end
+    const size_t need = a256(rows * cell_bytes) * (NPASS == 3 ? 2 : 1) +
+                        a256(cells * sizeof(int)) +
+                        (gather ? a256((size_t)nbl * sizeof(int)) + 256 : 0);
     if (need > ws.tc_arena_bytes) continue;  // a window larger than the arena: CUDA cores
     if (used + need > ws.tc_arena_bytes || prm.nlev == kTcMaxLevels) {
       // contract the levels packed so far, then pack the next ones into the
@@ -1058,27 +1265,53 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
       nb = 0;
       used = 0;
     }
-    T* bhi = reinterpret_cast<T*>(arena + used);
-    T* blo = NPASS == 3 ? reinterpret_cast<T*>(arena + used + a256(cells * cell_bytes)) : nullptr;
-    int* map = reinterpret_cast<int*>(arena + used + a256(cells * cell_bytes) * (NPASS == 3 ? 2 : 1));
+    char* at = arena + used;
+    T* bhi = reinterpret_cast<T*>(at);
+    at += a256(rows * cell_bytes);
+    T* blo = nullptr;
+    if (NPASS == 3) {
+      blo = reinterpret_cast<T*>(at);
+      at += a256(rows * cell_bytes);
+    }
+    int* map = reinterpret_cast<int*>(at);
+    at += a256(cells * sizeof(int));
+    int* tlist = gather ? reinterpret_cast<int*>(at) : nullptr;
+    int* toff = gather ? reinterpret_cast<int*>(at + a256((size_t)nbl * sizeof(int))) : nullptr;
     used += need;
-    cudaMemsetAsync(bhi, 0, cells * cell_bytes, st);
-    if (blo) cudaMemsetAsync(blo, 0, cells * cell_bytes, st);
+    cudaMemsetAsync(bhi, 0, rows * cell_bytes, st);
+    if (blo) cudaMemsetAsync(blo, 0, rows * cell_bytes, st);
     cudaMemsetAsync(map, 0xff, cells * sizeof(int), st);
-    const unsigned nbl = (unsigned)(t.loff[l + 1] - t.loff[l]);
     k_apack<F><<<std::min<unsigned>((nbl * JP + 255) / 256, 152 * 8), 256, 0, st>>>(
         t, l, ws.mp, nj, JP, W0[0], W0[1], W0[2], H[0], H[1], H[2], bhi, blo, map);
     ++*nl;
+    if (gather) {
+      k_alist<<<1, 1024, 0, st>>>(t, l, W0[0], W0[1], W0[2], H[0], H[1], tlist, toff);
+      ++*nl;
+    }
     TcLevel& v = prm.lev[prm.nlev++];
     v.l = l;
     v.l2 = 0;
     v.Hx = H[0];
     v.Hy = H[1];
     v.Hz = H[2];
-    tile_shape(H[0], H[1], H[2], &v);
-    const int ntz = (H[2] + v.BZ - 1) / v.BZ;
+    v.gather = gather ? 1 : 0;
+    v.tlist = tlist;
+    v.toff = toff;
+    v.zero_row = (int)cells;
     v.first_block = nb;
-    nb += v.ntx * v.nty * ntz * ngrp;
+    if (gather) {  // 128 list entries per CTA, the classes interleaved; a class holds at
+                   // most one cell per parent of the window
+      v.BX = 8;
+      v.BY = 4;
+      v.BZ = 4;
+      v.ntx = v.nty = 1;
+      const size_t per_cls = std::min<size_t>(nbl, cells / 8);
+      nb += 8 * (int)((per_cls + kBM - 1) / kBM);
+    } else {
+      tile_shape(H[0], H[1], H[2], &v);
+      const int ntz = (H[2] + v.BZ - 1) / v.BZ;
+      nb += v.ntx * v.nty * ntz * ngrp;
+    }
     v.lc = ws.lc;
     v.map = map;
     v.scale = 1.0f;
@@ -1087,11 +1320,16 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
       v.scale = pd.kernel == FMM_KERNEL_LAPLACE ? std::ldexp(1.0f, k) : std::ldexp(1.0f, -k);
     }
     if (!offset_maps<F, NPASS>(ws, shared_t ? 0 : l - 2, prm, &v)) return cudaErrorInvalidValue;
-    if (!source_map<F, NPASS>(&v.S, bhi, JP, H[0], H[1], H[2], v.BX, v.BY, v.BZ))
-      return cudaErrorInvalidValue;
-    v.Slo = v.S;
-    if (NPASS == 3 && !source_map<F, NPASS>(&v.Slo, blo, JP, H[0], H[1], H[2], v.BX, v.BY, v.BZ))
-      return cudaErrorInvalidValue;
+    v.ghi = reinterpret_cast<const char*>(bhi);
+    v.glo = reinterpret_cast<const char*>(NPASS == 3 ? blo : bhi);
+    if (!gather) {
+      if (!source_map<F, NPASS>(&v.S, bhi, JP, H[0], H[1], H[2], v.BX, v.BY, v.BZ))
+        return cudaErrorInvalidValue;
+      v.Slo = v.S;
+      if (NPASS == 3 &&
+          !source_map<F, NPASS>(&v.Slo, blo, JP, H[0], H[1], H[2], v.BX, v.BY, v.BZ))
+        return cudaErrorInvalidValue;
+    }
     *done |= 1u << l;
   }
   if (prm.nlev == 0) return cudaGetLastError();

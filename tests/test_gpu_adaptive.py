@@ -11,6 +11,7 @@ from paper_2305_17867_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-12
+TC_TOL = {"tf32x3": 2e-5, "bf16x3": 1e-4, "tf32": 3e-3}
 
 
 def rel_l2(a, b):
@@ -111,19 +112,22 @@ def test_tiny_and_empty(torch_cuda, oracle):
     assert np.all(got == 0.0)
 
 
-def test_yukawa_plummer_full_size_sampled(torch_cuda, oracle):
+@pytest.mark.parametrize("precision", ["fp64", "bf16x3"])
+def test_yukawa_plummer_full_size_sampled(torch_cuda, oracle, precision):
     # the adaptive Yukawa workload: 2e6 Plummer sources, 2e6 uniform targets,
     # p = 12, at most 64 points per leaf; the oracle evaluates 16 seeded
-    # targets on the same tree
+    # targets on the same tree.  In BF16x3 the sparse levels (6-8) run the
+    # tensor-core M2L over gathered target lists of thousands of entries per
+    # class, the dense ones (2-5) over window tiles.
     wl = W.WORKLOADS["yukawa3d_p12_adaptive_n2m"]
     src, w, tgt = W.make_inputs(wl)
     got, (nb, depth) = gpu_adaptive(torch_cuda, "yukawa", 12, src, w, tgt, lam=wl.lam,
-                                    max_leaf=wl.max_leaf)
+                                    max_leaf=wl.max_leaf, precision=precision)
     idx = np.random.default_rng(96).choice(len(tgt), 16, replace=False)
     ref, st, _ = oracle.fmm_adaptive("yukawa", 3, 12, src, w, tgt, max_leaf=wl.max_leaf,
                                      lam=wl.lam, sample=idx, want_stats=True)
     assert (nb, depth) == (st["boxes"], st["depth"])
-    assert rel_l2(got[idx], ref) < FP64_TOL
+    assert rel_l2(got[idx], ref) < (FP64_TOL if precision == "fp64" else TC_TOL[precision])
 
 
 # Float forms (P2M, M2L, P2L, L2P, P2P, M2P in float; M2M, L2L and the
@@ -167,9 +171,9 @@ def test_adaptive_fp32_leaf_shapes(torch_cuda, oracle):
     assert rel_l2(got, ref) < FP32_TOL
 
 
-# Tensor-core M2L on the adaptive tree (each level packed into a dense window);
-# tolerances as for the uniform tree's mixed-precision forms.
-TC_TOL = {"tf32x3": 2e-5, "bf16x3": 1e-4, "tf32": 3e-3}
+# Tensor-core M2L on the adaptive tree (dense levels in window tiles, sparse
+# ones over gathered target lists); tolerances (TC_TOL, top of the file) as for
+# the uniform tree's mixed-precision forms.
 
 
 @pytest.mark.parametrize("precision", ["tf32x3", "bf16x3", "tf32"])
