@@ -48,6 +48,11 @@ __device__ float far_horner(const PlanDev& pd, const float* __restrict__ cb, flo
   return F;
 }
 
+// (x - c) / s from float pairs x = xh + xl, c = ch + cl, inv_s a power of two
+__device__ __forceinline__ float box_rel(float xh, float xl, float ch, float cl, float inv_s) {
+  return __fmul_rn(__fadd_rn(__fsub_rn(xh, ch), __fsub_rn(xl, cl)), inv_s);
+}
+
 // neighbour k (0..26) of coordinates c
 __device__ __forceinline__ void nbr(const int* c, int k, int* nc) {
   nc[0] = c[0] + k % 3 - 1;
@@ -70,9 +75,9 @@ __device__ __forceinline__ void for_hits(bool pred, int A, F&& f) {
 __global__ void __launch_bounds__(32 * kLW) k_aleaf_w(
     PlanDev pd, const Geom* __restrict__ g, ATree t, const double* __restrict__ lc,
     const double* __restrict__ tx0, const double* __restrict__ tx1,
-    const double* __restrict__ tx2, const int* __restrict__ tperm, const double* __restrict__ sx0,
-    const double* __restrict__ sx1, const double* __restrict__ sx2, const double* __restrict__ sw,
-    double* __restrict__ phi, unsigned char* __restrict__ need_m2p, int* __restrict__ err) {
+    const double* __restrict__ tx2, const int* __restrict__ tperm, const float4* __restrict__ sxh,
+    const float4* __restrict__ sxl, double* __restrict__ phi, unsigned char* __restrict__ need_m2p,
+    int* __restrict__ err) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.x * kLW + warp;
   if (b >= t.loff[t.maxlev + 1] || !t.leaf[b] || t.t1[b] == t.t0[b]) return;  // warp-uniform
@@ -82,6 +87,13 @@ __global__ void __launch_bounds__(32 * kLW) k_aleaf_w(
   double cb[3], s;
   abox_center(g, l, bc, cb, &s);
   const double inv_s = 1.0 / s;
+  // the centre as float pairs, so that a source's box-relative coordinate
+  // ((xh - ch) + (xl - cl)) / s comes out of float arithmetic to a few
+  // float roundings of itself (s is a power of two)
+  const float ch[3] = {(float)cb[0], (float)cb[1], (float)cb[2]};
+  const float cl[3] = {(float)(cb[0] - (double)ch[0]), (float)(cb[1] - (double)ch[1]),
+                       (float)(cb[2] - (double)ch[2])};
+  const float inv_sf = (float)inv_s;
   extern __shared__ __align__(16) float smw[];
   const int per_warp = ((nfull + 3) & ~3) + 4 * 32;
   float* a = smw + (size_t)warp * per_warp;                      // decompressed Lt / m!
@@ -120,10 +132,13 @@ __global__ void __launch_bounds__(32 * kLW) k_aleaf_w(
       ti[k] = tb + k * 32 + lane / gs;
       val[k] = k < nblk && ti[k] < tb + nt;
       u[k][0] = u[k][1] = u[k][2] = 0.f;
-      if (val[k]) {
-        u[k][0] = (float)((tx0[ti[k]] - cb[0]) * inv_s);
-        u[k][1] = (float)((tx1[ti[k]] - cb[1]) * inv_s);
-        u[k][2] = (float)((tx2[ti[k]] - cb[2]) * inv_s);
+      if (val[k]) {  // the sources' arithmetic: a point that is both gets equal coordinates
+        const double x[3] = {tx0[ti[k]], tx1[ti[k]], tx2[ti[k]]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float h = (float)x[d], o = (float)(x[d] - (double)h);
+          u[k][d] = box_rel(h, o, ch[d], cl[d], inv_sf);
+        }
       }
     }
     float near[2] = {0.f, 0.f};
@@ -135,10 +150,10 @@ __global__ void __launch_bounds__(32 * kLW) k_aleaf_w(
         const int n = min(32, s1 - jb);
         __syncwarp();
         if (lane < n) {
-          const int j = jb + lane;
-          stage[lane] = make_float4((float)((sx0[j] - cb[0]) * inv_s),
-                                    (float)((sx1[j] - cb[1]) * inv_s),
-                                    (float)((sx2[j] - cb[2]) * inv_s), (float)sw[j]);
+          const float4 h = sxh[jb + lane], o = sxl[jb + lane];
+          stage[lane] = make_float4(box_rel(h.x, o.x, ch[0], cl[0], inv_sf),
+                                    box_rel(h.y, o.y, ch[1], cl[1], inv_sf),
+                                    box_rel(h.z, o.z, ch[2], cl[2], inv_sf), h.w);
         }
         __syncwarp();
         for (int q = sub; q < n; q += gs) {
@@ -360,8 +375,8 @@ cudaError_t launch_adaptive_leaf_warp(const fmm_plan_s* P, const Workspace& ws, 
   const size_t sm1 = sizeof(float) * kLW * (size_t)(((pd.nfull + 3) & ~3) + 4 * 32);
   cudaFuncSetAttribute(k_aleaf_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
   k_aleaf_w<<<(unsigned)((nbox + kLW - 1) / kLW), 32 * kLW, sm1, st>>>(
-      pd, ws.geom, t, ws.lc, ws.tx[0], ws.tx[1], ws.tx[2], ws.tperm, ws.sx[0], ws.sx[1], ws.sx[2],
-      ws.sw, phi, ws.am2p, &ws.geom->flag);
+      pd, ws.geom, t, ws.lc, ws.tx[0], ws.tx[1], ws.tx[2], ws.tperm, ws.asxh, ws.asxl, phi,
+      ws.am2p, &ws.geom->flag);
   const int sl = std::min(pd.c, pd.p + 1) * (pd.p + 1);
   const int per = (kernel_screened(pd.kernel) ? 6 : 3) * sl;
   const size_t sm2 = sizeof(float) * ((size_t)((pd.nj + 3) & ~3) + (size_t)32 * per);

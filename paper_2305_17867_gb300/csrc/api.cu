@@ -150,6 +150,10 @@ static int workspace_layout_adaptive(const fmm_plan_s* P, int64_t n_src, int64_t
   w.at1 = carve<int>(cur, nb);
   w.aleaf = carve<int>(cur, nb);
   w.am2p = carve<unsigned char>(cur, nb);
+  if (P->desc.precision != FMM_PREC_FP64 && P->pd.d == 3) {
+    w.asxh = carve<float4>(cur, std::max<int64_t>(n_src, 1));
+    w.asxl = carve<float4>(cur, std::max<int64_t>(n_src, 1));
+  }
   w.aloff = carve<int>(cur, FMM_MAX_ADEPTH + 4 + 6 * (FMM_MAX_ADEPTH + 2));
   w.anch = carve<int>(cur, nb);
   w.ascan = carve<int>(cur, nb + 1);

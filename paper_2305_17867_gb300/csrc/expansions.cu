@@ -977,16 +977,15 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l(PlanDev pd, const Geom* __re
 }
 
 // Float form of k_ap2l (mixed-precision modes): the X leaf's sources are
-// staged as float (c_B - y)/s_B (FP64 subtraction once per source), each
+// staged as float (c_B - y)/s_B (from the float pairs of the sources and of
+// the centre: no FP64 arithmetic per source), each
 // thread runs the float derivative recurrence for its sources and adds
 // w * Ht into a float accumulator in shared memory.
 constexpr int kAFStage = 256;
 
 __global__ void __launch_bounds__(kAThreads) k_ap2l_f32(PlanDev pd, const Geom* __restrict__ g,
-                                                        ATree t, const double* __restrict__ sx0,
-                                                        const double* __restrict__ sx1,
-                                                        const double* __restrict__ sx2,
-                                                        const double* __restrict__ sw,
+                                                        ATree t, const float4* __restrict__ sxh,
+                                                        const float4* __restrict__ sxl,
                                                         double* __restrict__ lc) {
   const int b = t.loff[2] + blockIdx.x;
   // a box of at most |j| targets has its X pairs summed directly by the leaves
@@ -1004,6 +1003,10 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l_f32(PlanDev pd, const Geom* 
   float* S = Lacc + ((nj + 3) & ~3) + threadIdx.x * per;
   for (int i = threadIdx.x; i < nj; i += blockDim.x) Lacc[i] = 0.f;
   const double inv_s = 1.0 / s;
+  const float ch[3] = {(float)cb[0], (float)cb[1], (float)cb[2]};
+  const float cl[3] = {(float)(cb[0] - (double)ch[0]), (float)(cb[1] - (double)ch[1]),
+                       (float)(cb[2] - (double)ch[2])};
+  const float inv_sf = (float)inv_s;
   const float lam = (float)(pd.lam * s), scale = (float)deriv_scale(pd, s);
   const int pc[3] = {bc[0] >> 1, bc[1] >> 1, bc[2] >> 1};
   bool any = false;
@@ -1019,9 +1022,10 @@ __global__ void __launch_bounds__(kAThreads) k_ap2l_f32(PlanDev pd, const Geom* 
         const int n = min(kAFStage, t.s1[A] - jb);
         __syncthreads();
         for (int q = threadIdx.x; q < n; q += blockDim.x) {
-          const int j = jb + q;
-          stage[q] = make_float4((float)((cb[0] - sx0[j]) * inv_s), (float)((cb[1] - sx1[j]) * inv_s),
-                                 (float)((cb[2] - sx2[j]) * inv_s), (float)sw[j]);
+          const float4 h = sxh[jb + q], o = sxl[jb + q];
+          stage[q] = make_float4(__fmul_rn(__fadd_rn(ch[0] - h.x, cl[0] - o.x), inv_sf),
+                                 __fmul_rn(__fadd_rn(ch[1] - h.y, cl[1] - o.y), inv_sf),
+                                 __fmul_rn(__fadd_rn(ch[2] - h.z, cl[2] - o.z), inv_sf), h.w);
         }
         __syncthreads();
         // A warp takes 32 sources at a time (lanes past the end take a
@@ -1110,8 +1114,8 @@ cudaError_t launch_adaptive_p2l_l2l(const fmm_plan_s* P, const Workspace& ws, co
       const size_t smem =
           sizeof(float) * (4 * kAFStage + ((pd.nj + 3) & ~3) + (size_t)per * kAThreads);
       set_smem(k_ap2l_f32, smem);
-      k_ap2l_f32<<<(unsigned)(nbox - t.loff[2]), kAThreads, smem, st>>>(
-          pd, ws.geom, t, ws.sx[0], ws.sx[1], ws.sx[2], ws.sw, ws.lc);
+      k_ap2l_f32<<<(unsigned)(nbox - t.loff[2]), kAThreads, smem, st>>>(pd, ws.geom, t, ws.asxh,
+                                                                        ws.asxl, ws.lc);
     }
     ++*nl;
   }

@@ -202,6 +202,11 @@ struct Workspace {
   int* at1;
   int* aleaf;
   unsigned char* am2p;  // per box: a leaf with W boxes of more than |j| sources (float pass)
+  // float leaf pass: the sorted sources as two floats per coordinate, hi = fl(x)
+  // (and the weight) and lo = fl(x - hi), so that box-relative coordinates
+  // need no FP64 arithmetic (null in the FP64 mode)
+  float4* asxh;
+  float4* asxl;
   int* aloff;           // tree build: level offsets on the device, the overflow flag, the
                         // per-level coordinate bounds
   int* anch;

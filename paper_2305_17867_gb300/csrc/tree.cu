@@ -317,6 +317,19 @@ __global__ void k_atree_root(int* lev, int* par, uint32_t* key, int* s0, int* s1
   t1[0] = nt;
 }
 
+// sources as (hi, lo) float pairs: hi = fl(x), lo = fl(x - hi), weight in hi.w
+__global__ void k_split_points(int64_t n, const double* __restrict__ x0,
+                               const double* __restrict__ x1, const double* __restrict__ x2,
+                               const double* __restrict__ w, float4* __restrict__ hi,
+                               float4* __restrict__ lo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float h0 = (float)x0[i], h1 = (float)x1[i], h2 = (float)x2[i];
+  hi[i] = make_float4(h0, h1, h2, (float)w[i]);
+  lo[i] = make_float4((float)(x0[i] - (double)h0), (float)(x1[i] - (double)h1),
+                      (float)(x2[i] - (double)h2), 0.f);
+}
+
 // per-level coordinate bounds of the boxes of levels >= 2 (the windows of the
 // adaptive tensor-core M2L): bnd[6 l + k] = min, bnd[6 l + 3 + k] = max
 __global__ void k_abounds_init(int* bnd, int n) {
@@ -587,6 +600,11 @@ cudaError_t launch_build_adaptive(const fmm_plan_s* P, const Workspace& ws, int6
   *overflow = 0;
   cudaError_t e = asort_points(ws, n_src, src, w, ws.sx, ws.sw, ws.sperm, ws.skey, D, st, nl);
   if (e != cudaSuccess) return e;
+  if (ws.asxh && n_src > 0) {  // the float leaf pass's split copy of the sorted sources
+    k_split_points<<<nblocks(n_src, 256), 256, 0, st>>>(n_src, ws.sx[0], ws.sx[1], ws.sx[2],
+                                                        ws.sw, ws.asxh, ws.asxl);
+    ++*nl;
+  }
   if (ws.tkey != ws.skey) {  // else the targets are the sources, sorted once
     e = asort_points(ws, n_tgt, tgt, nullptr, ws.tx, nullptr, ws.tperm, ws.tkey, D, st, nl);
     if (e != cudaSuccess) return e;
