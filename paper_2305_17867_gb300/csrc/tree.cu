@@ -375,24 +375,35 @@ __device__ inline int lower_bound_u32(const uint32_t* a, int lo, int hi, uint32_
   return lo;
 }
 
-// child ranges of box b (level l): boundaries of octants 0..8 in the sorted codes
-__device__ inline void child_bounds(const uint32_t* skey, const uint32_t* tkey, uint32_t key,
-                                    int l, int D, int s0, int s1, int t0, int t1, int* sb,
-                                    int* tb) {
-  const int shift = 3 * (D - l - 1);
+// A box's child ranges are the boundaries of its octants 1..7 in the sorted
+// source and target codes: fourteen binary searches, one per lane of a group
+// of 16 lanes (lanes 0..6 sources, 8..14 targets), so that a level's kernels
+// wait for one search's chain of dependent loads, not fourteen.  Every lane of
+// the group gets all boundaries sb[0..8], tb[0..8] by shuffles.
+constexpr int kBoxLanes = 16;
+__device__ __forceinline__ void child_bounds_group(const uint32_t* skey, const uint32_t* tkey,
+                                                   bool live, uint32_t key, int l, int D, int s0,
+                                                   int s1, int t0, int t1, int* sb, int* tb) {
+  const int k = threadIdx.x & (kBoxLanes - 1);
+  int v = 0;
+  if (live && k != 7 && k != 15) {
+    const int ci = (k & 7) + 1;
+    const uint32_t c = ((key << 3) | (uint32_t)ci) << (3 * (D - l - 1));
+    v = k < 8 ? lower_bound_u32(skey, s0, s1, c) : lower_bound_u32(tkey, t0, t1, c);
+  }
   sb[0] = s0;
   tb[0] = t0;
+#pragma unroll
   for (int ci = 1; ci < 8; ++ci) {
-    const uint32_t v = ((key << 3) | (uint32_t)ci) << shift;
-    sb[ci] = lower_bound_u32(skey, s0, s1, v);
-    tb[ci] = lower_bound_u32(tkey, t0, t1, v);
+    sb[ci] = __shfl_sync(0xffffffffu, v, ci - 1, kBoxLanes);
+    tb[ci] = __shfl_sync(0xffffffffu, v, ci + 7, kBoxLanes);
   }
   sb[8] = s1;
   tb[8] = t1;
 }
 
 // split decision and number of non-empty children of every box of level l,
-// boxes dlo[l] .. dlo[l+1] (level offsets kept on the device)
+// boxes dlo[l] .. dlo[l+1] (level offsets kept on the device); 16 lanes a box
 __global__ void k_atree_split(const int* __restrict__ dlo, int l, int D, int max_leaf,
                               const uint32_t* __restrict__ key, const int* __restrict__ s0,
                               const int* __restrict__ s1, const int* __restrict__ t0,
@@ -400,26 +411,33 @@ __global__ void k_atree_split(const int* __restrict__ dlo, int l, int D, int max
                               const uint32_t* __restrict__ tkey, int* __restrict__ leaf,
                               int* __restrict__ child, int* __restrict__ nch) {
   const int b0 = dlo[l], b1 = dlo[l + 1];
-  const int b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= b1) return;
-  for (int ci = 0; ci < 8; ++ci) child[8 * b + ci] = -1;
-  const int npt = (s1[b] - s0[b]) + (t1[b] - t0[b]);
-  if (npt <= max_leaf || l >= D) {
-    leaf[b] = 1;
-    nch[b - b0] = 0;
-    return;
+  const int b = b0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) / kBoxLanes);
+  const int k = threadIdx.x & (kBoxLanes - 1);
+  const bool live = b < b1;
+  bool split = false;
+  int bs0 = 0, bs1 = 0, bt0 = 0, bt1 = 0;
+  uint32_t bkey = 0;
+  if (live) {
+    bs0 = s0[b], bs1 = s1[b], bt0 = t0[b], bt1 = t1[b];
+    bkey = key[b];
+    split = (bs1 - bs0) + (bt1 - bt0) > max_leaf && l < D;
+    if (k < 8) child[8 * b + k] = -1;
+    if (k == 0) leaf[b] = split ? 0 : 1;
   }
-  leaf[b] = 0;
-  int sb[9], tb[9];
-  child_bounds(skey, tkey, key[b], l, D, s0[b], s1[b], t0[b], t1[b], sb, tb);
-  int n = 0;
-  for (int ci = 0; ci < 8; ++ci) n += (sb[ci + 1] > sb[ci] || tb[ci + 1] > tb[ci]) ? 1 : 0;
-  nch[b - b0] = n;
+  int sb[9], tb[9];  // every lane of the block reaches the shuffles
+  child_bounds_group(skey, tkey, live && split, bkey, l, D, bs0, bs1, bt0, bt1, sb, tb);
+  if (live && k == 0) {
+    int n = 0;
+    if (split)
+      for (int ci = 0; ci < 8; ++ci) n += (sb[ci + 1] > sb[ci] || tb[ci + 1] > tb[ci]) ? 1 : 0;
+    nch[b - b0] = n;
+  }
 }
 
 // create the children of level l's split boxes at dlo[l+1] + scan[b - b0]
 // (scan[nscan] = the children of the level, the counts past the level being
-// zero) and set dlo[l+2]; past the capacity, raise dlo[nlo] and add none
+// zero) and set dlo[l+2]; past the capacity, raise dlo[nlo] and add none.
+// 16 lanes a box: lane ci < 8 writes child ci.
 __global__ void k_atree_emit(int* __restrict__ dlo, int nlo, int cap, int nscan, int l, int D,
                              const int* __restrict__ scan,
                              uint32_t* __restrict__ key, int* __restrict__ lev,
@@ -433,23 +451,27 @@ __global__ void k_atree_emit(int* __restrict__ dlo, int nlo, int cap, int nscan,
     dlo[l + 2] = over ? b1 : b1 + total;
     if (over) dlo[nlo] = 1;
   }
-  const int b = b0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (over || b >= b1 || leaf[b]) return;
+  const int b = b0 + (int)((blockIdx.x * blockDim.x + threadIdx.x) / kBoxLanes);
+  const int k = threadIdx.x & (kBoxLanes - 1);
+  const bool live = !over && b < b1 && !leaf[b];
+  int bs0 = 0, bs1 = 0, bt0 = 0, bt1 = 0;
+  uint32_t bkey = 0;
+  if (live) bs0 = s0[b], bs1 = s1[b], bt0 = t0[b], bt1 = t1[b], bkey = key[b];
   int sb[9], tb[9];
-  child_bounds(skey, tkey, key[b], l, D, s0[b], s1[b], t0[b], t1[b], sb, tb);
+  child_bounds_group(skey, tkey, live, bkey, l, D, bs0, bs1, bt0, bt1, sb, tb);
+  if (!live || k >= 8) return;
+  const int ci = k;
+  if (sb[ci + 1] == sb[ci] && tb[ci + 1] == tb[ci]) return;
   int pos = b1 + scan[b - b0];
-  for (int ci = 0; ci < 8; ++ci) {
-    if (sb[ci + 1] == sb[ci] && tb[ci + 1] == tb[ci]) continue;
-    key[pos] = (key[b] << 3) | (uint32_t)ci;
-    lev[pos] = l + 1;
-    par[pos] = b;
-    s0[pos] = sb[ci];
-    s1[pos] = sb[ci + 1];
-    t0[pos] = tb[ci];
-    t1[pos] = tb[ci + 1];
-    child[8 * b + ci] = pos;
-    ++pos;
-  }
+  for (int cj = 0; cj < ci; ++cj) pos += (sb[cj + 1] > sb[cj] || tb[cj + 1] > tb[cj]) ? 1 : 0;
+  key[pos] = (bkey << 3) | (uint32_t)ci;
+  lev[pos] = l + 1;
+  par[pos] = b;
+  s0[pos] = sb[ci];
+  s1[pos] = sb[ci + 1];
+  t0[pos] = tb[ci];
+  t1[pos] = tb[ci + 1];
+  child[8 * b + ci] = pos;
 }
 
 unsigned nblocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -631,17 +653,16 @@ cudaError_t launch_build_adaptive(const fmm_plan_s* P, const Workspace& ws, int6
     // counts past the level's boxes stay zero, so the scan of nb counts ends
     // in the level's total
     cudaMemsetAsync(ws.anch, 0, sizeof(int) * (size_t)nb, st);
-    k_atree_split<<<nblocks(nb, 128), 128, 0, st>>>(dlo, l, D, P->desc.max_leaf, ws.akey,
-                                                    ws.as0, ws.as1, ws.at0, ws.at1, ws.skey,
-                                                    ws.tkey, ws.aleaf, ws.achild, ws.anch);
+    k_atree_split<<<nblocks((int64_t)nb * kBoxLanes, 256), 256, 0, st>>>(
+        dlo, l, D, P->desc.max_leaf, ws.akey, ws.as0, ws.as1, ws.at0, ws.at1, ws.skey, ws.tkey,
+        ws.aleaf, ws.achild, ws.anch);
     ++*nl;
     if (l == D) break;
     e = scan_ints(ws.anch, ws.ascan, nb, ws.hist_sums, st, nl);
     if (e != cudaSuccess) return e;
-    k_atree_emit<<<nblocks(nb, 128), 128, 0, st>>>(dlo, nlo, cap, nb, l, D, ws.ascan, ws.akey,
-                                                   ws.alev, ws.apar, ws.as0, ws.as1, ws.at0,
-                                                   ws.at1, ws.skey, ws.tkey, ws.aleaf,
-                                                   ws.achild);
+    k_atree_emit<<<nblocks((int64_t)nb * kBoxLanes, 256), 256, 0, st>>>(
+        dlo, nlo, cap, nb, l, D, ws.ascan, ws.akey, ws.alev, ws.apar, ws.as0, ws.as1, ws.at0,
+        ws.at1, ws.skey, ws.tkey, ws.aleaf, ws.achild);
     ++*nl;
     bound = std::min<int64_t>(8 * std::min<int64_t>(bound, splits_cap), std::max<int64_t>(npts, 1));
   }
