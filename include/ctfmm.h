@@ -168,10 +168,11 @@ int fmm_workspace_size(fmm_plan_t plan, int64_t n_src, int64_t n_tgt, size_t* by
 
 /* Evaluate phi (and, if grad_dev != NULL, grad phi) at the targets.
  * Adaptive plans (levels < 0) build the tree on the device level by level
- * and synchronise `stream` once per level to size the next one (so the call
- * returns after the tree is built, and it cannot be captured into a CUDA
- * graph: made while `stream` is capturing, it returns FMM_ERR_UNSUPPORTED
- * before any work is enqueued); they compute phi only (grad_dev must be
+ * and synchronise `stream` once, after the deepest level, to read the levels'
+ * sizes and extents that size the later launches (so the call returns after
+ * the tree is built, and it cannot be captured into a CUDA graph: made while
+ * `stream` is capturing, it returns FMM_ERR_UNSUPPORTED before any work is
+ * enqueued); they compute phi only (grad_dev must be
  * NULL, else FMM_ERR_UNSUPPORTED) and return FMM_ERR_WORKSPACE if the tree
  * outgrows the workspace (it cannot when the workspace has the size
  * fmm_workspace_size reports, which bounds the number of boxes).

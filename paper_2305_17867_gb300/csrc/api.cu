@@ -808,7 +808,7 @@ static int eval_internal(fmm_plan_t P, int64_t n_src, const double* src, const d
   };
   if (P->desc.levels < 0) {
     if (grad) return FMM_ERR_UNSUPPORTED;
-    {  // the adaptive build reads level sizes back to the host: not capturable
+    {  // the adaptive build reads the level sizes back to the host once: not capturable
       cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
       if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return FMM_ERR_CUDA;
       if (cs != cudaStreamCaptureStatusNone) return FMM_ERR_UNSUPPORTED;

@@ -1116,28 +1116,33 @@ cudaError_t run_all_levels(const fmm_plan_s* P, const Workspace& ws, cudaStream_
 // level offsets)
 
 // the level's boxes into Bpar[sigma][Tz][Ty][Tx][JP] (hi and lo) of a window
-// with parent origin W and size H, and map[sigma][Tz][Ty][Tx] = box
+// with parent origin W and size H, and map[sigma][Tz][Ty][Tx] = box; one warp
+// per box (the box's cell found once, the lanes over its coefficients)
 template <typename F>
-__global__ void k_apack(ATree t, int l, const double* __restrict__ mp, int nj, int JP, int W0x,
-                        int W0y, int W0z, int Hx, int Hy, int Hz, typename F::T* __restrict__ bhi,
-                        typename F::T* __restrict__ blo, int* __restrict__ map) {
-  const int b0 = t.loff[l];
-  const unsigned tot = (unsigned)(t.loff[l + 1] - b0) * (unsigned)JP;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
-    const unsigned bi = e / (unsigned)JP;
-    const int q = (int)(e - bi * (unsigned)JP);
-    const int b = b0 + (int)bi;
+__global__ void __launch_bounds__(256) k_apack(ATree t, int l, const double* __restrict__ mp,
+                                               int nj, int JP, int W0x, int W0y, int W0z, int Hx,
+                                               int Hy, int Hz, typename F::T* __restrict__ bhi,
+                                               typename F::T* __restrict__ blo,
+                                               int* __restrict__ map) {
+  const int b0 = t.loff[l], nbl = t.loff[l + 1] - b0;
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int bi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); bi < nbl; bi += nw) {
+    const int b = b0 + bi;
     int c[3];
     demorton3(t.key[b], l, c);
     const int sg = (c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2);
     const size_t cell =
         (((size_t)sg * Hz + ((c[2] >> 1) - W0z)) * Hy + ((c[1] >> 1) - W0y)) * Hx + ((c[0] >> 1) - W0x);
-    const float v = q < nj ? (float)mp[(size_t)b * nj + q] : 0.f;
-    typename F::T hi, lo;
-    F::split(v, hi, lo);
-    bhi[cell * JP + q] = hi;
-    if (blo) blo[cell * JP + q] = lo;
-    if (q == 0) map[cell] = t.t1[b] > t.t0[b] ? b : -1;  // only boxes with targets get locals
+    const double* src = mp + (size_t)b * nj;
+    for (int q = lane; q < JP; q += 32) {
+      const float v = q < nj ? (float)src[q] : 0.f;
+      typename F::T hi, lo;
+      F::split(v, hi, lo);
+      bhi[cell * JP + q] = hi;
+      if (blo) blo[cell * JP + q] = lo;
+    }
+    if (lane == 0) map[cell] = t.t1[b] > t.t0[b] ? b : -1;  // only boxes with targets get locals
   }
 }
 
@@ -1281,7 +1286,7 @@ cudaError_t run_adaptive(const fmm_plan_s* P, const Workspace& ws, const ATree& 
     cudaMemsetAsync(bhi, 0, rows * cell_bytes, st);
     if (blo) cudaMemsetAsync(blo, 0, rows * cell_bytes, st);
     cudaMemsetAsync(map, 0xff, cells * sizeof(int), st);
-    k_apack<F><<<std::min<unsigned>((nbl * JP + 255) / 256, 152 * 8), 256, 0, st>>>(
+    k_apack<F><<<std::min<unsigned>((nbl + 7) / 8, 152 * 16), 256, 0, st>>>(
         t, l, ws.mp, nj, JP, W0[0], W0[1], W0[2], H[0], H[1], H[2], bhi, blo, map);
     ++*nl;
     if (gather) {
