@@ -84,12 +84,39 @@ __device__ __forceinline__ dwf inv_fact_t<dwf>(const PlanDev& pd, int q) {
   return dwf(pd.inv_fact[q]);
 }
 
+// warp shuffle of a float, double or double-word value
+__device__ __forceinline__ float shfl_t(float v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ double shfl_t(double v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ dwf shfl_t(dwf v, int src) {
+  return dwf(__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src));
+}
+
+// The scaled recurrence coefficients of a block's sweep: computed once, by
+// the first nterms threads (FP64 work, 1/64 of the FP32 rate on this GPU),
+// into shared memory; the caller synchronises before reading.
+template <typename T>
+__device__ __forceinline__ const T* block_coefs(const PlanDev& pd, double s) {
+  __shared__ T cs[FMM_MAX_TERMS];
+  if (threadIdx.x < pd.nterms) cs[threadIdx.x] = scaled_coef_t<T>(pd, threadIdx.x, s);
+  return cs;
+}
+// the same for a warp: lane t computes coefficient t, shuffled to all lanes
+template <typename T>
+__device__ __forceinline__ void warp_coefs(const PlanDev& pd, double s, int lane, T* coef) {
+  const T mine = lane < pd.nterms ? scaled_coef_t<T>(pd, lane, s) : T(0);
+  for (int t = 0; t < pd.nterms; ++t) coef[t] = shfl_t(mine, t);
+}
+
 // D[j] given in a[0..nj); fill slabs c..p (decompression, eq. (decompression)).
 template <typename T>
 __device__ void decompress_smem(const PlanDev& pd, T* a, double s) {
   const int nt = pd.nterms > 0 ? pd.nterms : 1;
-  T coef[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) coef[t] = scaled_coef_t<T>(pd, t, s);
+  const T* coef = block_coefs<T>(pd, s);
+  __syncthreads();
   for (int ms = pd.c; ms <= pd.p; ++ms) {
     const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
     for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
@@ -106,8 +133,8 @@ __device__ void decompress_smem(const PlanDev& pd, T* a, double s) {
 template <typename T>
 __device__ void compress_smem(const PlanDev& pd, T* a, double s) {
   const int nt = pd.nterms > 0 ? pd.nterms : 1;
-  T coef[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) coef[t] = scaled_coef_t<T>(pd, t, s);
+  const T* coef = block_coefs<T>(pd, s);
+  __syncthreads();
   for (int ms = pd.p - 1; ms >= 0; --ms) {
     const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
     for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
@@ -132,7 +159,7 @@ template <typename T>
 __device__ void compress_warp(const PlanDev& pd, T* a, double s, int lane) {
   const int nt = pd.nterms > 0 ? pd.nterms : 1;
   T coef[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) coef[t] = scaled_coef_t<T>(pd, t, s);
+  warp_coefs<T>(pd, s, lane, coef);
   for (int ms = pd.p - 1; ms >= 0; --ms) {
     const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
     for (int i = b0 + lane; i < b1; i += 32) {
@@ -152,7 +179,7 @@ template <typename T>
 __device__ void decompress_warp(const PlanDev& pd, T* a, double s, int lane) {
   const int nt = pd.nterms > 0 ? pd.nterms : 1;
   T coef[FMM_MAX_TERMS];
-  for (int t = 0; t < pd.nterms; ++t) coef[t] = scaled_coef_t<T>(pd, t, s);
+  warp_coefs<T>(pd, s, lane, coef);
   for (int ms = pd.c; ms <= pd.p; ++ms) {
     const int b0 = slab_begin(pd, ms), b1 = slab_begin(pd, ms + 1);
     for (int i = b0 + lane; i < b1; i += 32) {
