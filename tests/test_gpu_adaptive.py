@@ -190,3 +190,29 @@ def test_adaptive_tensor_m2l(torch_cuda, oracle, kernel, p, lam, precision):
     err = rel_l2(got, ref)
     print(kernel, p, precision, "adaptive tensor-core rel err", err)
     assert err < TC_TOL[precision]
+
+
+def test_adaptive_tensor_m2l_window_paths(torch_cuda, oracle):
+    # Two Plummer clusters (scale 0.03) on the diagonal and uniform targets:
+    # the deep levels' windows span both clusters.  With 80,000 sources and
+    # 16,000 targets at most 32 points per leaf (Laplace p = 8, BF16x3: 128
+    # K columns per window row), a CPU count of the tree and of the window
+    # arena gives levels 7-8 windows larger than the arena (CUDA-core M2L),
+    # levels 5-6 gathered target lists with level 5 not fitting beside level
+    # 6 (a second contraction launch over the reused arena), levels 2-4 tiles.
+    rng = np.random.Generator(np.random.PCG64(11))
+    half = []
+    for c in (0.2, 0.8):
+        half.append(W.plummer_points(rng, 40000, 3, a=0.03, center=0.5) - 0.5 + c)
+    src = np.clip(np.concatenate(half), 0.0, 1.0 - 1e-12)
+    w = rng.normal(size=src.shape[0])
+    tgt = rng.random((16000, 3))
+    idx = np.sort(np.random.default_rng(12).choice(len(tgt), 64, replace=False))
+    ref, st, _ = oracle.fmm_adaptive("laplace", 3, 8, src, w, tgt, max_leaf=32, sample=idx,
+                                     want_stats=True)
+    got, (nb, depth) = gpu_adaptive(torch_cuda, "laplace", 8, src, w, tgt, max_leaf=32,
+                                    precision="bf16x3")
+    assert (nb, depth) == (st["boxes"], st["depth"])
+    err = rel_l2(got[idx], ref)
+    print("two clusters, bf16x3 adaptive rel err", err, "depth", depth)
+    assert err < TC_TOL["bf16x3"]
