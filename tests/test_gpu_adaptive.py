@@ -1,7 +1,8 @@
 """GPU parity of the adaptive-tree FMM (U, V, W, X lists) against the oracle.
 
 The tree (boxes and depth) must match the oracle's exactly; potentials must
-match the oracle's adaptive FMM with the same tree and p to 1e-12 (FP64).
+match the oracle's adaptive FMM with the same tree and p to 1e-12 (FP64), and
+to the stated tolerances in the float and tensor-core forms.
 """
 import numpy as np
 import pytest
@@ -130,8 +131,9 @@ def test_yukawa_plummer_full_size_sampled(torch_cuda, oracle, precision):
     assert rel_l2(got[idx], ref) < (FP64_TOL if precision == "fp64" else TC_TOL[precision])
 
 
-# Float forms (P2M, M2L, P2L, L2P, P2P, M2P in float; M2M, L2L and the
-# derivative tables in FP64): ~24-bit products with the sums' cancellation.
+# Float forms (P2M, M2L, P2L, L2P, P2P, M2P in float; M2M and L2L in
+# double-word floats, the derivative tables in FP64): ~24-bit products with the
+# sums' cancellation.
 FP32_TOL = 2e-5
 
 
